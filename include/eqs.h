@@ -1,0 +1,195 @@
+/*
+ * eqs.h - C ABI of the GB300 explicit Runge-Kutta-Chebyshev solver for
+ * nonlinear electro-quasistatic (EQS) fields on P1 tetrahedra.
+ *
+ * Method (Richter, Schoeps, Clemens, "GPU Accelerated Explicit Time
+ * Integration Methods for Electro-Quasistatic Fields"):
+ *   Eq. 1  div(kappa(|grad phi|) grad phi) + div(eps grad dphi/dt) = 0
+ *   Eq. 2  M dx/dt + K(x) x = b    (P1 finite elements)
+ *   Sec. II   explicit RKC time stepping; every stage needs one solve with
+ *             the constant Laplace-type matrix M (multiple right-hand sides)
+ *   Sec. III  K(x)x is formed tet by tet without assembling K(x)
+ *   Sec. IV   the M-solves use CG with a constant AMG preconditioner and a
+ *             start vector estimated from earlier solutions
+ *
+ * Conventions (all entry points):
+ *  - Every call returns eqs_status; EQS_OK == 0, errors are negative.  The
+ *    library never throws or aborts; eqs_last_error() returns a text for the
+ *    last failing call on a context.
+ *  - "host" pointers are read (or written) during the call only and are
+ *    never retained.  "device" pointers are CUDA global-memory pointers owned
+ *    by the caller; the library never frees them.  Everything the library
+ *    allocates is owned by the context and released by eqs_destroy().
+ *  - Node vectors of length n_nodes are in the caller's (mesh) node order.
+ *    "Free" vectors of length n_free hold the free (non-Dirichlet) nodes in
+ *    ascending mesh-node order.
+ *  - Device work is enqueued on the context stream (eqs_set_stream; default
+ *    the legacy default stream) and is asynchronous unless stated.
+ *  - Call order: eqs_mesh_create -> eqs_set_materials -> eqs_amg_setup ->
+ *    apply / solve / step; otherwise EQS_ERR_STATE.
+ */
+#ifndef EQS_H
+#define EQS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct eqs_ctx eqs_ctx;
+
+typedef enum {
+  EQS_OK = 0,
+  EQS_ERR_ARG = -1,     /* invalid argument (null pointer, size, range)      */
+  EQS_ERR_MESH = -2,    /* inverted/degenerate tet, bad index, bad tag       */
+  EQS_ERR_CUDA = -3,    /* a CUDA runtime call failed                        */
+  EQS_ERR_NOCONV = -4,  /* CG reached max_iter before the tolerance          */
+  EQS_ERR_TIMEOUT = -5, /* a bounded device wait gave up                     */
+  EQS_ERR_NAN = -6,     /* non-finite value in an input or residual          */
+  EQS_ERR_STATE = -7    /* call order violated                               */
+} eqs_status;
+
+/* Material law of Eq. 1: eps = eps0 * eps_r (eps0 = 8.8541878128e-12 F/m) and
+ * kappa(E) = kappa_lo + (kappa_hi - kappa_lo) / (1 + exp(-(E - E0) / w)),
+ * E = |grad phi| per tet.  kappa_hi == kappa_lo marks a constant
+ * conductivity (E0 and w are then ignored). */
+typedef struct {
+  double eps_r, kappa_lo, kappa_hi, E0, w;
+} eqs_material;
+
+typedef enum {
+  EQS_PREC_FP64 = 0,  /* every kernel in FP64                                */
+  EQS_PREC_MIXED = 1  /* FP32 element kernel and AMG V-cycle; FP64 CG
+                         residual, dot products, RKC recurrence, coarsest
+                         solve                                              */
+} eqs_precision;
+
+typedef enum {
+  EQS_GUESS_PREV = 0, /* start vector = previous M-solve solution           */
+  EQS_GUESS_MLP = 1,  /* learned per-node network (eqs_guess_* calls)       */
+  EQS_GUESS_ZERO = 2  /* start vector = 0                                    */
+} eqs_guess_mode;
+
+/* Options of eqs_amg_setup (fill with eqs_opts_default). */
+typedef struct {
+  int precision;       /* eqs_precision                                      */
+  double theta;        /* strength threshold on level 0 (halved per level)   */
+  int coarse_max;      /* stop coarsening at <= coarse_max rows              */
+  int max_levels;      /* hierarchy depth limit                              */
+  int cheb_degree;     /* Chebyshev smoother degree (1..4), pre and post     */
+  double cheb_alpha;   /* smoothing interval [lambda/alpha, lambda]          */
+  double rtol;         /* M-solve stopping test ||R - M z||/||R|| <= rtol    */
+  int max_iter;        /* CG iteration limit per solve                       */
+  int guess;           /* eqs_guess_mode                                     */
+  int flexible;        /* 1: Polak-Ribiere CG (default for MIXED)            */
+} eqs_opts;
+
+#define EQS_MAX_STAGES 64
+
+/* Per-step statistics (filled after a device synchronisation). */
+typedef struct {
+  int s;                        /* stages of the step                         */
+  int total_iters;              /* CG iterations summed over the s solves     */
+  int max_iters;                /* largest CG iteration count of one solve    */
+  int iters[EQS_MAX_STAGES];    /* CG iterations of solve j = 0..s-1          */
+  double max_relres;            /* largest final ||r||/||R|| of the s solves  */
+  int status;                   /* EQS_OK or EQS_ERR_NOCONV                   */
+} eqs_step_stats;
+
+/* Fill *o with the defaults (precision FP64, theta 0.08, coarse_max 500,
+ * max_levels 10, degree 2, alpha 30, rtol 1e-8, max_iter 500, GUESS_PREV). */
+void eqs_opts_default(eqs_opts* o);
+
+/* Create a context from a tetrahedral mesh (Eq. 2 discretisation input).
+ * xyz: host, n_nodes x 3 doubles, node-major (x0 y0 z0 x1 ...), metres.
+ * tets: host, n_tets x 4 int32 node indices (0-based), any orientation with
+ *   nonzero volume is accepted (negative orientation is flipped).
+ * node_tag: host, n_nodes bytes: 0 free, 1 Dirichlet phi = 0,
+ *   2 Dirichlet phi = g(t) (eqs_set_dirichlet).
+ * Errors: EQS_ERR_ARG (null/size), EQS_ERR_MESH (index out of range,
+ *   zero-volume tet, tag > 2, no free node), EQS_ERR_CUDA.
+ * *out is NULL on error. */
+eqs_status eqs_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets,
+                           int64_t n_tets, const uint8_t* node_tag, eqs_ctx** out);
+
+/* Material of every tet (Eq. 1 coefficients).  tet_mat: host, n_tets bytes,
+ * values < n_mat; mats: host array of n_mat (1..255) laws.
+ * Errors: EQS_ERR_ARG, EQS_ERR_MESH (id out of range), EQS_ERR_STATE. */
+eqs_status eqs_set_materials(eqs_ctx* ctx, const uint8_t* tet_mat, int n_mat,
+                             const eqs_material* mats);
+
+/* Drive of the tag-2 nodes: g(t) = V0 sin(2 pi freq_hz t + phase) [V]
+ * (the inhomogeneous Dirichlet data that makes up b in Eq. 2). */
+eqs_status eqs_set_dirichlet(eqs_ctx* ctx, double V0, double freq_hz, double phase);
+
+/* Assemble M (Eq. 2: eps-weighted P1 Laplacian, free-free block after
+ * Dirichlet elimination) and build the smoothed-aggregation AMG hierarchy
+ * once on the host, then upload it (Sec. II: the preconditioner of the
+ * constant M is set up once and reused for every right-hand side).
+ * opts may be NULL (defaults).  Calling it again rebuilds everything. */
+eqs_status eqs_amg_setup(eqs_ctx* ctx, const eqs_opts* opts);
+
+/* y = K(x) x for all nodes, before any boundary condition (Sec. III:
+ * formed tet by tet, never assembling K).  x, y: device, n_nodes doubles,
+ * mesh order; y is overwritten.  Uses the precision chosen at setup. */
+eqs_status eqs_apply_K(eqs_ctx* ctx, const double* x, double* y);
+
+/* Solve M_ff z = rhs for nrhs right-hand sides (Sec. IV) by AMG-PCG.
+ * rhs: device, n_free x nrhs doubles, column-major (column k at
+ *   rhs + k*n_free).  z: device, same shape; on entry the start vectors,
+ *   on exit the solutions.  rtol <= 0 uses the setup value.
+ * iters_out: host, nrhs ints or NULL.  Synchronises the stream.
+ * Returns EQS_ERR_NOCONV if any column hit max_iter (z then holds the last
+ * iterate). */
+eqs_status eqs_solve_M(eqs_ctx* ctx, const double* rhs, double* z, int nrhs, double rtol,
+                       int* iters_out);
+
+/* Apply the AMG V-cycle once: z = B r (device, n_free doubles each). */
+eqs_status eqs_vcycle(eqs_ctx* ctx, const double* r, double* z);
+
+/* y = M_ff x (device, n_free doubles each). */
+eqs_status eqs_spmv_M(eqs_ctx* ctx, const double* x, double* y);
+
+/* One RKC step of s stages (Sec. II; scheme of its ref. [9], damping 2/13)
+ * from time t to t + dt.  x: device, n_nodes doubles, mesh order: on entry
+ * x(t) (Dirichlet entries are ignored and replaced by g(t)), on exit
+ * x(t + dt) with Dirichlet entries g(t + dt).  2 <= s <= EQS_MAX_STAGES.
+ * The whole step runs as one CUDA graph (cached per s) whose CG loops are
+ * device-side while-loops.  stats: host or NULL; when non-NULL the call
+ * synchronises and returns EQS_ERR_NOCONV if a solve did not converge. */
+eqs_status eqs_rkc_step(eqs_ctx* ctx, double* x, double t, double dt, int s,
+                        eqs_step_stats* stats);
+
+/* Largest stable step for s stages: beta_s / rho with the a-priori bound
+ * rho = max over materials and E of max(kappa, d(kappa E)/dE) / eps of the
+ * spectral radius of M^-1 dK/dx; returns a negative value on error. */
+double eqs_rkc_dt_bound(const eqs_ctx* ctx, int s);
+
+/* Use this CUDA stream (cudaStream_t passed as void*) for all later work. */
+eqs_status eqs_set_stream(eqs_ctx* ctx, void* cuda_stream);
+
+/* Sizes: any pointer may be NULL. */
+eqs_status eqs_get_sizes(const eqs_ctx* ctx, int64_t* n_nodes, int64_t* n_free,
+                         int64_t* n_tets);
+
+/* AMG hierarchy description: *n_levels, and per level (host arrays of at
+ * least 16 entries, may be NULL) its rows and non-zeros. */
+eqs_status eqs_amg_info(const eqs_ctx* ctx, int* n_levels, int64_t* rows, int64_t* nnz);
+
+/* Aggregate index of every row of AMG level `level` (host, rows[level]
+ * int32 entries), for checking the setup. */
+eqs_status eqs_amg_aggregates(const eqs_ctx* ctx, int level, int32_t* agg_out);
+
+/* Release everything owned by ctx (NULL is accepted). */
+eqs_status eqs_destroy(eqs_ctx* ctx);
+
+/* Text of the last error on ctx (or of the last failed eqs_mesh_create when
+ * ctx is NULL). Never NULL. */
+const char* eqs_last_error(const eqs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EQS_H */
