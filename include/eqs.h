@@ -23,7 +23,7 @@
  *  - Node vectors of length n_nodes are in the caller's (mesh) node order.
  *    "Free" vectors of length n_free hold the free (non-Dirichlet) nodes in
  *    ascending mesh-node order.
- *  - Device work is enqueued on the context stream (eqs_set_stream; default
+ *  - Device work is enqueued on the context stream (eqs_set_stream; initially
  *    the legacy default stream) and is asynchronous unless stated.
  *  - Call order: eqs_mesh_create -> eqs_set_materials -> eqs_amg_setup ->
  *    apply / solve / step; otherwise EQS_ERR_STATE.
@@ -103,12 +103,13 @@ void eqs_opts_default(eqs_opts* o);
 
 /* Create a context from a tetrahedral mesh (Eq. 2 discretisation input).
  * xyz: host, n_nodes x 3 doubles, node-major (x0 y0 z0 x1 ...), metres.
- * tets: host, n_tets x 4 int32 node indices (0-based), any orientation with
- *   nonzero volume is accepted (negative orientation is flipped).
+ * tets: host, n_tets x 4 int32 node indices (0-based), positively oriented
+ *   (det[p1-p0, p2-p0, p3-p0] > 0); an inverted or flat tet is rejected.
  * node_tag: host, n_nodes bytes: 0 free, 1 Dirichlet phi = 0,
  *   2 Dirichlet phi = g(t) (eqs_set_dirichlet).
  * Errors: EQS_ERR_ARG (null/size), EQS_ERR_MESH (index out of range,
- *   zero-volume tet, tag > 2, no free node), EQS_ERR_CUDA.
+ *   inverted or flat tet, non-finite coordinate, tag > 2, no free node).
+ * Host work only; the GPU is first touched by eqs_amg_setup.
  * *out is NULL on error. */
 eqs_status eqs_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets,
                            int64_t n_tets, const uint8_t* node_tag, eqs_ctx** out);
@@ -166,7 +167,8 @@ eqs_status eqs_rkc_step(eqs_ctx* ctx, double* x, double t, double dt, int s,
  * spectral radius of M^-1 dK/dx; returns a negative value on error. */
 double eqs_rkc_dt_bound(const eqs_ctx* ctx, int s);
 
-/* Use this CUDA stream (cudaStream_t passed as void*) for all later work. */
+/* Use this CUDA stream (cudaStream_t passed as void*) for all later work;
+ * NULL selects the legacy default stream (the initial setting). */
 eqs_status eqs_set_stream(eqs_ctx* ctx, void* cuda_stream);
 
 /* Sizes: any pointer may be NULL. */

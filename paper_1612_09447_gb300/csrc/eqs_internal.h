@@ -1,0 +1,176 @@
+// Internal structures of the EQS RKC library (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "eqs.h"
+
+namespace eqs {
+
+// ---------------------------------------------------------------- host CSR
+struct HostCSR {
+  int64_t n_rows = 0, n_cols = 0;
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  int64_t nnz() const { return ptr.empty() ? 0 : ptr.back(); }
+};
+
+// --------------------------------------------------- device SELL-32 matrix
+// Rows are grouped in slices of 32; slice s stores width[s] columns, element
+// k of row 32 s + lane at slice_ptr[s] + 32 k + lane (coalesced per warp).
+// Padding entries have value 0 and a valid column index.
+template <typename T>
+struct DevSell {
+  int n_rows = 0, n_cols = 0, n_slices = 0;
+  int64_t stored = 0, nnz = 0;
+  int64_t* slice_ptr = nullptr;
+  int32_t* col = nullptr;
+  T* val = nullptr;
+};
+
+template <typename T>
+struct DevLevel {
+  int n = 0;
+  double lam_max = 0, inv_theta = 0, sigma = 0, delta = 0;
+  DevSell<T> A;     // level operator
+  DevSell<T> P;     // prolongation to this level from level+1 (n x n_c)
+  DevSell<T> R;     // restriction P^T (n_c x n)
+  T* dinv = nullptr;
+  T* b = nullptr;   // right-hand side of the level
+  T* x = nullptr;   // iterate
+  T* r = nullptr;   // residual work vector
+  T* dA = nullptr;  // Chebyshev directions (ping-pong)
+  T* dB = nullptr;
+};
+
+struct HostLevel {
+  HostCSR A, P;
+  std::vector<int32_t> agg;
+  int n_agg = 0;
+  double lam_max = 0, omega = 0;
+};
+
+// Per-solve reduction scalars (device).
+struct PcgScalars {
+  double bnorm2, rnorm2, rz, rz_old, zr_prev, pq, alpha, beta;
+  int it, conv, pad0, pad1;
+};
+
+struct StepParams {  // device-resident per-call parameters
+  double t, dt;
+};
+
+// All scratch used by the reduction kernels of one solve.
+struct ReduceScratch {
+  double* partials = nullptr;   // per block partial sums (up to 4 per block)
+  unsigned int* counter = nullptr;
+  int max_blocks = 0;
+};
+
+struct MaterialDev {  // one row of the material table
+  double eps, klo, khi, E0, inv_w;
+  int is_const, pad;
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  double* d_cj = nullptr;  // stage abscissae c_0..c_s of this graph
+};
+
+}  // namespace eqs
+
+struct eqs_ctx {
+  std::string err;
+  cudaStream_t stream = nullptr;      // stream of all work (NULL: legacy default stream)
+  cudaStream_t own_stream = nullptr;  // created at setup (marks that streams exist)
+  cudaStream_t cap_stream = nullptr;  // capture of step / solve graphs
+  cudaStream_t cap_stream2 = nullptr; // capture of while-loop bodies
+  int device = 0;
+  std::vector<void*> allocs;          // every device allocation of the context
+
+  // ---- mesh (host copies)
+  int64_t n_nodes = 0, n_tets = 0, n_free = 0;
+  std::vector<double> xyz;          // mesh order, n x 3
+  std::vector<int32_t> tets;        // mesh order, oriented (positive volume)
+  std::vector<uint8_t> tag;         // mesh order
+  std::vector<int32_t> internal_of_node, node_of_internal;  // free first
+  std::vector<uint8_t> tet_mat;
+  std::vector<eqs_material> mats;
+  bool have_materials = false;
+  double V0 = 0, freq = 0, phase = 0;
+
+  // ---- options / state
+  eqs_opts opts{};
+  bool setup_done = false;   // device data ready
+  bool hier_ready = false;   // host AMG hierarchy built
+
+  // ---- host AMG (kept for inspection)
+  std::vector<eqs::HostLevel> hlev;
+  int coarse_n = 0;
+
+  // ---- device mesh
+  int4* d_conn = nullptr;            // internal node ids, oriented
+  uint8_t* d_mat = nullptr;
+  double4* d_xyz = nullptr;          // internal order (x, y, z, 0)
+  float4* d_xyz_hi = nullptr;        // two-float split (mixed precision)
+  float4* d_xyz_lo = nullptr;
+  int32_t* d_node_of_internal = nullptr;
+  double* d_dir_scale = nullptr;     // per Dirichlet node: 1 driven, 0 grounded
+  double* d_mtop = nullptr;          // M_fd 1_top (n_free)
+  eqs::MaterialDev* d_mats = nullptr;
+
+  // ---- device matrices
+  eqs::DevSell<double> M64;          // M_ff in FP64 (CG operator)
+  std::vector<eqs::DevLevel<double>> lev64;
+  std::vector<eqs::DevLevel<float>> lev32;
+  double* d_coarse_inv = nullptr;    // dense inverse of the coarsest matrix
+
+  // ---- device vectors (FP64 unless noted)
+  double* d_Y[4] = {nullptr, nullptr, nullptr, nullptr};  // Y0 + 3 rotating, n_nodes
+  float2* d_Y32 = nullptr;           // two-float copy of the current stage vector
+  double* d_F[3] = {nullptr, nullptr, nullptr};  // F0, Fa, Fb (n_free)
+  double* d_R = nullptr;             // stage right-hand side (n_free)
+  float* d_y32 = nullptr;            // FP32 accumulation of K(x)x (n_nodes)
+  double* d_r = nullptr;
+  double* d_rprev = nullptr;
+  double* d_p = nullptr;
+  double* d_q = nullptr;
+  double* d_sol = nullptr;           // solve_M work solution
+  double* d_zd = nullptr;            // preconditioned residual in FP64
+  double* d_tmpn = nullptr;          // n_nodes scratch (apply_K)
+  double* d_tmpn2 = nullptr;
+  eqs::PcgScalars* d_sc = nullptr;
+  eqs::StepParams* d_params = nullptr;
+  int* d_iters = nullptr;            // per stage iteration counts
+  double* d_relres = nullptr;        // per stage final relative residuals
+  int* d_zero = nullptr;             // per stage: right-hand side was zero
+  double* d_g = nullptr;             // drive g(t_j) at the stage times
+  double* d_gp = nullptr;            // drive derivative g'(t_j)
+  eqs::ReduceScratch red;
+
+  std::map<std::pair<int, uintptr_t>, eqs::GraphEntry> step_graphs;  // key: (s, x)
+  std::map<double, eqs::GraphEntry> solve_graphs;                   // key: rtol
+};
+
+namespace eqs {
+
+// host_setup.cpp
+eqs_status validate_and_orient(eqs_ctx* c);
+void build_internal_numbering(eqs_ctx* c);
+void assemble_M(const eqs_ctx* c, HostCSR& Mff, std::vector<double>& mtop);
+void build_hierarchy(const HostCSR& A, const eqs_opts& o, std::vector<HostLevel>& lev);
+bool dense_spd_inverse(const HostCSR& A, std::vector<double>& inv);
+void rkc_coefficients(int s, std::vector<double>& mu, std::vector<double>& nu,
+                      std::vector<double>& mut, std::vector<double>& gt, std::vector<double>& c,
+                      double& beta);
+double rho_bound(const std::vector<eqs_material>& mats);
+
+}  // namespace eqs

@@ -1,0 +1,573 @@
+// Device kernels of the EQS RKC library (sm_103a).
+//
+// Vector kernels run one thread per row; matrices are SELL-32 (slices of 32
+// rows stored column-major), so the 32 lanes of a warp read 32 consecutive
+// values/column indices per step (coalesced) and no shuffles are needed.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "eqs_internal.h"
+
+namespace eqs {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+
+// (A x)_row for a SELL-32 matrix; accumulation in T.
+template <typename T>
+__device__ __forceinline__ T sell_row(const DevSell<T>& A, int row, const T* __restrict__ x) {
+  const int s = row >> 5, lane = row & 31;
+  const int64_t beg = A.slice_ptr[s] + lane, end = A.slice_ptr[s + 1];
+  T acc = T(0);
+#pragma unroll 4
+  for (int64_t k = beg; k < end; k += 32) acc = fmadd(A.val[k], __ldg(x + A.col[k]), acc);
+  return acc;
+}
+
+// (A x)_row with a T matrix applied to an FP64 vector, FP64 accumulation.
+__device__ __forceinline__ double sell_row_d(const DevSell<double>& A, int row,
+                                             const double* __restrict__ x) {
+  return sell_row<double>(A, row, x);
+}
+
+// ------------------------------------------------------------ V-cycle pieces
+// One Chebyshev step:  r_out = r_in - A d_in ;  d_out = c1 d_in + c2 D^-1 r_out ;
+// x += d_out (+ d_in when the previous direction was not yet added to x).
+template <typename T>
+__global__ void k_cheb_step(DevSell<T> A, int n, const T* r_in,
+                            const T* __restrict__ d_in, const T* __restrict__ dinv, T c1, T c2,
+                            T* r_out, T* __restrict__ d_out, T* __restrict__ x, int add_pending) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T di = d_in[i];
+  const T r = r_in[i] - sell_row(A, i, d_in);
+  const T dn = c1 * di + c2 * dinv[i] * r;
+  r_out[i] = r;
+  d_out[i] = dn;
+  x[i] += add_pending ? dn + di : dn;
+}
+
+// r -= A d  (in place; r is row-local)
+template <typename T>
+__global__ void k_resid_update(DevSell<T> A, int n, T* r, const T* __restrict__ d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  r[i] = r[i] - sell_row(A, i, d);
+}
+
+// out = b - A x
+template <typename T>
+__global__ void k_resid(DevSell<T> A, int n, const T* __restrict__ b, const T* __restrict__ x,
+                        T* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = b[i] - sell_row(A, i, x);
+}
+
+// b_c = R r_f ; when first_step: x_c = d_c = D_c^-1 b_c / theta_c (the first
+// Chebyshev step of the coarse level from a zero initial guess).
+template <typename T>
+__global__ void k_restrict(DevSell<T> R, int nc, const T* __restrict__ rf, T* __restrict__ bc,
+                           const T* __restrict__ dinv_c, T inv_theta_c, T* __restrict__ xc,
+                           T* __restrict__ dc, int first_step) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  const T b = sell_row(R, i, rf);
+  bc[i] = b;
+  if (first_step) {
+    const T d = dinv_c[i] * b * inv_theta_c;
+    xc[i] = d;
+    dc[i] = d;
+  }
+}
+
+// x_f += P x_c
+template <typename T>
+__global__ void k_prolong(DevSell<T> P, int nf, const T* __restrict__ xc, T* __restrict__ xf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nf) return;
+  xf[i] += sell_row(P, i, xc);
+}
+
+// First post-smoothing step from the current x: r = b - A x ; d = D^-1 r / theta.
+// x is not updated here (other rows still read it); the next step adds d.
+template <typename T>
+__global__ void k_post_first(DevSell<T> A, int n, const T* __restrict__ b,
+                             const T* __restrict__ x, const T* __restrict__ dinv, T inv_theta,
+                             T* __restrict__ r_out, T* __restrict__ d_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T r = b[i] - sell_row(A, i, x);
+  r_out[i] = r;
+  d_out[i] = dinv[i] * r * inv_theta;
+}
+
+template <typename T>
+__global__ void k_axpy1(int n, T* __restrict__ x, const T* __restrict__ d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] += d[i];
+}
+
+// Coarsest level: x = A_c^-1 b with the dense FP64 inverse; one warp per row.
+template <typename T>
+__global__ void k_coarse_solve(int n, const double* __restrict__ inv, const T* __restrict__ b,
+                               T* __restrict__ x) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc = fma(inv[(int64_t)warp * n + j], (double)b[j], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[warp] = (T)acc;
+}
+
+// ---------------------------------------------------------------- reductions
+// Block sum of NV doubles; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][kBlock / 32];
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k][w] = v[k];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = lane < (kBlock / 32) ? sh[k][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      v[k] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// Grid-wide deterministic sum: every block stores its partials; the last
+// block to finish (atomic ticket) sums them in block order and returns true
+// in all of its threads with the totals in `tot` (thread 0).
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* counter,
+                                         int max_blocks, double (&tot)[NV]) {
+  __shared__ bool am_last;
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[k * max_blocks + blockIdx.x] = v[k];
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(partials + k * max_blocks + b);
+    tot[k] = t;
+  }
+  block_sum<NV>(tot);
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// ------------------------------------------------------------------ PCG
+// Initial residual r = R - M x, norms of R and r, and the first V-cycle
+// input (b0 = r in T, x0 = d0 = D0^-1 b0 / theta0).  The last block decides
+// whether the CG loop runs (condition handle).
+template <typename T>
+__global__ void k_pcg_init(DevSell<double> M, int n, const double* __restrict__ R,
+                           const double* __restrict__ x, double* __restrict__ r,
+                           const T* __restrict__ dinv0, T inv_theta0, T* __restrict__ b0,
+                           T* __restrict__ x0, T* __restrict__ d0, PcgScalars* sc,
+                           double* partials, unsigned int* counter, int max_blocks, double tol2,
+                           int maxit, cudaGraphConditionalHandle h, int use_handle,
+                           int* iters_out, double* relres_out, int* zero_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  if (i < n) {
+    const double Ri = R[i];
+    const double ri = Ri - sell_row_d(M, i, x);
+    r[i] = ri;
+    const T bi = (T)ri;
+    b0[i] = bi;
+    const T d = dinv0[i] * bi * inv_theta0;
+    x0[i] = d;
+    d0[i] = d;
+    v[0] = Ri * Ri;
+    v[1] = ri * ri;
+  }
+  double tot[2];
+  if (grid_sum<2>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    sc->bnorm2 = tot[0];
+    sc->rnorm2 = tot[1];
+    sc->it = 0;
+    const int zero = tot[0] == 0.0;
+    const int go = !zero && tot[1] > tol2 * tot[0] && maxit > 0;
+    sc->conv = !go;
+    if (use_handle) cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = zero ? 0.0 : sqrt(tot[1] / tot[0]);
+    if (zero_out) *zero_out = zero;
+  }
+}
+
+// w = M z (z from the V-cycle, in T), dot products r.z and r_prev.z; the
+// last block forms beta (Fletcher-Reeves or Polak-Ribiere).
+template <typename T>
+__global__ void k_pcg_dots(DevSell<double> M, int n, const double* __restrict__ r,
+                           const double* __restrict__ rprev, const T* __restrict__ z,
+                           double* __restrict__ zd, double* __restrict__ w, PcgScalars* sc,
+                           double* partials, unsigned int* counter, int max_blocks,
+                           int flexible) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  if (i < n) {
+    const double zi = (double)z[i];
+    zd[i] = zi;
+    v[0] = r[i] * zi;
+    v[1] = rprev[i] * zi;
+  }
+  (void)M;
+  (void)w;
+  double tot[2];
+  if (grid_sum<2>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    const double rz = tot[0];
+    double beta = 0.0;
+    if (sc->it > 0) beta = flexible ? (rz - tot[1]) / sc->rz_old : rz / sc->rz_old;
+    sc->beta = beta;
+    sc->rz = rz;
+    sc->rz_old = rz;
+  }
+}
+
+// p = z + beta p ; q = M p is done by k_pcg_q.
+__global__ void k_pcg_p(int n, const double* __restrict__ zd, double* __restrict__ p,
+                        const PcgScalars* sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  p[i] = zd[i] + sc->beta * p[i];
+}
+
+// q = M p and p.q ; alpha = r.z / p.q
+__global__ void k_pcg_q(DevSell<double> M, int n, const double* __restrict__ p,
+                        double* __restrict__ q, PcgScalars* sc, double* partials,
+                        unsigned int* counter, int max_blocks) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (i < n) {
+    const double qi = sell_row_d(M, i, p);
+    q[i] = qi;
+    v[0] = p[i] * qi;
+  }
+  double tot[1];
+  if (grid_sum<1>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    sc->pq = tot[0];
+    sc->alpha = sc->rz / tot[0];
+  }
+}
+
+// x += alpha p ; r_prev = r ; r -= alpha q ; ||r||^2 ; next V-cycle input;
+// the last block updates the loop condition and the statistics.
+template <typename T>
+__global__ void k_pcg_update(int n, double* __restrict__ x, double* __restrict__ r,
+                             double* __restrict__ rprev, const double* __restrict__ p,
+                             const double* __restrict__ q, const T* __restrict__ dinv0,
+                             T inv_theta0, T* __restrict__ b0, T* __restrict__ x0,
+                             T* __restrict__ d0, PcgScalars* sc, double* partials,
+                             unsigned int* counter, int max_blocks, double tol2, int maxit,
+                             cudaGraphConditionalHandle h, int use_handle, int* iters_out,
+                             double* relres_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (i < n) {
+    const double a = sc->alpha;
+    x[i] = fma(a, p[i], x[i]);
+    const double ro = r[i];
+    rprev[i] = ro;
+    const double rn = fma(-a, q[i], ro);
+    r[i] = rn;
+    v[0] = rn * rn;
+    const T bi = (T)rn;
+    b0[i] = bi;
+    const T d = dinv0[i] * bi * inv_theta0;
+    x0[i] = d;
+    d0[i] = d;
+  }
+  double tot[1];
+  if (grid_sum<1>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    sc->rnorm2 = tot[0];
+    const int it = sc->it + 1;
+    sc->it = it;
+    const int conv = tot[0] <= tol2 * sc->bnorm2;
+    sc->conv = conv;
+    const int go = !conv && it < maxit;
+    if (use_handle) cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (iters_out) *iters_out = it;
+    if (relres_out) *relres_out = sqrt(tot[0] / sc->bnorm2);
+  }
+}
+
+// ---------------------------------------------------------- element kernels
+// One thread per tet (Section III): gather the 4 vertices and potentials,
+// form the gradient and kappa(|E|), and add r_e = kappa V G (G^T phi_e) to y
+// (only rows < n_limit).  With e_k = p_k - p_0 and c_1 = e_2 x e_3,
+// c_2 = e_3 x e_1, c_3 = e_1 x e_2, D = e_1 . c_1 = det J = 6V:
+//   grad(lambda_k) = c_k / D,  grad phi = g / D,  g = sum_k (phi_k - phi_0) c_k
+//   r_k = kappa V grad(lambda_k) . grad phi = kappa (c_k . g) / (6 D),
+//   r_0 = -(r_1 + r_2 + r_3).
+__device__ __forceinline__ double kappa64(const MaterialDev& m, double E) {
+  if (m.is_const) return m.klo;
+  const double u = (E - m.E0) * m.inv_w;
+  double s;
+  if (u >= 0.0) {
+    s = 1.0 / (1.0 + exp(-u));
+  } else {
+    const double e = exp(u);
+    s = e / (1.0 + e);
+  }
+  return m.klo + (m.khi - m.klo) * s;
+}
+
+__device__ __forceinline__ float kappa32(const MaterialDev& m, float E) {
+  if (m.is_const) return (float)m.klo;
+  const float u = (E - (float)m.E0) * (float)m.inv_w;
+  float s;
+  if (u >= 0.0f) {
+    s = 1.0f / (1.0f + expf(-u));
+  } else {
+    const float e = expf(u);
+    s = e / (1.0f + e);
+  }
+  return (float)m.klo + (float)(m.khi - m.klo) * s;
+}
+
+__global__ void k_elem64(int64_t nt, const int4* __restrict__ conn, const uint8_t* __restrict__ mat,
+                         const MaterialDev* __restrict__ mats, const double4* __restrict__ xyz,
+                         const double* __restrict__ x, int n_limit, double sign,
+                         double* __restrict__ y) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt) return;
+  const int4 t = conn[e];
+  const double4 p0 = xyz[t.x], p1 = xyz[t.y], p2 = xyz[t.z], p3 = xyz[t.w];
+  const double f0 = __ldg(x + t.x);
+  const double d1 = __ldg(x + t.y) - f0, d2 = __ldg(x + t.z) - f0, d3 = __ldg(x + t.w) - f0;
+  const double e1x = p1.x - p0.x, e1y = p1.y - p0.y, e1z = p1.z - p0.z;
+  const double e2x = p2.x - p0.x, e2y = p2.y - p0.y, e2z = p2.z - p0.z;
+  const double e3x = p3.x - p0.x, e3y = p3.y - p0.y, e3z = p3.z - p0.z;
+  const double c1x = e2y * e3z - e2z * e3y, c1y = e2z * e3x - e2x * e3z, c1z = e2x * e3y - e2y * e3x;
+  const double c2x = e3y * e1z - e3z * e1y, c2y = e3z * e1x - e3x * e1z, c2z = e3x * e1y - e3y * e1x;
+  const double c3x = e1y * e2z - e1z * e2y, c3y = e1z * e2x - e1x * e2z, c3z = e1x * e2y - e1y * e2x;
+  const double D = e1x * c1x + e1y * c1y + e1z * c1z;
+  const double gx = d1 * c1x + d2 * c2x + d3 * c3x;
+  const double gy = d1 * c1y + d2 * c2y + d3 * c3y;
+  const double gz = d1 * c1z + d2 * c2z + d3 * c3z;
+  const MaterialDev m = mats[mat[e]];
+  double kap;
+  if (m.is_const) {
+    kap = m.klo;
+  } else {
+    const double E = sqrt(gx * gx + gy * gy + gz * gz) / D;
+    kap = kappa64(m, E);
+  }
+  const double s = sign * kap / (6.0 * D);
+  const double r1 = s * (c1x * gx + c1y * gy + c1z * gz);
+  const double r2 = s * (c2x * gx + c2y * gy + c2z * gz);
+  const double r3 = s * (c3x * gx + c3y * gy + c3z * gz);
+  const double r0 = -(r1 + r2 + r3);
+  if (t.x < n_limit) atomicAdd(y + t.x, r0);
+  if (t.y < n_limit) atomicAdd(y + t.y, r1);
+  if (t.z < n_limit) atomicAdd(y + t.z, r2);
+  if (t.w < n_limit) atomicAdd(y + t.w, r3);
+}
+
+// Mixed precision: coordinates and potentials are stored as FP32 (hi, lo)
+// pairs, so edge vectors and potential differences are formed as
+// (hi_a - hi_b) + (lo_a - lo_b) with FP32 relative accuracy; everything else
+// is FP32 with FP32 accumulation.  r_0 = -(r_1 + r_2 + r_3) keeps the
+// local residual's zero sum exactly.
+__global__ void k_elem32(int64_t nt, const int4* __restrict__ conn, const uint8_t* __restrict__ mat,
+                         const MaterialDev* __restrict__ mats, const float4* __restrict__ xh,
+                         const float4* __restrict__ xl, const float2* __restrict__ x,
+                         int n_limit, float* __restrict__ y) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt) return;
+  const int4 t = conn[e];
+  const float4 h0 = xh[t.x], h1 = xh[t.y], h2 = xh[t.z], h3 = xh[t.w];
+  const float4 l0 = xl[t.x], l1 = xl[t.y], l2 = xl[t.z], l3 = xl[t.w];
+  const float2 f0 = x[t.x], f1 = x[t.y], f2 = x[t.z], f3 = x[t.w];
+  const float d1 = (f1.x - f0.x) + (f1.y - f0.y);
+  const float d2 = (f2.x - f0.x) + (f2.y - f0.y);
+  const float d3 = (f3.x - f0.x) + (f3.y - f0.y);
+  const float e1x = (h1.x - h0.x) + (l1.x - l0.x), e1y = (h1.y - h0.y) + (l1.y - l0.y),
+              e1z = (h1.z - h0.z) + (l1.z - l0.z);
+  const float e2x = (h2.x - h0.x) + (l2.x - l0.x), e2y = (h2.y - h0.y) + (l2.y - l0.y),
+              e2z = (h2.z - h0.z) + (l2.z - l0.z);
+  const float e3x = (h3.x - h0.x) + (l3.x - l0.x), e3y = (h3.y - h0.y) + (l3.y - l0.y),
+              e3z = (h3.z - h0.z) + (l3.z - l0.z);
+  const float c1x = e2y * e3z - e2z * e3y, c1y = e2z * e3x - e2x * e3z, c1z = e2x * e3y - e2y * e3x;
+  const float c2x = e3y * e1z - e3z * e1y, c2y = e3z * e1x - e3x * e1z, c2z = e3x * e1y - e3y * e1x;
+  const float c3x = e1y * e2z - e1z * e2y, c3y = e1z * e2x - e1x * e2z, c3z = e1x * e2y - e1y * e2x;
+  const float D = e1x * c1x + e1y * c1y + e1z * c1z;
+  const float gx = d1 * c1x + d2 * c2x + d3 * c3x;
+  const float gy = d1 * c1y + d2 * c2y + d3 * c3y;
+  const float gz = d1 * c1z + d2 * c2z + d3 * c3z;
+  const MaterialDev m = mats[mat[e]];
+  float kap;
+  if (m.is_const) {
+    kap = (float)m.klo;
+  } else {
+    const float E = sqrtf(gx * gx + gy * gy + gz * gz) / D;
+    kap = kappa32(m, E);
+  }
+  const float s = kap / (6.0f * D);
+  const float r1 = s * (c1x * gx + c1y * gy + c1z * gz);
+  const float r2 = s * (c2x * gx + c2y * gy + c2z * gz);
+  const float r3 = s * (c3x * gx + c3y * gy + c3z * gz);
+  const float r0 = -(r1 + r2 + r3);
+  if (t.x < n_limit) atomicAdd(y + t.x, r0);
+  if (t.y < n_limit) atomicAdd(y + t.y, r1);
+  if (t.z < n_limit) atomicAdd(y + t.z, r2);
+  if (t.w < n_limit) atomicAdd(y + t.w, r3);
+}
+
+// ------------------------------------------------------------- RKC pieces
+__device__ __forceinline__ float2 split2(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
+// Drive values at the stage times: g[j] = V0 sin(w t_j + phase),
+// gp[j] = V0 w cos(w t_j + phase), t_j = t + c_j dt, j = 0..s.
+__global__ void k_stage_scalars(int s1, const double* __restrict__ cj, const StepParams* prm,
+                                double V0, double w, double phase, double* __restrict__ g,
+                                double* __restrict__ gp) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= s1) return;
+  const double tj = prm->t + cj[j] * prm->dt;
+  const double a = w * tj + phase;
+  g[j] = V0 * sin(a);
+  gp[j] = V0 * w * cos(a);
+}
+
+// Y0 (internal order) from the caller's mesh-order x, Dirichlet rows = g(t);
+// the start vector of the first solve (previous solution) and, in FP64 mode,
+// R = -g'(t) M_fd 1_top (the element kernel then subtracts K(Y0)Y0).
+__global__ void k_gather_state(int n, int nf, const double* __restrict__ xmesh,
+                               const int32_t* __restrict__ node_of_internal,
+                               const double* __restrict__ dir_scale, const double* __restrict__ g,
+                               const double* __restrict__ gp, const double* __restrict__ mtop,
+                               double* __restrict__ Y0, float2* __restrict__ Y32,
+                               const double* __restrict__ Fsrc, double* __restrict__ Fdst,
+                               double* __restrict__ R) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v;
+  if (i < nf) {
+    v = xmesh[node_of_internal[i]];
+    if (Fdst) Fdst[i] = Fsrc[i];
+    if (R) R[i] = -gp[0] * mtop[i];
+  } else {
+    v = dir_scale[i - nf] * g[0];
+  }
+  Y0[i] = v;
+  if (Y32) Y32[i] = split2(v);
+}
+
+// Stage recurrence (Section II; ref. [9]):
+//   Y_j = c0 Y0 + mu Y_{j-1} + nu Y_{j-2} + mut dt F_{j-1} + gt dt F_0
+// on free rows, g(t_j) on Dirichlet rows.  Also the next solve's start vector
+// (F_j <- F_{j-1}), the FP64 right-hand side start R = -g'(t_j) M_fd 1_top,
+// and, after the last stage, x(t + dt) in mesh order.
+__global__ void k_recurrence(int n, int nf, double c0, double mu, double nu, double mut, double gt,
+                             const StepParams* prm, const double* __restrict__ Y0,
+                             const double* __restrict__ Yjm1, const double* __restrict__ Yjm2,
+                             const double* __restrict__ Fjm1, const double* __restrict__ F0,
+                             const int* __restrict__ zero_flags, int jm1,
+                             const double* __restrict__ dir_scale, const double* __restrict__ gj,
+                             const double* __restrict__ gpj, const double* __restrict__ mtop,
+                             double* __restrict__ Yj, float2* __restrict__ Y32,
+                             double* __restrict__ Fguess, double* __restrict__ R,
+                             double* __restrict__ xmesh, const int32_t* __restrict__ node_of_internal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v;
+  if (i < nf) {
+    const double dt = prm->dt;
+    const double fj = zero_flags[jm1] ? 0.0 : Fjm1[i];
+    const double f0 = zero_flags[0] ? 0.0 : F0[i];
+    v = c0 * Y0[i] + mu * Yjm1[i] + nu * Yjm2[i] + (mut * dt) * fj + (gt * dt) * f0;
+    if (Fguess) Fguess[i] = Fjm1[i];
+    if (R) R[i] = -(*gpj) * mtop[i];
+  } else {
+    v = dir_scale[i - nf] * (*gj);
+  }
+  Yj[i] = v;
+  if (Y32) Y32[i] = split2(v);
+  if (xmesh) xmesh[node_of_internal[i]] = v;
+}
+
+// Mixed precision: R = -y32 - g'(t_j) M_fd 1_top in FP64, and clear y32.
+__global__ void k_rhs_from_y32(int nf, float* __restrict__ y32, const double* __restrict__ gpj,
+                               const double* __restrict__ mtop, double* __restrict__ R) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nf) return;
+  R[i] = -(double)y32[i] - (*gpj) * mtop[i];
+  y32[i] = 0.0f;
+}
+
+// ------------------------------------------------------- small utilities
+__global__ void k_gather_perm(int n, const double* __restrict__ src, const int32_t* __restrict__ perm,
+                              double* __restrict__ dst, float2* __restrict__ dst32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = src[perm[i]];
+  dst[i] = v;
+  if (dst32) dst32[i] = split2(v);
+}
+
+__global__ void k_scatter_perm(int n, const double* __restrict__ src, const float* __restrict__ src32,
+                               const int32_t* __restrict__ perm, double* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  dst[perm[i]] = src32 ? (double)src32[i] : src[i];
+}
+
+template <typename T>
+__global__ void k_to_T(int n, const double* __restrict__ a, T* __restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (T)a[i];
+}
+
+template <typename T>
+__global__ void k_from_T(int n, const T* __restrict__ a, double* __restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+template <typename T>
+__global__ void k_first_step(int n, const T* __restrict__ b, const T* __restrict__ dinv, T inv_theta,
+                             T* __restrict__ x, T* __restrict__ d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T v = dinv[i] * b[i] * inv_theta;
+  x[i] = v;
+  d[i] = v;
+}
+
+__global__ void k_spmv64(DevSell<double> A, int n, const double* __restrict__ x, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = sell_row_d(A, i, x);
+}
+
+}  // namespace eqs

@@ -1,0 +1,761 @@
+// Device orchestration and the C ABI of the EQS RKC library.
+//
+// One RKC step (Section II) is one CUDA graph: for every stage the element
+// kernel (Section III) forms the right-hand side, and the M-solve (Section
+// IV) runs as a device-side while-loop (conditional graph node) around the
+// AMG V-cycle and the CG updates, so no host round trip happens inside a
+// step.  Graphs are cached per (stages, output pointer).
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace eqs;
+
+static thread_local std::string g_create_err = "no error";
+
+static eqs_status fail(eqs_ctx* c, eqs_status st, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_create_err = msg;
+  return st;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(c, EQS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+static inline int nblk(int64_t n, int b = kBlock) { return (int)((n + b - 1) / b); }
+
+// ---------------------------------------------------------- device memory
+static void free_all(eqs_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+}
+
+template <typename T>
+static cudaError_t dalloc(eqs_ctx* c, T** p, size_t n, bool zero = true) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) return e;
+  c->allocs.push_back((void*)*p);
+  if (zero) e = cudaMemset(*p, 0, n * sizeof(T));
+  return e;
+}
+
+template <typename T>
+static cudaError_t upload(eqs_ctx* c, T** p, const T* h, size_t n) {
+  cudaError_t e = dalloc(c, p, n, false);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*p, h, n * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+static cudaError_t upload_sell(eqs_ctx* c, const HostCSR& A, DevSell<T>& S) {
+  S.n_rows = (int)A.n_rows;
+  S.n_cols = (int)A.n_cols;
+  S.n_slices = (int)((A.n_rows + 31) / 32);
+  S.nnz = A.nnz();
+  std::vector<int64_t> sp(S.n_slices + 1, 0);
+  for (int s = 0; s < S.n_slices; ++s) {
+    int64_t w = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int64_t r = (int64_t)s * 32 + l;
+      if (r < A.n_rows) w = std::max<int64_t>(w, A.ptr[r + 1] - A.ptr[r]);
+    }
+    sp[s + 1] = sp[s] + 32 * w;
+  }
+  S.stored = sp[S.n_slices];
+  std::vector<int32_t> col(S.stored, 0);
+  std::vector<T> val(S.stored, T(0));
+  for (int s = 0; s < S.n_slices; ++s) {
+    const int64_t w = (sp[s + 1] - sp[s]) / 32;
+    for (int l = 0; l < 32; ++l) {
+      const int64_t r = (int64_t)s * 32 + l;
+      if (r >= A.n_rows) continue;
+      const int64_t len = A.ptr[r + 1] - A.ptr[r];
+      for (int64_t k = 0; k < w; ++k) {
+        const int64_t d = sp[s] + 32 * k + l;
+        if (k < len) {
+          col[d] = A.col[A.ptr[r] + k];
+          val[d] = (T)A.val[A.ptr[r] + k];
+        }
+      }
+    }
+  }
+  cudaError_t e = upload(c, &S.slice_ptr, sp.data(), sp.size());
+  if (e == cudaSuccess) e = upload(c, &S.col, col.data(), col.size());
+  if (e == cudaSuccess) e = upload(c, &S.val, val.data(), val.size());
+  return e;
+}
+
+// Chebyshev coefficients of step k (2..deg): c1 = rho_k rho_{k-1},
+// c2 = 2 rho_k / delta, rho_1 = 1/sigma, rho_k = 1/(2 sigma - rho_{k-1}).
+static void cheb_coeffs(double sigma, double delta, int deg, std::vector<double>& c1,
+                        std::vector<double>& c2) {
+  c1.assign(deg + 1, 0.0);
+  c2.assign(deg + 1, 0.0);
+  double rho_old = 1.0 / sigma;
+  for (int k = 2; k <= deg; ++k) {
+    const double rho = 1.0 / (2.0 * sigma - rho_old);
+    c1[k] = rho * rho_old;
+    c2[k] = 2.0 * rho / delta;
+    rho_old = rho;
+  }
+}
+
+template <typename T>
+static cudaError_t upload_levels(eqs_ctx* c, std::vector<DevLevel<T>>& L) {
+  const int nl = (int)c->hlev.size();
+  L.assign(nl, DevLevel<T>());
+  for (int l = 0; l < nl; ++l) {
+    const HostLevel& H = c->hlev[l];
+    DevLevel<T>& D = L[l];
+    D.n = (int)H.A.n_rows;
+    D.lam_max = H.lam_max;
+    const double lmin = H.lam_max / c->opts.cheb_alpha;
+    const double theta = 0.5 * (H.lam_max + lmin);
+    D.delta = 0.5 * (H.lam_max - lmin);
+    D.sigma = theta / D.delta;
+    D.inv_theta = 1.0 / theta;
+    cudaError_t e = upload_sell(c, H.A, D.A);
+    if (e != cudaSuccess) return e;
+    if (l + 1 < nl) {
+      if ((e = upload_sell(c, H.P, D.P)) != cudaSuccess) return e;
+      HostCSR Pt;
+      {  // transpose P for the restriction
+        const HostCSR& P = H.P;
+        Pt.n_rows = P.n_cols;
+        Pt.n_cols = P.n_rows;
+        Pt.ptr.assign(Pt.n_rows + 1, 0);
+        for (int64_t k = 0; k < P.nnz(); ++k) Pt.ptr[P.col[k] + 1]++;
+        for (int64_t i = 0; i < Pt.n_rows; ++i) Pt.ptr[i + 1] += Pt.ptr[i];
+        Pt.col.resize(P.nnz());
+        Pt.val.resize(P.nnz());
+        std::vector<int64_t> fill(Pt.ptr.begin(), Pt.ptr.end() - 1);
+        for (int64_t i = 0; i < P.n_rows; ++i)
+          for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) {
+            const int64_t d = fill[P.col[k]]++;
+            Pt.col[d] = (int32_t)i;
+            Pt.val[d] = P.val[k];
+          }
+      }
+      if ((e = upload_sell(c, Pt, D.R)) != cudaSuccess) return e;
+    }
+    std::vector<T> dinv(D.n);
+    for (int64_t i = 0; i < D.n; ++i) {
+      double d = 0.0;
+      for (int64_t k = H.A.ptr[i]; k < H.A.ptr[i + 1]; ++k)
+        if (H.A.col[k] == i) d = H.A.val[k];
+      dinv[i] = (T)(1.0 / d);
+    }
+    if ((e = upload(c, &D.dinv, dinv.data(), dinv.size())) != cudaSuccess) return e;
+    for (T** v : {&D.b, &D.x, &D.r, &D.dA, &D.dB})
+      if ((e = dalloc(c, v, D.n)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------ V-cycle
+template <typename T>
+static void vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStream_t st) {
+  const int nl = (int)L.size();
+  DevLevel<T>& V = L[l];
+  if (l == nl - 1) {
+    k_coarse_solve<T><<<nblk((int64_t)V.n * 32), kBlock, 0, st>>>(V.n, c->d_coarse_inv, V.b, V.x);
+    return;
+  }
+  const int deg = c->opts.cheb_degree;
+  std::vector<double> c1, c2;
+  cheb_coeffs(V.sigma, V.delta, deg, c1, c2);
+  const int g = nblk(V.n);
+  // pre-smoothing: x = d = D^-1 b / theta was set by the producer of b
+  T* din = V.dA;
+  T* dout = V.dB;
+  const T* rin = V.b;
+  for (int k = 2; k <= deg; ++k) {
+    k_cheb_step<T><<<g, kBlock, 0, st>>>(V.A, V.n, rin, din, V.dinv, (T)c1[k], (T)c2[k], V.r, dout,
+                                         V.x, 0);
+    rin = V.r;
+    std::swap(din, dout);
+  }
+  if (deg >= 2)
+    k_resid_update<T><<<g, kBlock, 0, st>>>(V.A, V.n, V.r, din);
+  else
+    k_resid<T><<<g, kBlock, 0, st>>>(V.A, V.n, V.b, V.x, V.r);
+  DevLevel<T>& C = L[l + 1];
+  const int first = (l + 1 < nl - 1) ? 1 : 0;
+  k_restrict<T><<<nblk(C.n), kBlock, 0, st>>>(V.R, C.n, V.r, C.b, C.dinv, (T)C.inv_theta, C.x, C.dA,
+                                               first);
+  vcycle_level(c, L, l + 1, st);
+  k_prolong<T><<<g, kBlock, 0, st>>>(V.P, V.n, C.x, V.x);
+  k_post_first<T><<<g, kBlock, 0, st>>>(V.A, V.n, V.b, V.x, V.dinv, (T)V.inv_theta, V.r, V.dA);
+  din = V.dA;
+  dout = V.dB;
+  for (int k = 2; k <= deg; ++k) {
+    k_cheb_step<T><<<g, kBlock, 0, st>>>(V.A, V.n, V.r, din, V.dinv, (T)c1[k], (T)c2[k], V.r, dout,
+                                         V.x, k == 2 ? 1 : 0);
+    std::swap(din, dout);
+  }
+  if (deg == 1) k_axpy1<T><<<g, kBlock, 0, st>>>(V.n, V.x, V.dA);
+}
+
+// ------------------------------------------------------------- PCG
+struct SolveSlots {
+  int* iters;
+  double* relres;
+  int* zero;
+};
+
+template <typename T>
+static void pcg_init_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st,
+                            const double* R, double* x, double tol2, cudaGraphConditionalHandle h,
+                            int use_handle, SolveSlots sl) {
+  DevLevel<T>& V = L[0];
+  const int n = (int)c->n_free;
+  k_pcg_init<T><<<nblk(n), kBlock, 0, st>>>(c->M64, n, R, x, c->d_r, V.dinv, (T)V.inv_theta, V.b, V.x,
+                                            V.dA, c->d_sc, c->red.partials, c->red.counter,
+                                            c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle,
+                                            sl.iters, sl.relres, sl.zero);
+}
+
+template <typename T>
+static void pcg_body_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st, double* x,
+                            double tol2, cudaGraphConditionalHandle h, int use_handle,
+                            SolveSlots sl) {
+  DevLevel<T>& V = L[0];
+  const int n = (int)c->n_free;
+  const int g = nblk(n);
+  vcycle_level(c, L, 0, st);
+  k_pcg_dots<T><<<g, kBlock, 0, st>>>(c->M64, n, c->d_r, c->d_rprev, V.x, c->d_zd, nullptr, c->d_sc,
+                                      c->red.partials, c->red.counter, c->red.max_blocks,
+                                      c->opts.flexible);
+  k_pcg_p<<<g, kBlock, 0, st>>>(n, c->d_zd, c->d_p, c->d_sc);
+  k_pcg_q<<<g, kBlock, 0, st>>>(c->M64, n, c->d_p, c->d_q, c->d_sc, c->red.partials, c->red.counter,
+                                c->red.max_blocks);
+  k_pcg_update<T><<<g, kBlock, 0, st>>>(n, x, c->d_r, c->d_rprev, c->d_p, c->d_q, V.dinv,
+                                        (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials,
+                                        c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h,
+                                        use_handle, sl.iters, sl.relres);
+}
+
+// Append "init; while (not converged) body" to the graph being captured on
+// c->cap_stream; the loop body is captured on c->cap_stream2.
+template <typename T>
+static eqs_status pcg_capture(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* R, double* x,
+                              double tol2, SolveSlots sl) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  pcg_init_launch<T>(c, L, c->cap_stream, R, x, tol2, h, 1, sl);
+  CK(cudaGetLastError());
+  CK(cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(c->cap_stream2, body, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeRelaxed));
+  pcg_body_launch<T>(c, L, c->cap_stream2, x, tol2, h, 1, sl);
+  cudaError_t le = cudaGetLastError();
+  cudaGraph_t body_out = nullptr;
+  CK(cudaStreamEndCapture(c->cap_stream2, &body_out));
+  CK(le);
+  CK(cudaStreamUpdateCaptureDependencies(c->cap_stream, &node, nullptr, 1,
+                                         cudaStreamSetCaptureDependencies));
+  return EQS_OK;
+}
+
+static bool mixed(const eqs_ctx* c) { return c->opts.precision == EQS_PREC_MIXED; }
+
+// ------------------------------------------------------------ element
+static void elem_launch(eqs_ctx* c, cudaStream_t st, const double* Y, int n_limit, double* y64,
+                        float* y32) {
+  if (mixed(c))
+    k_elem32<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn, c->d_mat, c->d_mats,
+                                                 c->d_xyz_hi, c->d_xyz_lo, c->d_Y32, n_limit, y32);
+  else
+    k_elem64<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn, c->d_mat, c->d_mats, c->d_xyz,
+                                                 Y, n_limit, y64 == c->d_R ? -1.0 : 1.0, y64);
+}
+
+// -------------------------------------------------------- step graph
+static double* Ybuf(eqs_ctx* c, int j) { return j == 0 ? c->d_Y[0] : c->d_Y[1 + (j - 1) % 3]; }
+static double* Fbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_F[0] : c->d_F[1 + (j - 1) % 2]; }
+
+template <typename T>
+static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, double* xdev,
+                               GraphEntry& ge) {
+  std::vector<double> mu, nu, mut, gt, cj;
+  double beta;
+  rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
+  CK(upload(c, &ge.d_cj, cj.data(), cj.size()));
+  const int n = (int)c->n_nodes, nf = (int)c->n_free;
+  const double tol2 = c->opts.rtol * c->opts.rtol;
+  const double w = 2.0 * M_PI * c->freq;
+  cudaStream_t st = c->cap_stream;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  k_stage_scalars<<<1, 64, 0, st>>>(s + 1, ge.d_cj, c->d_params, c->V0, w, c->phase, c->d_g, c->d_gp);
+  const bool mx = mixed(c);
+  k_gather_state<<<nblk(n), kBlock, 0, st>>>(n, nf, xdev, c->d_node_of_internal, c->d_dir_scale, c->d_g,
+                                             c->d_gp, c->d_mtop, Ybuf(c, 0), mx ? c->d_Y32 : nullptr,
+                                             Fbuf(c, s - 1), Fbuf(c, 0), mx ? nullptr : c->d_R);
+  eqs_status stt = EQS_OK;
+  for (int j = 0; j <= s && stt == EQS_OK; ++j) {
+    if (j >= 1) {
+      const bool first = (j == 1);
+      const double c0 = first ? 1.0 : 1.0 - mu[j] - nu[j];
+      const bool last = (j == s);
+      k_recurrence<<<nblk(n), kBlock, 0, st>>>(
+          n, nf, c0, first ? 0.0 : mu[j], first ? 0.0 : nu[j], mut[j], first ? 0.0 : gt[j], c->d_params,
+          Ybuf(c, 0), Ybuf(c, j - 1), Ybuf(c, j >= 2 ? j - 2 : 0), Fbuf(c, j - 1), Fbuf(c, 0), c->d_zero,
+          j - 1, c->d_dir_scale, c->d_g + j, c->d_gp + j, c->d_mtop, Ybuf(c, j),
+          (mx && !last) ? c->d_Y32 : nullptr, last ? nullptr : Fbuf(c, j),
+          (mx || last) ? nullptr : c->d_R, last ? xdev : nullptr, c->d_node_of_internal);
+      if (last) break;
+    }
+    if (mx) {
+      elem_launch(c, st, nullptr, nf, nullptr, c->d_y32);
+      k_rhs_from_y32<<<nblk(nf), kBlock, 0, st>>>(nf, c->d_y32, c->d_gp + j, c->d_mtop, c->d_R);
+    } else {
+      elem_launch(c, st, Ybuf(c, j), nf, c->d_R, nullptr);
+    }
+    SolveSlots sl{c->d_iters + j, c->d_relres + j, c->d_zero + j};
+    stt = pcg_capture<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl);
+  }
+  cudaError_t le = cudaGetLastError();
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  if (stt != EQS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return stt;
+  }
+  CK(le);
+  CK(ee);
+  ge.graph = graph;
+  CK(cudaGraphInstantiate(&ge.exec, graph, 0));
+  return EQS_OK;
+}
+
+template <typename T>
+static eqs_status capture_solve(eqs_ctx* c, std::vector<DevLevel<T>>& L, double rtol, GraphEntry& ge) {
+  cudaStream_t st = c->cap_stream;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  SolveSlots sl{c->d_iters, c->d_relres, c->d_zero};
+  eqs_status stt = pcg_capture<T>(c, L, c->d_R, c->d_sol, rtol * rtol, sl);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  if (stt != EQS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return stt;
+  }
+  CK(ee);
+  ge.graph = graph;
+  CK(cudaGraphInstantiate(&ge.exec, graph, 0));
+  return EQS_OK;
+}
+
+static void destroy_graph(GraphEntry& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  g.exec = nullptr;
+  g.graph = nullptr;
+}
+
+static void destroy_graphs(eqs_ctx* c) {
+  for (auto& kv : c->step_graphs) destroy_graph(kv.second);
+  c->step_graphs.clear();
+  for (auto& kv : c->solve_graphs) destroy_graph(kv.second);
+  c->solve_graphs.clear();
+}
+
+template <typename T>
+static eqs_status vcycle_impl(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* r, double* z) {
+  const int nf = (int)c->n_free;
+  cudaStream_t st = c->stream;
+  DevLevel<T>& V = L[0];
+  k_to_T<T><<<nblk(nf), kBlock, 0, st>>>(nf, r, V.b);
+  if (L.size() > 1) k_first_step<T><<<nblk(nf), kBlock, 0, st>>>(nf, V.b, V.dinv, (T)V.inv_theta, V.x, V.dA);
+  vcycle_level(c, L, 0, st);
+  k_from_T<T><<<nblk(nf), kBlock, 0, st>>>(nf, V.x, z);
+  CK(cudaGetLastError());
+  return EQS_OK;
+}
+
+// ================================================================ C ABI
+extern "C" {
+
+void eqs_opts_default(eqs_opts* o) {
+  if (!o) return;
+  o->precision = EQS_PREC_FP64;
+  o->theta = 0.08;
+  o->coarse_max = 500;
+  o->max_levels = 10;
+  o->cheb_degree = 2;
+  o->cheb_alpha = 30.0;
+  o->rtol = 1e-8;
+  o->max_iter = 500;
+  o->guess = EQS_GUESS_PREV;
+  o->flexible = 1;
+}
+
+eqs_status eqs_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                           const uint8_t* node_tag, eqs_ctx** out) {
+  if (!out) return fail(nullptr, EQS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!xyz || !tets || !node_tag || n_nodes <= 0 || n_tets <= 0)
+    return fail(nullptr, EQS_ERR_ARG, "null pointer or non-positive size");
+  if (n_nodes > (int64_t)INT32_MAX / 2 || n_tets > (int64_t)INT32_MAX * 16)
+    return fail(nullptr, EQS_ERR_ARG, "mesh too large for 32-bit node indices");
+  eqs_ctx* c = new eqs_ctx();
+  c->n_nodes = n_nodes;
+  c->n_tets = n_tets;
+  c->xyz.assign(xyz, xyz + 3 * n_nodes);
+  c->tets.assign(tets, tets + 4 * n_tets);
+  c->tag.assign(node_tag, node_tag + n_nodes);
+  eqs_opts_default(&c->opts);
+  eqs_status st = validate_and_orient(c);
+  if (st != EQS_OK) {
+    g_create_err = c->err;
+    delete c;
+    return st;
+  }
+  build_internal_numbering(c);
+  *out = c;
+  return EQS_OK;
+}
+
+eqs_status eqs_set_materials(eqs_ctx* c, const uint8_t* tet_mat, int n_mat, const eqs_material* mats) {
+  if (!c) return fail(nullptr, EQS_ERR_ARG, "ctx is NULL");
+  if (!tet_mat || !mats || n_mat < 1 || n_mat > 255) return fail(c, EQS_ERR_ARG, "bad material arguments");
+  for (int m = 0; m < n_mat; ++m) {
+    const eqs_material& q = mats[m];
+    if (!(q.eps_r > 0) || !(q.kappa_lo >= 0) || !(q.kappa_hi >= 0) ||
+        (q.kappa_hi != q.kappa_lo && !(q.w > 0)))
+      return fail(c, EQS_ERR_ARG, "material " + std::to_string(m) + " has invalid parameters");
+  }
+  for (int64_t e = 0; e < c->n_tets; ++e)
+    if (tet_mat[e] >= n_mat) return fail(c, EQS_ERR_MESH, "tet material id out of range");
+  c->tet_mat.assign(tet_mat, tet_mat + c->n_tets);
+  c->mats.assign(mats, mats + n_mat);
+  c->have_materials = true;
+  c->setup_done = false;
+  return EQS_OK;
+}
+
+eqs_status eqs_set_dirichlet(eqs_ctx* c, double V0, double freq_hz, double phase) {
+  if (!c) return fail(nullptr, EQS_ERR_ARG, "ctx is NULL");
+  if (!std::isfinite(V0) || !std::isfinite(freq_hz) || !std::isfinite(phase))
+    return fail(c, EQS_ERR_ARG, "non-finite drive parameter");
+  c->V0 = V0;
+  c->freq = freq_hz;
+  c->phase = phase;
+  destroy_graphs(c);  // drive parameters are baked into the step graphs
+  return EQS_OK;
+}
+
+eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
+  if (!c) return fail(nullptr, EQS_ERR_ARG, "ctx is NULL");
+  if (!c->have_materials) return fail(c, EQS_ERR_STATE, "eqs_set_materials must come first");
+  eqs_opts o;
+  if (opts)
+    o = *opts;
+  else
+    eqs_opts_default(&o);
+  if (o.cheb_degree < 1 || o.cheb_degree > 4 || o.max_levels < 1 || o.coarse_max < 1 ||
+      !(o.theta >= 0) || !(o.cheb_alpha > 1) || !(o.rtol > 0) || o.max_iter < 1 ||
+      (o.precision != EQS_PREC_FP64 && o.precision != EQS_PREC_MIXED))
+    return fail(c, EQS_ERR_ARG, "invalid eqs_opts");
+  // release an earlier setup
+  destroy_graphs(c);
+  free_all(c);
+  c->setup_done = false;
+  c->opts = o;
+  c->hier_ready = false;
+
+  // host part: M, M_fd 1_top and the AMG hierarchy (inspectable without a GPU)
+  HostCSR Mff;
+  std::vector<double> mtop;
+  assemble_M(c, Mff, mtop);
+  build_hierarchy(Mff, o, c->hlev);
+  if (c->hlev.back().A.n_rows > 4096)
+    return fail(c, EQS_ERR_ARG, "coarsest AMG level has more than 4096 rows: raise max_levels");
+  std::vector<double> inv;
+  if (!dense_spd_inverse(c->hlev.back().A, inv))
+    return fail(c, EQS_ERR_MESH, "coarsest AMG matrix is not SPD");
+  c->coarse_n = (int)c->hlev.back().A.n_rows;
+  c->hier_ready = true;
+
+  // device part
+  if (!c->own_stream) {
+    CK(cudaGetDevice(&c->device));
+    CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking));
+  }
+  CK(cudaSetDevice(c->device));
+
+  const int64_t n = c->n_nodes, nf = c->n_free;
+  // mesh data in internal numbering
+  std::vector<int4> conn(c->n_tets);
+  for (int64_t e = 0; e < c->n_tets; ++e) {
+    const int32_t* t = &c->tets[4 * e];
+    conn[e] = make_int4(c->internal_of_node[t[0]], c->internal_of_node[t[1]], c->internal_of_node[t[2]],
+                        c->internal_of_node[t[3]]);
+  }
+  std::vector<double4> xyz(n);
+  std::vector<float4> xh(n), xl(n);
+  for (int64_t i = 0; i < n; ++i) {
+    const double* p = &c->xyz[3 * (int64_t)c->node_of_internal[i]];
+    xyz[i] = make_double4(p[0], p[1], p[2], 0.0);
+    float h[3], l[3];
+    for (int d = 0; d < 3; ++d) {
+      h[d] = (float)p[d];
+      l[d] = (float)(p[d] - (double)h[d]);
+    }
+    xh[i] = make_float4(h[0], h[1], h[2], 0.f);
+    xl[i] = make_float4(l[0], l[1], l[2], 0.f);
+  }
+  std::vector<double> dir_scale(n - nf);
+  for (int64_t i = nf; i < n; ++i) dir_scale[i - nf] = c->tag[c->node_of_internal[i]] == 2 ? 1.0 : 0.0;
+  std::vector<MaterialDev> md(c->mats.size());
+  for (size_t m = 0; m < c->mats.size(); ++m) {
+    const eqs_material& q = c->mats[m];
+    md[m].eps = 8.8541878128e-12 * q.eps_r;
+    md[m].klo = q.kappa_lo;
+    md[m].khi = q.kappa_hi;
+    md[m].E0 = q.E0;
+    md[m].inv_w = q.kappa_hi != q.kappa_lo ? 1.0 / q.w : 0.0;
+    md[m].is_const = q.kappa_hi == q.kappa_lo;
+    md[m].pad = 0;
+  }
+  CK(upload(c, &c->d_conn, conn.data(), conn.size()));
+  CK(upload(c, &c->d_mat, c->tet_mat.data(), c->tet_mat.size()));
+  CK(upload(c, &c->d_mats, md.data(), md.size()));
+  CK(upload(c, &c->d_xyz, xyz.data(), xyz.size()));
+  CK(upload(c, &c->d_xyz_hi, xh.data(), xh.size()));
+  CK(upload(c, &c->d_xyz_lo, xl.data(), xl.size()));
+  CK(upload(c, &c->d_node_of_internal, c->node_of_internal.data(), c->node_of_internal.size()));
+  CK(upload(c, &c->d_dir_scale, dir_scale.data(), dir_scale.size()));
+  CK(upload(c, &c->d_mtop, mtop.data(), mtop.size()));
+  CK(upload_sell(c, Mff, c->M64));
+  CK(upload(c, &c->d_coarse_inv, inv.data(), inv.size()));
+  c->lev64.clear();
+  c->lev32.clear();
+  if (mixed(c))
+    CK(upload_levels(c, c->lev32));
+  else
+    CK(upload_levels(c, c->lev64));
+  for (int k = 0; k < 4; ++k) CK(dalloc(c, &c->d_Y[k], n));
+  for (int k = 0; k < 3; ++k) CK(dalloc(c, &c->d_F[k], nf));
+  CK(dalloc(c, &c->d_Y32, n));
+  CK(dalloc(c, &c->d_y32, n));
+  for (double** v : {&c->d_R, &c->d_r, &c->d_rprev, &c->d_p, &c->d_q, &c->d_zd, &c->d_sol})
+    CK(dalloc(c, v, nf));
+  CK(dalloc(c, &c->d_tmpn, n));
+  CK(dalloc(c, &c->d_tmpn2, n));
+  CK(dalloc(c, &c->d_sc, 1));
+  CK(dalloc(c, &c->d_params, 1));
+  CK(dalloc(c, &c->d_iters, EQS_MAX_STAGES + 1));
+  CK(dalloc(c, &c->d_relres, EQS_MAX_STAGES + 1));
+  CK(dalloc(c, &c->d_zero, EQS_MAX_STAGES + 1));
+  CK(dalloc(c, &c->d_g, EQS_MAX_STAGES + 1));
+  CK(dalloc(c, &c->d_gp, EQS_MAX_STAGES + 1));
+  c->red.max_blocks = nblk(std::max<int64_t>(nf, 1));
+  CK(dalloc(c, &c->red.partials, 4 * (size_t)c->red.max_blocks));
+  CK(dalloc(c, &c->red.counter, 1));
+  CK(cudaDeviceSynchronize());
+  c->setup_done = true;
+  return EQS_OK;
+}
+
+#define REQUIRE_SETUP(c)                                                   \
+  do {                                                                     \
+    if (!(c)) return fail(nullptr, EQS_ERR_ARG, "ctx is NULL");            \
+    if (!(c)->setup_done) return fail((c), EQS_ERR_STATE, "call eqs_amg_setup first"); \
+  } while (0)
+
+eqs_status eqs_apply_K(eqs_ctx* c, const double* x, double* y) {
+  REQUIRE_SETUP(c);
+  if (!x || !y) return fail(c, EQS_ERR_ARG, "null vector");
+  const int n = (int)c->n_nodes;
+  cudaStream_t st = c->stream;
+  const bool mx = mixed(c);
+  k_gather_perm<<<nblk(n), kBlock, 0, st>>>(n, x, c->d_node_of_internal, c->d_tmpn, mx ? c->d_Y32 : nullptr);
+  if (mx) {
+    CK(cudaMemsetAsync(c->d_y32, 0, n * sizeof(float), st));
+    elem_launch(c, st, nullptr, n, nullptr, c->d_y32);
+    k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, nullptr, c->d_y32, c->d_node_of_internal, y);
+    CK(cudaMemsetAsync(c->d_y32, 0, n * sizeof(float), st));
+  } else {
+    CK(cudaMemsetAsync(c->d_tmpn2, 0, n * sizeof(double), st));
+    elem_launch(c, st, c->d_tmpn, n, c->d_tmpn2, nullptr);
+    k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, c->d_tmpn2, nullptr, c->d_node_of_internal, y);
+  }
+  CK(cudaGetLastError());
+  return EQS_OK;
+}
+
+eqs_status eqs_spmv_M(eqs_ctx* c, const double* x, double* y) {
+  REQUIRE_SETUP(c);
+  if (!x || !y) return fail(c, EQS_ERR_ARG, "null vector");
+  const int nf = (int)c->n_free;
+  k_spmv64<<<nblk(nf), kBlock, 0, c->stream>>>(c->M64, nf, x, y);
+  CK(cudaGetLastError());
+  return EQS_OK;
+}
+
+eqs_status eqs_vcycle(eqs_ctx* c, const double* r, double* z) {
+  REQUIRE_SETUP(c);
+  if (!r || !z) return fail(c, EQS_ERR_ARG, "null vector");
+  return mixed(c) ? vcycle_impl(c, c->lev32, r, z) : vcycle_impl(c, c->lev64, r, z);
+}
+
+eqs_status eqs_solve_M(eqs_ctx* c, const double* rhs, double* z, int nrhs, double rtol, int* iters_out) {
+  REQUIRE_SETUP(c);
+  if (!rhs || !z || nrhs < 1) return fail(c, EQS_ERR_ARG, "bad solve arguments");
+  const double tol = rtol > 0 ? rtol : c->opts.rtol;
+  auto it = c->solve_graphs.find(tol);
+  if (it == c->solve_graphs.end()) {
+    GraphEntry ge;
+    eqs_status st = mixed(c) ? capture_solve(c, c->lev32, tol, ge) : capture_solve(c, c->lev64, tol, ge);
+    if (st != EQS_OK) return st;
+    it = c->solve_graphs.emplace(tol, ge).first;
+  }
+  const int64_t nf = c->n_free;
+  eqs_status res = EQS_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    CK(cudaMemcpyAsync(c->d_R, rhs + k * nf, nf * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_sol, z + k * nf, nf * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaGraphLaunch(it->second.exec, c->stream));
+    int itn = 0, zero = 0;
+    double rr = 0;
+    CK(cudaMemcpyAsync(&itn, c->d_iters, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&rr, c->d_relres, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&zero, c->d_zero, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (zero)
+      CK(cudaMemsetAsync(z + k * nf, 0, nf * sizeof(double), c->stream));
+    else
+      CK(cudaMemcpyAsync(z + k * nf, c->d_sol, nf * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (iters_out) iters_out[k] = itn;
+    if (!std::isfinite(rr)) res = fail(c, EQS_ERR_NAN, "non-finite residual in solve");
+    else if (!zero && rr > tol) res = fail(c, EQS_ERR_NOCONV, "CG reached max_iter");
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return res;
+}
+
+eqs_status eqs_rkc_step(eqs_ctx* c, double* x, double t, double dt, int s, eqs_step_stats* stats) {
+  REQUIRE_SETUP(c);
+  if (!x) return fail(c, EQS_ERR_ARG, "x is NULL");
+  if (s < 2 || s > EQS_MAX_STAGES) return fail(c, EQS_ERR_ARG, "s out of range [2, 64]");
+  if (!std::isfinite(t) || !(dt > 0) || !std::isfinite(dt)) return fail(c, EQS_ERR_ARG, "bad t or dt");
+  const std::pair<int, uintptr_t> key(s, (uintptr_t)x);
+  auto it = c->step_graphs.find(key);
+  if (it == c->step_graphs.end()) {
+    GraphEntry ge;
+    eqs_status st = mixed(c) ? capture_step(c, c->lev32, s, x, ge) : capture_step(c, c->lev64, s, x, ge);
+    if (st != EQS_OK) return st;
+    it = c->step_graphs.emplace(key, ge).first;
+  }
+  StepParams prm{t, dt};
+  CK(cudaMemcpyAsync(c->d_params, &prm, sizeof(prm), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaGraphLaunch(it->second.exec, c->stream));
+  if (!stats) return EQS_OK;
+  int iters[EQS_MAX_STAGES];
+  double rr[EQS_MAX_STAGES];
+  CK(cudaMemcpyAsync(iters, c->d_iters, s * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(rr, c->d_relres, s * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::memset(stats, 0, sizeof(*stats));
+  stats->s = s;
+  eqs_status res = EQS_OK;
+  for (int j = 0; j < s; ++j) {
+    stats->iters[j] = iters[j];
+    stats->total_iters += iters[j];
+    stats->max_iters = std::max(stats->max_iters, iters[j]);
+    stats->max_relres = std::max(stats->max_relres, rr[j]);
+    if (!std::isfinite(rr[j])) res = EQS_ERR_NAN;
+    else if (rr[j] > c->opts.rtol && res == EQS_OK) res = EQS_ERR_NOCONV;
+  }
+  stats->status = res;
+  if (res == EQS_ERR_NOCONV) return fail(c, res, "a stage solve reached max_iter");
+  if (res == EQS_ERR_NAN) return fail(c, res, "non-finite residual in a stage solve");
+  return EQS_OK;
+}
+
+double eqs_rkc_dt_bound(const eqs_ctx* c, int s) {
+  if (!c || !c->have_materials || s < 2 || s > EQS_MAX_STAGES) return -1.0;
+  std::vector<double> mu, nu, mut, gt, cj;
+  double beta;
+  rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
+  const double rho = rho_bound(c->mats);
+  return rho > 0 ? beta / rho : -1.0;
+}
+
+eqs_status eqs_set_stream(eqs_ctx* c, void* stream) {
+  if (!c) return fail(nullptr, EQS_ERR_ARG, "ctx is NULL");
+  c->stream = (cudaStream_t)stream;  // NULL: the legacy default stream
+  return EQS_OK;
+}
+
+eqs_status eqs_get_sizes(const eqs_ctx* c, int64_t* n_nodes, int64_t* n_free, int64_t* n_tets) {
+  if (!c) return fail(nullptr, EQS_ERR_ARG, "ctx is NULL");
+  if (n_nodes) *n_nodes = c->n_nodes;
+  if (n_free) *n_free = c->n_free;
+  if (n_tets) *n_tets = c->n_tets;
+  return EQS_OK;
+}
+
+eqs_status eqs_amg_info(const eqs_ctx* c, int* n_levels, int64_t* rows, int64_t* nnz) {
+  if (!c) return fail(nullptr, EQS_ERR_ARG, "ctx is NULL");
+  if (!c->hier_ready) return fail(const_cast<eqs_ctx*>(c), EQS_ERR_STATE, "call eqs_amg_setup first");
+  const int nl = (int)c->hlev.size();
+  if (n_levels) *n_levels = nl;
+  for (int l = 0; l < nl && l < 16; ++l) {
+    if (rows) rows[l] = c->hlev[l].A.n_rows;
+    if (nnz) nnz[l] = c->hlev[l].A.nnz();
+  }
+  return EQS_OK;
+}
+
+eqs_status eqs_amg_aggregates(const eqs_ctx* c, int level, int32_t* agg_out) {
+  if (!c) return fail(nullptr, EQS_ERR_ARG, "ctx is NULL");
+  if (!c->hier_ready) return fail(const_cast<eqs_ctx*>(c), EQS_ERR_STATE, "call eqs_amg_setup first");
+  if (!agg_out || level < 0 || level + 1 >= (int)c->hlev.size())
+    return fail(const_cast<eqs_ctx*>(c), EQS_ERR_ARG, "level has no aggregates");
+  std::memcpy(agg_out, c->hlev[level].agg.data(), c->hlev[level].agg.size() * sizeof(int32_t));
+  return EQS_OK;
+}
+
+eqs_status eqs_destroy(eqs_ctx* c) {
+  if (!c) return EQS_OK;
+  if (c->setup_done) cudaStreamSynchronize(c->stream);
+  destroy_graphs(c);
+  free_all(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+  return EQS_OK;
+}
+
+const char* eqs_last_error(const eqs_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+"""ctypes binding of ``libeqs.so`` (the C ABI declared in include/eqs.h).
+
+Each ``eqs_*`` function here has the C function's name and arguments and only
+marshals them: host arrays are numpy arrays, device buffers are CUDA torch
+tensors (passed by data pointer).  A non-zero status raises ``EqsError``
+carrying ``eqs_last_error``.  There is no fallback: if the library is
+missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libeqs.so")
+
+EQS_OK, EQS_ERR_ARG, EQS_ERR_MESH, EQS_ERR_CUDA = 0, -1, -2, -3
+EQS_ERR_NOCONV, EQS_ERR_TIMEOUT, EQS_ERR_NAN, EQS_ERR_STATE = -4, -5, -6, -7
+EQS_PREC_FP64, EQS_PREC_MIXED = 0, 1
+EQS_GUESS_PREV, EQS_GUESS_MLP, EQS_GUESS_ZERO = 0, 1, 2
+EQS_MAX_STAGES = 64
+
+
+class EqsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"eqs status {status}: {msg}")
+        self.status = status
+
+
+class eqs_material(C.Structure):
+    _fields_ = [("eps_r", C.c_double), ("kappa_lo", C.c_double), ("kappa_hi", C.c_double),
+                ("E0", C.c_double), ("w", C.c_double)]
+
+
+class eqs_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("theta", C.c_double), ("coarse_max", C.c_int),
+                ("max_levels", C.c_int), ("cheb_degree", C.c_int), ("cheb_alpha", C.c_double),
+                ("rtol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int),
+                ("flexible", C.c_int)]
+
+
+class eqs_step_stats(C.Structure):
+    _fields_ = [("s", C.c_int), ("total_iters", C.c_int), ("max_iters", C.c_int),
+                ("iters", C.c_int * EQS_MAX_STAGES), ("max_relres", C.c_double),
+                ("status", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libeqs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is missing: run __graft_entry__.build() first")
+        _lib = C.CDLL(_LIB_PATH)
+        _declare(_lib)
+    return _lib
+
+
+def _declare(L):
+    P, I64, I, D = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "eqs_opts_default": (None, [C.POINTER(eqs_opts)]),
+        "eqs_mesh_create": (I, [P, I64, P, I64, P, C.POINTER(C.c_void_p)]),
+        "eqs_set_materials": (I, [P, P, I, P]),
+        "eqs_set_dirichlet": (I, [P, D, D, D]),
+        "eqs_amg_setup": (I, [P, C.POINTER(eqs_opts)]),
+        "eqs_apply_K": (I, [P, P, P]),
+        "eqs_solve_M": (I, [P, P, P, I, D, P]),
+        "eqs_vcycle": (I, [P, P, P]),
+        "eqs_spmv_M": (I, [P, P, P]),
+        "eqs_rkc_step": (I, [P, P, D, D, I, C.POINTER(eqs_step_stats)]),
+        "eqs_rkc_dt_bound": (D, [P, I]),
+        "eqs_set_stream": (I, [P, P]),
+        "eqs_get_sizes": (I, [P, P, P, P]),
+        "eqs_amg_info": (I, [P, P, P, P]),
+        "eqs_amg_aggregates": (I, [P, I, P]),
+        "eqs_destroy": (I, [P]),
+        "eqs_last_error": (C.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _check(status, ctx=None):
+    if status != EQS_OK:
+        raise EqsError(status, lib().eqs_last_error(ctx).decode())
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def _dev(t):
+    """Device pointer of a CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------- C entry points
+def eqs_opts_default():
+    o = eqs_opts()
+    lib().eqs_opts_default(C.byref(o))
+    return o
+
+
+def eqs_mesh_create(xyz, tets, node_tag):
+    xyz, pxyz = _host(xyz, np.float64)
+    tets, ptets = _host(tets, np.int32)
+    tag, ptag = _host(node_tag, np.uint8)
+    out = C.c_void_p()
+    _check(lib().eqs_mesh_create(pxyz, len(xyz), ptets, len(tets), ptag, C.byref(out)))
+    return out
+
+
+def eqs_set_materials(ctx, tet_mat, materials):
+    tm, ptm = _host(tet_mat, np.uint8)
+    arr = (eqs_material * len(materials))()
+    for k, m in enumerate(materials):
+        t = m.as_tuple() if hasattr(m, "as_tuple") else tuple(m)
+        arr[k] = eqs_material(*t)
+    _check(lib().eqs_set_materials(ctx, ptm, len(materials), arr), ctx)
+
+
+def eqs_set_dirichlet(ctx, V0, freq_hz, phase=0.0):
+    _check(lib().eqs_set_dirichlet(ctx, V0, freq_hz, phase), ctx)
+
+
+def eqs_amg_setup(ctx, opts=None):
+    _check(lib().eqs_amg_setup(ctx, C.byref(opts) if opts is not None else None), ctx)
+
+
+def eqs_apply_K(ctx, x, y):
+    _check(lib().eqs_apply_K(ctx, _dev(x), _dev(y)), ctx)
+
+
+def eqs_solve_M(ctx, rhs, z, nrhs=1, rtol=0.0):
+    iters = (C.c_int * nrhs)()
+    st = lib().eqs_solve_M(ctx, _dev(rhs), _dev(z), nrhs, rtol, iters)
+    _check(st, ctx)
+    return list(iters)
+
+
+def eqs_vcycle(ctx, r, z):
+    _check(lib().eqs_vcycle(ctx, _dev(r), _dev(z)), ctx)
+
+
+def eqs_spmv_M(ctx, x, y):
+    _check(lib().eqs_spmv_M(ctx, _dev(x), _dev(y)), ctx)
+
+
+def eqs_rkc_step(ctx, x, t, dt, s, want_stats=True):
+    st = eqs_step_stats() if want_stats else None
+    _check(lib().eqs_rkc_step(ctx, _dev(x), t, dt, s, C.byref(st) if st is not None else None), ctx)
+    return st
+
+
+def eqs_rkc_dt_bound(ctx, s):
+    return lib().eqs_rkc_dt_bound(ctx, s)
+
+
+def eqs_set_stream(ctx, stream_ptr):
+    _check(lib().eqs_set_stream(ctx, C.c_void_p(stream_ptr) if stream_ptr else None), ctx)
+
+
+def eqs_get_sizes(ctx):
+    n, nf, nt = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().eqs_get_sizes(ctx, C.byref(n), C.byref(nf), C.byref(nt)), ctx)
+    return n.value, nf.value, nt.value
+
+
+def eqs_amg_info(ctx):
+    nl = C.c_int()
+    rows = (C.c_int64 * 16)()
+    nnz = (C.c_int64 * 16)()
+    _check(lib().eqs_amg_info(ctx, C.byref(nl), rows, nnz), ctx)
+    return [rows[i] for i in range(nl.value)], [nnz[i] for i in range(nl.value)]
+
+
+def eqs_amg_aggregates(ctx, level, n_rows):
+    out = np.empty(n_rows, dtype=np.int32)
+    _check(lib().eqs_amg_aggregates(ctx, level, out.ctypes.data_as(C.c_void_p)), ctx)
+    return out
+
+
+def eqs_destroy(ctx):
+    if ctx:
+        lib().eqs_destroy(ctx)
+
+
+def eqs_last_error(ctx=None):
+    return lib().eqs_last_error(ctx).decode()
+
+
+# ---------------------------------------------------------- convenience
+class Solver:
+    """One EQS instance on the GPU: mesh + materials + drive + AMG setup.
+
+    ``problem`` has xyz, tets, node_tag, tet_mat, materials, V0, freq, phase
+    (eqs_inputs.Problem).  Vectors are CUDA float64 tensors."""
+
+    def __init__(self, problem, precision=EQS_PREC_FP64, rtol=1e-8, **opt):
+        import torch
+
+        self.torch = torch
+        self.p = problem
+        self.ctx = eqs_mesh_create(problem.xyz, problem.tets, problem.node_tag)
+        eqs_set_materials(self.ctx, problem.tet_mat, problem.materials)
+        eqs_set_dirichlet(self.ctx, problem.V0, problem.freq, problem.phase)
+        o = eqs_opts_default()
+        o.precision = precision
+        o.rtol = rtol
+        for k, v in opt.items():
+            setattr(o, k, v)
+        self.opts = o
+        eqs_amg_setup(self.ctx, o)
+        self.n, self.nf, self.nt = eqs_get_sizes(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            eqs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def zeros(self, n=None):
+        return self.torch.zeros(n or self.n, dtype=self.torch.float64, device="cuda")
+
+    def apply_K(self, x):
+        y = self.torch.empty_like(x)
+        eqs_apply_K(self.ctx, x, y)
+        return y
+
+    def spmv_M(self, x):
+        y = self.torch.empty_like(x)
+        eqs_spmv_M(self.ctx, x, y)
+        return y
+
+    def vcycle(self, r):
+        z = self.torch.empty_like(r)
+        eqs_vcycle(self.ctx, r, z)
+        return z
+
+    def solve_M(self, rhs, z0=None, rtol=0.0):
+        nrhs = 1 if rhs.dim() == 1 else rhs.shape[0]
+        z = self.torch.zeros_like(rhs) if z0 is None else z0.clone()
+        iters = eqs_solve_M(self.ctx, rhs.contiguous(), z, nrhs, rtol)
+        return z, iters
+
+    def step(self, x, t, dt, s, stats=True):
+        return eqs_rkc_step(self.ctx, x, t, dt, s, stats)
+
+    def dt_bound(self, s):
+        return eqs_rkc_dt_bound(self.ctx, s)
+
+    def amg_info(self):
+        return eqs_amg_info(self.ctx)

@@ -1,0 +1,96 @@
+"""C ABI checks that need no GPU: symbols, host validation, host AMG setup
+against the oracle (aggregates bit-exact), dt bound against the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import eqs_inputs as ei
+from oracle import amg, dtbound, system
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def E():
+    from paper_1612_09447_gb300 import build, eqs
+
+    if not os.path.exists(build.LIB):
+        build.build()
+    eqs.lib()
+    return eqs
+
+
+def test_exports_every_header_symbol(E):
+    hdr = open(os.path.join(ROOT, "include", "eqs.h")).read()
+    names = set(re.findall(r"\b(eqs_[A-Za-z_0-9]+)\s*\(", hdr))
+    assert len(names) >= 17
+    L = E.lib()
+    for n in sorted(names):
+        assert hasattr(L, n), n
+
+
+def test_mesh_validation(E):
+    p = ei.make_problem(3)
+    bad = p.tets.copy()
+    bad[5, [2, 3]] = bad[5, [3, 2]]
+    with pytest.raises(E.EqsError) as ex:
+        E.eqs_mesh_create(p.xyz, bad, p.node_tag)
+    assert ex.value.status == E.EQS_ERR_MESH
+    oob = p.tets.copy()
+    oob[0, 0] = p.n_nodes
+    with pytest.raises(E.EqsError) as ex:
+        E.eqs_mesh_create(p.xyz, oob, p.node_tag)
+    assert ex.value.status == E.EQS_ERR_MESH
+    tag = p.node_tag.copy()
+    tag[0] = 3
+    with pytest.raises(E.EqsError):
+        E.eqs_mesh_create(p.xyz, p.tets, tag)
+    xyz = p.xyz.copy()
+    xyz[3, 1] = np.nan
+    with pytest.raises(E.EqsError):
+        E.eqs_mesh_create(xyz, p.tets, p.node_tag)
+    with pytest.raises(E.EqsError):
+        E.eqs_mesh_create(p.xyz, p.tets, np.ones(p.n_nodes, np.uint8))  # no free node
+    ctx = E.eqs_mesh_create(p.xyz, p.tets, p.node_tag)
+    with pytest.raises(E.EqsError) as ex:  # setup before materials
+        E.eqs_amg_setup(ctx)
+    assert ex.value.status == E.EQS_ERR_STATE
+    with pytest.raises(E.EqsError):
+        E.eqs_set_materials(ctx, np.full(p.n_tets, 2, np.uint8), p.materials)
+    E.eqs_destroy(ctx)
+
+
+def test_dt_bound_matches_oracle(E):
+    p = ei.make_problem(2)
+    ctx = E.eqs_mesh_create(p.xyz, p.tets, p.node_tag)
+    E.eqs_set_materials(ctx, p.tet_mat, p.materials)
+    for s in (2, 10, 20, 64):
+        assert E.eqs_rkc_dt_bound(ctx, s) == pytest.approx(dtbound.dt_bound(p.materials, s), rel=1e-12)
+    assert E.eqs_rkc_dt_bound(ctx, 1) < 0
+    E.eqs_destroy(ctx)
+
+
+def _host_setup(E, p):
+    ctx = E.eqs_mesh_create(p.xyz, p.tets, p.node_tag)
+    E.eqs_set_materials(ctx, p.tet_mat, p.materials)
+    try:
+        E.eqs_amg_setup(ctx)
+    except E.EqsError as e:  # no GPU here: the host hierarchy is still built
+        assert e.status == E.EQS_ERR_CUDA
+    return ctx
+
+
+@pytest.mark.parametrize("cfg,N", [(0, 12), (2, 10), (4, 16), (1, 20)])
+def test_host_amg_matches_oracle(E, cfg, N):
+    p = ei.config_problem(cfg, N=N)
+    ctx = _host_setup(E, p)
+    rows, nnz = E.eqs_amg_info(ctx)
+    H = amg.SAHierarchy(system.EQSSystem(p).Mff)
+    assert rows == [l.n for l in H.levels]
+    for l in range(len(rows) - 1):
+        agg = E.eqs_amg_aggregates(ctx, l, rows[l])
+        assert np.array_equal(agg, H.levels[l].agg)
+    assert nnz[0] == H.levels[0].A.nnz
+    E.eqs_destroy(ctx)

@@ -1,0 +1,139 @@
+"""CUDA path against the CPU oracle, through the C ABI (needs a GPU)."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import eqs_inputs as ei
+from oracle import amg, fem, pcg, rkc, system
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64, MIXED = 0, 1
+
+
+@pytest.fixture(scope="module")
+def E():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_09447_gb300 import build, eqs
+    import os
+    if not os.path.exists(build.LIB):
+        build.build()
+    return eqs
+
+
+PROBLEMS = {
+    "cube12": lambda: ei.config_problem(0),                 # 2197 nodes, block varistor
+    "jitter10": lambda: ei.config_problem(2, N=10),         # jittered, two spheres, ragged
+    "cube2": lambda: ei.make_problem(2),                    # 27 nodes: single-level AMG
+    "batch7": lambda: ei.config_problem(4, N=7, instance=3),
+}
+
+
+def _state(p, Emag=5.2e5, seed=0):
+    """A potential whose field reaches the varistor switching range."""
+    rng = np.random.default_rng(seed)
+    return -Emag * p.xyz[:, 2] + 0.3 * Emag * (0.1 / p.N) * rng.standard_normal(p.n_nodes)
+
+
+def _cuda(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _relmax(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-12), (MIXED, 2e-5)])
+def test_apply_K(E, name, prec, tol):
+    p = PROBLEMS[name]()
+    S = E.Solver(p, precision=prec)
+    for seed in (0, 1):
+        x = _state(p, seed=seed)
+        got = S.apply_K(_cuda(x)).cpu().numpy()
+        ref = fem.apply_K(p.xyz, p.tets, p.tet_mat, p.materials, x)
+        assert _relmax(got, ref) <= tol
+    S.close()
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_spmv_M(E, name):
+    p = PROBLEMS[name]()
+    S = E.Solver(p)
+    Sy = system.EQSSystem(p)
+    x = np.random.default_rng(3).standard_normal(p.n_free)
+    got = S.spmv_M(_cuda(x)).cpu().numpy()
+    assert _relmax(got, Sy.Mff @ x) <= 1e-14
+    S.close()
+
+
+@pytest.mark.parametrize("name", ["cube12", "jitter10", "cube2"])
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-4)])
+def test_vcycle(E, name, prec, tol):
+    p = PROBLEMS[name]()
+    S = E.Solver(p, precision=prec)
+    H = amg.SAHierarchy(system.EQSSystem(p).Mff)
+    r = np.random.default_rng(4).standard_normal(p.n_free)
+    got = S.vcycle(_cuda(r)).cpu().numpy()
+    assert _relmax(got, H(r)) <= tol
+    S.close()
+
+
+@pytest.mark.parametrize("name", ["cube12", "jitter10", "cube2"])
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_solve_M(E, name, prec):
+    p = PROBLEMS[name]()
+    S = E.Solver(p, precision=prec)
+    Sy = system.EQSSystem(p)
+    R = np.random.default_rng(5).standard_normal(p.n_free)
+    zd = spla.spsolve(Sy.Mff.tocsc(), R)
+    z, iters = S.solve_M(_cuda(R), rtol=1e-12)
+    z = z.cpu().numpy()
+    assert np.linalg.norm(z - zd) / np.linalg.norm(zd) <= 1e-9
+    res = np.linalg.norm(R - Sy.Mff @ z) / np.linalg.norm(R)
+    assert res <= 1e-11
+    H = amg.SAHierarchy(Sy.Mff)
+    _, it_or, _ = pcg.pcg(Sy.Mff, R, precond=H, rtol=1e-12)
+    if prec == FP64:
+        assert abs(iters[0] - it_or) <= 1
+    else:
+        assert iters[0] <= it_or + 3
+    # zero right-hand side and a perfect start vector
+    z0, it0 = S.solve_M(_cuda(np.zeros(p.n_free)), z0=_cuda(R))
+    assert it0[0] == 0 and not z0.cpu().numpy().any()
+    z1, it1 = S.solve_M(_cuda(R), z0=_cuda(zd), rtol=1e-8)
+    assert it1[0] == 0
+    S.close()
+
+
+def _oracle_run(p, s, steps, dt):
+    Sy = system.EQSSystem(p)
+    coef = rkc.RKCCoefficients(s)
+    xf, t, out = np.zeros(p.n_free), 0.0, []
+    for _ in range(steps):
+        xf, _ = rkc.rkc_step(Sy.F, t, xf, dt, coef)
+        t += dt
+        out.append(Sy.full(t, xf))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("name,s,steps", [("cube12", 10, 12), ("jitter10", 20, 4), ("batch7", 10, 6)])
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6)])
+def test_rkc_trajectory(E, name, s, steps, prec, tol):
+    p = PROBLEMS[name]()
+    S = E.Solver(p, precision=prec, rtol=1e-13)
+    dt = S.dt_bound(s)
+    ref = _oracle_run(p, s, steps, dt)
+    x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+    got, t = [], 0.0
+    for _ in range(steps):
+        st = S.step(x, t, dt, s)
+        assert st.status == 0 and st.max_relres <= 1e-13
+        t += dt
+        got.append(x.cpu().numpy())
+    got = np.array(got)
+    err = np.linalg.norm(got - ref, axis=1).max() / np.linalg.norm(ref, axis=1).max()
+    assert err <= tol, err
+    S.close()
