@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark of the explicit RKC EQS solver on GB300.
+
+Metric: RKC DOF-stages/s (free unknowns x stages x steps / second) with
+every stage M-solve at ||R - M z|| / ||R|| <= 1e-8, on the 64^3-cell
+Kuhn cube (274,625 nodes, 266,175 free, 1.57 M tets, block varistor,
+s = 20 stages, dt at the RKC stability bound).  The timed form is the
+mixed-precision path; the plain FP64 AMG-PCG form is measured beside it.
+
+A "step" is one RKC step (20 stages: element kernel, right-hand side, AMG-PCG
+solve, recurrence) through the C ABI.  L2 is flushed (256 MiB write) between
+timed steps, outside the timed intervals.  Multi-GPU runs are independent
+replicas (one instance per GPU, no collective on the data path).
+
+--impl reference times the CPU oracle on a bounded sample of the same
+workload (first stages of an RKC step) with the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RKC DOF-stages/s and M-solve ms/RHS vs plain FP64 AMG-PCG at 1e-8 residual"
+WORKLOAD = "cube64_block: 64^3-cell Kuhn cube, 274625 nodes (266175 free), 1572864 P1 tets, " \
+           "block varistor, s=20, dt=beta_s/rho, rtol=1e-8"
+RTOL = 1e-8
+S_STAGES = 20
+CONFIG_INDEX = 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--N", type=int, default=None, help="override mesh size (testing)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ oracle
+ORACLE_SNIPPET = r"""
+import json, os, sys
+sys.path.insert(0, {root!r})
+import eqs_inputs as ei
+from oracle import run
+p = ei.config_problem({cfg}, N={N})
+r = run.time_stage_sample(p, {s}, {n_stages}, rtol={rtol})
+print(json.dumps(r))
+"""
+
+
+def oracle_sample(n_stages, N=None):
+    """Run the oracle in a fresh single-threaded process (spawned, no CUDA)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SNIPPET.format(root=ROOT, cfg=CONFIG_INDEX, N=N, s=S_STAGES, n_stages=n_stages,
+                                 rtol=RTOL)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    n_stages = 2
+    t_total, dof = 0.0, 0
+    for k in range(args.warmup + args.steps):
+        r = oracle_sample(n_stages, args.N)
+        if k >= args.warmup:
+            t_total += r["seconds"]
+            dof += r["n_free"] * r["stages"]
+    value = dof / t_total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-stages/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"first {n_stages} stages of an RKC step per step"},
+        "cpu_baseline": {"value": value, "unit": "DOF-stages/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n_stages} stage evaluations per step, oracle numpy/scipy "
+                                   f"FP64 AMG-PCG, single thread"},
+        "e2e": {"value": value, "unit": "DOF-stages/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(dev_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def time_steps(torch, solver, x, t, dt, steps, flush, stream_sync=True):
+    times, launches, iters = [], 0, []
+    for _ in range(steps):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        solver.step(x, t, dt, S_STAGES, stats=False)
+        e1.record()
+        st = solver.last_stats()  # synchronises; outside the timed interval
+        times.append(e0.elapsed_time(e1))
+        launches += st.launches
+        iters.append(st.total_iters / S_STAGES)
+        t += dt
+    return times, launches, iters, t
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import eqs_inputs as ei
+    from paper_1612_09447_gb300 import eqs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    eqs.lib()
+    p = ei.config_problem(CONFIG_INDEX, N=args.N)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    flushbuf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def flush():
+        flushbuf.zero_()
+
+    def measure(precision, steps, warmup):
+        solver = eqs.Solver(p, precision=precision, rtol=RTOL)
+        dt = solver.dt_bound(S_STAGES)
+        x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+        t = 0.0
+        for _ in range(warmup):
+            solver.step(x, t, dt, S_STAGES)
+            t += dt
+        barrier()
+        clk = ClockSampler(local)
+        times, launches, iters, t = time_steps(torch, solver, x, t, dt, steps, flush)
+        barrier()
+        clocks = clk.stop()
+        return solver, x, t, dt, times, launches, iters, clocks
+
+    solver, x, t, dt, times, launches, iters, clocks = measure(eqs.EQS_PREC_MIXED, args.steps,
+                                                               args.warmup)
+    total_ms = sum(times)
+    if dist is not None:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    units = world * p.n_free * S_STAGES * args.steps
+    value = units / (total_ms / 1e3)
+
+    # end to end through the public API: pinned host x in, step, x back to host
+    xh = torch.zeros(p.n_nodes, dtype=torch.float64).pin_memory()
+    xh.copy_(x.cpu())
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        flush()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t_host = time.perf_counter()
+        e0.record()
+        x.copy_(xh, non_blocking=True)
+        solver.step(x, t, dt, S_STAGES, stats=False)
+        xh.copy_(x, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        e2e_ms += max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_host))
+        t += dt
+    if dist is not None:
+        tt = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = units / (e2e_ms / 1e3)
+
+    # dominant kernel, timed alone with L2 flushed between launches
+    roof = dominant_kernel_roofline(torch, eqs, solver, p, flush)
+
+    # plain FP64 AMG-PCG form of the same workload
+    fp64 = None
+    if not args.no_fp64:
+        s64, _, _, _, t64, _, it64, _ = measure(eqs.EQS_PREC_FP64, max(3, args.steps // 4), 2)
+        fp64 = {"value": p.n_free * S_STAGES * len(t64) / (sum(t64) / 1e3),
+                "ms_per_step": sum(t64) / len(t64), "cg_iters_per_solve": float(np.mean(it64))}
+        s64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample(4, args.N)
+        cpu = {"value": r["dof_stages_per_s"], "unit": "DOF-stages/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {r['stages']} stage evaluations of one RKC step "
+                         f"({r['seconds']:.1f} s, numpy/scipy FP64 AMG-PCG, single thread)"}
+    if rank != 0:
+        solver.close()
+        return
+    ms_step = total_ms / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF-stages/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/f64 mixed", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_free": p.n_free, "stages": S_STAGES, "rtol": RTOL,
+                   "precision": "mixed (FP32 element kernel and V-cycle; FP64 CG, recurrence)",
+                   "m_solve_ms_per_rhs": ms_step / S_STAGES,
+                   "cg_iters_per_solve": float(np.mean(iters)),
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "fp64_plain": fp64,
+        "e2e": {"value": e2e_value, "unit": "DOF-stages/s", "h2d_bytes_per_step": p.n_nodes * 8,
+                "d2h_bytes_per_step": p.n_nodes * 8},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def dominant_kernel_roofline(torch, eqs, solver, p, flush):
+    """FP64 M SpMV (the CG operator, the SpMV of every CG iteration) timed
+    alone: algorithmic bytes = stored SELL values/indices + x gather + y."""
+    nf = p.n_free
+    rows, nnz = solver.amg_info()
+    x = torch.randn(nf, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    ts = []
+    for _ in range(20):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        eqs.eqs_spmv_M(solver.ctx, x, y)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts[3:])
+    bytes_alg = nnz[0] * 12 + nf * 8 * 2 + (nf // 32 + 1) * 8
+    peak, kind = _peaks()
+    ach = bytes_alg / (ms / 1e3) / 1e9
+    return {"kernel": "k_spmv64 (FP64 SELL-32 M_ff SpMV)", "bound": "hbm", "achieved": ach,
+            "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+            "bytes_per_launch": bytes_alg, "ms_per_launch": ms,
+            "peak_kind": f"{kind} hbm_gbs (burst: kernel timed alone, L2 flushed)"}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

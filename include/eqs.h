@@ -95,6 +95,9 @@ typedef struct {
   int iters[EQS_MAX_STAGES];    /* CG iterations of solve j = 0..s-1          */
   double max_relres;            /* largest final ||r||/||R|| of the s solves  */
   int status;                   /* EQS_OK or EQS_ERR_NOCONV                   */
+  int64_t launches;             /* kernels the step launched (graph kernel
+                                   nodes outside loops + loop-body kernel
+                                   nodes x CG iterations)                    */
 } eqs_step_stats;
 
 /* Fill *o with the defaults (precision FP64, theta 0.08, coarse_max 500,
@@ -161,6 +164,9 @@ eqs_status eqs_spmv_M(eqs_ctx* ctx, const double* x, double* y);
  * synchronises and returns EQS_ERR_NOCONV if a solve did not converge. */
 eqs_status eqs_rkc_step(eqs_ctx* ctx, double* x, double t, double dt, int s,
                         eqs_step_stats* stats);
+
+/* Statistics of the last eqs_rkc_step on ctx (synchronises the stream). */
+eqs_status eqs_get_step_stats(eqs_ctx* ctx, eqs_step_stats* stats);
 
 /* Largest stable step for s stages: beta_s / rho with the a-priori bound
  * rho = max over materials and E of max(kappa, d(kappa E)/dE) / eps of the

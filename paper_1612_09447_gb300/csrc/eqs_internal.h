@@ -22,13 +22,24 @@ struct HostCSR {
   int64_t nnz() const { return ptr.empty() ? 0 : ptr.back(); }
 };
 
-// --------------------------------------------------- device SELL-32 matrix
-// Rows are grouped in slices of 32; slice s stores width[s] columns, element
-// k of row 32 s + lane at slice_ptr[s] + 32 k + lane (coalesced per warp).
-// Padding entries have value 0 and a valid column index.
+// ------------------------------------------------------- device matrix
+// Two layouts, chosen by the mean row length:
+//  G == 1 (short rows): SELL-32.  Rows are grouped in slices of 32; slice s
+//    stores width[s] columns, element k of row 32 s + lane at
+//    ptr[s] + 32 k + lane (coalesced per warp, one thread per row).
+//    Padding entries have value 0 and a valid column index.
+//  G  > 1 (long rows): CSR with a group of G lanes per row (ptr = row
+//    pointer); the group strides over the row and reduces with shuffles.
+//  G == 0 (few diagonals): DIA.  Value of diagonal d, row i at
+//    val[d * n_rows + i], column i + off[d] (zero where out of range);
+//    reads of val and x are coalesced and no index is loaded.
+constexpr int kMaxDiag = 32;
 template <typename T>
 struct DevSell {
   int n_rows = 0, n_cols = 0, n_slices = 0;
+  int G = 1, logG = 0;
+  int ndiag = 0;
+  int off[kMaxDiag] = {};
   int64_t stored = 0, nnz = 0;
   int64_t* slice_ptr = nullptr;
   int32_t* col = nullptr;
@@ -83,6 +94,9 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   double* d_cj = nullptr;  // stage abscissae c_0..c_s of this graph
+  int64_t fixed_kernels = 0;     // kernel nodes outside the CG loops
+  int64_t per_iter_kernels = 0;  // kernel nodes of one CG loop body
+  int s = 0;
 };
 
 }  // namespace eqs
@@ -157,6 +171,8 @@ struct eqs_ctx {
   eqs::ReduceScratch red;
 
   std::map<std::pair<int, uintptr_t>, eqs::GraphEntry> step_graphs;  // key: (s, x)
+  const eqs::GraphEntry* last_step = nullptr;                       // graph of the last step
+  int64_t body_kernels = 0;  // kernel nodes of the last captured CG loop body
   std::map<double, eqs::GraphEntry> solve_graphs;                   // key: rtol
 };
 

@@ -16,22 +16,72 @@ constexpr int kBlock = 256;
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
 
-// (A x)_row for a SELL-32 matrix; accumulation in T.
+// (A x)_row, accumulation in T.  Thread `tid` serves row tid >> A.logG; with
+// G > 1 every lane of the row's group returns the full sum (all lanes of a
+// warp must call this, also those past the last row).
 template <typename T>
-__device__ __forceinline__ T sell_row(const DevSell<T>& A, int row, const T* __restrict__ x) {
-  const int s = row >> 5, lane = row & 31;
-  const int64_t beg = A.slice_ptr[s] + lane, end = A.slice_ptr[s + 1];
+__device__ __forceinline__ T mat_row(const DevSell<T>& A, int64_t tid, int n, const T* __restrict__ x) {
+  const int row = (int)(tid >> A.logG);
   T acc = T(0);
-#pragma unroll 4
-  for (int64_t k = beg; k < end; k += 32) acc = fmadd(A.val[k], __ldg(x + A.col[k]), acc);
+  if (A.G == 0) {  // DIA: independent, coalesced loads
+    if (row >= n) return acc;
+    const T* __restrict__ v = A.val + row;
+#pragma unroll 8
+    for (int d = 0; d < A.ndiag; ++d) {
+      const int j = row + A.off[d];
+      const T a = __ldg(v + (int64_t)d * n);
+      if ((unsigned)j < (unsigned)A.n_cols) acc = fmadd(a, __ldg(x + j), acc);
+    }
+    return acc;
+  }
+  if (A.G == 1) {  // SELL-32: load a batch of indices, then the gathers
+    if (row >= n) return acc;
+    const int s = row >> 5, lane = row & 31;
+    int64_t k = A.slice_ptr[s] + lane;
+    const int64_t end = A.slice_ptr[s + 1];
+    for (; k < end; k += 32 * 8) {
+      int c[8];
+      T a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t kk = k + 32 * u;
+        c[u] = kk < end ? __ldg(A.col + kk) : 0;
+        a[u] = kk < end ? __ldg(A.val + kk) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc = fmadd(a[u], __ldg(x + c[u]), acc);
+    }
+    return acc;
+  }
+  const int g = (int)(tid & (A.G - 1));
+  int64_t k = 0, end = 0;
+  if (row < n) {
+    k = A.slice_ptr[row] + g;
+    end = A.slice_ptr[row + 1];
+  }
+  for (; k < end; k += (int64_t)A.G * 4) {
+    int c[4];
+    T a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t kk = k + (int64_t)A.G * u;
+      c[u] = kk < end ? __ldg(A.col + kk) : 0;
+      a[u] = kk < end ? __ldg(A.val + kk) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc = fmadd(a[u], __ldg(x + c[u]), acc);
+  }
+  for (int o = A.G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   return acc;
 }
 
-// (A x)_row with a T matrix applied to an FP64 vector, FP64 accumulation.
-__device__ __forceinline__ double sell_row_d(const DevSell<double>& A, int row,
-                                             const double* __restrict__ x) {
-  return sell_row<double>(A, row, x);
+// True for the one thread that writes row `row` (lane 0 of its group).
+template <typename T>
+__device__ __forceinline__ bool row_leader(const DevSell<T>& A, int64_t tid, int n) {
+  return (int)(tid >> A.logG) < n && (A.G <= 1 || (tid & (A.G - 1)) == 0);
 }
+
+__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 
 // ------------------------------------------------------------ V-cycle pieces
 // One Chebyshev step:  r_out = r_in - A d_in ;  d_out = c1 d_in + c2 D^-1 r_out ;
@@ -40,10 +90,12 @@ template <typename T>
 __global__ void k_cheb_step(DevSell<T> A, int n, const T* r_in,
                             const T* __restrict__ d_in, const T* __restrict__ dinv, T c1, T c2,
                             T* r_out, T* __restrict__ d_out, T* __restrict__ x, int add_pending) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t tid = gtid();
+  const T ad = mat_row(A, tid, n, d_in);
+  if (!row_leader(A, tid, n)) return;
+  const int i = (int)(tid >> A.logG);
   const T di = d_in[i];
-  const T r = r_in[i] - sell_row(A, i, d_in);
+  const T r = r_in[i] - ad;
   const T dn = c1 * di + c2 * dinv[i] * r;
   r_out[i] = r;
   d_out[i] = dn;
@@ -53,18 +105,22 @@ __global__ void k_cheb_step(DevSell<T> A, int n, const T* r_in,
 // r -= A d  (in place; r is row-local)
 template <typename T>
 __global__ void k_resid_update(DevSell<T> A, int n, T* r, const T* __restrict__ d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  r[i] = r[i] - sell_row(A, i, d);
+  const int64_t tid = gtid();
+  const T ad = mat_row(A, tid, n, d);
+  if (!row_leader(A, tid, n)) return;
+  const int i = (int)(tid >> A.logG);
+  r[i] = r[i] - ad;
 }
 
 // out = b - A x
 template <typename T>
 __global__ void k_resid(DevSell<T> A, int n, const T* __restrict__ b, const T* __restrict__ x,
                         T* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  out[i] = b[i] - sell_row(A, i, x);
+  const int64_t tid = gtid();
+  const T ax = mat_row(A, tid, n, x);
+  if (!row_leader(A, tid, n)) return;
+  const int i = (int)(tid >> A.logG);
+  out[i] = b[i] - ax;
 }
 
 // b_c = R r_f ; when first_step: x_c = d_c = D_c^-1 b_c / theta_c (the first
@@ -73,9 +129,10 @@ template <typename T>
 __global__ void k_restrict(DevSell<T> R, int nc, const T* __restrict__ rf, T* __restrict__ bc,
                            const T* __restrict__ dinv_c, T inv_theta_c, T* __restrict__ xc,
                            T* __restrict__ dc, int first_step) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nc) return;
-  const T b = sell_row(R, i, rf);
+  const int64_t tid = gtid();
+  const T b = mat_row(R, tid, nc, rf);
+  if (!row_leader(R, tid, nc)) return;
+  const int i = (int)(tid >> R.logG);
   bc[i] = b;
   if (first_step) {
     const T d = dinv_c[i] * b * inv_theta_c;
@@ -87,9 +144,10 @@ __global__ void k_restrict(DevSell<T> R, int nc, const T* __restrict__ rf, T* __
 // x_f += P x_c
 template <typename T>
 __global__ void k_prolong(DevSell<T> P, int nf, const T* __restrict__ xc, T* __restrict__ xf) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nf) return;
-  xf[i] += sell_row(P, i, xc);
+  const int64_t tid = gtid();
+  const T px = mat_row(P, tid, nf, xc);
+  if (!row_leader(P, tid, nf)) return;
+  xf[tid >> P.logG] += px;
 }
 
 // First post-smoothing step from the current x: r = b - A x ; d = D^-1 r / theta.
@@ -98,9 +156,11 @@ template <typename T>
 __global__ void k_post_first(DevSell<T> A, int n, const T* __restrict__ b,
                              const T* __restrict__ x, const T* __restrict__ dinv, T inv_theta,
                              T* __restrict__ r_out, T* __restrict__ d_out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const T r = b[i] - sell_row(A, i, x);
+  const int64_t tid = gtid();
+  const T ax = mat_row(A, tid, n, x);
+  if (!row_leader(A, tid, n)) return;
+  const int i = (int)(tid >> A.logG);
+  const T r = b[i] - ax;
   r_out[i] = r;
   d_out[i] = dinv[i] * r * inv_theta;
 }
@@ -197,7 +257,7 @@ __global__ void k_pcg_init(DevSell<double> M, int n, const double* __restrict__ 
   double v[2] = {0.0, 0.0};
   if (i < n) {
     const double Ri = R[i];
-    const double ri = Ri - sell_row_d(M, i, x);
+    const double ri = Ri - mat_row<double>(M, i, n, x);
     r[i] = ri;
     const T bi = (T)ri;
     b0[i] = bi;
@@ -266,7 +326,7 @@ __global__ void k_pcg_q(DevSell<double> M, int n, const double* __restrict__ p,
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double v[1] = {0.0};
   if (i < n) {
-    const double qi = sell_row_d(M, i, p);
+    const double qi = mat_row<double>(M, i, n, p);
     q[i] = qi;
     v[0] = p[i] * qi;
   }
@@ -567,7 +627,8 @@ __global__ void k_first_step(int n, const T* __restrict__ b, const T* __restrict
 
 __global__ void k_spmv64(DevSell<double> A, int n, const double* __restrict__ x, double* __restrict__ y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = sell_row_d(A, i, x);
+  const double v = mat_row<double>(A, i, n, x);
+  if (i < n) y[i] = v;
 }
 
 }  // namespace eqs

@@ -7,6 +7,7 @@
 // step.  Graphs are cached per (stages, output pointer).
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -58,12 +59,64 @@ static cudaError_t upload(eqs_ctx* c, T** p, const T* h, size_t n) {
   return cudaMemcpy(*p, h, n * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+// Lanes per row for a mean row length: 1 selects SELL-32 (thread per row).
+static int lanes_for(double mean_row) {
+  if (mean_row <= 16.0) return 1;
+  if (mean_row <= 40.0) return 4;
+  if (mean_row <= 80.0) return 8;
+  if (mean_row <= 160.0) return 16;
+  return 32;
+}
+
 template <typename T>
-static cudaError_t upload_sell(eqs_ctx* c, const HostCSR& A, DevSell<T>& S) {
+static cudaError_t upload_sell(eqs_ctx* c, const HostCSR& A, DevSell<T>& S, bool allow_groups = true) {
   S.n_rows = (int)A.n_rows;
   S.n_cols = (int)A.n_cols;
   S.n_slices = (int)((A.n_rows + 31) / 32);
   S.nnz = A.nnz();
+  // DIA when the non-zeros lie on few diagonals with little padding
+  {
+    std::map<int64_t, int64_t> diag;
+    bool ok = A.n_rows == A.n_cols && A.n_rows > 0;
+    for (int64_t i = 0; ok && i < A.n_rows; ++i)
+      for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+        diag[(int64_t)A.col[k] - i]++;
+        if ((int)diag.size() > kMaxDiag) {
+          ok = false;
+          break;
+        }
+      }
+    if (ok && (double)A.nnz() >= 0.6 * (double)A.n_rows * (double)diag.size()) {
+      S.G = 0;
+      S.logG = 0;
+      S.ndiag = (int)diag.size();
+      int d = 0;
+      std::map<int64_t, int> slot;
+      for (auto& kv : diag) {
+        S.off[d] = (int)kv.first;
+        slot[kv.first] = d++;
+      }
+      const int64_t n = A.n_rows;
+      std::vector<T> val((size_t)n * S.ndiag, T(0));
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+          val[(size_t)slot[(int64_t)A.col[k] - i] * n + i] = (T)A.val[k];
+      S.stored = (int64_t)val.size();
+      return upload(c, &S.val, val.data(), val.size());
+    }
+  }
+  S.G = allow_groups ? lanes_for(A.n_rows ? (double)A.nnz() / (double)A.n_rows : 0.0) : 1;
+  S.logG = 0;
+  while ((1 << S.logG) < S.G) ++S.logG;
+  if (S.G > 1) {  // CSR, G lanes per row
+    std::vector<T> val(A.nnz());
+    for (int64_t k = 0; k < A.nnz(); ++k) val[k] = (T)A.val[k];
+    S.stored = A.nnz();
+    cudaError_t e = upload(c, &S.slice_ptr, A.ptr.data(), A.ptr.size());
+    if (e == cudaSuccess) e = upload(c, &S.col, A.col.data(), std::max<size_t>(A.col.size(), 1));
+    if (e == cudaSuccess) e = upload(c, &S.val, val.data(), std::max<size_t>(val.size(), 1));
+    return e;
+  }
   std::vector<int64_t> sp(S.n_slices + 1, 0);
   for (int s = 0; s < S.n_slices; ++s) {
     int64_t w = 0;
@@ -74,8 +127,8 @@ static cudaError_t upload_sell(eqs_ctx* c, const HostCSR& A, DevSell<T>& S) {
     sp[s + 1] = sp[s] + 32 * w;
   }
   S.stored = sp[S.n_slices];
-  std::vector<int32_t> col(S.stored, 0);
-  std::vector<T> val(S.stored, T(0));
+  std::vector<int32_t> col(std::max<int64_t>(S.stored, 1), 0);
+  std::vector<T> val(std::max<int64_t>(S.stored, 1), T(0));
   for (int s = 0; s < S.n_slices; ++s) {
     const int64_t w = (sp[s + 1] - sp[s]) / 32;
     for (int l = 0; l < 32; ++l) {
@@ -176,7 +229,7 @@ static void vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStr
   const int deg = c->opts.cheb_degree;
   std::vector<double> c1, c2;
   cheb_coeffs(V.sigma, V.delta, deg, c1, c2);
-  const int g = nblk(V.n);
+  const int g = nblk((int64_t)V.n * std::max(V.A.G, 1));
   // pre-smoothing: x = d = D^-1 b / theta was set by the producer of b
   T* din = V.dA;
   T* dout = V.dB;
@@ -193,10 +246,10 @@ static void vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStr
     k_resid<T><<<g, kBlock, 0, st>>>(V.A, V.n, V.b, V.x, V.r);
   DevLevel<T>& C = L[l + 1];
   const int first = (l + 1 < nl - 1) ? 1 : 0;
-  k_restrict<T><<<nblk(C.n), kBlock, 0, st>>>(V.R, C.n, V.r, C.b, C.dinv, (T)C.inv_theta, C.x, C.dA,
+  k_restrict<T><<<nblk((int64_t)C.n * std::max(V.R.G, 1)), kBlock, 0, st>>>(V.R, C.n, V.r, C.b, C.dinv, (T)C.inv_theta, C.x, C.dA,
                                                first);
   vcycle_level(c, L, l + 1, st);
-  k_prolong<T><<<g, kBlock, 0, st>>>(V.P, V.n, C.x, V.x);
+  k_prolong<T><<<nblk((int64_t)V.n * std::max(V.P.G, 1)), kBlock, 0, st>>>(V.P, V.n, C.x, V.x);
   k_post_first<T><<<g, kBlock, 0, st>>>(V.A, V.n, V.b, V.x, V.dinv, (T)V.inv_theta, V.r, V.dA);
   din = V.dA;
   dout = V.dB;
@@ -205,7 +258,7 @@ static void vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStr
                                          V.x, k == 2 ? 1 : 0);
     std::swap(din, dout);
   }
-  if (deg == 1) k_axpy1<T><<<g, kBlock, 0, st>>>(V.n, V.x, V.dA);
+  if (deg == 1) k_axpy1<T><<<nblk(V.n), kBlock, 0, st>>>(V.n, V.x, V.dA);
 }
 
 // ------------------------------------------------------------- PCG
@@ -247,6 +300,21 @@ static void pcg_body_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_
                                         use_handle, sl.iters, sl.relres);
 }
 
+// Kernel nodes at the top level of graph g (loop bodies are not entered).
+static int64_t count_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return -1;
+  int64_t k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess) return -1;
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
 // Append "init; while (not converged) body" to the graph being captured on
 // c->cap_stream; the loop body is captured on c->cap_stream2.
 template <typename T>
@@ -276,6 +344,7 @@ static eqs_status pcg_capture(eqs_ctx* c, std::vector<DevLevel<T>>& L, const dou
   cudaGraph_t body_out = nullptr;
   CK(cudaStreamEndCapture(c->cap_stream2, &body_out));
   CK(le);
+  c->body_kernels = count_kernel_nodes(body_out);
   CK(cudaStreamUpdateCaptureDependencies(c->cap_stream, &node, nullptr, 1,
                                          cudaStreamSetCaptureDependencies));
   return EQS_OK;
@@ -348,6 +417,9 @@ static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
   CK(le);
   CK(ee);
   ge.graph = graph;
+  ge.s = s;
+  ge.fixed_kernels = count_kernel_nodes(graph);
+  ge.per_iter_kernels = c->body_kernels;
   CK(cudaGraphInstantiate(&ge.exec, graph, 0));
   return EQS_OK;
 }
@@ -378,6 +450,7 @@ static void destroy_graph(GraphEntry& g) {
 }
 
 static void destroy_graphs(eqs_ctx* c) {
+  c->last_step = nullptr;
   for (auto& kv : c->step_graphs) destroy_graph(kv.second);
   c->step_graphs.clear();
   for (auto& kv : c->solve_graphs) destroy_graph(kv.second);
@@ -553,7 +626,7 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
   CK(upload(c, &c->d_node_of_internal, c->node_of_internal.data(), c->node_of_internal.size()));
   CK(upload(c, &c->d_dir_scale, dir_scale.data(), dir_scale.size()));
   CK(upload(c, &c->d_mtop, mtop.data(), mtop.size()));
-  CK(upload_sell(c, Mff, c->M64));
+  CK(upload_sell(c, Mff, c->M64, false));  // CG kernels use one thread per row (DIA or SELL)
   CK(upload(c, &c->d_coarse_inv, inv.data(), inv.size()));
   c->lev64.clear();
   c->lev32.clear();
@@ -677,7 +750,16 @@ eqs_status eqs_rkc_step(eqs_ctx* c, double* x, double t, double dt, int s, eqs_s
   StepParams prm{t, dt};
   CK(cudaMemcpyAsync(c->d_params, &prm, sizeof(prm), cudaMemcpyHostToDevice, c->stream));
   CK(cudaGraphLaunch(it->second.exec, c->stream));
+  c->last_step = &it->second;
   if (!stats) return EQS_OK;
+  return eqs_get_step_stats(c, stats);
+}
+
+eqs_status eqs_get_step_stats(eqs_ctx* c, eqs_step_stats* stats) {
+  REQUIRE_SETUP(c);
+  if (!stats) return fail(c, EQS_ERR_ARG, "stats is NULL");
+  if (!c->last_step) return fail(c, EQS_ERR_STATE, "no step has run");
+  const int s = c->last_step->s;
   int iters[EQS_MAX_STAGES];
   double rr[EQS_MAX_STAGES];
   CK(cudaMemcpyAsync(iters, c->d_iters, s * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -694,6 +776,7 @@ eqs_status eqs_rkc_step(eqs_ctx* c, double* x, double t, double dt, int s, eqs_s
     if (!std::isfinite(rr[j])) res = EQS_ERR_NAN;
     else if (rr[j] > c->opts.rtol && res == EQS_OK) res = EQS_ERR_NOCONV;
   }
+  stats->launches = c->last_step->fixed_kernels + c->last_step->per_iter_kernels * stats->total_iters;
   stats->status = res;
   if (res == EQS_ERR_NOCONV) return fail(c, res, "a stage solve reached max_iter");
   if (res == EQS_ERR_NAN) return fail(c, res, "non-finite residual in a stage solve");

@@ -43,7 +43,7 @@ class eqs_opts(C.Structure):
 class eqs_step_stats(C.Structure):
     _fields_ = [("s", C.c_int), ("total_iters", C.c_int), ("max_iters", C.c_int),
                 ("iters", C.c_int * EQS_MAX_STAGES), ("max_relres", C.c_double),
-                ("status", C.c_int)]
+                ("status", C.c_int), ("launches", C.c_int64)]
 
 
 _lib = None
@@ -74,6 +74,7 @@ def _declare(L):
         "eqs_spmv_M": (I, [P, P, P]),
         "eqs_rkc_step": (I, [P, P, D, D, I, C.POINTER(eqs_step_stats)]),
         "eqs_rkc_dt_bound": (D, [P, I]),
+        "eqs_get_step_stats": (I, [P, C.POINTER(eqs_step_stats)]),
         "eqs_set_stream": (I, [P, P]),
         "eqs_get_sizes": (I, [P, P, P, P]),
         "eqs_amg_info": (I, [P, P, P, P]),
@@ -161,6 +162,12 @@ def eqs_spmv_M(ctx, x, y):
 def eqs_rkc_step(ctx, x, t, dt, s, want_stats=True):
     st = eqs_step_stats() if want_stats else None
     _check(lib().eqs_rkc_step(ctx, _dev(x), t, dt, s, C.byref(st) if st is not None else None), ctx)
+    return st
+
+
+def eqs_get_step_stats(ctx):
+    st = eqs_step_stats()
+    _check(lib().eqs_get_step_stats(ctx, C.byref(st)), ctx)
     return st
 
 
@@ -262,6 +269,9 @@ class Solver:
 
     def step(self, x, t, dt, s, stats=True):
         return eqs_rkc_step(self.ctx, x, t, dt, s, stats)
+
+    def last_stats(self):
+        return eqs_get_step_stats(self.ctx)
 
     def dt_bound(self, s):
         return eqs_rkc_dt_bound(self.ctx, s)
