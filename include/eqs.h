@@ -45,7 +45,7 @@ typedef enum {
   EQS_ERR_MESH = -2,    /* inverted/degenerate tet, bad index, bad tag       */
   EQS_ERR_CUDA = -3,    /* a CUDA runtime call failed                        */
   EQS_ERR_NOCONV = -4,  /* CG reached max_iter before the tolerance          */
-  EQS_ERR_TIMEOUT = -5, /* a bounded device wait gave up                     */
+  EQS_ERR_TIMEOUT = -5, /* a bounded device wait (grid barrier) gave up       */
   EQS_ERR_NAN = -6,     /* non-finite value in an input or residual          */
   EQS_ERR_STATE = -7    /* call order violated                               */
 } eqs_status;
@@ -82,7 +82,11 @@ typedef struct {
   double rtol;         /* M-solve stopping test ||R - M z||/||R|| <= rtol    */
   int max_iter;        /* CG iteration limit per solve                       */
   int guess;           /* eqs_guess_mode                                     */
-  int flexible;        /* 1: Polak-Ribiere CG (default for MIXED)            */
+  int flexible;        /* 1: Polak-Ribiere CG                                */
+  int persistent;      /* 1: each M-solve is one cooperative persistent
+                          kernel (grid barriers); 0: one kernel per CG/V-cycle
+                          phase inside a device-side graph loop               */
+  int blocks_per_sm;   /* CTAs per SM of the persistent solve (0: 1)         */
 } eqs_opts;
 
 #define EQS_MAX_STAGES 64
@@ -101,7 +105,8 @@ typedef struct {
 } eqs_step_stats;
 
 /* Fill *o with the defaults (precision FP64, theta 0.08, coarse_max 500,
- * max_levels 10, degree 2, alpha 30, rtol 1e-8, max_iter 500, GUESS_PREV). */
+ * max_levels 10, degree 2, alpha 30, rtol 1e-8, max_iter 500, GUESS_PREV,
+ * flexible 1, persistent 1, blocks_per_sm 1). */
 void eqs_opts_default(eqs_opts* o);
 
 /* Create a context from a tetrahedral mesh (Eq. 2 discretisation input).

@@ -71,7 +71,7 @@ struct HostLevel {
 // Per-solve reduction scalars (device).
 struct PcgScalars {
   double bnorm2, rnorm2, rz, rz_old, zr_prev, pq, alpha, beta;
-  int it, conv, pad0, pad1;
+  int it, conv, parity, pad1;  // parity: which search-direction buffer is current
 };
 
 struct StepParams {  // device-resident per-call parameters
@@ -108,6 +108,7 @@ struct eqs_ctx {
   cudaStream_t cap_stream = nullptr;  // capture of step / solve graphs
   cudaStream_t cap_stream2 = nullptr; // capture of while-loop bodies
   int device = 0;
+  int sms = 0;                        // SM count of the device
   std::vector<void*> allocs;          // every device allocation of the context
 
   // ---- mesh (host copies)
@@ -159,6 +160,11 @@ struct eqs_ctx {
   double* d_q = nullptr;
   double* d_sol = nullptr;           // solve_M work solution
   double* d_zd = nullptr;            // preconditioned residual in FP64
+  double* d_p2 = nullptr;            // second search-direction buffer (persistent solve)
+  void* d_plan = nullptr;            // device PPlan<T> of the persistent solve
+  void* d_bar = nullptr;             // grid barrier state
+  double* d_ppartials = nullptr;     // 8 slots x persistent grid
+  int pblocks = 0;                   // CTAs of the persistent solve
   double* d_tmpn = nullptr;          // n_nodes scratch (apply_K)
   double* d_tmpn2 = nullptr;
   eqs::PcgScalars* d_sc = nullptr;

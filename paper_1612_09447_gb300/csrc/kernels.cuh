@@ -13,6 +13,14 @@ namespace eqs {
 
 constexpr int kBlock = 256;
 
+// Programmatic dependent launch: wait until the preceding kernel of the
+// stream has completed (its writes visible), then allow the next kernel to
+// start launching.  A no-op for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
+}
+
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
 
@@ -75,6 +83,31 @@ __device__ __forceinline__ T mat_row(const DevSell<T>& A, int64_t tid, int n, co
   return acc;
 }
 
+// (A (x1 + beta x2))_row for a one-thread-per-row matrix (DIA or SELL-32).
+__device__ __forceinline__ double mat_row_axpy(const DevSell<double>& A, int row, int n,
+                                               const double* __restrict__ x1,
+                                               const double* __restrict__ x2, double beta) {
+  double acc = 0.0;
+  if (row >= n) return acc;
+  if (A.G == 0) {
+    const double* __restrict__ v = A.val + row;
+#pragma unroll 8
+    for (int d = 0; d < A.ndiag; ++d) {
+      const int j = row + A.off[d];
+      const double a = __ldg(v + (int64_t)d * n);
+      if ((unsigned)j < (unsigned)A.n_cols) acc = fma(a, fma(beta, __ldg(x2 + j), __ldg(x1 + j)), acc);
+    }
+    return acc;
+  }
+  const int s = row >> 5, lane = row & 31;
+  const int64_t end = A.slice_ptr[s + 1];
+  for (int64_t k = A.slice_ptr[s] + lane; k < end; k += 32) {
+    const int c = __ldg(A.col + k);
+    acc = fma(__ldg(A.val + k), fma(beta, __ldg(x2 + c), __ldg(x1 + c)), acc);
+  }
+  return acc;
+}
+
 // True for the one thread that writes row `row` (lane 0 of its group).
 template <typename T>
 __device__ __forceinline__ bool row_leader(const DevSell<T>& A, int64_t tid, int n) {
@@ -84,98 +117,142 @@ __device__ __forceinline__ bool row_leader(const DevSell<T>& A, int64_t tid, int
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 
 // ------------------------------------------------------------ V-cycle pieces
+// Row kernels use resident-sized grids: a grid-stride loop in which every
+// thread keeps two rows (t and t + stride) in flight, loading both before
+// any store.  Loop bounds are multiples of 32, so warps stay converged for
+// the G-lane shuffles.
+#define EQS_ROWS2(A_, n_, BODY2)                                              \
+  const int64_t lim_ = round32((int64_t)(n_) << (A_).logG);                   \
+  const int64_t st_ = (int64_t)gridDim.x * blockDim.x;                        \
+  for (int64_t t0 = gtid(); t0 < lim_; t0 += 2 * st_) {                       \
+    const int64_t t1 = t0 + st_;                                               \
+    BODY2                                                                      \
+  }
+
+__device__ __forceinline__ int64_t round32(int64_t v) { return (v + 31) & ~(int64_t)31; }
+
 // One Chebyshev step:  r_out = r_in - A d_in ;  d_out = c1 d_in + c2 D^-1 r_out ;
 // x += d_out (+ d_in when the previous direction was not yet added to x).
 template <typename T>
-__global__ void k_cheb_step(DevSell<T> A, int n, const T* r_in,
-                            const T* __restrict__ d_in, const T* __restrict__ dinv, T c1, T c2,
-                            T* r_out, T* __restrict__ d_out, T* __restrict__ x, int add_pending) {
-  const int64_t tid = gtid();
-  const T ad = mat_row(A, tid, n, d_in);
-  if (!row_leader(A, tid, n)) return;
-  const int i = (int)(tid >> A.logG);
-  const T di = d_in[i];
-  const T r = r_in[i] - ad;
-  const T dn = c1 * di + c2 * dinv[i] * r;
-  r_out[i] = r;
-  d_out[i] = dn;
-  x[i] += add_pending ? dn + di : dn;
+__global__ void __launch_bounds__(kBlock, 4)
+k_cheb_step(DevSell<T> A, int n, const T* r_in, const T* __restrict__ d_in,
+            const T* __restrict__ dinv, T c1, T c2, T* r_out, T* __restrict__ d_out,
+            T* __restrict__ x, int add_pending) {
+  pdl_enter();
+  EQS_ROWS2(A, n, {
+    const T a0 = mat_row(A, t0, n, d_in);
+    const T a1 = mat_row(A, t1, n, d_in);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t t = h ? t1 : t0;
+      if (!row_leader(A, t, n)) continue;
+      const int i = (int)(t >> A.logG);
+      const T di = d_in[i];
+      const T r = r_in[i] - (h ? a1 : a0);
+      const T dn = c1 * di + c2 * dinv[i] * r;
+      r_out[i] = r;
+      d_out[i] = dn;
+      x[i] += add_pending ? dn + di : dn;
+    }
+  })
 }
 
 // r -= A d  (in place; r is row-local)
 template <typename T>
-__global__ void k_resid_update(DevSell<T> A, int n, T* r, const T* __restrict__ d) {
-  const int64_t tid = gtid();
-  const T ad = mat_row(A, tid, n, d);
-  if (!row_leader(A, tid, n)) return;
-  const int i = (int)(tid >> A.logG);
-  r[i] = r[i] - ad;
+__global__ void __launch_bounds__(kBlock, 4) k_resid_update(DevSell<T> A, int n, T* r, const T* __restrict__ d) {
+  pdl_enter();
+  EQS_ROWS2(A, n, {
+    const T a0 = mat_row(A, t0, n, d);
+    const T a1 = mat_row(A, t1, n, d);
+    if (row_leader(A, t0, n)) r[t0 >> A.logG] -= a0;
+    if (row_leader(A, t1, n)) r[t1 >> A.logG] -= a1;
+  })
 }
 
 // out = b - A x
 template <typename T>
-__global__ void k_resid(DevSell<T> A, int n, const T* __restrict__ b, const T* __restrict__ x,
+__global__ void __launch_bounds__(kBlock, 4) k_resid(DevSell<T> A, int n, const T* __restrict__ b, const T* __restrict__ x,
                         T* __restrict__ out) {
-  const int64_t tid = gtid();
-  const T ax = mat_row(A, tid, n, x);
-  if (!row_leader(A, tid, n)) return;
-  const int i = (int)(tid >> A.logG);
-  out[i] = b[i] - ax;
+  pdl_enter();
+  EQS_ROWS2(A, n, {
+    const T a0 = mat_row(A, t0, n, x);
+    const T a1 = mat_row(A, t1, n, x);
+    if (row_leader(A, t0, n)) out[t0 >> A.logG] = b[t0 >> A.logG] - a0;
+    if (row_leader(A, t1, n)) out[t1 >> A.logG] = b[t1 >> A.logG] - a1;
+  })
 }
 
 // b_c = R r_f ; when first_step: x_c = d_c = D_c^-1 b_c / theta_c (the first
 // Chebyshev step of the coarse level from a zero initial guess).
 template <typename T>
-__global__ void k_restrict(DevSell<T> R, int nc, const T* __restrict__ rf, T* __restrict__ bc,
+__global__ void __launch_bounds__(kBlock, 4) k_restrict(DevSell<T> R, int nc, const T* __restrict__ rf, T* __restrict__ bc,
                            const T* __restrict__ dinv_c, T inv_theta_c, T* __restrict__ xc,
                            T* __restrict__ dc, int first_step) {
-  const int64_t tid = gtid();
-  const T b = mat_row(R, tid, nc, rf);
-  if (!row_leader(R, tid, nc)) return;
-  const int i = (int)(tid >> R.logG);
-  bc[i] = b;
-  if (first_step) {
-    const T d = dinv_c[i] * b * inv_theta_c;
-    xc[i] = d;
-    dc[i] = d;
-  }
+  pdl_enter();
+  EQS_ROWS2(R, nc, {
+    const T b0 = mat_row(R, t0, nc, rf);
+    const T b1 = mat_row(R, t1, nc, rf);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t t = h ? t1 : t0;
+      if (!row_leader(R, t, nc)) continue;
+      const int i = (int)(t >> R.logG);
+      const T b = h ? b1 : b0;
+      bc[i] = b;
+      if (first_step) {
+        const T d = dinv_c[i] * b * inv_theta_c;
+        xc[i] = d;
+        dc[i] = d;
+      }
+    }
+  })
 }
 
 // x_f += P x_c
 template <typename T>
-__global__ void k_prolong(DevSell<T> P, int nf, const T* __restrict__ xc, T* __restrict__ xf) {
-  const int64_t tid = gtid();
-  const T px = mat_row(P, tid, nf, xc);
-  if (!row_leader(P, tid, nf)) return;
-  xf[tid >> P.logG] += px;
+__global__ void __launch_bounds__(kBlock, 4) k_prolong(DevSell<T> P, int nf, const T* __restrict__ xc, T* __restrict__ xf) {
+  pdl_enter();
+  EQS_ROWS2(P, nf, {
+    const T p0 = mat_row(P, t0, nf, xc);
+    const T p1 = mat_row(P, t1, nf, xc);
+    if (row_leader(P, t0, nf)) xf[t0 >> P.logG] += p0;
+    if (row_leader(P, t1, nf)) xf[t1 >> P.logG] += p1;
+  })
 }
 
 // First post-smoothing step from the current x: r = b - A x ; d = D^-1 r / theta.
 // x is not updated here (other rows still read it); the next step adds d.
 template <typename T>
-__global__ void k_post_first(DevSell<T> A, int n, const T* __restrict__ b,
+__global__ void __launch_bounds__(kBlock, 4) k_post_first(DevSell<T> A, int n, const T* __restrict__ b,
                              const T* __restrict__ x, const T* __restrict__ dinv, T inv_theta,
                              T* __restrict__ r_out, T* __restrict__ d_out) {
-  const int64_t tid = gtid();
-  const T ax = mat_row(A, tid, n, x);
-  if (!row_leader(A, tid, n)) return;
-  const int i = (int)(tid >> A.logG);
-  const T r = b[i] - ax;
-  r_out[i] = r;
-  d_out[i] = dinv[i] * r * inv_theta;
+  pdl_enter();
+  EQS_ROWS2(A, n, {
+    const T a0 = mat_row(A, t0, n, x);
+    const T a1 = mat_row(A, t1, n, x);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t t = h ? t1 : t0;
+      if (!row_leader(A, t, n)) continue;
+      const int i = (int)(t >> A.logG);
+      const T r = b[i] - (h ? a1 : a0);
+      r_out[i] = r;
+      d_out[i] = dinv[i] * r * inv_theta;
+    }
+  })
 }
 
 template <typename T>
 __global__ void k_axpy1(int n, T* __restrict__ x, const T* __restrict__ d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  x[i] += d[i];
+  pdl_enter();
+  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] += d[i];
 }
 
 // Coarsest level: x = A_c^-1 b with the dense FP64 inverse; one warp per row.
 template <typename T>
 __global__ void k_coarse_solve(int n, const double* __restrict__ inv, const T* __restrict__ b,
                                T* __restrict__ x) {
+  pdl_enter();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
@@ -187,10 +264,12 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ inv, const T* _
 }
 
 // ---------------------------------------------------------------- reductions
-// Block sum of NV doubles; result valid in thread 0.
+// Block sum of NV doubles (any block size up to 1024 threads, a multiple of
+// 32); result valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV]) {
-  __shared__ double sh[NV][kBlock / 32];
+  __shared__ double sh[NV][32];
+  const int nw = (int)(blockDim.x >> 5);
 #pragma unroll
   for (int k = 0; k < NV; ++k)
 #pragma unroll
@@ -203,7 +282,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   if (w == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double t = lane < (kBlock / 32) ? sh[k][lane] : 0.0;
+      double t = lane < nw ? sh[k][lane] : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       v[k] = t;
@@ -242,6 +321,9 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, unsi
 }
 
 // ------------------------------------------------------------------ PCG
+// CG kernels run grid-stride over rows with a capped grid (fewer blocks take
+// part in the atomic ticket of each grid reduction).
+//
 // Initial residual r = R - M x, norms of R and r, and the first V-cycle
 // input (b0 = r in T, x0 = d0 = D0^-1 b0 / theta0).  The last block decides
 // whether the CG loop runs (condition handle).
@@ -253,9 +335,9 @@ __global__ void k_pcg_init(DevSell<double> M, int n, const double* __restrict__ 
                            double* partials, unsigned int* counter, int max_blocks, double tol2,
                            int maxit, cudaGraphConditionalHandle h, int use_handle,
                            int* iters_out, double* relres_out, int* zero_out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_enter();
   double v[2] = {0.0, 0.0};
-  if (i < n) {
+  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double Ri = R[i];
     const double ri = Ri - mat_row<double>(M, i, n, x);
     r[i] = ri;
@@ -264,14 +346,15 @@ __global__ void k_pcg_init(DevSell<double> M, int n, const double* __restrict__ 
     const T d = dinv0[i] * bi * inv_theta0;
     x0[i] = d;
     d0[i] = d;
-    v[0] = Ri * Ri;
-    v[1] = ri * ri;
+    v[0] += Ri * Ri;
+    v[1] += ri * ri;
   }
   double tot[2];
   if (grid_sum<2>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
     sc->bnorm2 = tot[0];
     sc->rnorm2 = tot[1];
     sc->it = 0;
+    sc->parity = 0;
     const int zero = tot[0] == 0.0;
     const int go = !zero && tot[1] > tol2 * tot[0] && maxit > 0;
     sc->conv = !go;
@@ -282,24 +365,20 @@ __global__ void k_pcg_init(DevSell<double> M, int n, const double* __restrict__ 
   }
 }
 
-// w = M z (z from the V-cycle, in T), dot products r.z and r_prev.z; the
-// last block forms beta (Fletcher-Reeves or Polak-Ribiere).
+// z (from the V-cycle, in T) to FP64, r.z and r_prev.z; the last block forms
+// beta (Fletcher-Reeves, or Polak-Ribiere when flexible).
 template <typename T>
-__global__ void k_pcg_dots(DevSell<double> M, int n, const double* __restrict__ r,
-                           const double* __restrict__ rprev, const T* __restrict__ z,
-                           double* __restrict__ zd, double* __restrict__ w, PcgScalars* sc,
-                           double* partials, unsigned int* counter, int max_blocks,
-                           int flexible) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_pcg_dots(int n, const double* __restrict__ r, const double* __restrict__ rprev,
+                           const T* __restrict__ z, double* __restrict__ zd, PcgScalars* sc,
+                           double* partials, unsigned int* counter, int max_blocks, int flexible) {
+  pdl_enter();
   double v[2] = {0.0, 0.0};
-  if (i < n) {
+  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double zi = (double)z[i];
     zd[i] = zi;
-    v[0] = r[i] * zi;
-    v[1] = rprev[i] * zi;
+    v[0] += r[i] * zi;
+    v[1] += rprev[i] * zi;
   }
-  (void)M;
-  (void)w;
   double tot[2];
   if (grid_sum<2>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
     const double rz = tot[0];
@@ -311,24 +390,21 @@ __global__ void k_pcg_dots(DevSell<double> M, int n, const double* __restrict__ 
   }
 }
 
-// p = z + beta p ; q = M p is done by k_pcg_q.
-__global__ void k_pcg_p(int n, const double* __restrict__ zd, double* __restrict__ p,
-                        const PcgScalars* sc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  p[i] = zd[i] + sc->beta * p[i];
-}
-
-// q = M p and p.q ; alpha = r.z / p.q
-__global__ void k_pcg_q(DevSell<double> M, int n, const double* __restrict__ p,
-                        double* __restrict__ q, PcgScalars* sc, double* partials,
-                        unsigned int* counter, int max_blocks) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// p = z + beta p and q = M p through q = M z + beta q (M p_old = q_old), so
+// p and q stay row-local and M costs one FMA per non-zero; p.q and alpha.
+__global__ void k_pcg_pq(DevSell<double> M, int n, const double* __restrict__ zd, double* __restrict__ p,
+                         double* __restrict__ q, PcgScalars* sc, double* partials,
+                         unsigned int* counter, int max_blocks) {
+  pdl_enter();
+  const double beta = sc->beta;
   double v[1] = {0.0};
-  if (i < n) {
-    const double qi = mat_row<double>(M, i, n, p);
+  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double w = mat_row<double>(M, i, n, zd);
+    const double qi = beta == 0.0 ? w : fma(beta, q[i], w);
+    const double pi = beta == 0.0 ? zd[i] : fma(beta, p[i], zd[i]);
+    p[i] = pi;
     q[i] = qi;
-    v[0] = p[i] * qi;
+    v[0] += pi * qi;
   }
   double tot[1];
   if (grid_sum<1>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
@@ -348,16 +424,16 @@ __global__ void k_pcg_update(int n, double* __restrict__ x, double* __restrict__
                              unsigned int* counter, int max_blocks, double tol2, int maxit,
                              cudaGraphConditionalHandle h, int use_handle, int* iters_out,
                              double* relres_out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_enter();
+  const double a = sc->alpha;
   double v[1] = {0.0};
-  if (i < n) {
-    const double a = sc->alpha;
+  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] = fma(a, p[i], x[i]);
     const double ro = r[i];
     rprev[i] = ro;
     const double rn = fma(-a, q[i], ro);
     r[i] = rn;
-    v[0] = rn * rn;
+    v[0] += rn * rn;
     const T bi = (T)rn;
     b0[i] = bi;
     const T d = dinv0[i] * bi * inv_theta0;
@@ -416,6 +492,7 @@ __global__ void k_elem64(int64_t nt, const int4* __restrict__ conn, const uint8_
                          const MaterialDev* __restrict__ mats, const double4* __restrict__ xyz,
                          const double* __restrict__ x, int n_limit, double sign,
                          double* __restrict__ y) {
+  pdl_enter();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nt) return;
   const int4 t = conn[e];
@@ -460,6 +537,7 @@ __global__ void k_elem32(int64_t nt, const int4* __restrict__ conn, const uint8_
                          const MaterialDev* __restrict__ mats, const float4* __restrict__ xh,
                          const float4* __restrict__ xl, const float2* __restrict__ x,
                          int n_limit, float* __restrict__ y) {
+  pdl_enter();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nt) return;
   const int4 t = conn[e];
@@ -512,6 +590,7 @@ __device__ __forceinline__ float2 split2(double v) {
 __global__ void k_stage_scalars(int s1, const double* __restrict__ cj, const StepParams* prm,
                                 double V0, double w, double phase, double* __restrict__ g,
                                 double* __restrict__ gp) {
+  pdl_enter();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= s1) return;
   const double tj = prm->t + cj[j] * prm->dt;
@@ -530,6 +609,7 @@ __global__ void k_gather_state(int n, int nf, const double* __restrict__ xmesh,
                                double* __restrict__ Y0, float2* __restrict__ Y32,
                                const double* __restrict__ Fsrc, double* __restrict__ Fdst,
                                double* __restrict__ R) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double v;
@@ -559,6 +639,7 @@ __global__ void k_recurrence(int n, int nf, double c0, double mu, double nu, dou
                              double* __restrict__ Yj, float2* __restrict__ Y32,
                              double* __restrict__ Fguess, double* __restrict__ R,
                              double* __restrict__ xmesh, const int32_t* __restrict__ node_of_internal) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double v;
@@ -580,6 +661,7 @@ __global__ void k_recurrence(int n, int nf, double c0, double mu, double nu, dou
 // Mixed precision: R = -y32 - g'(t_j) M_fd 1_top in FP64, and clear y32.
 __global__ void k_rhs_from_y32(int nf, float* __restrict__ y32, const double* __restrict__ gpj,
                                const double* __restrict__ mtop, double* __restrict__ R) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nf) return;
   R[i] = -(double)y32[i] - (*gpj) * mtop[i];
@@ -589,6 +671,7 @@ __global__ void k_rhs_from_y32(int nf, float* __restrict__ y32, const double* __
 // ------------------------------------------------------- small utilities
 __global__ void k_gather_perm(int n, const double* __restrict__ src, const int32_t* __restrict__ perm,
                               double* __restrict__ dst, float2* __restrict__ dst32) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double v = src[perm[i]];
@@ -598,6 +681,7 @@ __global__ void k_gather_perm(int n, const double* __restrict__ src, const int32
 
 __global__ void k_scatter_perm(int n, const double* __restrict__ src, const float* __restrict__ src32,
                                const int32_t* __restrict__ perm, double* __restrict__ dst) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   dst[perm[i]] = src32 ? (double)src32[i] : src[i];
@@ -605,12 +689,14 @@ __global__ void k_scatter_perm(int n, const double* __restrict__ src, const floa
 
 template <typename T>
 __global__ void k_to_T(int n, const double* __restrict__ a, T* __restrict__ b) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (T)a[i];
 }
 
 template <typename T>
 __global__ void k_from_T(int n, const T* __restrict__ a, double* __restrict__ b) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (double)a[i];
 }
@@ -618,6 +704,7 @@ __global__ void k_from_T(int n, const T* __restrict__ a, double* __restrict__ b)
 template <typename T>
 __global__ void k_first_step(int n, const T* __restrict__ b, const T* __restrict__ dinv, T inv_theta,
                              T* __restrict__ x, T* __restrict__ d) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const T v = dinv[i] * b[i] * inv_theta;
@@ -626,9 +713,376 @@ __global__ void k_first_step(int n, const T* __restrict__ b, const T* __restrict
 }
 
 __global__ void k_spmv64(DevSell<double> A, int n, const double* __restrict__ x, double* __restrict__ y) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const double v = mat_row<double>(A, i, n, x);
   if (i < n) y[i] = v;
+}
+
+}  // namespace eqs
+
+// ===================================================== persistent M-solve
+// One cooperative launch runs a whole CG solve (Section IV): every CTA
+// loops over the CG iterations; the V-cycle and CG phases are grid-stride
+// loops over rows separated by grid barriers.  Each barrier wait is bounded:
+// on time-out the CTA raises an error flag and every CTA returns.
+namespace eqs {
+
+constexpr int kMaxLevels = 12;
+constexpr int kPBlock = 512;
+constexpr long long kMaxSpins = 1LL << 22;
+
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+  int err;   // 1: a barrier wait timed out
+  int pad;
+};
+
+template <typename T>
+struct PLevel {
+  DevSell<T> A, P, R;
+  T *dinv, *b, *x, *r, *dA, *dB;
+  int n;
+  T inv_theta;
+  T c1[5], c2[5];
+};
+
+template <typename T>
+struct PPlan {
+  int nl, deg, nf, maxit, flexible, pad;
+  const double* coarse_inv;
+  DevSell<double> M;
+  double *r, *rprev, *pA, *pB, *q, *zd;
+  double* partials;  // 8 slots x gridDim
+  GridBarrier* bar;
+  PLevel<T> lev[kMaxLevels];
+};
+
+struct GridCtx {
+  int64_t tid, stride;
+  unsigned int nblocks;
+};
+
+__device__ __forceinline__ bool grid_barrier(GridBarrier* b, unsigned int nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &b->gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&b->count, 1u) + 1u == nblocks) {
+      b->count = 0u;
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if (*(volatile int*)&b->err || ++spins > kMaxSpins) {
+          atomicExch(&b->err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    if (*(volatile int*)&b->err) ok = 0;
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Block partial of NV values into partials[(slot + k) * nblocks + block].
+template <int NV>
+__device__ __forceinline__ void put_partials(double (&v)[NV], double* partials, int slot, unsigned nb) {
+  block_sum<NV>(v);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[(slot + k) * nb + blockIdx.x] = v[k];
+}
+
+// Sum of the block partials of one slot, in fixed order (same value in every
+// CTA); must follow a grid barrier.
+__device__ __forceinline__ double get_total(const double* partials, int slot, unsigned nb) {
+  __shared__ double s_tot;
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (unsigned b = threadIdx.x; b < nb; b += 32) t += __ldcg(partials + slot * nb + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) s_tot = t;
+  }
+  __syncthreads();
+  const double r = s_tot;
+  __syncthreads();
+  return r;
+}
+
+// ---- V-cycle phases (grid-stride; loops are warp-uniform)
+template <typename T>
+__device__ __forceinline__ void ph_cheb(const PLevel<T>& L, const T* r_in, const T* d_in, T* r_out,
+                                        T* d_out, T c1, T c2, int pending, const GridCtx& g) {
+  const int n = L.n;
+  const int64_t lim = round32((int64_t)n << L.A.logG);
+  for (int64_t t = g.tid; t < lim; t += g.stride) {
+    const T ad = mat_row(L.A, t, n, d_in);
+    if (!row_leader(L.A, t, n)) continue;
+    const int i = (int)(t >> L.A.logG);
+    const T di = d_in[i];
+    const T r = r_in[i] - ad;
+    const T dn = c1 * di + c2 * L.dinv[i] * r;
+    r_out[i] = r;
+    d_out[i] = dn;
+    L.x[i] += pending ? dn + di : dn;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void ph_resid_update(const PLevel<T>& L, const T* d, const GridCtx& g) {
+  const int n = L.n;
+  const int64_t lim = round32((int64_t)n << L.A.logG);
+  for (int64_t t = g.tid; t < lim; t += g.stride) {
+    const T ad = mat_row(L.A, t, n, d);
+    if (!row_leader(L.A, t, n)) continue;
+    const int i = (int)(t >> L.A.logG);
+    L.r[i] = L.r[i] - ad;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void ph_resid(const PLevel<T>& L, const GridCtx& g) {
+  const int n = L.n;
+  const int64_t lim = round32((int64_t)n << L.A.logG);
+  for (int64_t t = g.tid; t < lim; t += g.stride) {
+    const T ax = mat_row(L.A, t, n, L.x);
+    if (!row_leader(L.A, t, n)) continue;
+    const int i = (int)(t >> L.A.logG);
+    L.r[i] = L.b[i] - ax;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void ph_restrict(const PLevel<T>& F, const PLevel<T>& C, int first,
+                                            const GridCtx& g) {
+  const int nc = C.n;
+  const int64_t lim = round32((int64_t)nc << F.R.logG);
+  for (int64_t t = g.tid; t < lim; t += g.stride) {
+    const T b = mat_row(F.R, t, nc, F.r);
+    if (!row_leader(F.R, t, nc)) continue;
+    const int i = (int)(t >> F.R.logG);
+    C.b[i] = b;
+    if (first) {
+      const T d = C.dinv[i] * b * C.inv_theta;
+      C.x[i] = d;
+      C.dA[i] = d;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void ph_prolong(const PLevel<T>& F, const PLevel<T>& C, const GridCtx& g) {
+  const int n = F.n;
+  const int64_t lim = round32((int64_t)n << F.P.logG);
+  for (int64_t t = g.tid; t < lim; t += g.stride) {
+    const T px = mat_row(F.P, t, n, C.x);
+    if (!row_leader(F.P, t, n)) continue;
+    F.x[t >> F.P.logG] += px;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void ph_post_first(const PLevel<T>& L, const GridCtx& g) {
+  const int n = L.n;
+  const int64_t lim = round32((int64_t)n << L.A.logG);
+  for (int64_t t = g.tid; t < lim; t += g.stride) {
+    const T ax = mat_row(L.A, t, n, L.x);
+    if (!row_leader(L.A, t, n)) continue;
+    const int i = (int)(t >> L.A.logG);
+    const T r = L.b[i] - ax;
+    L.r[i] = r;
+    L.dA[i] = L.dinv[i] * r * L.inv_theta;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void ph_coarse(const PLevel<T>& L, const double* inv, const GridCtx& g) {
+  const int n = L.n;
+  const int64_t lim = (int64_t)n * 32;
+  for (int64_t t = g.tid; t < round32(lim); t += g.stride) {
+    const int row = (int)(t >> 5), lane = (int)(t & 31);
+    double acc = 0.0;
+    if (row < n)
+      for (int j = lane; j < n; j += 32) acc = fma(inv[(int64_t)row * n + j], (double)L.b[j], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (row < n && lane == 0) L.x[row] = (T)acc;
+  }
+}
+
+// Whole V-cycle from level 0 (its b, x = dA = first step already set).
+template <typename T>
+__device__ bool vcycle_persistent(const PPlan<T>& P, const GridCtx& g) {
+  const int nl = P.nl, deg = P.deg;
+  for (int l = 0; l < nl - 1; ++l) {
+    const PLevel<T>& L = P.lev[l];
+    T* din = L.dA;
+    T* dout = L.dB;
+    const T* rin = L.b;
+    for (int k = 2; k <= deg; ++k) {
+      ph_cheb(L, rin, din, L.r, dout, L.c1[k], L.c2[k], 0, g);
+      if (!grid_barrier(P.bar, g.nblocks)) return false;
+      rin = L.r;
+      T* tmp = din;
+      din = dout;
+      dout = tmp;
+    }
+    if (deg >= 2)
+      ph_resid_update(L, din, g);
+    else
+      ph_resid(L, g);
+    if (!grid_barrier(P.bar, g.nblocks)) return false;
+    ph_restrict(L, P.lev[l + 1], l + 1 < nl - 1, g);
+    if (!grid_barrier(P.bar, g.nblocks)) return false;
+  }
+  ph_coarse(P.lev[nl - 1], P.coarse_inv, g);
+  if (!grid_barrier(P.bar, g.nblocks)) return false;
+  for (int l = nl - 2; l >= 0; --l) {
+    const PLevel<T>& L = P.lev[l];
+    ph_prolong(L, P.lev[l + 1], g);
+    if (!grid_barrier(P.bar, g.nblocks)) return false;
+    ph_post_first(L, g);
+    if (!grid_barrier(P.bar, g.nblocks)) return false;
+    T* din = L.dA;
+    T* dout = L.dB;
+    for (int k = 2; k <= deg; ++k) {
+      ph_cheb(L, L.r, din, L.r, dout, L.c1[k], L.c2[k], k == 2, g);
+      if (!grid_barrier(P.bar, g.nblocks)) return false;
+      T* tmp = din;
+      din = dout;
+      dout = tmp;
+    }
+    if (deg == 1) {
+      for (int64_t i = g.tid; i < L.n; i += g.stride) L.x[i] += L.dA[i];
+      if (!grid_barrier(P.bar, g.nblocks)) return false;
+    }
+  }
+  return true;
+}
+
+// Preconditioned CG for M_ff x = R from the start vector in x.  Slots of the
+// partial sums: 0-1 init, 2-3 dots, 4 p.q, 5 update.
+template <typename T>
+__global__ void __launch_bounds__(kPBlock) k_pcg_persistent(const PPlan<T>* __restrict__ plan,
+                                                             const double* __restrict__ R,
+                                                             double* __restrict__ x,
+                                                             int* iters_out, double* relres_out,
+                                                             int* zero_out, double tol2) {
+  const PPlan<T>& P = *plan;
+  GridCtx g;
+  g.tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  g.stride = (int64_t)gridDim.x * blockDim.x;
+  g.nblocks = gridDim.x;
+  const unsigned nb = gridDim.x;
+  const int n = P.nf;
+  const PLevel<T>& L0 = P.lev[0];
+  const bool single = (P.nl == 1);
+  // init: r = R - M x, level-0 input
+  {
+    double v[2] = {0.0, 0.0};
+    for (int64_t i = g.tid; i < n; i += g.stride) {
+      const double Ri = R[i];
+      const double ri = Ri - mat_row<double>(P.M, i, n, x);
+      P.r[i] = ri;
+      const T bi = (T)ri;
+      L0.b[i] = bi;
+      if (!single) {
+        const T d = L0.dinv[i] * bi * L0.inv_theta;
+        L0.x[i] = d;
+        L0.dA[i] = d;
+      }
+      v[0] += Ri * Ri;
+      v[1] += ri * ri;
+    }
+    put_partials<2>(v, P.partials, 0, nb);
+  }
+  if (!grid_barrier(P.bar, g.nblocks)) return;
+  const double bnorm2 = get_total(P.partials, 0, nb);
+  double rnorm2 = get_total(P.partials, 1, nb);
+  const int zero = bnorm2 == 0.0;
+  int conv = zero || !(rnorm2 > tol2 * bnorm2);
+  int it = 0;
+  double rz_old = 1.0;
+  double* pold = P.pA;
+  double* pnew = P.pB;
+  while (!conv && it < P.maxit) {
+    if (!vcycle_persistent(P, g)) return;
+    // z in FP64, r.z and r_prev.z
+    {
+      double v[2] = {0.0, 0.0};
+      for (int64_t i = g.tid; i < n; i += g.stride) {
+        const double zi = (double)L0.x[i];
+        P.zd[i] = zi;
+        v[0] += P.r[i] * zi;
+        v[1] += P.rprev[i] * zi;
+      }
+      put_partials<2>(v, P.partials, 2, nb);
+    }
+    if (!grid_barrier(P.bar, g.nblocks)) return;
+    const double rz = get_total(P.partials, 2, nb);
+    const double zrp = get_total(P.partials, 3, nb);
+    const double beta = it == 0 ? 0.0 : (P.flexible ? (rz - zrp) / rz_old : rz / rz_old);
+    rz_old = rz;
+    // p_new = z + beta p_old ; q = M p_new (p_new of neighbours formed on the fly)
+    {
+      double v[1] = {0.0};
+      for (int64_t i = g.tid; i < n; i += g.stride) {
+        const double qi = beta == 0.0 ? mat_row<double>(P.M, i, n, P.zd)
+                                      : mat_row_axpy(P.M, (int)i, n, P.zd, pold, beta);
+        const double pi = beta == 0.0 ? P.zd[i] : fma(beta, pold[i], P.zd[i]);
+        pnew[i] = pi;
+        P.q[i] = qi;
+        v[0] += pi * qi;
+      }
+      put_partials<1>(v, P.partials, 4, nb);
+    }
+    if (!grid_barrier(P.bar, g.nblocks)) return;
+    const double alpha = rz / get_total(P.partials, 4, nb);
+    // x += alpha p ; r -= alpha q ; next V-cycle input
+    {
+      double v[1] = {0.0};
+      for (int64_t i = g.tid; i < n; i += g.stride) {
+        x[i] = fma(alpha, pnew[i], x[i]);
+        const double ro = P.r[i];
+        P.rprev[i] = ro;
+        const double rn = fma(-alpha, P.q[i], ro);
+        P.r[i] = rn;
+        v[0] += rn * rn;
+        const T bi = (T)rn;
+        L0.b[i] = bi;
+        if (!single) {
+          const T d = L0.dinv[i] * bi * L0.inv_theta;
+          L0.x[i] = d;
+          L0.dA[i] = d;
+        }
+      }
+      put_partials<1>(v, P.partials, 5, nb);
+    }
+    if (!grid_barrier(P.bar, g.nblocks)) return;
+    rnorm2 = get_total(P.partials, 5, nb);
+    ++it;
+    conv = !(rnorm2 > tol2 * bnorm2);
+    double* tmp = pold;
+    pold = pnew;
+    pnew = tmp;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (iters_out) *iters_out = it;
+    if (relres_out) *relres_out = zero ? 0.0 : sqrt(rnorm2 / bnorm2);
+    if (zero_out) *zero_out = zero;
+  }
 }
 
 }  // namespace eqs

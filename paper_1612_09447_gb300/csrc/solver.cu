@@ -35,6 +35,31 @@ static eqs_status fail(eqs_ctx* c, eqs_status st, const std::string& msg) {
 
 static inline int nblk(int64_t n, int b = kBlock) { return (int)((n + b - 1) / b); }
 
+// Grid of a two-rows-per-thread row kernel: enough blocks for the work, at
+// most the resident capacity (4 blocks of kBlock threads per SM).
+static inline int rows_grid(const eqs_ctx* c, int64_t lanes) {
+  return std::max(1, std::min(nblk((lanes + 1) / 2), 4 * c->sms));
+}
+// Grid of a CG vector kernel (grid-stride, one reduction ticket per block).
+static inline int vec_grid(const eqs_ctx* c, int64_t n) { return std::max(1, std::min(nblk(n), 2 * c->sms)); }
+
+// Launch with programmatic dependent launch allowed (the kernels call
+// pdl_enter() before touching memory), so consecutive kernels of a stream or
+// graph overlap launch latency with the predecessor's tail.
+template <typename... KArgs, typename... Args>
+static void launch(void (*k)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = st;
+  cudaLaunchAttribute a[1];
+  a[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  a[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = a;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
+}
+
 // ---------------------------------------------------------- device memory
 static void free_all(eqs_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
@@ -223,42 +248,42 @@ static void vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStr
   const int nl = (int)L.size();
   DevLevel<T>& V = L[l];
   if (l == nl - 1) {
-    k_coarse_solve<T><<<nblk((int64_t)V.n * 32), kBlock, 0, st>>>(V.n, c->d_coarse_inv, V.b, V.x);
+    launch(k_coarse_solve<T>, nblk((int64_t)V.n * 32), kBlock, st, V.n, c->d_coarse_inv, V.b, V.x);
     return;
   }
   const int deg = c->opts.cheb_degree;
   std::vector<double> c1, c2;
   cheb_coeffs(V.sigma, V.delta, deg, c1, c2);
-  const int g = nblk((int64_t)V.n * std::max(V.A.G, 1));
+  const int g = rows_grid(c, (int64_t)V.n * std::max(V.A.G, 1));
   // pre-smoothing: x = d = D^-1 b / theta was set by the producer of b
   T* din = V.dA;
   T* dout = V.dB;
   const T* rin = V.b;
   for (int k = 2; k <= deg; ++k) {
-    k_cheb_step<T><<<g, kBlock, 0, st>>>(V.A, V.n, rin, din, V.dinv, (T)c1[k], (T)c2[k], V.r, dout,
+    launch(k_cheb_step<T>, g, kBlock, st, V.A, V.n, rin, din, V.dinv, (T)c1[k], (T)c2[k], V.r, dout,
                                          V.x, 0);
     rin = V.r;
     std::swap(din, dout);
   }
   if (deg >= 2)
-    k_resid_update<T><<<g, kBlock, 0, st>>>(V.A, V.n, V.r, din);
+    launch(k_resid_update<T>, g, kBlock, st, V.A, V.n, V.r, din);
   else
-    k_resid<T><<<g, kBlock, 0, st>>>(V.A, V.n, V.b, V.x, V.r);
+    launch(k_resid<T>, g, kBlock, st, V.A, V.n, V.b, V.x, V.r);
   DevLevel<T>& C = L[l + 1];
   const int first = (l + 1 < nl - 1) ? 1 : 0;
-  k_restrict<T><<<nblk((int64_t)C.n * std::max(V.R.G, 1)), kBlock, 0, st>>>(V.R, C.n, V.r, C.b, C.dinv, (T)C.inv_theta, C.x, C.dA,
+  launch(k_restrict<T>, rows_grid(c, (int64_t)C.n * std::max(V.R.G, 1)), kBlock, st, V.R, C.n, V.r, C.b, C.dinv, (T)C.inv_theta, C.x, C.dA,
                                                first);
   vcycle_level(c, L, l + 1, st);
-  k_prolong<T><<<nblk((int64_t)V.n * std::max(V.P.G, 1)), kBlock, 0, st>>>(V.P, V.n, C.x, V.x);
-  k_post_first<T><<<g, kBlock, 0, st>>>(V.A, V.n, V.b, V.x, V.dinv, (T)V.inv_theta, V.r, V.dA);
+  launch(k_prolong<T>, rows_grid(c, (int64_t)V.n * std::max(V.P.G, 1)), kBlock, st, V.P, V.n, C.x, V.x);
+  launch(k_post_first<T>, g, kBlock, st, V.A, V.n, V.b, V.x, V.dinv, (T)V.inv_theta, V.r, V.dA);
   din = V.dA;
   dout = V.dB;
   for (int k = 2; k <= deg; ++k) {
-    k_cheb_step<T><<<g, kBlock, 0, st>>>(V.A, V.n, V.r, din, V.dinv, (T)c1[k], (T)c2[k], V.r, dout,
+    launch(k_cheb_step<T>, g, kBlock, st, V.A, V.n, V.r, din, V.dinv, (T)c1[k], (T)c2[k], V.r, dout,
                                          V.x, k == 2 ? 1 : 0);
     std::swap(din, dout);
   }
-  if (deg == 1) k_axpy1<T><<<nblk(V.n), kBlock, 0, st>>>(V.n, V.x, V.dA);
+  if (deg == 1) launch(k_axpy1<T>, nblk(V.n), kBlock, st, V.n, V.x, V.dA);
 }
 
 // ------------------------------------------------------------- PCG
@@ -274,7 +299,7 @@ static void pcg_init_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_
                             int use_handle, SolveSlots sl) {
   DevLevel<T>& V = L[0];
   const int n = (int)c->n_free;
-  k_pcg_init<T><<<nblk(n), kBlock, 0, st>>>(c->M64, n, R, x, c->d_r, V.dinv, (T)V.inv_theta, V.b, V.x,
+  launch(k_pcg_init<T>, vec_grid(c, n), kBlock, st, c->M64, n, R, x, c->d_r, V.dinv, (T)V.inv_theta, V.b, V.x,
                                             V.dA, c->d_sc, c->red.partials, c->red.counter,
                                             c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle,
                                             sl.iters, sl.relres, sl.zero);
@@ -286,18 +311,15 @@ static void pcg_body_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_
                             SolveSlots sl) {
   DevLevel<T>& V = L[0];
   const int n = (int)c->n_free;
-  const int g = nblk(n);
+  const int g = vec_grid(c, n);
   vcycle_level(c, L, 0, st);
-  k_pcg_dots<T><<<g, kBlock, 0, st>>>(c->M64, n, c->d_r, c->d_rprev, V.x, c->d_zd, nullptr, c->d_sc,
-                                      c->red.partials, c->red.counter, c->red.max_blocks,
-                                      c->opts.flexible);
-  k_pcg_p<<<g, kBlock, 0, st>>>(n, c->d_zd, c->d_p, c->d_sc);
-  k_pcg_q<<<g, kBlock, 0, st>>>(c->M64, n, c->d_p, c->d_q, c->d_sc, c->red.partials, c->red.counter,
-                                c->red.max_blocks);
-  k_pcg_update<T><<<g, kBlock, 0, st>>>(n, x, c->d_r, c->d_rprev, c->d_p, c->d_q, V.dinv,
-                                        (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials,
-                                        c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h,
-                                        use_handle, sl.iters, sl.relres);
+  launch(k_pcg_dots<T>, g, kBlock, st, n, c->d_r, c->d_rprev, V.x, c->d_zd, c->d_sc, c->red.partials,
+         c->red.counter, c->red.max_blocks, c->opts.flexible);
+  launch(k_pcg_pq, g, kBlock, st, c->M64, n, c->d_zd, c->d_p, c->d_q, c->d_sc, c->red.partials,
+         c->red.counter, c->red.max_blocks);
+  launch(k_pcg_update<T>, g, kBlock, st, n, x, c->d_r, c->d_rprev, c->d_p, c->d_q, V.dinv,
+         (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials, c->red.counter,
+         c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres);
 }
 
 // Kernel nodes at the top level of graph g (loop bodies are not entered).
@@ -350,16 +372,100 @@ static eqs_status pcg_capture(eqs_ctx* c, std::vector<DevLevel<T>>& L, const dou
   return EQS_OK;
 }
 
+// ------------------------------------------------------ persistent solve
+template <typename T>
+static eqs_status build_plan(eqs_ctx* c, std::vector<DevLevel<T>>& L) {
+  if ((int)L.size() > kMaxLevels) return fail(c, EQS_ERR_ARG, "too many AMG levels for the persistent solve");
+  PPlan<T> P{};
+  P.nl = (int)L.size();
+  P.deg = c->opts.cheb_degree;
+  P.nf = (int)c->n_free;
+  P.maxit = c->opts.max_iter;
+  P.flexible = c->opts.flexible;
+  P.coarse_inv = c->d_coarse_inv;
+  P.M = c->M64;
+  P.r = c->d_r;
+  P.rprev = c->d_rprev;
+  P.pA = c->d_p;
+  P.pB = c->d_p2;
+  P.q = c->d_q;
+  P.zd = c->d_zd;
+  int dev = 0, sms = 0, occ = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg_persistent<T>, kPBlock, 0));
+  if (occ < 1) return fail(c, EQS_ERR_CUDA, "persistent solve kernel cannot be resident");
+  const int bps = std::min(occ, std::max(1, c->opts.blocks_per_sm));
+  c->pblocks = sms * bps;
+  CK(dalloc(c, &c->d_ppartials, 8 * (size_t)c->pblocks));
+  GridBarrier* bar = nullptr;
+  CK(dalloc(c, &bar, 1));
+  c->d_bar = bar;
+  P.partials = c->d_ppartials;
+  P.bar = bar;
+  for (int l = 0; l < P.nl; ++l) {
+    DevLevel<T>& D = L[l];
+    PLevel<T>& Q = P.lev[l];
+    Q.A = D.A;
+    Q.P = D.P;
+    Q.R = D.R;
+    Q.dinv = D.dinv;
+    Q.b = D.b;
+    Q.x = D.x;
+    Q.r = D.r;
+    Q.dA = D.dA;
+    Q.dB = D.dB;
+    Q.n = D.n;
+    Q.inv_theta = (T)D.inv_theta;
+    std::vector<double> c1, c2;
+    cheb_coeffs(D.sigma, D.delta, P.deg, c1, c2);
+    for (int k = 0; k <= P.deg && k < 5; ++k) {
+      Q.c1[k] = (T)c1[k];
+      Q.c2[k] = (T)c2[k];
+    }
+  }
+  PPlan<T>* dp = nullptr;
+  CK(upload(c, &dp, &P, 1));
+  c->d_plan = dp;
+  return EQS_OK;
+}
+
+template <typename T>
+static eqs_status persistent_launch(eqs_ctx* c, cudaStream_t st, const double* R, double* x,
+                                    double tol2, SolveSlots sl) {
+  CK(cudaMemsetAsync(c->d_bar, 0, sizeof(GridBarrier), st));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c->pblocks);
+  cfg.blockDim = dim3(kPBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CK(cudaLaunchKernelEx(&cfg, k_pcg_persistent<T>, (const PPlan<T>*)c->d_plan, R, x, sl.iters,
+                        sl.relres, sl.zero, tol2));
+  return EQS_OK;
+}
+
+template <typename T>
+static eqs_status solve_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* R, double* x,
+                               double tol2, SolveSlots sl) {
+  if (c->opts.persistent) return persistent_launch<T>(c, c->cap_stream, R, x, tol2, sl);
+  return pcg_capture<T>(c, L, R, x, tol2, sl);
+}
+
 static bool mixed(const eqs_ctx* c) { return c->opts.precision == EQS_PREC_MIXED; }
 
 // ------------------------------------------------------------ element
 static void elem_launch(eqs_ctx* c, cudaStream_t st, const double* Y, int n_limit, double* y64,
                         float* y32) {
   if (mixed(c))
-    k_elem32<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn, c->d_mat, c->d_mats,
+    launch(k_elem32, nblk(c->n_tets), kBlock, st, c->n_tets, c->d_conn, c->d_mat, c->d_mats,
                                                  c->d_xyz_hi, c->d_xyz_lo, c->d_Y32, n_limit, y32);
   else
-    k_elem64<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn, c->d_mat, c->d_mats, c->d_xyz,
+    launch(k_elem64, nblk(c->n_tets), kBlock, st, c->n_tets, c->d_conn, c->d_mat, c->d_mats, c->d_xyz,
                                                  Y, n_limit, y64 == c->d_R ? -1.0 : 1.0, y64);
 }
 
@@ -379,9 +485,9 @@ static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
   const double w = 2.0 * M_PI * c->freq;
   cudaStream_t st = c->cap_stream;
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-  k_stage_scalars<<<1, 64, 0, st>>>(s + 1, ge.d_cj, c->d_params, c->V0, w, c->phase, c->d_g, c->d_gp);
+  launch(k_stage_scalars, 1, 64, st, s + 1, ge.d_cj, c->d_params, c->V0, w, c->phase, c->d_g, c->d_gp);
   const bool mx = mixed(c);
-  k_gather_state<<<nblk(n), kBlock, 0, st>>>(n, nf, xdev, c->d_node_of_internal, c->d_dir_scale, c->d_g,
+  launch(k_gather_state, nblk(n), kBlock, st, n, nf, xdev, c->d_node_of_internal, c->d_dir_scale, c->d_g,
                                              c->d_gp, c->d_mtop, Ybuf(c, 0), mx ? c->d_Y32 : nullptr,
                                              Fbuf(c, s - 1), Fbuf(c, 0), mx ? nullptr : c->d_R);
   eqs_status stt = EQS_OK;
@@ -390,7 +496,7 @@ static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
       const bool first = (j == 1);
       const double c0 = first ? 1.0 : 1.0 - mu[j] - nu[j];
       const bool last = (j == s);
-      k_recurrence<<<nblk(n), kBlock, 0, st>>>(
+      launch(k_recurrence, nblk(n), kBlock, st, 
           n, nf, c0, first ? 0.0 : mu[j], first ? 0.0 : nu[j], mut[j], first ? 0.0 : gt[j], c->d_params,
           Ybuf(c, 0), Ybuf(c, j - 1), Ybuf(c, j >= 2 ? j - 2 : 0), Fbuf(c, j - 1), Fbuf(c, 0), c->d_zero,
           j - 1, c->d_dir_scale, c->d_g + j, c->d_gp + j, c->d_mtop, Ybuf(c, j),
@@ -400,12 +506,12 @@ static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
     }
     if (mx) {
       elem_launch(c, st, nullptr, nf, nullptr, c->d_y32);
-      k_rhs_from_y32<<<nblk(nf), kBlock, 0, st>>>(nf, c->d_y32, c->d_gp + j, c->d_mtop, c->d_R);
+      launch(k_rhs_from_y32, nblk(nf), kBlock, st, nf, c->d_y32, c->d_gp + j, c->d_mtop, c->d_R);
     } else {
       elem_launch(c, st, Ybuf(c, j), nf, c->d_R, nullptr);
     }
     SolveSlots sl{c->d_iters + j, c->d_relres + j, c->d_zero + j};
-    stt = pcg_capture<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl);
+    stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl);
   }
   cudaError_t le = cudaGetLastError();
   cudaGraph_t graph = nullptr;
@@ -429,7 +535,7 @@ static eqs_status capture_solve(eqs_ctx* c, std::vector<DevLevel<T>>& L, double 
   cudaStream_t st = c->cap_stream;
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
   SolveSlots sl{c->d_iters, c->d_relres, c->d_zero};
-  eqs_status stt = pcg_capture<T>(c, L, c->d_R, c->d_sol, rtol * rtol, sl);
+  eqs_status stt = solve_launch<T>(c, L, c->d_R, c->d_sol, rtol * rtol, sl);
   cudaGraph_t graph = nullptr;
   cudaError_t ee = cudaStreamEndCapture(st, &graph);
   if (stt != EQS_OK) {
@@ -462,10 +568,10 @@ static eqs_status vcycle_impl(eqs_ctx* c, std::vector<DevLevel<T>>& L, const dou
   const int nf = (int)c->n_free;
   cudaStream_t st = c->stream;
   DevLevel<T>& V = L[0];
-  k_to_T<T><<<nblk(nf), kBlock, 0, st>>>(nf, r, V.b);
-  if (L.size() > 1) k_first_step<T><<<nblk(nf), kBlock, 0, st>>>(nf, V.b, V.dinv, (T)V.inv_theta, V.x, V.dA);
+  launch(k_to_T<T>, nblk(nf), kBlock, st, nf, r, V.b);
+  if (L.size() > 1) launch(k_first_step<T>, nblk(nf), kBlock, st, nf, V.b, V.dinv, (T)V.inv_theta, V.x, V.dA);
   vcycle_level(c, L, 0, st);
-  k_from_T<T><<<nblk(nf), kBlock, 0, st>>>(nf, V.x, z);
+  launch(k_from_T<T>, nblk(nf), kBlock, st, nf, V.x, z);
   CK(cudaGetLastError());
   return EQS_OK;
 }
@@ -485,6 +591,8 @@ void eqs_opts_default(eqs_opts* o) {
   o->max_iter = 500;
   o->guess = EQS_GUESS_PREV;
   o->flexible = 1;
+  o->persistent = 1;
+  o->blocks_per_sm = 1;
 }
 
 eqs_status eqs_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
@@ -550,7 +658,7 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     o = *opts;
   else
     eqs_opts_default(&o);
-  if (o.cheb_degree < 1 || o.cheb_degree > 4 || o.max_levels < 1 || o.coarse_max < 1 ||
+  if (o.cheb_degree < 1 || o.cheb_degree > 4 || o.blocks_per_sm < 0 || o.max_levels < 1 || o.coarse_max < 1 ||
       !(o.theta >= 0) || !(o.cheb_alpha > 1) || !(o.rtol > 0) || o.max_iter < 1 ||
       (o.precision != EQS_PREC_FP64 && o.precision != EQS_PREC_MIXED))
     return fail(c, EQS_ERR_ARG, "invalid eqs_opts");
@@ -582,6 +690,7 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     CK(cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking));
   }
   CK(cudaSetDevice(c->device));
+  CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
 
   const int64_t n = c->n_nodes, nf = c->n_free;
   // mesh data in internal numbering
@@ -638,7 +747,7 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
   for (int k = 0; k < 3; ++k) CK(dalloc(c, &c->d_F[k], nf));
   CK(dalloc(c, &c->d_Y32, n));
   CK(dalloc(c, &c->d_y32, n));
-  for (double** v : {&c->d_R, &c->d_r, &c->d_rprev, &c->d_p, &c->d_q, &c->d_zd, &c->d_sol})
+  for (double** v : {&c->d_R, &c->d_r, &c->d_rprev, &c->d_p, &c->d_p2, &c->d_q, &c->d_zd, &c->d_sol})
     CK(dalloc(c, v, nf));
   CK(dalloc(c, &c->d_tmpn, n));
   CK(dalloc(c, &c->d_tmpn2, n));
@@ -652,6 +761,10 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
   c->red.max_blocks = nblk(std::max<int64_t>(nf, 1));
   CK(dalloc(c, &c->red.partials, 4 * (size_t)c->red.max_blocks));
   CK(dalloc(c, &c->red.counter, 1));
+  {
+    const eqs_status ps = mixed(c) ? build_plan(c, c->lev32) : build_plan(c, c->lev64);
+    if (ps != EQS_OK) return ps;
+  }
   CK(cudaDeviceSynchronize());
   c->setup_done = true;
   return EQS_OK;
@@ -669,16 +782,16 @@ eqs_status eqs_apply_K(eqs_ctx* c, const double* x, double* y) {
   const int n = (int)c->n_nodes;
   cudaStream_t st = c->stream;
   const bool mx = mixed(c);
-  k_gather_perm<<<nblk(n), kBlock, 0, st>>>(n, x, c->d_node_of_internal, c->d_tmpn, mx ? c->d_Y32 : nullptr);
+  launch(k_gather_perm, nblk(n), kBlock, st, n, x, c->d_node_of_internal, c->d_tmpn, mx ? c->d_Y32 : nullptr);
   if (mx) {
     CK(cudaMemsetAsync(c->d_y32, 0, n * sizeof(float), st));
     elem_launch(c, st, nullptr, n, nullptr, c->d_y32);
-    k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, nullptr, c->d_y32, c->d_node_of_internal, y);
+    launch(k_scatter_perm, nblk(n), kBlock, st, n, nullptr, c->d_y32, c->d_node_of_internal, y);
     CK(cudaMemsetAsync(c->d_y32, 0, n * sizeof(float), st));
   } else {
     CK(cudaMemsetAsync(c->d_tmpn2, 0, n * sizeof(double), st));
     elem_launch(c, st, c->d_tmpn, n, c->d_tmpn2, nullptr);
-    k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, c->d_tmpn2, nullptr, c->d_node_of_internal, y);
+    launch(k_scatter_perm, nblk(n), kBlock, st, n, c->d_tmpn2, nullptr, c->d_node_of_internal, y);
   }
   CK(cudaGetLastError());
   return EQS_OK;
@@ -727,6 +840,11 @@ eqs_status eqs_solve_M(eqs_ctx* c, const double* rhs, double* z, int nrhs, doubl
     else
       CK(cudaMemcpyAsync(z + k * nf, c->d_sol, nf * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     if (iters_out) iters_out[k] = itn;
+    if (c->d_bar) {
+      GridBarrier b;
+      CK(cudaMemcpy(&b, c->d_bar, sizeof(b), cudaMemcpyDeviceToHost));
+      if (b.err) return fail(c, EQS_ERR_TIMEOUT, "a grid barrier of the persistent solve timed out");
+    }
     if (!std::isfinite(rr)) res = fail(c, EQS_ERR_NAN, "non-finite residual in solve");
     else if (!zero && rr > tol) res = fail(c, EQS_ERR_NOCONV, "CG reached max_iter");
   }
@@ -777,7 +895,13 @@ eqs_status eqs_get_step_stats(eqs_ctx* c, eqs_step_stats* stats) {
     else if (rr[j] > c->opts.rtol && res == EQS_OK) res = EQS_ERR_NOCONV;
   }
   stats->launches = c->last_step->fixed_kernels + c->last_step->per_iter_kernels * stats->total_iters;
+  if (c->d_bar) {
+    GridBarrier b;
+    CK(cudaMemcpy(&b, c->d_bar, sizeof(b), cudaMemcpyDeviceToHost));
+    if (b.err) res = EQS_ERR_TIMEOUT;
+  }
   stats->status = res;
+  if (res == EQS_ERR_TIMEOUT) return fail(c, res, "a grid barrier of the persistent solve timed out");
   if (res == EQS_ERR_NOCONV) return fail(c, res, "a stage solve reached max_iter");
   if (res == EQS_ERR_NAN) return fail(c, res, "non-finite residual in a stage solve");
   return EQS_OK;
