@@ -27,4 +27,7 @@ from .mesh import (  # noqa: F401
     batch_instance_params,
     BACKGROUND,
     VARISTOR,
+    MLP_SIZES,
+    MLP_NPARAM,
+    mlp_init,
 )

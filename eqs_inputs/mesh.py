@@ -219,3 +219,23 @@ def config_problem(idx: int, N: int | None = None, instance: int = 0):
         return make_problem(N or Ni, block=(lo, lo + frac), V0=V0, s=10, steps=100,
                             name=f"batch{instance}_cube{N or Ni}")
     raise ValueError(idx)
+
+
+# ------------------------------------------------------------------ guess MLP
+MLP_SIZES = (8, 32, 32, 1)
+MLP_NPARAM = 8 * 32 + 32 + 32 * 32 + 32 + 32 + 1  # 1377
+
+
+def mlp_init(seed: int = CONFIG_SEED + 3) -> np.ndarray:
+    """Initial FP32 parameters of the 8-32-32-1 guess network, packed as
+    [W1 (32x8, row-major), b1 (32), W2 (32x32), b2 (32), w3 (32), b3 (1)].
+    W1 ~ U(-1/sqrt(8), 1/sqrt(8)), W2 ~ U(-1/sqrt(32), 1/sqrt(32)) drawn as
+    values 0.. of stream ``seed``; biases and the output layer are zero so the
+    untrained network returns the previous-solution guess."""
+    u = uniform01(seed, np.arange(256 + 1024, dtype=np.uint64))
+    W1 = (2 * u[:256] - 1) / np.sqrt(8.0)
+    W2 = (2 * u[256:] - 1) / np.sqrt(32.0)
+    out = np.zeros(MLP_NPARAM, dtype=np.float32)
+    out[:256] = W1
+    out[288:288 + 1024] = W2
+    return out
