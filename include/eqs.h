@@ -102,6 +102,8 @@ typedef struct {
   int64_t launches;             /* kernels the step launched (graph kernel
                                    nodes outside loops + loop-body kernel
                                    nodes x CG iterations)                    */
+  int guess_kept;               /* solves that started from the learned guess
+                                   (EQS_GUESS_MLP; else 0)                   */
 } eqs_step_stats;
 
 /* Fill *o with the defaults (precision FP64, theta 0.08, coarse_max 500,
@@ -193,6 +195,45 @@ eqs_status eqs_amg_info(const eqs_ctx* ctx, int* n_levels, int64_t* rows, int64_
 /* Aggregate index of every row of AMG level `level` (host, rows[level]
  * int32 entries), for checking the setup. */
 eqs_status eqs_amg_aggregates(const eqs_ctx* ctx, int level, int32_t* agg_out);
+
+/* ---- Learned start vector (Sec. IV estimates start vectors from earlier
+ * solutions; the per-node network is an addition without counterpart in the
+ * paper).  Inputs at a free node: its last four M-solve solutions h1..h4
+ * and their means over the free mesh neighbours, divided by the RMS s_h of
+ * h1; network 8 -> 32 -> 32 -> 1 with exact-erf GELU, BF16 weights, FP32
+ * accumulation; start vector z0 = h1 + s_h * output.  In EQS_GUESS_MLP mode
+ * each solve starts from z0 unless ||R - M h1|| < ||R - M z0||. */
+
+/* Select the start vector of the stage solves (an eqs_guess_mode value). */
+eqs_status eqs_set_guess(eqs_ctx* ctx, int mode);
+
+/* Set / read the 1377 FP32 master parameters, packed as W1 (32x8 row-major),
+ * b1 (32), W2 (32x32), b2 (32), w3 (32), b3 (host arrays).  Setting resets
+ * the Adam state. */
+eqs_status eqs_guess_set_params(eqs_ctx* ctx, const float* theta, int n);
+eqs_status eqs_guess_get_params(eqs_ctx* ctx, float* theta, int n);
+
+/* Record the next `capacity` stage solutions of eqs_rkc_step (device, FP32)
+ * as training data; 0 stops recording and frees the record.  Restarts the
+ * solution history. */
+eqs_status eqs_guess_record(eqs_ctx* ctx, int64_t capacity);
+
+/* Train on the recorded solutions: `iters` Adam steps (learning rate lr) on
+ * mini-batches of `batch` (solve, node) samples drawn on the device from the
+ * splitmix64 stream `seed`; target (z - h1)/s_h, MSE loss.  loss_first /
+ * loss_last (host, nullable) receive the first and last mini-batch losses. */
+eqs_status eqs_guess_train(eqs_ctx* ctx, int iters, int batch, float lr, uint64_t seed,
+                           float* loss_first, float* loss_last);
+
+/* Gradient of the mini-batch MSE loss for given normalised inputs X (host,
+ * B x 8) and targets T (host, B) with the current BF16 weights: grad (host,
+ * 1377), loss (host, nullable).  For checking the training kernel. */
+eqs_status eqs_guess_grad(eqs_ctx* ctx, const float* X, const float* T, int B, float* grad,
+                          float* loss);
+
+/* z0 of the network for the history H (device, 4 x n_free doubles: h1 first)
+ * into z0 (device, n_free doubles); synchronises. */
+eqs_status eqs_guess_eval(eqs_ctx* ctx, const double* H, double* z0);
 
 /* Release everything owned by ctx (NULL is accepted). */
 eqs_status eqs_destroy(eqs_ctx* ctx);

@@ -71,7 +71,7 @@ struct HostLevel {
 // Per-solve reduction scalars (device).
 struct PcgScalars {
   double bnorm2, rnorm2, rz, rz_old, zr_prev, pq, alpha, beta;
-  int it, conv, parity, pad1;  // parity: which search-direction buffer is current
+  int it, conv, parity, use_prev;  // use_prev: the previous solution replaced the learned guess
 };
 
 struct StepParams {  // device-resident per-call parameters
@@ -175,6 +175,28 @@ struct eqs_ctx {
   double* d_g = nullptr;             // drive g(t_j) at the stage times
   double* d_gp = nullptr;            // drive derivative g'(t_j)
   eqs::ReduceScratch red;
+
+  // ---- learned start vector (mlp.cu)
+  int32_t* d_adj_ptr = nullptr;      // free-node graph (mesh edges), CSR
+  int32_t* d_adj_col = nullptr;
+  float* d_inv_deg = nullptr;
+  float* d_theta = nullptr;          // FP32 master parameters (1377)
+  void* d_theta_bf16 = nullptr;      // BF16 copy used by the kernels
+  float* d_adam_m = nullptr;
+  float* d_adam_v = nullptr;
+  float* d_grad = nullptr;
+  float* d_loss = nullptr;
+  int64_t adam_t = 0;
+  float* d_ring = nullptr;           // 4 x n_free history of solutions (FP32)
+  long long* d_stepcount = nullptr;  // steps since the history was reset
+  double* d_sh = nullptr;            // RMS of h1 (scale of the features)
+  int* d_mlp_used = nullptr;         // per stage: 1 if the network's guess was kept
+  float* d_store = nullptr;          // recorded solutions (capacity x n_free)
+  float* d_store_rms = nullptr;
+  int64_t store_cap = 0, recorded = 0;
+  bool recording = false;
+  double* d_rtmp = nullptr;          // residual of the fallback start vector
+  bool mlp_ready = false;
 
   std::map<std::pair<int, uintptr_t>, eqs::GraphEntry> step_graphs;  // key: (s, x)
   const eqs::GraphEntry* last_step = nullptr;                       // graph of the last step

@@ -365,6 +365,75 @@ __global__ void k_pcg_init(DevSell<double> M, int n, const double* __restrict__ 
   }
 }
 
+// Start from the learned guess x unless the previous solution h1 has the
+// smaller residual: r = R - M x, rtmp = R - M h1, norms of R, r, rtmp; the
+// last block records the choice (sc->use_prev) and sets the loop condition.
+template <typename T>
+__global__ void k_pcg_init_dual(DevSell<double> M, int n, const double* __restrict__ R,
+                                const double* __restrict__ x, const double* __restrict__ h1,
+                                double* __restrict__ r, double* __restrict__ rtmp,
+                                const T* __restrict__ dinv0, T inv_theta0, T* __restrict__ b0,
+                                T* __restrict__ x0, T* __restrict__ d0, PcgScalars* sc,
+                                double* partials, unsigned int* counter, int max_blocks, double tol2,
+                                int maxit, cudaGraphConditionalHandle h, int use_handle,
+                                int* iters_out, double* relres_out, int* zero_out, int* kept_out) {
+  pdl_enter();
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double Ri = R[i];
+    const double r1 = Ri - mat_row<double>(M, i, n, x);
+    const double r2 = Ri - mat_row<double>(M, i, n, h1);
+    r[i] = r1;
+    rtmp[i] = r2;
+    const T bi = (T)r1;
+    b0[i] = bi;
+    const T d = dinv0[i] * bi * inv_theta0;
+    x0[i] = d;
+    d0[i] = d;
+    v[0] += Ri * Ri;
+    v[1] += r1 * r1;
+    v[2] += r2 * r2;
+  }
+  double tot[3];
+  if (grid_sum<3>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    const int prev = tot[2] < tot[1];
+    const double rn = prev ? tot[2] : tot[1];
+    sc->bnorm2 = tot[0];
+    sc->rnorm2 = rn;
+    sc->it = 0;
+    sc->parity = 0;
+    sc->use_prev = prev;
+    const int zero = tot[0] == 0.0;
+    const int go = !zero && rn > tol2 * tot[0] && maxit > 0;
+    sc->conv = !go;
+    if (use_handle) cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = zero ? 0.0 : sqrt(rn / tot[0]);
+    if (zero_out) *zero_out = zero;
+    if (kept_out) *kept_out = !prev;
+  }
+}
+
+// Fallback of k_pcg_init_dual: x = h1, r = rtmp and the V-cycle input.
+template <typename T>
+__global__ void k_pcg_select(int n, double* __restrict__ x, const double* __restrict__ h1,
+                             double* __restrict__ r, const double* __restrict__ rtmp,
+                             const T* __restrict__ dinv0, T inv_theta0, T* __restrict__ b0,
+                             T* __restrict__ x0, T* __restrict__ d0, const PcgScalars* sc) {
+  pdl_enter();
+  if (!sc->use_prev) return;
+  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = h1[i];
+    const double ri = rtmp[i];
+    r[i] = ri;
+    const T bi = (T)ri;
+    b0[i] = bi;
+    const T d = dinv0[i] * bi * inv_theta0;
+    x0[i] = d;
+    d0[i] = d;
+  }
+}
+
 // z (from the V-cycle, in T) to FP64, r.z and r_prev.z; the last block forms
 // beta (Fletcher-Reeves, or Polak-Ribiere when flexible).
 template <typename T>
@@ -589,9 +658,13 @@ __device__ __forceinline__ float2 split2(double v) {
 // gp[j] = V0 w cos(w t_j + phase), t_j = t + c_j dt, j = 0..s.
 __global__ void k_stage_scalars(int s1, const double* __restrict__ cj, const StepParams* prm,
                                 double V0, double w, double phase, double* __restrict__ g,
-                                double* __restrict__ gp) {
+                                double* __restrict__ gp, long long* stepcount) {
   pdl_enter();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j == 0) {  // [0]: index of this step in the solution history, [1]: next
+    stepcount[0] = stepcount[1];
+    stepcount[1] += 1;
+  }
   if (j >= s1) return;
   const double tj = prm->t + cj[j] * prm->dt;
   const double a = w * tj + phase;
@@ -638,12 +711,19 @@ __global__ void k_recurrence(int n, int nf, double c0, double mu, double nu, dou
                              const double* __restrict__ gpj, const double* __restrict__ mtop,
                              double* __restrict__ Yj, float2* __restrict__ Y32,
                              double* __restrict__ Fguess, double* __restrict__ R,
-                             double* __restrict__ xmesh, const int32_t* __restrict__ node_of_internal) {
+                             double* __restrict__ xmesh, const int32_t* __restrict__ node_of_internal,
+                             float* __restrict__ ring, const long long* __restrict__ stepcount, int s,
+                             float* __restrict__ store, long long store_cap) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double v;
   if (i < nf) {
+    // F_{j-1} enters the solution history (ring slot g % 4; recorded copy)
+    const long long gidx = stepcount[0] * (long long)s + jm1;
+    const float f32 = (float)Fjm1[i];
+    ring[(size_t)(gidx & 3) * nf + i] = f32;
+    if (store && gidx < store_cap) store[(size_t)gidx * nf + i] = f32;
     const double dt = prm->dt;
     const double fj = zero_flags[jm1] ? 0.0 : Fjm1[i];
     const double f0 = zero_flags[0] ? 0.0 : F0[i];

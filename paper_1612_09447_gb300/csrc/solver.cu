@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "mlp_kernels.cuh"
 
 using namespace eqs;
 
@@ -296,13 +297,21 @@ struct SolveSlots {
 template <typename T>
 static void pcg_init_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st,
                             const double* R, double* x, double tol2, cudaGraphConditionalHandle h,
-                            int use_handle, SolveSlots sl) {
+                            int use_handle, SolveSlots sl, const double* h1 = nullptr,
+                            int* kept = nullptr) {
   DevLevel<T>& V = L[0];
   const int n = (int)c->n_free;
+  if (h1) {  // learned start vector with the previous solution as fallback
+    launch(k_pcg_init_dual<T>, vec_grid(c, n), kBlock, st, c->M64, n, R, x, h1, c->d_r, c->d_rtmp, V.dinv,
+           (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials, c->red.counter,
+           c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres, sl.zero, kept);
+    launch(k_pcg_select<T>, vec_grid(c, n), kBlock, st, n, x, h1, c->d_r, c->d_rtmp, V.dinv,
+           (T)V.inv_theta, V.b, V.x, V.dA, (const PcgScalars*)c->d_sc);
+    return;
+  }
   launch(k_pcg_init<T>, vec_grid(c, n), kBlock, st, c->M64, n, R, x, c->d_r, V.dinv, (T)V.inv_theta, V.b, V.x,
-                                            V.dA, c->d_sc, c->red.partials, c->red.counter,
-                                            c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle,
-                                            sl.iters, sl.relres, sl.zero);
+         V.dA, c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h,
+         use_handle, sl.iters, sl.relres, sl.zero);
 }
 
 template <typename T>
@@ -341,7 +350,7 @@ static int64_t count_kernel_nodes(cudaGraph_t g) {
 // c->cap_stream; the loop body is captured on c->cap_stream2.
 template <typename T>
 static eqs_status pcg_capture(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* R, double* x,
-                              double tol2, SolveSlots sl) {
+                              double tol2, SolveSlots sl, const double* h1 = nullptr, int* kept = nullptr) {
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -349,7 +358,7 @@ static eqs_status pcg_capture(eqs_ctx* c, std::vector<DevLevel<T>>& L, const dou
   CK(cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphConditionalHandle h;
   CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
-  pcg_init_launch<T>(c, L, c->cap_stream, R, x, tol2, h, 1, sl);
+  pcg_init_launch<T>(c, L, c->cap_stream, R, x, tol2, h, 1, sl, h1, kept);
   CK(cudaGetLastError());
   CK(cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
@@ -451,9 +460,9 @@ static eqs_status persistent_launch(eqs_ctx* c, cudaStream_t st, const double* R
 
 template <typename T>
 static eqs_status solve_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* R, double* x,
-                               double tol2, SolveSlots sl) {
-  if (c->opts.persistent) return persistent_launch<T>(c, c->cap_stream, R, x, tol2, sl);
-  return pcg_capture<T>(c, L, R, x, tol2, sl);
+                               double tol2, SolveSlots sl, const double* h1 = nullptr, int* kept = nullptr) {
+  if (c->opts.persistent && !h1) return persistent_launch<T>(c, c->cap_stream, R, x, tol2, sl);
+  return pcg_capture<T>(c, L, R, x, tol2, sl, h1, kept);
 }
 
 static bool mixed(const eqs_ctx* c) { return c->opts.precision == EQS_PREC_MIXED; }
@@ -485,7 +494,8 @@ static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
   const double w = 2.0 * M_PI * c->freq;
   cudaStream_t st = c->cap_stream;
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-  launch(k_stage_scalars, 1, 64, st, s + 1, ge.d_cj, c->d_params, c->V0, w, c->phase, c->d_g, c->d_gp);
+  launch(k_stage_scalars, 1, 64, st, s + 1, ge.d_cj, c->d_params, c->V0, w, c->phase, c->d_g, c->d_gp,
+         c->d_stepcount);
   const bool mx = mixed(c);
   launch(k_gather_state, nblk(n), kBlock, st, n, nf, xdev, c->d_node_of_internal, c->d_dir_scale, c->d_g,
                                              c->d_gp, c->d_mtop, Ybuf(c, 0), mx ? c->d_Y32 : nullptr,
@@ -501,7 +511,8 @@ static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
           Ybuf(c, 0), Ybuf(c, j - 1), Ybuf(c, j >= 2 ? j - 2 : 0), Fbuf(c, j - 1), Fbuf(c, 0), c->d_zero,
           j - 1, c->d_dir_scale, c->d_g + j, c->d_gp + j, c->d_mtop, Ybuf(c, j),
           (mx && !last) ? c->d_Y32 : nullptr, last ? nullptr : Fbuf(c, j),
-          (mx || last) ? nullptr : c->d_R, last ? xdev : nullptr, c->d_node_of_internal);
+          (mx || last) ? nullptr : c->d_R, last ? xdev : nullptr, c->d_node_of_internal, c->d_ring,
+          (const long long*)c->d_stepcount, s, c->recording ? c->d_store : nullptr, (long long)c->store_cap);
       if (last) break;
     }
     if (mx) {
@@ -511,7 +522,20 @@ static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
       elem_launch(c, st, Ybuf(c, j), nf, c->d_R, nullptr);
     }
     SolveSlots sl{c->d_iters + j, c->d_relres + j, c->d_zero + j};
-    stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl);
+    if (c->opts.guess == EQS_GUESS_MLP) {
+      const double* h1 = Fbuf(c, j == 0 ? s - 1 : j - 1);
+      launch(k_rms, vec_grid(c, nf), kBlock, st, nf, h1, c->d_sh, c->red.partials, c->red.counter,
+             c->red.max_blocks);
+      launch(k_mlp_guess, std::max(1, std::min(nblk(nf), 4 * c->sms)), kBlock, st, nf, h1,
+             (const float*)c->d_ring, (const long long*)c->d_stepcount, s, j, (const int32_t*)c->d_adj_ptr,
+             (const int32_t*)c->d_adj_col, (const float*)c->d_inv_deg,
+             (const __nv_bfloat16*)c->d_theta_bf16, (const double*)c->d_sh, Fbuf(c, j));
+      stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, h1, c->d_mlp_used + j);
+    } else {
+      if (c->opts.guess == EQS_GUESS_ZERO && cudaMemsetAsync(Fbuf(c, j), 0, nf * sizeof(double), st) != cudaSuccess)
+        stt = fail(c, EQS_ERR_CUDA, "cudaMemsetAsync failed during capture");
+      stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl);
+    }
   }
   cudaError_t le = cudaGetLastError();
   cudaGraph_t graph = nullptr;
@@ -765,6 +789,42 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     const eqs_status ps = mixed(c) ? build_plan(c, c->lev32) : build_plan(c, c->lev64);
     if (ps != EQS_OK) return ps;
   }
+  // learned start vector: free-node graph from the pattern of M_ff, network
+  // state (zero parameters = previous-solution guess), history ring
+  {
+    std::vector<int32_t> aptr(nf + 1, 0), acol;
+    std::vector<float> ideg(nf, 0.f);
+    acol.reserve(Mff.nnz());
+    for (int64_t i = 0; i < nf; ++i) {
+      for (int64_t k = Mff.ptr[i]; k < Mff.ptr[i + 1]; ++k)
+        if (Mff.col[k] != i) acol.push_back(Mff.col[k]);
+      aptr[i + 1] = (int32_t)acol.size();
+      const int deg = aptr[i + 1] - aptr[i];
+      ideg[i] = deg > 0 ? 1.0f / (float)deg : 0.0f;
+    }
+    CK(upload(c, &c->d_adj_ptr, aptr.data(), aptr.size()));
+    CK(upload(c, &c->d_adj_col, acol.data(), std::max<size_t>(acol.size(), 1)));
+    CK(upload(c, &c->d_inv_deg, ideg.data(), ideg.size()));
+    CK(dalloc(c, &c->d_theta, kNP));
+    __nv_bfloat16* wb = nullptr;
+    CK(dalloc(c, &wb, kNP));
+    c->d_theta_bf16 = wb;
+    CK(dalloc(c, &c->d_adam_m, kNP));
+    CK(dalloc(c, &c->d_adam_v, kNP));
+    CK(dalloc(c, &c->d_grad, kNP));
+    CK(dalloc(c, &c->d_loss, 1));
+    CK(dalloc(c, &c->d_ring, 4 * (size_t)nf));
+    CK(dalloc(c, &c->d_stepcount, 2));
+    CK(dalloc(c, &c->d_sh, 1));
+    CK(dalloc(c, &c->d_mlp_used, EQS_MAX_STAGES + 1));
+    CK(dalloc(c, &c->d_rtmp, nf));
+    c->adam_t = 0;
+    c->d_store = nullptr;
+    c->d_store_rms = nullptr;
+    c->store_cap = 0;
+    c->recorded = 0;
+    c->recording = false;
+  }
   CK(cudaDeviceSynchronize());
   c->setup_done = true;
   return EQS_OK;
@@ -869,6 +929,7 @@ eqs_status eqs_rkc_step(eqs_ctx* c, double* x, double t, double dt, int s, eqs_s
   CK(cudaMemcpyAsync(c->d_params, &prm, sizeof(prm), cudaMemcpyHostToDevice, c->stream));
   CK(cudaGraphLaunch(it->second.exec, c->stream));
   c->last_step = &it->second;
+  if (c->recording) c->recorded = std::min<int64_t>(c->recorded + s, c->store_cap);
   if (!stats) return EQS_OK;
   return eqs_get_step_stats(c, stats);
 }
@@ -895,6 +956,11 @@ eqs_status eqs_get_step_stats(eqs_ctx* c, eqs_step_stats* stats) {
     else if (rr[j] > c->opts.rtol && res == EQS_OK) res = EQS_ERR_NOCONV;
   }
   stats->launches = c->last_step->fixed_kernels + c->last_step->per_iter_kernels * stats->total_iters;
+  if (c->opts.guess == EQS_GUESS_MLP) {
+    int kept[EQS_MAX_STAGES];
+    CK(cudaMemcpy(kept, c->d_mlp_used, s * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int j = 0; j < s; ++j) stats->guess_kept += kept[j];
+  }
   if (c->d_bar) {
     GridBarrier b;
     CK(cudaMemcpy(&b, c->d_bar, sizeof(b), cudaMemcpyDeviceToHost));
@@ -948,6 +1014,156 @@ eqs_status eqs_amg_aggregates(const eqs_ctx* c, int level, int32_t* agg_out) {
   if (!agg_out || level < 0 || level + 1 >= (int)c->hlev.size())
     return fail(const_cast<eqs_ctx*>(c), EQS_ERR_ARG, "level has no aggregates");
   std::memcpy(agg_out, c->hlev[level].agg.data(), c->hlev[level].agg.size() * sizeof(int32_t));
+  return EQS_OK;
+}
+
+eqs_status eqs_set_guess(eqs_ctx* c, int mode) {
+  REQUIRE_SETUP(c);
+  if (mode != EQS_GUESS_PREV && mode != EQS_GUESS_MLP && mode != EQS_GUESS_ZERO)
+    return fail(c, EQS_ERR_ARG, "unknown guess mode");
+  if (mode != c->opts.guess) destroy_graphs(c);
+  c->opts.guess = mode;
+  return EQS_OK;
+}
+
+eqs_status eqs_guess_set_params(eqs_ctx* c, const float* theta, int n) {
+  REQUIRE_SETUP(c);
+  if (!theta || n != kNP) return fail(c, EQS_ERR_ARG, "expected 1377 parameters");
+  for (int k = 0; k < n; ++k)
+    if (!std::isfinite(theta[k])) return fail(c, EQS_ERR_NAN, "non-finite network parameter");
+  CK(cudaMemcpyAsync(c->d_theta, theta, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  k_to_bf16<<<nblk(kNP), kBlock, 0, c->stream>>>(kNP, c->d_theta, (__nv_bfloat16*)c->d_theta_bf16);
+  CK(cudaMemsetAsync(c->d_adam_m, 0, kNP * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(c->d_adam_v, 0, kNP * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(c->d_grad, 0, kNP * sizeof(float), c->stream));
+  c->adam_t = 0;
+  CK(cudaStreamSynchronize(c->stream));
+  return EQS_OK;
+}
+
+eqs_status eqs_guess_get_params(eqs_ctx* c, float* theta, int n) {
+  REQUIRE_SETUP(c);
+  if (!theta || n != kNP) return fail(c, EQS_ERR_ARG, "expected 1377 parameters");
+  CK(cudaMemcpyAsync(theta, c->d_theta, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return EQS_OK;
+}
+
+eqs_status eqs_guess_record(eqs_ctx* c, int64_t capacity) {
+  REQUIRE_SETUP(c);
+  if (capacity < 0) return fail(c, EQS_ERR_ARG, "negative capacity");
+  destroy_graphs(c);  // the record target is part of the step graphs
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->d_store) {
+    for (auto it = c->allocs.begin(); it != c->allocs.end();)
+      if (*it == c->d_store || *it == c->d_store_rms) {
+        cudaFree(*it);
+        it = c->allocs.erase(it);
+      } else {
+        ++it;
+      }
+    c->d_store = nullptr;
+    c->d_store_rms = nullptr;
+  }
+  c->store_cap = 0;
+  c->recording = false;
+  c->recorded = 0;
+  if (capacity == 0) return EQS_OK;
+  CK(dalloc(c, &c->d_store, (size_t)capacity * (size_t)c->n_free, false));
+  CK(dalloc(c, &c->d_store_rms, (size_t)capacity));
+  CK(cudaMemset(c->d_stepcount, 0, 2 * sizeof(long long)));  // history index restarts at 0
+  c->store_cap = capacity;
+  c->recording = true;
+  return EQS_OK;
+}
+
+static eqs_status train_batch(eqs_ctx* c, int count, int B, unsigned long long seed, long long step,
+                              const float* X, const float* T) {
+  const int S = kTrainBlock + 1;
+  const size_t smem = sizeof(float) * (kNP + 3 + (size_t)S * (8 + 32 * 4 + 1));
+  CK(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_mlp_train<<<nblk(B, kTrainBlock), kTrainBlock, smem, c->stream>>>(
+      (int)c->n_free, c->d_store, c->d_store_rms, count, c->d_adj_ptr, c->d_adj_col, c->d_inv_deg,
+      (const __nv_bfloat16*)c->d_theta_bf16, c->d_grad, c->d_loss, seed, step, B, X, T);
+  CK(cudaGetLastError());
+  return EQS_OK;
+}
+
+eqs_status eqs_guess_train(eqs_ctx* c, int iters, int batch, float lr, uint64_t seed, float* loss_first,
+                           float* loss_last) {
+  REQUIRE_SETUP(c);
+  if (iters < 1 || batch < 1 || !(lr > 0)) return fail(c, EQS_ERR_ARG, "bad training arguments");
+  if (c->recorded < 5) return fail(c, EQS_ERR_STATE, "record at least 5 solutions first");
+  CK(cudaStreamSynchronize(c->stream));
+  const int count = (int)c->recorded;
+  k_store_rms<<<count, kBlock, 0, c->stream>>>((int)c->n_free, c->d_store, c->d_store_rms);
+  float lf = 0.f, ll = 0.f;
+  for (int it = 0; it < iters; ++it) {
+    CK(cudaMemsetAsync(c->d_loss, 0, sizeof(float), c->stream));
+    const eqs_status st = train_batch(c, count, batch, seed, it, nullptr, nullptr);
+    if (st != EQS_OK) return st;
+    c->adam_t += 1;
+    const float bc1 = 1.0f - std::pow(0.9f, (float)c->adam_t);
+    const float bc2 = 1.0f - std::pow(0.999f, (float)c->adam_t);
+    k_adam<<<nblk(kNP), kBlock, 0, c->stream>>>(c->d_theta, c->d_adam_m, c->d_adam_v, c->d_grad,
+                                                (__nv_bfloat16*)c->d_theta_bf16, lr, bc1, bc2);
+    if (it == 0 || it == iters - 1) {
+      float l = 0.f;
+      CK(cudaMemcpyAsync(&l, c->d_loss, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      (it == 0 ? lf : ll) = l;
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (loss_first) *loss_first = lf;
+  if (loss_last) *loss_last = ll;
+  return EQS_OK;
+}
+
+eqs_status eqs_guess_grad(eqs_ctx* c, const float* X, const float* T, int B, float* grad, float* loss) {
+  REQUIRE_SETUP(c);
+  if (!X || !T || !grad || B < 1) return fail(c, EQS_ERR_ARG, "bad gradient arguments");
+  float *dX = nullptr, *dT = nullptr;
+  CK(cudaMalloc(&dX, (size_t)B * 8 * sizeof(float)));
+  CK(cudaMalloc(&dT, (size_t)B * sizeof(float)));
+  cudaMemcpy(dX, X, (size_t)B * 8 * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(dT, T, (size_t)B * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemset(c->d_grad, 0, kNP * sizeof(float));
+  cudaMemset(c->d_loss, 0, sizeof(float));
+  eqs_status st = train_batch(c, 5, B, 0ull, 0, dX, dT);
+  if (st == EQS_OK) {
+    cudaError_t e = cudaMemcpy(grad, c->d_grad, kNP * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && loss) e = cudaMemcpy(loss, c->d_loss, sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(c->d_grad, 0, kNP * sizeof(float));
+    if (e != cudaSuccess) st = fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
+  }
+  cudaFree(dX);
+  cudaFree(dT);
+  return st;
+}
+
+eqs_status eqs_guess_eval(eqs_ctx* c, const double* H, double* z0) {
+  REQUIRE_SETUP(c);
+  if (!H || !z0) return fail(c, EQS_ERR_ARG, "null vector");
+  const int nf = (int)c->n_free;
+  cudaStream_t st = c->stream;
+  float* ring = nullptr;
+  long long* cnt = nullptr;
+  CK(cudaMalloc(&ring, 4 * (size_t)nf * sizeof(float)));
+  CK(cudaMalloc(&cnt, 2 * sizeof(long long)));
+  // solve index g = 4: h_l (l = 1..4) goes to slot (4 - l) % 4
+  for (int l = 0; l < 4; ++l)
+    k_push_solution<<<nblk(nf), kBlock, 0, st>>>(nf, H + (size_t)l * nf, ring + (size_t)((3 - l) & 3) * nf);
+  const long long four[2] = {4, 5};
+  cudaMemcpyAsync(cnt, four, sizeof(four), cudaMemcpyHostToDevice, st);
+  k_rms<<<vec_grid(c, nf), kBlock, 0, st>>>(nf, H, c->d_sh, c->red.partials, c->red.counter,
+                                           c->red.max_blocks);
+  k_mlp_guess<<<nblk(nf), kBlock, 0, st>>>(nf, H, ring, cnt, 1, 0, c->d_adj_ptr, c->d_adj_col, c->d_inv_deg,
+                                         (const __nv_bfloat16*)c->d_theta_bf16, c->d_sh, z0);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(ring);
+  cudaFree(cnt);
+  if (e != cudaSuccess) return fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
   return EQS_OK;
 }
 

@@ -43,7 +43,7 @@ class eqs_opts(C.Structure):
 class eqs_step_stats(C.Structure):
     _fields_ = [("s", C.c_int), ("total_iters", C.c_int), ("max_iters", C.c_int),
                 ("iters", C.c_int * EQS_MAX_STAGES), ("max_relres", C.c_double),
-                ("status", C.c_int), ("launches", C.c_int64)]
+                ("status", C.c_int), ("launches", C.c_int64), ("guess_kept", C.c_int)]
 
 
 _lib = None
@@ -79,6 +79,13 @@ def _declare(L):
         "eqs_get_sizes": (I, [P, P, P, P]),
         "eqs_amg_info": (I, [P, P, P, P]),
         "eqs_amg_aggregates": (I, [P, I, P]),
+        "eqs_set_guess": (I, [P, I]),
+        "eqs_guess_set_params": (I, [P, P, I]),
+        "eqs_guess_get_params": (I, [P, P, I]),
+        "eqs_guess_record": (I, [P, I64]),
+        "eqs_guess_train": (I, [P, I, I, C.c_float, C.c_uint64, P, P]),
+        "eqs_guess_grad": (I, [P, P, P, I, P, P]),
+        "eqs_guess_eval": (I, [P, P, P]),
         "eqs_destroy": (I, [P]),
         "eqs_last_error": (C.c_char_p, [P]),
     }
@@ -197,6 +204,44 @@ def eqs_amg_aggregates(ctx, level, n_rows):
     out = np.empty(n_rows, dtype=np.int32)
     _check(lib().eqs_amg_aggregates(ctx, level, out.ctypes.data_as(C.c_void_p)), ctx)
     return out
+
+
+def eqs_set_guess(ctx, mode):
+    _check(lib().eqs_set_guess(ctx, mode), ctx)
+
+
+def eqs_guess_set_params(ctx, theta):
+    th, pth = _host(theta, np.float32)
+    _check(lib().eqs_guess_set_params(ctx, pth, len(th)), ctx)
+
+
+def eqs_guess_get_params(ctx):
+    out = np.empty(1377, dtype=np.float32)
+    _check(lib().eqs_guess_get_params(ctx, out.ctypes.data_as(C.c_void_p), len(out)), ctx)
+    return out
+
+
+def eqs_guess_record(ctx, capacity):
+    _check(lib().eqs_guess_record(ctx, int(capacity)), ctx)
+
+
+def eqs_guess_train(ctx, iters, batch, lr, seed):
+    lf, ll = C.c_float(), C.c_float()
+    _check(lib().eqs_guess_train(ctx, iters, batch, lr, seed, C.byref(lf), C.byref(ll)), ctx)
+    return lf.value, ll.value
+
+
+def eqs_guess_grad(ctx, X, T):
+    X, pX = _host(X, np.float32)
+    T, pT = _host(T, np.float32)
+    g = np.empty(1377, dtype=np.float32)
+    loss = C.c_float()
+    _check(lib().eqs_guess_grad(ctx, pX, pT, len(T), g.ctypes.data_as(C.c_void_p), C.byref(loss)), ctx)
+    return g, loss.value
+
+
+def eqs_guess_eval(ctx, H, z0):
+    _check(lib().eqs_guess_eval(ctx, _dev(H), _dev(z0)), ctx)
 
 
 def eqs_destroy(ctx):
