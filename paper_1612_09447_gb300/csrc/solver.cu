@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -600,6 +601,36 @@ static eqs_status vcycle_impl(eqs_ctx* c, std::vector<DevLevel<T>>& L, const dou
   return EQS_OK;
 }
 
+// ----------------------------------------------- allocation-free K(x)x
+// Scratch of eqs_apply_K_static: three regions of 8 bytes per node (the
+// gathered potential, its two-float copy, the accumulated result), for at most
+// kStaticMaxNodes nodes.  It lives in the module's static device memory, so
+// every GPU that loads the library holds these 12 MiB until the process exits.
+constexpr int64_t kStaticMaxNodes = 524288;
+static __device__ __align__(256) unsigned char g_static_scratch[3 * 8 * kStaticMaxNodes];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_ptr[256] = {};  // device address of g_static_scratch, per device
+}  // namespace
+
+// Host code cannot use g_static_scratch's address directly (in host code the
+// name is a host-side stand-in); look up the device address once per device,
+// with that device current.
+static eqs_status static_scratch(eqs_ctx* c, int dev, unsigned char** out) {
+  if (dev < 0 || dev >= 256) return fail(c, EQS_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess)
+      return fail(c, EQS_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+    g_static_ptr[dev] = p;
+  }
+  *out = (unsigned char*)g_static_ptr[dev];
+  return EQS_OK;
+}
+
 // ================================================================ C ABI
 extern "C" {
 
@@ -852,6 +883,42 @@ eqs_status eqs_apply_K(eqs_ctx* c, const double* x, double* y) {
     CK(cudaMemsetAsync(c->d_tmpn2, 0, n * sizeof(double), st));
     elem_launch(c, st, c->d_tmpn, n, c->d_tmpn2, nullptr);
     launch(k_scatter_perm, nblk(n), kBlock, st, n, c->d_tmpn2, nullptr, c->d_node_of_internal, y);
+  }
+  CK(cudaGetLastError());
+  return EQS_OK;
+}
+
+eqs_status eqs_apply_K_static(eqs_ctx* c, const double* x, double* y) {
+  if (!c) return fail(nullptr, EQS_ERR_ARG, "ctx is NULL");
+  if (!x || !y) return fail(c, EQS_ERR_ARG, "null vector");
+  if (c->n_nodes > kStaticMaxNodes)
+    return fail(c, EQS_ERR_ARG, "eqs_apply_K_static: mesh has " + std::to_string(c->n_nodes) +
+                                    " nodes, the static scratch holds at most " +
+                                    std::to_string(kStaticMaxNodes) + "; use eqs_apply_K");
+  if (!c->setup_done) return fail(c, EQS_ERR_STATE, "call eqs_amg_setup first");
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != c->device) return fail(c, EQS_ERR_ARG, "make the context's device current");
+  unsigned char* base = nullptr;
+  const eqs_status ss = static_scratch(c, dev, &base);
+  if (ss != EQS_OK) return ss;
+  const int n = (int)c->n_nodes;
+  double* xg = (double*)base;                            // region 0: gathered potential
+  float2* x2 = (float2*)(base + 8 * kStaticMaxNodes);    // region 1: two-float copy
+  unsigned char* yacc = base + 16 * kStaticMaxNodes;     // region 2: accumulated K(x)x
+  cudaStream_t st = c->stream;
+  const bool mx = mixed(c);
+  k_gather_perm<<<nblk(n), kBlock, 0, st>>>(n, x, c->d_node_of_internal, xg, mx ? x2 : nullptr);
+  // the accumulator keeps the previous call's contents: clear it
+  CK(cudaMemsetAsync(yacc, 0, (size_t)n * (mx ? sizeof(float) : sizeof(double)), st));
+  if (mx) {
+    k_elem32<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn, c->d_mat, c->d_mats, c->d_xyz_hi,
+                                                 c->d_xyz_lo, x2, n, (float*)yacc);
+    k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, nullptr, (const float*)yacc, c->d_node_of_internal, y);
+  } else {
+    k_elem64<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn, c->d_mat, c->d_mats, c->d_xyz, xg, n,
+                                                 1.0, (double*)yacc);
+    k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, (const double*)yacc, nullptr, c->d_node_of_internal, y);
   }
   CK(cudaGetLastError());
   return EQS_OK;

@@ -69,6 +69,7 @@ def _declare(L):
         "eqs_set_dirichlet": (I, [P, D, D, D]),
         "eqs_amg_setup": (I, [P, C.POINTER(eqs_opts)]),
         "eqs_apply_K": (I, [P, P, P]),
+        "eqs_apply_K_static": (I, [P, P, P]),
         "eqs_solve_M": (I, [P, P, P, I, D, P]),
         "eqs_vcycle": (I, [P, P, P]),
         "eqs_spmv_M": (I, [P, P, P]),
@@ -149,6 +150,10 @@ def eqs_amg_setup(ctx, opts=None):
 
 def eqs_apply_K(ctx, x, y):
     _check(lib().eqs_apply_K(ctx, _dev(x), _dev(y)), ctx)
+
+
+def eqs_apply_K_static(ctx, x, y):
+    _check(lib().eqs_apply_K_static(ctx, _dev(x), _dev(y)), ctx)
 
 
 def eqs_solve_M(ctx, rhs, z, nrhs=1, rtol=0.0):
