@@ -38,6 +38,9 @@ CONFIG_INDEX = 1
 # smoothing and a 2066-row coarsest level (dense FP64 inverse) gave the
 # lowest step time on GB300 among degree 1-3 and coarse sizes 88/2066.
 SOLVER_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0)
+# DRAM bytes (read + write) of one k_spmv64 launch on this workload from an ncu
+# capture (profiles/k_spmv64_cube64.md); None until measured for this kernel.
+TRAFFIC_SPMV64 = None
 
 
 def parse():
@@ -49,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--N", type=int, default=None, help="override mesh size (testing)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the CG loops from the host (same kernels; for ncu launch lists)")
     return ap.parse_args()
 
 
@@ -193,7 +198,7 @@ def run_ours(args, rank, world):
         flushbuf.zero_()
 
     def measure(precision, steps, warmup):
-        solver = eqs.Solver(p, precision=precision, rtol=RTOL, **SOLVER_OPTS)
+        solver = eqs.Solver(p, precision=precision, rtol=RTOL, host_loop=int(args.host_loop), **SOLVER_OPTS)
         dt = solver.dt_bound(S_STAGES)
         x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
         t = 0.0
@@ -315,13 +320,16 @@ def dominant_kernel_roofline(torch, eqs, solver, p, flush):
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
     ms = statistics.median(ts[3:])
-    bytes_alg = nnz[0] * 12 + nf * 8 * 2 + (nf // 32 + 1) * 8
+    # algorithmic bytes of y = M_ff x: one FP64 value per stored non-zero plus
+    # x and y once per row (the layout needs no index loads: DIA storage)
+    bytes_alg = nnz[0] * 8 + nf * 8 * 2
     peak, kind = _peaks()
     ach = bytes_alg / (ms / 1e3) / 1e9
-    return {"kernel": "k_spmv64 (FP64 SELL-32 M_ff SpMV)", "bound": "hbm", "achieved": ach,
-            "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
-            "bytes_per_launch": bytes_alg, "ms_per_launch": ms,
-            "peak_kind": f"{kind} hbm_gbs (burst: kernel timed alone, L2 flushed)"}
+    return {"kernel": "k_spmv64 (FP64 DIA SpMV of M_ff, the operator of every CG iteration)",
+            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": TRAFFIC_SPMV64, "bytes_per_launch": bytes_alg, "ms_per_launch": ms,
+            "fp64_tflops": 2.0 * nnz[0] / (ms / 1e3) / 1e12,
+            "peak_kind": f"{kind} hbm_gbs (burst: kernel timed alone, L2 flushed before each launch)"}
 
 
 def main():

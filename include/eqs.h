@@ -87,6 +87,11 @@ typedef struct {
                           kernel (grid barriers); 0: one kernel per CG/V-cycle
                           phase inside a device-side graph loop               */
   int blocks_per_sm;   /* CTAs per SM of the persistent solve (0: 1)         */
+  int host_loop;       /* 1: eqs_rkc_step launches the same kernels directly
+                          and drives each CG loop from the host (reads the
+                          convergence flag after every iteration) instead of
+                          replaying a graph; for profilers that cannot enter
+                          graph loops.  Default 0.                            */
 } eqs_opts;
 
 #define EQS_MAX_STAGES 64

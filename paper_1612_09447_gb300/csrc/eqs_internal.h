@@ -197,6 +197,7 @@ struct eqs_ctx {
   bool recording = false;
   double* d_rtmp = nullptr;          // residual of the fallback start vector
   bool mlp_ready = false;
+  bool direct = false;               // enqueue_step launches directly (host-driven CG loop)
 
   std::map<std::pair<int, uintptr_t>, eqs::GraphEntry> step_graphs;  // key: (s, x)
   const eqs::GraphEntry* last_step = nullptr;                       // graph of the last step

@@ -31,16 +31,24 @@ template <typename T>
 __device__ __forceinline__ T mat_row(const DevSell<T>& A, int64_t tid, int n, const T* __restrict__ x) {
   const int row = (int)(tid >> A.logG);
   T acc = T(0);
-  if (A.G == 0) {  // DIA: independent, coalesced loads
+  if (A.G == 0) {  // DIA: independent, coalesced loads; two accumulation chains
     if (row >= n) return acc;
     const T* __restrict__ v = A.val + row;
-#pragma unroll 8
-    for (int d = 0; d < A.ndiag; ++d) {
+    T acc1 = T(0);
+    int d = 0;
+#pragma unroll 4
+    for (; d + 1 < A.ndiag; d += 2) {
+      const int j0 = row + A.off[d], j1 = row + A.off[d + 1];
+      const T a0 = __ldg(v + (int64_t)d * n), a1 = __ldg(v + (int64_t)(d + 1) * n);
+      if ((unsigned)j0 < (unsigned)A.n_cols) acc = fmadd(a0, __ldg(x + j0), acc);
+      if ((unsigned)j1 < (unsigned)A.n_cols) acc1 = fmadd(a1, __ldg(x + j1), acc1);
+    }
+    if (d < A.ndiag) {
       const int j = row + A.off[d];
       const T a = __ldg(v + (int64_t)d * n);
       if ((unsigned)j < (unsigned)A.n_cols) acc = fmadd(a, __ldg(x + j), acc);
     }
-    return acc;
+    return acc + acc1;
   }
   if (A.G == 1) {  // SELL-32: load a batch of indices, then the gathers
     if (row >= n) return acc;
@@ -303,8 +311,18 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, unsi
 #pragma unroll
     for (int k = 0; k < NV; ++k) partials[k * max_blocks + blockIdx.x] = v[k];
     __threadfence();
-    const unsigned int prev = atomicAdd(counter, 1u);
-    am_last = (prev == gridDim.x - 1);
+    // two-level ticket: blocks arrive on one of 8 group counters (counter[1..8]);
+    // the last block of each group arrives on counter[0]
+    const unsigned int grp = blockIdx.x & 7u;
+    const unsigned int in_grp = (gridDim.x - grp + 7u) / 8u;  // blocks with this residue
+    bool last = false;
+    if (atomicAdd(counter + 1 + grp, 1u) == in_grp - 1u) {
+      counter[1 + grp] = 0u;
+      __threadfence();  // order the group's arrivals before the main ticket
+      const unsigned int groups = gridDim.x < 8u ? gridDim.x : 8u;
+      last = atomicAdd(counter, 1u) == groups - 1u;
+    }
+    am_last = last;
   }
   __syncthreads();
   if (!am_last) return false;
@@ -467,13 +485,22 @@ __global__ void k_pcg_pq(DevSell<double> M, int n, const double* __restrict__ zd
   pdl_enter();
   const double beta = sc->beta;
   double v[1] = {0.0};
-  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double w = mat_row<double>(M, i, n, zd);
-    const double qi = beta == 0.0 ? w : fma(beta, q[i], w);
-    const double pi = beta == 0.0 ? zd[i] : fma(beta, p[i], zd[i]);
-    p[i] = pi;
-    q[i] = qi;
-    v[0] += pi * qi;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = gtid(); i0 < n; i0 += 2 * st) {  // two rows in flight per thread
+    const int64_t i1 = i0 + st;
+    const double w0 = mat_row<double>(M, i0, n, zd);
+    const double w1 = mat_row<double>(M, i1, n, zd);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t i = h ? i1 : i0;
+      if (i >= n) continue;
+      const double w = h ? w1 : w0;
+      const double qi = beta == 0.0 ? w : fma(beta, q[i], w);
+      const double pi = beta == 0.0 ? zd[i] : fma(beta, p[i], zd[i]);
+      p[i] = pi;
+      q[i] = qi;
+      v[0] += pi * qi;
+    }
   }
   double tot[1];
   if (grid_sum<1>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {

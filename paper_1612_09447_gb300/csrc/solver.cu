@@ -43,13 +43,16 @@ static inline int rows_grid(const eqs_ctx* c, int64_t lanes) {
   return std::max(1, std::min(nblk((lanes + 1) / 2), 4 * c->sms));
 }
 // Grid of a CG vector kernel (grid-stride, one reduction ticket per block).
-static inline int vec_grid(const eqs_ctx* c, int64_t n) { return std::max(1, std::min(nblk(n), 2 * c->sms)); }
+static inline int vec_grid(const eqs_ctx* c, int64_t n) { return std::max(1, std::min(nblk(n), 4 * c->sms)); }
 
 // Launch with programmatic dependent launch allowed (the kernels call
 // pdl_enter() before touching memory), so consecutive kernels of a stream or
 // graph overlap launch latency with the predecessor's tail.
+static thread_local int64_t g_launches = 0;  // kernels enqueued by launch() (host-loop steps)
+
 template <typename... KArgs, typename... Args>
 static void launch(void (*k)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+  ++g_launches;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
@@ -459,9 +462,28 @@ static eqs_status persistent_launch(eqs_ctx* c, cudaStream_t st, const double* R
   return EQS_OK;
 }
 
+// CG loop driven from the host (same kernels; the convergence flag is read
+// back after every iteration).  Used by the host-loop execution mode.
+template <typename T>
+static eqs_status pcg_direct(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* R, double* x,
+                             double tol2, SolveSlots sl, const double* h1, int* kept) {
+  cudaStream_t st = c->stream;
+  pcg_init_launch<T>(c, L, st, R, x, tol2, 0, 0, sl, h1, kept);
+  for (int it = 0; it < c->opts.max_iter; ++it) {
+    int conv = 0;
+    CK(cudaMemcpyAsync(&conv, &c->d_sc->conv, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (conv) break;
+    pcg_body_launch<T>(c, L, st, x, tol2, 0, 0, sl);
+  }
+  CK(cudaGetLastError());
+  return EQS_OK;
+}
+
 template <typename T>
 static eqs_status solve_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* R, double* x,
                                double tol2, SolveSlots sl, const double* h1 = nullptr, int* kept = nullptr) {
+  if (c->direct) return pcg_direct<T>(c, L, R, x, tol2, sl, h1, kept);
   if (c->opts.persistent && !h1) return persistent_launch<T>(c, c->cap_stream, R, x, tol2, sl);
   return pcg_capture<T>(c, L, R, x, tol2, sl, h1, kept);
 }
@@ -483,19 +505,18 @@ static void elem_launch(eqs_ctx* c, cudaStream_t st, const double* Y, int n_limi
 static double* Ybuf(eqs_ctx* c, int j) { return j == 0 ? c->d_Y[0] : c->d_Y[1 + (j - 1) % 3]; }
 static double* Fbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_F[0] : c->d_F[1 + (j - 1) % 2]; }
 
+// Enqueue one RKC step on st: captured into a graph (c->direct false) or
+// launched directly with a host-driven CG loop (c->direct true).
 template <typename T>
-static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, double* xdev,
-                               GraphEntry& ge) {
+static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, double* xdev,
+                               const double* d_cj, cudaStream_t st) {
   std::vector<double> mu, nu, mut, gt, cj;
   double beta;
   rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
-  CK(upload(c, &ge.d_cj, cj.data(), cj.size()));
   const int n = (int)c->n_nodes, nf = (int)c->n_free;
   const double tol2 = c->opts.rtol * c->opts.rtol;
   const double w = 2.0 * M_PI * c->freq;
-  cudaStream_t st = c->cap_stream;
-  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-  launch(k_stage_scalars, 1, 64, st, s + 1, ge.d_cj, c->d_params, c->V0, w, c->phase, c->d_g, c->d_gp,
+  launch(k_stage_scalars, 1, 64, st, s + 1, d_cj, c->d_params, c->V0, w, c->phase, c->d_g, c->d_gp,
          c->d_stepcount);
   const bool mx = mixed(c);
   launch(k_gather_state, nblk(n), kBlock, st, n, nf, xdev, c->d_node_of_internal, c->d_dir_scale, c->d_g,
@@ -538,6 +559,20 @@ static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
       stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl);
     }
   }
+  return stt;
+}
+
+template <typename T>
+static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, double* xdev,
+                               GraphEntry& ge) {
+  std::vector<double> mu, nu, mut, gt, cj;
+  double beta;
+  rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
+  CK(upload(c, &ge.d_cj, cj.data(), cj.size()));
+  cudaStream_t st = c->cap_stream;
+  c->direct = false;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  eqs_status stt = enqueue_step<T>(c, L, s, xdev, ge.d_cj, st);
   cudaError_t le = cudaGetLastError();
   cudaGraph_t graph = nullptr;
   cudaError_t ee = cudaStreamEndCapture(st, &graph);
@@ -648,6 +683,7 @@ void eqs_opts_default(eqs_opts* o) {
   o->flexible = 1;
   o->persistent = 1;
   o->blocks_per_sm = 1;
+  o->host_loop = 0;
 }
 
 eqs_status eqs_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
@@ -815,7 +851,7 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
   CK(dalloc(c, &c->d_gp, EQS_MAX_STAGES + 1));
   c->red.max_blocks = nblk(std::max<int64_t>(nf, 1));
   CK(dalloc(c, &c->red.partials, 4 * (size_t)c->red.max_blocks));
-  CK(dalloc(c, &c->red.counter, 1));
+  CK(dalloc(c, &c->red.counter, 9));  // main + 8 group tickets
   {
     const eqs_status ps = mixed(c) ? build_plan(c, c->lev32) : build_plan(c, c->lev64);
     if (ps != EQS_OK) return ps;
@@ -984,6 +1020,32 @@ eqs_status eqs_rkc_step(eqs_ctx* c, double* x, double t, double dt, int s, eqs_s
   if (!x) return fail(c, EQS_ERR_ARG, "x is NULL");
   if (s < 2 || s > EQS_MAX_STAGES) return fail(c, EQS_ERR_ARG, "s out of range [2, 64]");
   if (!std::isfinite(t) || !(dt > 0) || !std::isfinite(dt)) return fail(c, EQS_ERR_ARG, "bad t or dt");
+  if (c->opts.host_loop) {  // same kernels, CG loops driven from the host
+    const std::pair<int, uintptr_t> dkey(-s, 0);
+    auto dit = c->step_graphs.find(dkey);
+    if (dit == c->step_graphs.end()) {
+      GraphEntry ge;
+      std::vector<double> mu, nu, mut, gt, cj;
+      double beta;
+      rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
+      CK(upload(c, &ge.d_cj, cj.data(), cj.size()));
+      ge.s = s;
+      dit = c->step_graphs.emplace(dkey, ge).first;
+    }
+    StepParams prm{t, dt};
+    CK(cudaMemcpyAsync(c->d_params, &prm, sizeof(prm), cudaMemcpyHostToDevice, c->stream));
+    c->direct = true;
+    g_launches = 0;
+    eqs_status st = mixed(c) ? enqueue_step(c, c->lev32, s, x, dit->second.d_cj, c->stream)
+                             : enqueue_step(c, c->lev64, s, x, dit->second.d_cj, c->stream);
+    c->direct = false;
+    if (st != EQS_OK) return st;
+    dit->second.fixed_kernels = g_launches;
+    dit->second.per_iter_kernels = 0;
+    c->last_step = &dit->second;
+    if (c->recording) c->recorded = std::min<int64_t>(c->recorded + s, c->store_cap);
+    return stats ? eqs_get_step_stats(c, stats) : EQS_OK;
+  }
   const std::pair<int, uintptr_t> key(s, (uintptr_t)x);
   auto it = c->step_graphs.find(key);
   if (it == c->step_graphs.end()) {

@@ -37,7 +37,8 @@ class eqs_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("theta", C.c_double), ("coarse_max", C.c_int),
                 ("max_levels", C.c_int), ("cheb_degree", C.c_int), ("cheb_alpha", C.c_double),
                 ("rtol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int),
-                ("flexible", C.c_int), ("persistent", C.c_int), ("blocks_per_sm", C.c_int)]
+                ("flexible", C.c_int), ("persistent", C.c_int), ("blocks_per_sm", C.c_int),
+                ("host_loop", C.c_int)]
 
 
 class eqs_step_stats(C.Structure):

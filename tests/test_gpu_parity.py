@@ -137,3 +137,25 @@ def test_rkc_trajectory(E, name, s, steps, prec, tol):
     err = np.linalg.norm(got - ref, axis=1).max() / np.linalg.norm(ref, axis=1).max()
     assert err <= tol, err
     S.close()
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_host_loop_matches_graph(E, prec):
+    """The host-driven CG loop runs the same kernels as the graph's device loop."""
+    p = PROBLEMS["jitter10"]()
+    out = []
+    for host_loop in (0, 1):
+        S = E.Solver(p, precision=prec, rtol=1e-10, host_loop=host_loop, persistent=0)
+        x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+        dt, t, its = S.dt_bound(10), 0.0, []
+        for _ in range(3):
+            st = S.step(x, t, dt, 10)
+            its.append(list(st.iters[:10]))
+            t += dt
+        out.append((x.cpu().numpy(), its, st.launches))
+        S.close()
+    assert out[0][1] == out[1][1]
+    assert out[0][2] == out[1][2]  # launch counts agree
+    # FP32 atomics in the mixed element kernel sum in a different order per run
+    tol = 1e-11 if prec == FP64 else 1e-7
+    np.testing.assert_allclose(out[1][0], out[0][0], rtol=0, atol=tol * np.abs(out[0][0]).max())
