@@ -40,7 +40,7 @@ CONFIG_INDEX = 1
 SOLVER_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0)
 # DRAM bytes (read + write) of one k_spmv64 launch on this workload from an ncu
 # capture (profiles/k_spmv64_cube64.md); None until measured for this kernel.
-TRAFFIC_SPMV64 = None
+TRAFFIC_SPMV64 = 34096128
 
 
 def parse():
