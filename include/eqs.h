@@ -257,6 +257,46 @@ eqs_status eqs_guess_grad(eqs_ctx* ctx, const float* X, const float* T, int B, f
  * into z0 (device, n_free doubles); synchronises. */
 eqs_status eqs_guess_eval(eqs_ctx* ctx, const double* H, double* z0);
 
+/* ---- Batched serving: many independent instances advance together.
+ * Every RKC stage of all instances is one cooperative launch in which each
+ * instance owns a group of CTAs proportional to its free rows (at least
+ * rows_per_block rows per CTA; scaled up until all CTAs are co-resident) and
+ * runs its recurrence, element kernel, right-hand side and whole CG solve
+ * with its own bounded group barrier (EQS_ERR_TIMEOUT when a wait gives up).
+ * The step is one CUDA graph per s.  Contexts must be set up in
+ * EQS_PREC_MIXED with equal rtol on one device; while a batch uses them they
+ * must not run other work concurrently.  The batch keeps the context
+ * pointers (the caller keeps the contexts alive) and owns the rest. */
+typedef struct eqs_batch eqs_batch;
+
+typedef struct {
+  int n_inst, s;
+  int64_t total_iters;   /* CG iterations summed over instances and stages  */
+  int max_iters;         /* largest iteration count of one solve            */
+  double max_relres;     /* largest final ||r||/||R||                        */
+  int status;            /* EQS_OK, EQS_ERR_NOCONV or EQS_ERR_TIMEOUT        */
+  int64_t launches;      /* kernels of the step graph                        */
+} eqs_batch_stats;
+
+eqs_status eqs_batch_create(eqs_ctx* const* ctxs, int n, int rows_per_block, eqs_batch** out);
+
+/* One RKC step of s stages for every instance: x is a host array of n
+ * device pointers (instance k: n_nodes of ctx k doubles, mesh order, in x(t),
+ * out x(t + dt)); drive, materials and tolerances come from each context.
+ * stats: host or NULL (then the call is asynchronous). */
+eqs_status eqs_batch_rkc_step(eqs_batch* b, double* const* x, double t, double dt, int s,
+                              eqs_batch_stats* stats);
+
+/* Statistics of the last batched step (synchronises); inst_iters: host array
+ * of n totals per instance, or NULL. */
+eqs_status eqs_batch_get_stats(eqs_batch* b, eqs_batch_stats* stats, int64_t* inst_iters);
+
+/* CTAs of the batched stage launch and the rows per CTA finally used. */
+eqs_status eqs_batch_info(const eqs_batch* b, int* total_blocks, int* rows_per_block);
+
+eqs_status eqs_batch_destroy(eqs_batch* b);
+const char* eqs_batch_last_error(const eqs_batch* b);
+
 /* Release everything owned by ctx (NULL is accepted). */
 eqs_status eqs_destroy(eqs_ctx* ctx);
 

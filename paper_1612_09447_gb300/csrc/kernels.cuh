@@ -629,13 +629,11 @@ __global__ void k_elem64(int64_t nt, const int4* __restrict__ conn, const uint8_
 // (hi_a - hi_b) + (lo_a - lo_b) with FP32 relative accuracy; everything else
 // is FP32 with FP32 accumulation.  r_0 = -(r_1 + r_2 + r_3) keeps the
 // local residual's zero sum exactly.
-__global__ void k_elem32(int64_t nt, const int4* __restrict__ conn, const uint8_t* __restrict__ mat,
-                         const MaterialDev* __restrict__ mats, const float4* __restrict__ xh,
-                         const float4* __restrict__ xl, const float2* __restrict__ x,
-                         int n_limit, float* __restrict__ y) {
-  pdl_enter();
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nt) return;
+__device__ __forceinline__ void elem32_tet(int64_t e, const int4* __restrict__ conn,
+                                           const uint8_t* __restrict__ mat,
+                                           const MaterialDev* __restrict__ mats,
+                                           const float4* __restrict__ xh, const float4* __restrict__ xl,
+                                           const float2* __restrict__ x, int n_limit, float* __restrict__ y) {
   const int4 t = conn[e];
   const float4 h0 = xh[t.x], h1 = xh[t.y], h2 = xh[t.z], h3 = xh[t.w];
   const float4 l0 = xl[t.x], l1 = xl[t.y], l2 = xl[t.z], l3 = xl[t.w];
@@ -673,6 +671,16 @@ __global__ void k_elem32(int64_t nt, const int4* __restrict__ conn, const uint8_
   if (t.y < n_limit) atomicAdd(y + t.y, r1);
   if (t.z < n_limit) atomicAdd(y + t.z, r2);
   if (t.w < n_limit) atomicAdd(y + t.w, r3);
+}
+
+__global__ void k_elem32(int64_t nt, const int4* __restrict__ conn, const uint8_t* __restrict__ mat,
+                         const MaterialDev* __restrict__ mats, const float4* __restrict__ xh,
+                         const float4* __restrict__ xl, const float2* __restrict__ x,
+                         int n_limit, float* __restrict__ y) {
+  pdl_enter();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt) return;
+  elem32_tet(e, conn, mat, mats, xh, xl, x, n_limit, y);
 }
 
 // ------------------------------------------------------------- RKC pieces
@@ -866,9 +874,14 @@ struct PPlan {
   PLevel<T> lev[kMaxLevels];
 };
 
+// A group of CTAs working on one solve: the whole grid (single instance) or
+// the CTAs of one instance of a batch.
 struct GridCtx {
-  int64_t tid, stride;
-  unsigned int nblocks;
+  int64_t tid, stride;      // group-relative thread id, threads in the group
+  unsigned int nblocks;     // CTAs in the group
+  unsigned int rank;        // this CTA's index in the group
+  GridBarrier* bar;         // the group's barrier
+  double* partials;         // the group's reduction slots (8 x nblocks)
 };
 
 __device__ __forceinline__ bool grid_barrier(GridBarrier* b, unsigned int nblocks) {
@@ -902,13 +915,14 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* b, unsigned int nblock
   return s_ok != 0;
 }
 
-// Block partial of NV values into partials[(slot + k) * nblocks + block].
+// Block partial of NV values into partials[(slot + k) * nblocks + rank].
 template <int NV>
-__device__ __forceinline__ void put_partials(double (&v)[NV], double* partials, int slot, unsigned nb) {
+__device__ __forceinline__ void put_partials(double (&v)[NV], double* partials, int slot, unsigned nb,
+                                             unsigned rank) {
   block_sum<NV>(v);
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int k = 0; k < NV; ++k) partials[(slot + k) * nb + blockIdx.x] = v[k];
+    for (int k = 0; k < NV; ++k) partials[(slot + k) * nb + rank] = v[k];
 }
 
 // Sum of the block partials of one slot, in fixed order (same value in every
@@ -1040,7 +1054,7 @@ __device__ bool vcycle_persistent(const PPlan<T>& P, const GridCtx& g) {
     const T* rin = L.b;
     for (int k = 2; k <= deg; ++k) {
       ph_cheb(L, rin, din, L.r, dout, L.c1[k], L.c2[k], 0, g);
-      if (!grid_barrier(P.bar, g.nblocks)) return false;
+      if (!grid_barrier(g.bar, g.nblocks)) return false;
       rin = L.r;
       T* tmp = din;
       din = dout;
@@ -1050,53 +1064,46 @@ __device__ bool vcycle_persistent(const PPlan<T>& P, const GridCtx& g) {
       ph_resid_update(L, din, g);
     else
       ph_resid(L, g);
-    if (!grid_barrier(P.bar, g.nblocks)) return false;
+    if (!grid_barrier(g.bar, g.nblocks)) return false;
     ph_restrict(L, P.lev[l + 1], l + 1 < nl - 1, g);
-    if (!grid_barrier(P.bar, g.nblocks)) return false;
+    if (!grid_barrier(g.bar, g.nblocks)) return false;
   }
   ph_coarse(P.lev[nl - 1], P.coarse_inv, g);
-  if (!grid_barrier(P.bar, g.nblocks)) return false;
+  if (!grid_barrier(g.bar, g.nblocks)) return false;
   for (int l = nl - 2; l >= 0; --l) {
     const PLevel<T>& L = P.lev[l];
     ph_prolong(L, P.lev[l + 1], g);
-    if (!grid_barrier(P.bar, g.nblocks)) return false;
+    if (!grid_barrier(g.bar, g.nblocks)) return false;
     ph_post_first(L, g);
-    if (!grid_barrier(P.bar, g.nblocks)) return false;
+    if (!grid_barrier(g.bar, g.nblocks)) return false;
     T* din = L.dA;
     T* dout = L.dB;
     for (int k = 2; k <= deg; ++k) {
       ph_cheb(L, L.r, din, L.r, dout, L.c1[k], L.c2[k], k == 2, g);
-      if (!grid_barrier(P.bar, g.nblocks)) return false;
+      if (!grid_barrier(g.bar, g.nblocks)) return false;
       T* tmp = din;
       din = dout;
       dout = tmp;
     }
     if (deg == 1) {
       for (int64_t i = g.tid; i < L.n; i += g.stride) L.x[i] += L.dA[i];
-      if (!grid_barrier(P.bar, g.nblocks)) return false;
+      if (!grid_barrier(g.bar, g.nblocks)) return false;
     }
   }
   return true;
 }
 
-// Preconditioned CG for M_ff x = R from the start vector in x.  Slots of the
-// partial sums: 0-1 init, 2-3 dots, 4 p.q, 5 update.
+// Preconditioned CG for M_ff x = R from the start vector in x, run by the
+// CTAs of group g.  Slots of the partial sums: 0-1 init, 2-3 dots, 4 p.q,
+// 5 update.  Returns false if a barrier wait timed out.
 template <typename T>
-__global__ void __launch_bounds__(kPBlock) k_pcg_persistent(const PPlan<T>* __restrict__ plan,
-                                                             const double* __restrict__ R,
-                                                             double* __restrict__ x,
-                                                             int* iters_out, double* relres_out,
-                                                             int* zero_out, double tol2) {
-  const PPlan<T>& P = *plan;
-  GridCtx g;
-  g.tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  g.stride = (int64_t)gridDim.x * blockDim.x;
-  g.nblocks = gridDim.x;
-  const unsigned nb = gridDim.x;
+__device__ bool pcg_group_solve(const PPlan<T>& P, const GridCtx& g, const double* __restrict__ R,
+                                double* __restrict__ x, double tol2, int* iters_out, double* relres_out,
+                                int* zero_out) {
+  const unsigned nb = g.nblocks;
   const int n = P.nf;
   const PLevel<T>& L0 = P.lev[0];
   const bool single = (P.nl == 1);
-  // init: r = R - M x, level-0 input
   {
     double v[2] = {0.0, 0.0};
     for (int64_t i = g.tid; i < n; i += g.stride) {
@@ -1113,20 +1120,17 @@ __global__ void __launch_bounds__(kPBlock) k_pcg_persistent(const PPlan<T>* __re
       v[0] += Ri * Ri;
       v[1] += ri * ri;
     }
-    put_partials<2>(v, P.partials, 0, nb);
+    put_partials<2>(v, g.partials, 0, nb, g.rank);
   }
-  if (!grid_barrier(P.bar, g.nblocks)) return;
-  const double bnorm2 = get_total(P.partials, 0, nb);
-  double rnorm2 = get_total(P.partials, 1, nb);
+  if (!grid_barrier(g.bar, nb)) return false;
+  const double bnorm2 = get_total(g.partials, 0, nb);
+  double rnorm2 = get_total(g.partials, 1, nb);
   const int zero = bnorm2 == 0.0;
   int conv = zero || !(rnorm2 > tol2 * bnorm2);
   int it = 0;
   double rz_old = 1.0;
-  double* pold = P.pA;
-  double* pnew = P.pB;
   while (!conv && it < P.maxit) {
-    if (!vcycle_persistent(P, g)) return;
-    // z in FP64, r.z and r_prev.z
+    if (!vcycle_persistent(P, g)) return false;
     {
       double v[2] = {0.0, 0.0};
       for (int64_t i = g.tid; i < n; i += g.stride) {
@@ -1135,33 +1139,32 @@ __global__ void __launch_bounds__(kPBlock) k_pcg_persistent(const PPlan<T>* __re
         v[0] += P.r[i] * zi;
         v[1] += P.rprev[i] * zi;
       }
-      put_partials<2>(v, P.partials, 2, nb);
+      put_partials<2>(v, g.partials, 2, nb, g.rank);
     }
-    if (!grid_barrier(P.bar, g.nblocks)) return;
-    const double rz = get_total(P.partials, 2, nb);
-    const double zrp = get_total(P.partials, 3, nb);
+    if (!grid_barrier(g.bar, nb)) return false;
+    const double rz = get_total(g.partials, 2, nb);
+    const double zrp = get_total(g.partials, 3, nb);
     const double beta = it == 0 ? 0.0 : (P.flexible ? (rz - zrp) / rz_old : rz / rz_old);
     rz_old = rz;
-    // p_new = z + beta p_old ; q = M p_new (p_new of neighbours formed on the fly)
+    // p = z + beta p ; q = M z + beta q (q_old = M p_old), row-local
     {
       double v[1] = {0.0};
       for (int64_t i = g.tid; i < n; i += g.stride) {
-        const double qi = beta == 0.0 ? mat_row<double>(P.M, i, n, P.zd)
-                                      : mat_row_axpy(P.M, (int)i, n, P.zd, pold, beta);
-        const double pi = beta == 0.0 ? P.zd[i] : fma(beta, pold[i], P.zd[i]);
-        pnew[i] = pi;
+        const double w = mat_row<double>(P.M, i, n, P.zd);
+        const double qi = beta == 0.0 ? w : fma(beta, P.q[i], w);
+        const double pi = beta == 0.0 ? P.zd[i] : fma(beta, P.pA[i], P.zd[i]);
+        P.pA[i] = pi;
         P.q[i] = qi;
         v[0] += pi * qi;
       }
-      put_partials<1>(v, P.partials, 4, nb);
+      put_partials<1>(v, g.partials, 4, nb, g.rank);
     }
-    if (!grid_barrier(P.bar, g.nblocks)) return;
-    const double alpha = rz / get_total(P.partials, 4, nb);
-    // x += alpha p ; r -= alpha q ; next V-cycle input
+    if (!grid_barrier(g.bar, nb)) return false;
+    const double alpha = rz / get_total(g.partials, 4, nb);
     {
       double v[1] = {0.0};
       for (int64_t i = g.tid; i < n; i += g.stride) {
-        x[i] = fma(alpha, pnew[i], x[i]);
+        x[i] = fma(alpha, P.pA[i], x[i]);
         const double ro = P.r[i];
         P.rprev[i] = ro;
         const double rn = fma(-alpha, P.q[i], ro);
@@ -1175,21 +1178,36 @@ __global__ void __launch_bounds__(kPBlock) k_pcg_persistent(const PPlan<T>* __re
           L0.dA[i] = d;
         }
       }
-      put_partials<1>(v, P.partials, 5, nb);
+      put_partials<1>(v, g.partials, 5, nb, g.rank);
     }
-    if (!grid_barrier(P.bar, g.nblocks)) return;
-    rnorm2 = get_total(P.partials, 5, nb);
+    if (!grid_barrier(g.bar, nb)) return false;
+    rnorm2 = get_total(g.partials, 5, nb);
     ++it;
     conv = !(rnorm2 > tol2 * bnorm2);
-    double* tmp = pold;
-    pold = pnew;
-    pnew = tmp;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (g.rank == 0 && threadIdx.x == 0) {
     if (iters_out) *iters_out = it;
     if (relres_out) *relres_out = zero ? 0.0 : sqrt(rnorm2 / bnorm2);
     if (zero_out) *zero_out = zero;
   }
+  return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPBlock) k_pcg_persistent(const PPlan<T>* __restrict__ plan,
+                                                             const double* __restrict__ R,
+                                                             double* __restrict__ x,
+                                                             int* iters_out, double* relres_out,
+                                                             int* zero_out, double tol2) {
+  const PPlan<T>& P = *plan;
+  GridCtx g;
+  g.tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  g.stride = (int64_t)gridDim.x * blockDim.x;
+  g.nblocks = gridDim.x;
+  g.rank = blockIdx.x;
+  g.bar = P.bar;
+  g.partials = P.partials;
+  pcg_group_solve(P, g, R, x, tol2, iters_out, relres_out, zero_out);
 }
 
 }  // namespace eqs

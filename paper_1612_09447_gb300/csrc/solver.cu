@@ -15,6 +15,7 @@
 
 #include "kernels.cuh"
 #include "mlp_kernels.cuh"
+#include "batch_kernels.cuh"
 
 using namespace eqs;
 
@@ -1295,6 +1296,293 @@ eqs_status eqs_guess_eval(eqs_ctx* c, const double* H, double* z0) {
   if (e != cudaSuccess) return fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
   return EQS_OK;
 }
+
+// ------------------------------------------------------------- batches
+}  // extern "C"
+
+struct eqs_batch {
+  std::vector<eqs_ctx*> ctx;
+  int device = 0, sms = 0, total_blocks = 0, rows_per_block = 0;
+  std::vector<int> first, nblk, blk2inst;
+  BatchInst* d_insts = nullptr;
+  int *d_blk2inst = nullptr, *d_first = nullptr, *d_nblk = nullptr;
+  GridBarrier* d_bars = nullptr;
+  double *d_gtab = nullptr, *d_gptab = nullptr;
+  double** d_x = nullptr;
+  StepParams* d_params = nullptr;
+  cudaStream_t stream = nullptr, cap = nullptr;
+  std::map<int, GraphEntry> graphs;
+  std::vector<void*> allocs;
+  std::string err;
+  int last_s = 0;
+};
+
+static eqs_status bfail(eqs_batch* b, eqs_status st, const std::string& m) {
+  if (b)
+    b->err = m;
+  else
+    g_create_err = m;
+  return st;
+}
+
+#define BCK(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return bfail(b, EQS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+template <typename T>
+static cudaError_t balloc(eqs_batch* b, T** p, size_t n) {
+  cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
+  if (e == cudaSuccess) {
+    b->allocs.push_back(*p);
+    e = cudaMemset(*p, 0, std::max<size_t>(n, 1) * sizeof(T));
+  }
+  return e;
+}
+
+static void batch_free(eqs_batch* b) {
+  for (auto& kv : b->graphs) destroy_graph(kv.second);
+  b->graphs.clear();
+  for (void* p : b->allocs) cudaFree(p);
+  b->allocs.clear();
+}
+
+static eqs_status batch_capture(eqs_batch* b, int s, GraphEntry& ge) {
+  std::vector<double> mu, nu, mut, gt, cj;
+  double beta;
+  rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
+  double* d_cj = nullptr;
+  BCK(balloc(b, &d_cj, cj.size()));
+  BCK(cudaMemcpy(d_cj, cj.data(), cj.size() * sizeof(double), cudaMemcpyHostToDevice));
+  ge.d_cj = d_cj;
+  const int ninst = (int)b->ctx.size();
+  const double tol2 = b->ctx[0]->opts.rtol * b->ctx[0]->opts.rtol;
+  cudaStream_t st = b->cap;
+  BCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  cudaMemsetAsync(b->d_bars, 0, ninst * sizeof(GridBarrier), st);
+  k_batch_drive<<<nblk((int64_t)ninst * (s + 1)), kBlock, 0, st>>>(ninst, s + 1, b->d_insts, d_cj, b->d_params,
+                                                                    b->d_gtab, b->d_gptab);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(b->total_blocks);
+  cfg.blockDim = dim3(kPBlock);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  for (int j = 0; j < s; ++j) {
+    const bool first = (j <= 1);
+    const double c0 = j == 0 ? 0.0 : (j == 1 ? 1.0 : 1.0 - mu[j] - nu[j]);
+    cudaLaunchKernelEx(&cfg, k_batch_stage, (const BatchInst*)b->d_insts, (const int*)b->d_blk2inst,
+                       (const int*)b->d_first, (const int*)b->d_nblk, j, s, c0, first ? 0.0 : mu[j],
+                       first ? 0.0 : nu[j], j == 0 ? 0.0 : mut[j], first ? 0.0 : gt[j],
+                       (const StepParams*)b->d_params, (const double*)b->d_gtab, (const double*)b->d_gptab,
+                       (double* const*)b->d_x, tol2);
+  }
+  k_batch_final<<<b->total_blocks, kPBlock, 0, st>>>(b->d_insts, b->d_blk2inst, b->d_first, b->d_nblk, s,
+                                                    1.0 - mu[s] - nu[s], mu[s], nu[s], mut[s], gt[s],
+                                                    b->d_params, b->d_gtab, b->d_x);
+  cudaError_t le = cudaGetLastError();
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  BCK(le);
+  BCK(ee);
+  ge.graph = graph;
+  ge.s = s;
+  ge.fixed_kernels = count_kernel_nodes(graph);
+  ge.per_iter_kernels = 0;
+  BCK(cudaGraphInstantiate(&ge.exec, graph, 0));
+  return EQS_OK;
+}
+
+extern "C" {
+
+eqs_status eqs_batch_create(eqs_ctx* const* ctxs, int n, int rows_per_block, eqs_batch** out) {
+  if (!out) return bfail(nullptr, EQS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!ctxs || n < 1 || rows_per_block < 32) return bfail(nullptr, EQS_ERR_ARG, "bad batch arguments");
+  for (int k = 0; k < n; ++k) {
+    if (!ctxs[k] || !ctxs[k]->setup_done) return bfail(nullptr, EQS_ERR_STATE, "every context must be set up");
+    if (ctxs[k]->opts.precision != EQS_PREC_MIXED)
+      return bfail(nullptr, EQS_ERR_ARG, "batched stages run in mixed precision");
+    if (ctxs[k]->device != ctxs[0]->device) return bfail(nullptr, EQS_ERR_ARG, "contexts on different devices");
+    if (ctxs[k]->opts.rtol != ctxs[0]->opts.rtol) return bfail(nullptr, EQS_ERR_ARG, "contexts differ in rtol");
+  }
+  eqs_batch* b = new eqs_batch();
+  b->ctx.assign(ctxs, ctxs + n);
+  b->device = ctxs[0]->device;
+  b->sms = ctxs[0]->sms;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_stage, kPBlock, 0) != cudaSuccess || occ < 1) {
+    delete b;
+    return bfail(nullptr, EQS_ERR_CUDA, "batched stage kernel cannot be resident");
+  }
+  const int cap_blocks = occ * b->sms;
+  // CTAs per instance proportional to its free rows; scale until co-resident
+  int r = rows_per_block;
+  for (;;) {
+    b->first.assign(n, 0);
+    b->nblk.assign(n, 0);
+    int tot = 0;
+    for (int k = 0; k < n; ++k) {
+      const int64_t nf = ctxs[k]->n_free;
+      b->nblk[k] = (int)std::min<int64_t>(std::max<int64_t>(1, (nf + r - 1) / r), ctxs[k]->pblocks);
+      b->first[k] = tot;
+      tot += b->nblk[k];
+    }
+    if (tot <= cap_blocks) {
+      b->total_blocks = tot;
+      break;
+    }
+    if (n > cap_blocks) {
+      delete b;
+      return bfail(nullptr, EQS_ERR_ARG, "more instances than co-resident CTAs");
+    }
+    r += r / 4 + 1;
+  }
+  b->rows_per_block = r;
+  b->blk2inst.resize(b->total_blocks);
+  for (int k = 0; k < n; ++k)
+    for (int q = 0; q < b->nblk[k]; ++q) b->blk2inst[b->first[k] + q] = k;
+  std::vector<BatchInst> hi(n);
+  for (int k = 0; k < n; ++k) {
+    eqs_ctx* c = ctxs[k];
+    BatchInst& I = hi[k];
+    I.plan = (const PPlan<float>*)c->d_plan;
+    I.partials = c->d_ppartials;
+    I.n = (int)c->n_nodes;
+    I.nf = (int)c->n_free;
+    I.nt = c->n_tets;
+    I.conn = c->d_conn;
+    I.mat = c->d_mat;
+    I.mats = c->d_mats;
+    I.xh = c->d_xyz_hi;
+    I.xl = c->d_xyz_lo;
+    I.node_of_internal = c->d_node_of_internal;
+    I.dir_scale = c->d_dir_scale;
+    I.mtop = c->d_mtop;
+    for (int q = 0; q < 4; ++q) I.Y[q] = c->d_Y[q];
+    I.Y32 = c->d_Y32;
+    for (int q = 0; q < 3; ++q) I.F[q] = c->d_F[q];
+    I.R = c->d_R;
+    I.y32 = c->d_y32;
+    I.iters = c->d_iters;
+    I.relres = c->d_relres;
+    I.zero = c->d_zero;
+    I.V0 = c->V0;
+    I.w = 2.0 * M_PI * c->freq;
+    I.phase = c->phase;
+  }
+  cudaError_t e = cudaSetDevice(b->device);
+  if (e == cudaSuccess) e = balloc(b, &b->d_bars, n);
+  for (int k = 0; k < n && e == cudaSuccess; ++k) hi[k].bar = b->d_bars + k;
+  if (e == cudaSuccess) e = balloc(b, &b->d_insts, n);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_insts, hi.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = balloc(b, &b->d_blk2inst, b->total_blocks);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_blk2inst, b->blk2inst.data(), b->total_blocks * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = balloc(b, &b->d_first, n);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_first, b->first.data(), n * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = balloc(b, &b->d_nblk, n);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_nblk, b->nblk.data(), n * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = balloc(b, &b->d_gtab, (size_t)n * (EQS_MAX_STAGES + 1));
+  if (e == cudaSuccess) e = balloc(b, &b->d_gptab, (size_t)n * (EQS_MAX_STAGES + 1));
+  if (e == cudaSuccess) e = balloc(b, &b->d_x, n);
+  if (e == cudaSuccess) e = balloc(b, &b->d_params, 1);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    g_create_err = std::string("batch setup: ") + cudaGetErrorString(e);
+    batch_free(b);
+    delete b;
+    return EQS_ERR_CUDA;
+  }
+  b->stream = ctxs[0]->stream;
+  *out = b;
+  return EQS_OK;
+}
+
+eqs_status eqs_batch_rkc_step(eqs_batch* b, double* const* x, double t, double dt, int s,
+                              eqs_batch_stats* stats) {
+  if (!b) return bfail(nullptr, EQS_ERR_ARG, "batch is NULL");
+  if (!x) return bfail(b, EQS_ERR_ARG, "x is NULL");
+  if (s < 2 || s > EQS_MAX_STAGES) return bfail(b, EQS_ERR_ARG, "s out of range [2, 64]");
+  if (!std::isfinite(t) || !(dt > 0) || !std::isfinite(dt)) return bfail(b, EQS_ERR_ARG, "bad t or dt");
+  const int n = (int)b->ctx.size();
+  for (int k = 0; k < n; ++k)
+    if (!x[k]) return bfail(b, EQS_ERR_ARG, "null instance vector");
+  auto it = b->graphs.find(s);
+  if (it == b->graphs.end()) {
+    GraphEntry ge;
+    const eqs_status st = batch_capture(b, s, ge);
+    if (st != EQS_OK) return st;
+    it = b->graphs.emplace(s, ge).first;
+  }
+  const StepParams prm{t, dt};
+  BCK(cudaMemcpyAsync(b->d_params, &prm, sizeof(prm), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaMemcpyAsync(b->d_x, x, n * sizeof(double*), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaGraphLaunch(it->second.exec, b->stream));
+  b->last_s = s;
+  if (!stats) return EQS_OK;
+  return eqs_batch_get_stats(b, stats, nullptr);
+}
+
+eqs_status eqs_batch_get_stats(eqs_batch* b, eqs_batch_stats* stats, int64_t* inst_iters) {
+  if (!b || !stats) return bfail(b, EQS_ERR_ARG, "null argument");
+  if (!b->last_s) return bfail(b, EQS_ERR_STATE, "no batched step has run");
+  const int s = b->last_s, n = (int)b->ctx.size();
+  BCK(cudaStreamSynchronize(b->stream));
+  std::memset(stats, 0, sizeof(*stats));
+  stats->n_inst = n;
+  stats->s = s;
+  stats->launches = b->graphs[s].fixed_kernels;
+  eqs_status res = EQS_OK;
+  for (int k = 0; k < n; ++k) {
+    int iters[EQS_MAX_STAGES];
+    double rr[EQS_MAX_STAGES];
+    BCK(cudaMemcpy(iters, b->ctx[k]->d_iters, s * sizeof(int), cudaMemcpyDeviceToHost));
+    BCK(cudaMemcpy(rr, b->ctx[k]->d_relres, s * sizeof(double), cudaMemcpyDeviceToHost));
+    int64_t tot = 0;
+    for (int j = 0; j < s; ++j) {
+      tot += iters[j];
+      stats->max_iters = std::max(stats->max_iters, iters[j]);
+      stats->max_relres = std::max(stats->max_relres, rr[j]);
+      if (!std::isfinite(rr[j])) res = EQS_ERR_NAN;
+      else if (rr[j] > b->ctx[k]->opts.rtol && res == EQS_OK) res = EQS_ERR_NOCONV;
+    }
+    stats->total_iters += tot;
+    if (inst_iters) inst_iters[k] = tot;
+  }
+  std::vector<GridBarrier> bars(n);
+  BCK(cudaMemcpy(bars.data(), b->d_bars, n * sizeof(GridBarrier), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < n; ++k)
+    if (bars[k].err) res = EQS_ERR_TIMEOUT;
+  stats->status = res;
+  if (res == EQS_ERR_TIMEOUT) return bfail(b, res, "a group barrier of the batched step timed out");
+  if (res == EQS_ERR_NOCONV) return bfail(b, res, "a stage solve reached max_iter");
+  if (res == EQS_ERR_NAN) return bfail(b, res, "non-finite residual in a stage solve");
+  return EQS_OK;
+}
+
+eqs_status eqs_batch_info(const eqs_batch* b, int* total_blocks, int* rows_per_block) {
+  if (!b) return bfail(nullptr, EQS_ERR_ARG, "batch is NULL");
+  if (total_blocks) *total_blocks = b->total_blocks;
+  if (rows_per_block) *rows_per_block = b->rows_per_block;
+  return EQS_OK;
+}
+
+eqs_status eqs_batch_destroy(eqs_batch* b) {
+  if (!b) return EQS_OK;
+  if (b->stream || !b->allocs.empty()) cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+  return EQS_OK;
+}
+
+const char* eqs_batch_last_error(const eqs_batch* b) { return b ? b->err.c_str() : g_create_err.c_str(); }
 
 eqs_status eqs_destroy(eqs_ctx* c) {
   if (!c) return EQS_OK;

@@ -41,6 +41,12 @@ class eqs_opts(C.Structure):
                 ("host_loop", C.c_int)]
 
 
+class eqs_batch_stats(C.Structure):
+    _fields_ = [("n_inst", C.c_int), ("s", C.c_int), ("total_iters", C.c_int64),
+                ("max_iters", C.c_int), ("max_relres", C.c_double), ("status", C.c_int),
+                ("launches", C.c_int64)]
+
+
 class eqs_step_stats(C.Structure):
     _fields_ = [("s", C.c_int), ("total_iters", C.c_int), ("max_iters", C.c_int),
                 ("iters", C.c_int * EQS_MAX_STAGES), ("max_relres", C.c_double),
@@ -88,6 +94,12 @@ def _declare(L):
         "eqs_guess_train": (I, [P, I, I, C.c_float, C.c_uint64, P, P]),
         "eqs_guess_grad": (I, [P, P, P, I, P, P]),
         "eqs_guess_eval": (I, [P, P, P]),
+        "eqs_batch_create": (I, [P, I, I, C.POINTER(C.c_void_p)]),
+        "eqs_batch_rkc_step": (I, [P, P, D, D, I, C.POINTER(eqs_batch_stats)]),
+        "eqs_batch_get_stats": (I, [P, C.POINTER(eqs_batch_stats), P]),
+        "eqs_batch_info": (I, [P, P, P]),
+        "eqs_batch_destroy": (I, [P]),
+        "eqs_batch_last_error": (C.c_char_p, [P]),
         "eqs_destroy": (I, [P]),
         "eqs_last_error": (C.c_char_p, [P]),
     }
@@ -248,6 +260,43 @@ def eqs_guess_grad(ctx, X, T):
 
 def eqs_guess_eval(ctx, H, z0):
     _check(lib().eqs_guess_eval(ctx, _dev(H), _dev(z0)), ctx)
+
+
+def _bcheck(status, b=None):
+    if status != EQS_OK:
+        raise EqsError(status, lib().eqs_batch_last_error(b).decode())
+
+
+def eqs_batch_create(ctxs, rows_per_block=1024):
+    arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    out = C.c_void_p()
+    _bcheck(lib().eqs_batch_create(arr, len(ctxs), rows_per_block, C.byref(out)))
+    return out
+
+
+def eqs_batch_rkc_step(b, xs, t, dt, s, want_stats=True):
+    arr = (C.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+    st = eqs_batch_stats() if want_stats else None
+    _bcheck(lib().eqs_batch_rkc_step(b, arr, t, dt, s, C.byref(st) if st is not None else None), b)
+    return st
+
+
+def eqs_batch_get_stats(b, n):
+    st = eqs_batch_stats()
+    per = (C.c_int64 * n)()
+    _bcheck(lib().eqs_batch_get_stats(b, C.byref(st), per), b)
+    return st, list(per)
+
+
+def eqs_batch_info(b):
+    tb, rpb = C.c_int(), C.c_int()
+    _bcheck(lib().eqs_batch_info(b, C.byref(tb), C.byref(rpb)), b)
+    return tb.value, rpb.value
+
+
+def eqs_batch_destroy(b):
+    if b:
+        lib().eqs_batch_destroy(b)
 
 
 def eqs_destroy(ctx):
