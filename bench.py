@@ -29,18 +29,24 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "RKC DOF-stages/s and M-solve ms/RHS vs plain FP64 AMG-PCG at 1e-8 residual"
-WORKLOAD = "cube64_block: 64^3-cell Kuhn cube, 274625 nodes (266175 free), 1572864 P1 tets, " \
-           "block varistor, s=20, dt=beta_s/rho, rtol=1e-8"
+WORKLOADS = {
+    1: "cube64_block: 64^3-cell Kuhn cube, 274625 nodes (266175 free), 1572864 P1 tets, "
+       "block varistor, s=20, dt=beta_s/rho, rtol=1e-8",
+    2: "cube128_jitter_spheres: 128^3-cell Kuhn cube with interior nodes jittered by +-0.2h, "
+       "2146689 nodes (2113407 free), 12582912 P1 tets, two varistor spheres, s=20, "
+       "dt=beta_s/rho, rtol=1e-8",
+}
 RTOL = 1e-8
 S_STAGES = 20
 CONFIG_INDEX = 1
+WORKLOAD = WORKLOADS[CONFIG_INDEX]
 # AMG/solver options of the timed runs (both precisions): degree-1 Chebyshev
 # smoothing and a 2066-row coarsest level (dense FP64 inverse) gave the
 # lowest step time on GB300 among degree 1-3 and coarse sizes 88/2066.
 SOLVER_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0)
-# DRAM bytes (read + write) of one k_spmv64 launch on this workload from an ncu
-# capture (profiles/k_spmv64_cube64.md); None until measured for this kernel.
-TRAFFIC_SPMV64 = 34096128
+# DRAM bytes (read + write) of one k_spmv64 launch per workload from an ncu
+# capture (profiles/k_spmv64_cube64.md); None where not captured.
+TRAFFIC_SPMV64 = {1: 34096128, 2: None}
 
 
 def parse():
@@ -52,6 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--N", type=int, default=None, help="override mesh size (testing)")
+    ap.add_argument("--config", type=int, default=1, choices=[1, 2],
+                    help="workload: 1 = 64^3 block cube (default), 2 = 128^3 jittered spheres")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the CG loops from the host (same kernels; for ncu launch lists)")
     return ap.parse_args()
@@ -327,13 +335,16 @@ def dominant_kernel_roofline(torch, eqs, solver, p, flush):
     ach = bytes_alg / (ms / 1e3) / 1e9
     return {"kernel": "k_spmv64 (FP64 DIA SpMV of M_ff, the operator of every CG iteration)",
             "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": TRAFFIC_SPMV64, "bytes_per_launch": bytes_alg, "ms_per_launch": ms,
+            "traffic": TRAFFIC_SPMV64.get(CONFIG_INDEX), "bytes_per_launch": bytes_alg, "ms_per_launch": ms,
             "fp64_tflops": 2.0 * nnz[0] / (ms / 1e3) / 1e12,
             "peak_kind": f"{kind} hbm_gbs (burst: kernel timed alone, L2 flushed before each launch)"}
 
 
 def main():
+    global CONFIG_INDEX, WORKLOAD
     args = parse()
+    CONFIG_INDEX = args.config
+    WORKLOAD = WORKLOADS[CONFIG_INDEX]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
