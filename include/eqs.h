@@ -68,7 +68,9 @@ typedef enum {
 typedef enum {
   EQS_GUESS_PREV = 0, /* start vector = previous M-solve solution           */
   EQS_GUESS_MLP = 1,  /* learned per-node network (eqs_guess_* calls)       */
-  EQS_GUESS_ZERO = 2  /* start vector = 0                                    */
+  EQS_GUESS_ZERO = 2, /* start vector = 0                                   */
+  EQS_GUESS_SPE = 3   /* subspace projection extrapolation over the last
+                         spe_n solutions (Sec. IV, Eq. 4-5)                 */
 } eqs_guess_mode;
 
 /* Options of eqs_amg_setup (fill with eqs_opts_default). */
@@ -87,6 +89,7 @@ typedef struct {
                           kernel (grid barriers); 0: one kernel per CG/V-cycle
                           phase inside a device-side graph loop               */
   int blocks_per_sm;   /* CTAs per SM of the persistent solve (0: 1)         */
+  int spe_n;           /* solutions spanning the SPE subspace (1..6, def. 4) */
   int host_loop;       /* 1: eqs_rkc_step launches the same kernels directly
                           and drives each CG loop from the host (reads the
                           convergence flag after every iteration) instead of
@@ -113,7 +116,7 @@ typedef struct {
 
 /* Fill *o with the defaults (precision FP64, theta 0.08, coarse_max 500,
  * max_levels 10, degree 2, alpha 30, rtol 1e-8, max_iter 500, GUESS_PREV,
- * flexible 1, persistent 1, blocks_per_sm 1). */
+ * flexible 1, persistent 1, blocks_per_sm 1, spe_n 4, host_loop 0). */
 void eqs_opts_default(eqs_opts* o);
 
 /* Create a context from a tetrahedral mesh (Eq. 2 discretisation input).
@@ -296,6 +299,15 @@ eqs_status eqs_batch_info(const eqs_batch* b, int* total_blocks, int* rows_per_b
 
 eqs_status eqs_batch_destroy(eqs_batch* b);
 const char* eqs_batch_last_error(const eqs_batch* b);
+
+/* SPE start vector x0 = V (V^T M V)^-1 V^T b (Sec. IV, Eq. 4-5) for given
+ * history X (device, n x n_free doubles, most recent first), Rh = M X
+ * (device, same shape; the newest column's product is recomputed on the
+ * device), b and x0 (device, n_free).
+ * n must equal the setup's spe_n.  Overwrites the context's SPE history;
+ * synchronises.  For checking the projection. */
+eqs_status eqs_spe_eval(eqs_ctx* ctx, const double* X, const double* Rh, const double* b, int n,
+                        double* x0);
 
 /* Release everything owned by ctx (NULL is accepted). */
 eqs_status eqs_destroy(eqs_ctx* ctx);

@@ -196,6 +196,10 @@ struct eqs_ctx {
   int64_t store_cap = 0, recorded = 0;
   bool recording = false;
   double* d_rtmp = nullptr;          // residual of the fallback start vector
+  double* d_spe_X = nullptr;         // SPE: last solutions (spe_max x n_free)
+  double* d_spe_R = nullptr;         // SPE: W = M X of the stored solutions
+  double* d_spe_y = nullptr;         // SPE: projection coefficients
+  double* d_spe_partials = nullptr;  // SPE: reduction slots
   bool mlp_ready = false;
   bool direct = false;               // enqueue_step launches directly (host-driven CG loop)
 

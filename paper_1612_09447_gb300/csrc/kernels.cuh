@@ -748,7 +748,8 @@ __global__ void k_recurrence(int n, int nf, double c0, double mu, double nu, dou
                              double* __restrict__ Fguess, double* __restrict__ R,
                              double* __restrict__ xmesh, const int32_t* __restrict__ node_of_internal,
                              float* __restrict__ ring, const long long* __restrict__ stepcount, int s,
-                             float* __restrict__ store, long long store_cap) {
+                             float* __restrict__ store, long long store_cap, double* __restrict__ spe_ring,
+                             int spe_n) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -759,6 +760,7 @@ __global__ void k_recurrence(int n, int nf, double c0, double mu, double nu, dou
     const float f32 = (float)Fjm1[i];
     ring[(size_t)(gidx & 3) * nf + i] = f32;
     if (store && gidx < store_cap) store[(size_t)gidx * nf + i] = f32;
+    if (spe_ring) spe_ring[(size_t)(gidx % spe_n) * nf + i] = Fjm1[i];
     const double dt = prm->dt;
     const double fj = zero_flags[jm1] ? 0.0 : Fjm1[i];
     const double f0 = zero_flags[0] ? 0.0 : F0[i];
@@ -942,90 +944,109 @@ __device__ __forceinline__ double get_total(const double* partials, int slot, un
   return r;
 }
 
-// ---- V-cycle phases (grid-stride; loops are warp-uniform)
+// ---- V-cycle phases (group-stride; loops are warp-uniform).  Every thread
+// keeps two rows (t and t + stride) in flight, loading both before storing.
+#define EQS_GROUP_ROWS2(MAT, n_, g_, BODY2)                                    \
+  const int64_t lim_ = round32((int64_t)(n_) << (MAT).logG);                  \
+  for (int64_t t0 = (g_).tid; t0 < lim_; t0 += 2 * (g_).stride) {             \
+    const int64_t t1 = t0 + (g_).stride;                                       \
+    BODY2                                                                      \
+  }
+
 template <typename T>
 __device__ __forceinline__ void ph_cheb(const PLevel<T>& L, const T* r_in, const T* d_in, T* r_out,
                                         T* d_out, T c1, T c2, int pending, const GridCtx& g) {
   const int n = L.n;
-  const int64_t lim = round32((int64_t)n << L.A.logG);
-  for (int64_t t = g.tid; t < lim; t += g.stride) {
-    const T ad = mat_row(L.A, t, n, d_in);
-    if (!row_leader(L.A, t, n)) continue;
-    const int i = (int)(t >> L.A.logG);
-    const T di = d_in[i];
-    const T r = r_in[i] - ad;
-    const T dn = c1 * di + c2 * L.dinv[i] * r;
-    r_out[i] = r;
-    d_out[i] = dn;
-    L.x[i] += pending ? dn + di : dn;
-  }
+  EQS_GROUP_ROWS2(L.A, n, g, {
+    const T a0 = mat_row(L.A, t0, n, d_in);
+    const T a1 = mat_row(L.A, t1, n, d_in);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t t = h ? t1 : t0;
+      if (!row_leader(L.A, t, n)) continue;
+      const int i = (int)(t >> L.A.logG);
+      const T di = d_in[i];
+      const T r = r_in[i] - (h ? a1 : a0);
+      const T dn = c1 * di + c2 * L.dinv[i] * r;
+      r_out[i] = r;
+      d_out[i] = dn;
+      L.x[i] += pending ? dn + di : dn;
+    }
+  })
 }
 
 template <typename T>
 __device__ __forceinline__ void ph_resid_update(const PLevel<T>& L, const T* d, const GridCtx& g) {
   const int n = L.n;
-  const int64_t lim = round32((int64_t)n << L.A.logG);
-  for (int64_t t = g.tid; t < lim; t += g.stride) {
-    const T ad = mat_row(L.A, t, n, d);
-    if (!row_leader(L.A, t, n)) continue;
-    const int i = (int)(t >> L.A.logG);
-    L.r[i] = L.r[i] - ad;
-  }
+  EQS_GROUP_ROWS2(L.A, n, g, {
+    const T a0 = mat_row(L.A, t0, n, d);
+    const T a1 = mat_row(L.A, t1, n, d);
+    if (row_leader(L.A, t0, n)) L.r[t0 >> L.A.logG] -= a0;
+    if (row_leader(L.A, t1, n)) L.r[t1 >> L.A.logG] -= a1;
+  })
 }
 
 template <typename T>
 __device__ __forceinline__ void ph_resid(const PLevel<T>& L, const GridCtx& g) {
   const int n = L.n;
-  const int64_t lim = round32((int64_t)n << L.A.logG);
-  for (int64_t t = g.tid; t < lim; t += g.stride) {
-    const T ax = mat_row(L.A, t, n, L.x);
-    if (!row_leader(L.A, t, n)) continue;
-    const int i = (int)(t >> L.A.logG);
-    L.r[i] = L.b[i] - ax;
-  }
+  EQS_GROUP_ROWS2(L.A, n, g, {
+    const T a0 = mat_row(L.A, t0, n, L.x);
+    const T a1 = mat_row(L.A, t1, n, L.x);
+    if (row_leader(L.A, t0, n)) L.r[t0 >> L.A.logG] = L.b[t0 >> L.A.logG] - a0;
+    if (row_leader(L.A, t1, n)) L.r[t1 >> L.A.logG] = L.b[t1 >> L.A.logG] - a1;
+  })
 }
 
 template <typename T>
 __device__ __forceinline__ void ph_restrict(const PLevel<T>& F, const PLevel<T>& C, int first,
                                             const GridCtx& g) {
   const int nc = C.n;
-  const int64_t lim = round32((int64_t)nc << F.R.logG);
-  for (int64_t t = g.tid; t < lim; t += g.stride) {
-    const T b = mat_row(F.R, t, nc, F.r);
-    if (!row_leader(F.R, t, nc)) continue;
-    const int i = (int)(t >> F.R.logG);
-    C.b[i] = b;
-    if (first) {
-      const T d = C.dinv[i] * b * C.inv_theta;
-      C.x[i] = d;
-      C.dA[i] = d;
+  EQS_GROUP_ROWS2(F.R, nc, g, {
+    const T b0 = mat_row(F.R, t0, nc, F.r);
+    const T b1 = mat_row(F.R, t1, nc, F.r);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t t = h ? t1 : t0;
+      if (!row_leader(F.R, t, nc)) continue;
+      const int i = (int)(t >> F.R.logG);
+      const T b = h ? b1 : b0;
+      C.b[i] = b;
+      if (first) {
+        const T d = C.dinv[i] * b * C.inv_theta;
+        C.x[i] = d;
+        C.dA[i] = d;
+      }
     }
-  }
+  })
 }
 
 template <typename T>
 __device__ __forceinline__ void ph_prolong(const PLevel<T>& F, const PLevel<T>& C, const GridCtx& g) {
   const int n = F.n;
-  const int64_t lim = round32((int64_t)n << F.P.logG);
-  for (int64_t t = g.tid; t < lim; t += g.stride) {
-    const T px = mat_row(F.P, t, n, C.x);
-    if (!row_leader(F.P, t, n)) continue;
-    F.x[t >> F.P.logG] += px;
-  }
+  EQS_GROUP_ROWS2(F.P, n, g, {
+    const T p0 = mat_row(F.P, t0, n, C.x);
+    const T p1 = mat_row(F.P, t1, n, C.x);
+    if (row_leader(F.P, t0, n)) F.x[t0 >> F.P.logG] += p0;
+    if (row_leader(F.P, t1, n)) F.x[t1 >> F.P.logG] += p1;
+  })
 }
 
 template <typename T>
 __device__ __forceinline__ void ph_post_first(const PLevel<T>& L, const GridCtx& g) {
   const int n = L.n;
-  const int64_t lim = round32((int64_t)n << L.A.logG);
-  for (int64_t t = g.tid; t < lim; t += g.stride) {
-    const T ax = mat_row(L.A, t, n, L.x);
-    if (!row_leader(L.A, t, n)) continue;
-    const int i = (int)(t >> L.A.logG);
-    const T r = L.b[i] - ax;
-    L.r[i] = r;
-    L.dA[i] = L.dinv[i] * r * L.inv_theta;
-  }
+  EQS_GROUP_ROWS2(L.A, n, g, {
+    const T a0 = mat_row(L.A, t0, n, L.x);
+    const T a1 = mat_row(L.A, t1, n, L.x);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t t = h ? t1 : t0;
+      if (!row_leader(L.A, t, n)) continue;
+      const int i = (int)(t >> L.A.logG);
+      const T r = L.b[i] - (h ? a1 : a0);
+      L.r[i] = r;
+      L.dA[i] = L.dinv[i] * r * L.inv_theta;
+    }
+  })
 }
 
 template <typename T>
@@ -1149,13 +1170,21 @@ __device__ bool pcg_group_solve(const PPlan<T>& P, const GridCtx& g, const doubl
     // p = z + beta p ; q = M z + beta q (q_old = M p_old), row-local
     {
       double v[1] = {0.0};
-      for (int64_t i = g.tid; i < n; i += g.stride) {
-        const double w = mat_row<double>(P.M, i, n, P.zd);
-        const double qi = beta == 0.0 ? w : fma(beta, P.q[i], w);
-        const double pi = beta == 0.0 ? P.zd[i] : fma(beta, P.pA[i], P.zd[i]);
-        P.pA[i] = pi;
-        P.q[i] = qi;
-        v[0] += pi * qi;
+      for (int64_t i0 = g.tid; i0 < n; i0 += 2 * g.stride) {
+        const int64_t i1 = i0 + g.stride;
+        const double w0 = mat_row<double>(P.M, i0, n, P.zd);
+        const double w1 = mat_row<double>(P.M, i1, n, P.zd);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int64_t i = h ? i1 : i0;
+          if (i >= n) continue;
+          const double w = h ? w1 : w0;
+          const double qi = beta == 0.0 ? w : fma(beta, P.q[i], w);
+          const double pi = beta == 0.0 ? P.zd[i] : fma(beta, P.pA[i], P.zd[i]);
+          P.pA[i] = pi;
+          P.q[i] = qi;
+          v[0] += pi * qi;
+        }
       }
       put_partials<1>(v, g.partials, 4, nb, g.rank);
     }

@@ -16,6 +16,7 @@
 #include "kernels.cuh"
 #include "mlp_kernels.cuh"
 #include "batch_kernels.cuh"
+#include "spe_kernels.cuh"
 
 using namespace eqs;
 
@@ -506,6 +507,30 @@ static void elem_launch(eqs_ctx* c, cudaStream_t st, const double* Y, int n_limi
 static double* Ybuf(eqs_ctx* c, int j) { return j == 0 ? c->d_Y[0] : c->d_Y[1 + (j - 1) % 3]; }
 static double* Fbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_F[0] : c->d_F[1 + (j - 1) % 2]; }
 
+// SPE start vector of solve j into x0 (templated on the history length).
+template <int NH>
+static void spe_launch_n(eqs_ctx* c, cudaStream_t st, int s, int j, double* x0) {
+  const int nf = (int)c->n_free;
+  launch(k_spe_mx<NH>, nblk(nf), kBlock, st, c->M64, nf, (const double*)c->d_spe_X, c->d_spe_R,
+         (const long long*)c->d_stepcount, s, j);
+  launch(k_spe_gram<NH>, vec_grid(c, nf), kBlock, st, nf, (const double*)c->d_spe_X, (const double*)c->d_spe_R,
+         (const double*)c->d_R, (const long long*)c->d_stepcount, s, j, c->d_spe_partials, c->red.counter,
+         c->red.max_blocks, 1e-12, c->d_spe_y);
+  launch(k_spe_combine<NH>, vec_grid(c, nf), kBlock, st, nf, (const double*)c->d_spe_X,
+         (const double*)c->d_spe_y, (const long long*)c->d_stepcount, s, j, x0);
+}
+
+static void spe_launch(eqs_ctx* c, cudaStream_t st, int s, int j, double* x0) {
+  switch (c->opts.spe_n) {
+    case 1: spe_launch_n<1>(c, st, s, j, x0); break;
+    case 2: spe_launch_n<2>(c, st, s, j, x0); break;
+    case 3: spe_launch_n<3>(c, st, s, j, x0); break;
+    case 4: spe_launch_n<4>(c, st, s, j, x0); break;
+    case 5: spe_launch_n<5>(c, st, s, j, x0); break;
+    default: spe_launch_n<6>(c, st, s, j, x0); break;
+  }
+}
+
 // Enqueue one RKC step on st: captured into a graph (c->direct false) or
 // launched directly with a host-driven CG loop (c->direct true).
 template <typename T>
@@ -535,7 +560,8 @@ static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
           j - 1, c->d_dir_scale, c->d_g + j, c->d_gp + j, c->d_mtop, Ybuf(c, j),
           (mx && !last) ? c->d_Y32 : nullptr, last ? nullptr : Fbuf(c, j),
           (mx || last) ? nullptr : c->d_R, last ? xdev : nullptr, c->d_node_of_internal, c->d_ring,
-          (const long long*)c->d_stepcount, s, c->recording ? c->d_store : nullptr, (long long)c->store_cap);
+          (const long long*)c->d_stepcount, s, c->recording ? c->d_store : nullptr, (long long)c->store_cap,
+          c->d_spe_X, c->opts.spe_n);
       if (last) break;
     }
     if (mx) {
@@ -554,6 +580,9 @@ static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
              (const int32_t*)c->d_adj_col, (const float*)c->d_inv_deg,
              (const __nv_bfloat16*)c->d_theta_bf16, (const double*)c->d_sh, Fbuf(c, j));
       stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, h1, c->d_mlp_used + j);
+    } else if (c->opts.guess == EQS_GUESS_SPE) {
+      spe_launch(c, st, s, j, Fbuf(c, j));
+      stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl);
     } else {
       if (c->opts.guess == EQS_GUESS_ZERO && cudaMemsetAsync(Fbuf(c, j), 0, nf * sizeof(double), st) != cudaSuccess)
         stt = fail(c, EQS_ERR_CUDA, "cudaMemsetAsync failed during capture");
@@ -684,6 +713,7 @@ void eqs_opts_default(eqs_opts* o) {
   o->flexible = 1;
   o->persistent = 1;
   o->blocks_per_sm = 1;
+  o->spe_n = 4;
   o->host_loop = 0;
 }
 
@@ -750,7 +780,7 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     o = *opts;
   else
     eqs_opts_default(&o);
-  if (o.cheb_degree < 1 || o.cheb_degree > 4 || o.blocks_per_sm < 0 || o.max_levels < 1 || o.coarse_max < 1 ||
+  if (o.cheb_degree < 1 || o.cheb_degree > 4 || o.blocks_per_sm < 0 || o.spe_n < 1 || o.spe_n > kSpeMax || o.max_levels < 1 || o.coarse_max < 1 ||
       !(o.theta >= 0) || !(o.cheb_alpha > 1) || !(o.rtol > 0) || o.max_iter < 1 ||
       (o.precision != EQS_PREC_FP64 && o.precision != EQS_PREC_MIXED))
     return fail(c, EQS_ERR_ARG, "invalid eqs_opts");
@@ -886,6 +916,10 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     CK(dalloc(c, &c->d_sh, 1));
     CK(dalloc(c, &c->d_mlp_used, EQS_MAX_STAGES + 1));
     CK(dalloc(c, &c->d_rtmp, nf));
+    CK(dalloc(c, &c->d_spe_X, (size_t)kSpeMax * nf));
+    CK(dalloc(c, &c->d_spe_R, (size_t)kSpeMax * nf));
+    CK(dalloc(c, &c->d_spe_y, kSpeMax));
+    CK(dalloc(c, &c->d_spe_partials, (size_t)kSpeSums * c->red.max_blocks));
     c->adam_t = 0;
     c->d_store = nullptr;
     c->d_store_rms = nullptr;
@@ -1149,9 +1183,15 @@ eqs_status eqs_amg_aggregates(const eqs_ctx* c, int level, int32_t* agg_out) {
 
 eqs_status eqs_set_guess(eqs_ctx* c, int mode) {
   REQUIRE_SETUP(c);
-  if (mode != EQS_GUESS_PREV && mode != EQS_GUESS_MLP && mode != EQS_GUESS_ZERO)
+  if (mode != EQS_GUESS_PREV && mode != EQS_GUESS_MLP && mode != EQS_GUESS_ZERO && mode != EQS_GUESS_SPE)
     return fail(c, EQS_ERR_ARG, "unknown guess mode");
-  if (mode != c->opts.guess) destroy_graphs(c);
+  if (mode != c->opts.guess) {
+    destroy_graphs(c);
+    if (mode == EQS_GUESS_SPE) {  // the right-hand-side ring starts empty: restart the history
+      CK(cudaStreamSynchronize(c->stream));
+      CK(cudaMemset(c->d_stepcount, 0, 2 * sizeof(long long)));
+    }
+  }
   c->opts.guess = mode;
   return EQS_OK;
 }
@@ -1270,6 +1310,33 @@ eqs_status eqs_guess_grad(eqs_ctx* c, const float* X, const float* T, int B, flo
   cudaFree(dX);
   cudaFree(dT);
   return st;
+}
+
+eqs_status eqs_spe_eval(eqs_ctx* c, const double* X, const double* Rh, const double* b, int n, double* x0) {
+  REQUIRE_SETUP(c);
+  if (!X || !Rh || !b || !x0) return fail(c, EQS_ERR_ARG, "null vector");
+  if (n != c->opts.spe_n) return fail(c, EQS_ERR_ARG, "n must equal the context's spe_n");
+  const int64_t nf = c->n_free;
+  cudaStream_t st = c->stream;
+  long long* cnt = nullptr;
+  CK(cudaMalloc(&cnt, 2 * sizeof(long long)));
+  const long long gn[2] = {n, n + 1};  // solve index g = n: column k sits in slot n-1-k
+  cudaMemcpyAsync(cnt, gn, sizeof(gn), cudaMemcpyHostToDevice, st);
+  for (int k = 0; k < n; ++k) {
+    cudaMemcpyAsync(c->d_spe_X + (size_t)(n - 1 - k) * nf, X + (size_t)k * nf, nf * sizeof(double),
+                    cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(c->d_spe_R + (size_t)(n - 1 - k) * nf, Rh + (size_t)k * nf, nf * sizeof(double),
+                    cudaMemcpyDeviceToDevice, st);
+  }
+  cudaMemcpyAsync(c->d_R, b, nf * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  long long* saved = c->d_stepcount;
+  c->d_stepcount = cnt;
+  spe_launch(c, st, 1, 0, x0);
+  c->d_stepcount = saved;
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(cnt);
+  if (e != cudaSuccess) return fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
+  return EQS_OK;
 }
 
 eqs_status eqs_guess_eval(eqs_ctx* c, const double* H, double* z0) {

@@ -18,7 +18,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 EQS_OK, EQS_ERR_ARG, EQS_ERR_MESH, EQS_ERR_CUDA = 0, -1, -2, -3
 EQS_ERR_NOCONV, EQS_ERR_TIMEOUT, EQS_ERR_NAN, EQS_ERR_STATE = -4, -5, -6, -7
 EQS_PREC_FP64, EQS_PREC_MIXED = 0, 1
-EQS_GUESS_PREV, EQS_GUESS_MLP, EQS_GUESS_ZERO = 0, 1, 2
+EQS_GUESS_PREV, EQS_GUESS_MLP, EQS_GUESS_ZERO, EQS_GUESS_SPE = 0, 1, 2, 3
 EQS_MAX_STAGES = 64
 
 
@@ -38,7 +38,7 @@ class eqs_opts(C.Structure):
                 ("max_levels", C.c_int), ("cheb_degree", C.c_int), ("cheb_alpha", C.c_double),
                 ("rtol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int),
                 ("flexible", C.c_int), ("persistent", C.c_int), ("blocks_per_sm", C.c_int),
-                ("host_loop", C.c_int)]
+                ("spe_n", C.c_int), ("host_loop", C.c_int)]
 
 
 class eqs_batch_stats(C.Structure):
@@ -94,6 +94,7 @@ def _declare(L):
         "eqs_guess_train": (I, [P, I, I, C.c_float, C.c_uint64, P, P]),
         "eqs_guess_grad": (I, [P, P, P, I, P, P]),
         "eqs_guess_eval": (I, [P, P, P]),
+        "eqs_spe_eval": (I, [P, P, P, P, I, P]),
         "eqs_batch_create": (I, [P, I, I, C.POINTER(C.c_void_p)]),
         "eqs_batch_rkc_step": (I, [P, P, D, D, I, C.POINTER(eqs_batch_stats)]),
         "eqs_batch_get_stats": (I, [P, C.POINTER(eqs_batch_stats), P]),
@@ -297,6 +298,10 @@ def eqs_batch_info(b):
 def eqs_batch_destroy(b):
     if b:
         lib().eqs_batch_destroy(b)
+
+
+def eqs_spe_eval(ctx, X, Rh, b, n, x0):
+    _check(lib().eqs_spe_eval(ctx, _dev(X), _dev(Rh), _dev(b), n, _dev(x0)), ctx)
 
 
 def eqs_destroy(ctx):
