@@ -35,6 +35,9 @@ WORKLOADS = {
     2: "cube128_jitter_spheres: 128^3-cell Kuhn cube with interior nodes jittered by +-0.2h, "
        "2146689 nodes (2113407 free), 12582912 P1 tets, two varistor spheres, s=20, "
        "dt=beta_s/rho, rtol=1e-8",
+    4: "batch64: 64 independent Kuhn cubes of seeded 16^3..48^3 cells, seeded block varistor "
+       "(0.2-0.5 of the edge) and drive 5e3-2e4 V, s=10, dt=beta_s/rho, rtol=1e-8, "
+       "mixed precision, one cooperative launch per stage",
 }
 RTOL = 1e-8
 S_STAGES = 20
@@ -44,6 +47,7 @@ WORKLOAD = WORKLOADS[CONFIG_INDEX]
 # smoothing and a 2066-row coarsest level (dense FP64 inverse) gave the
 # lowest step time on GB300 among degree 1-3 and coarse sizes 88/2066.
 SOLVER_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0)
+SPE_N = 6  # solutions spanning the SPE subspace
 # DRAM bytes (read + write) of one k_spmv64 launch per workload from an ncu
 # capture (profiles/k_spmv64_cube64.md); None where not captured.
 TRAFFIC_SPMV64 = {1: 34096128, 2: None}
@@ -58,8 +62,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--N", type=int, default=None, help="override mesh size (testing)")
-    ap.add_argument("--config", type=int, default=1, choices=[1, 2],
-                    help="workload: 1 = 64^3 block cube (default), 2 = 128^3 jittered spheres")
+    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 4],
+                    help="workload: 1 = 64^3 block cube (default), 2 = 128^3 jittered spheres, "
+                         "4 = batched serving of 64 instances")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the CG loops from the host (same kernels; for ncu launch lists)")
     return ap.parse_args()
@@ -205,8 +210,15 @@ def run_ours(args, rank, world):
     def flush():
         flushbuf.zero_()
 
-    def measure(precision, steps, warmup):
-        solver = eqs.Solver(p, precision=precision, rtol=RTOL, host_loop=int(args.host_loop), **SOLVER_OPTS)
+    def make(precision, guess, theta=None):
+        solver = eqs.Solver(p, precision=precision, rtol=RTOL, host_loop=int(args.host_loop),
+                            spe_n=SPE_N, **SOLVER_OPTS)
+        if theta is not None:
+            eqs.eqs_guess_set_params(solver.ctx, theta)
+        eqs.eqs_set_guess(solver.ctx, guess)
+        return solver
+
+    def measure(solver, steps, warmup):
         dt = solver.dt_bound(S_STAGES)
         x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
         t = 0.0
@@ -217,11 +229,17 @@ def run_ours(args, rank, world):
         clk = ClockSampler(local)
         times, launches, iters, t = time_steps(torch, solver, x, t, dt, steps, flush)
         barrier()
-        clocks = clk.stop()
-        return solver, x, t, dt, times, launches, iters, clocks
+        return x, t, dt, times, launches, iters, clk.stop()
 
-    solver, x, t, dt, times, launches, iters, clocks = measure(eqs.EQS_PREC_MIXED, args.steps,
-                                                               args.warmup)
+    def summary(times, iters):
+        return {"value": p.n_free * S_STAGES * len(times) / (sum(times) / 1e3),
+                "ms_per_step": sum(times) / len(times),
+                "m_solve_ms_per_rhs": sum(times) / len(times) / S_STAGES,
+                "cg_iters_per_solve": float(np.mean(iters))}
+
+    # headline: mixed precision with the SPE start vector (Section IV)
+    solver = make(eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_SPE)
+    x, t, dt, times, launches, iters, clocks = measure(solver, args.steps, args.warmup)
     total_ms = sum(times)
     if dist is not None:
         tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
@@ -253,26 +271,45 @@ def run_ours(args, rank, world):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
     e2e_value = units / (e2e_ms / 1e3)
-
-    # dominant kernel, timed alone with L2 flushed between launches
     roof = dominant_kernel_roofline(torch, eqs, solver, p, flush)
+    solver.close()
 
-    # plain FP64 AMG-PCG form of the same workload
-    fp64 = None
+    variants = {}
     if not args.no_fp64:
-        s64, _, _, _, t64, _, it64, _ = measure(eqs.EQS_PREC_FP64, max(3, args.steps // 4), 2)
-        fp64 = {"value": p.n_free * S_STAGES * len(t64) / (sum(t64) / 1e3),
-                "ms_per_step": sum(t64) / len(t64), "cg_iters_per_solve": float(np.mean(it64))}
-        s64.close()
+        short = max(3, args.steps // 4)
+        # fp64_plain is the metric's baseline: plain FP64 AMG-PCG, previous-solution start
+        for name, prec, guess in (("fp64_plain", eqs.EQS_PREC_FP64, eqs.EQS_GUESS_PREV),
+                                  ("mixed_prev", eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_PREV),
+                                  ("fp64_spe", eqs.EQS_PREC_FP64, eqs.EQS_GUESS_SPE)):
+            S = make(prec, guess)
+            r = measure(S, short, 2)
+            variants[name] = summary(r[3], r[5])
+            S.close()
+        # learned start vector: record FP64 stage solutions, train on the GPU
+        rec = make(eqs.EQS_PREC_FP64, eqs.EQS_GUESS_PREV, ei.mlp_init())
+        eqs.eqs_guess_record(rec.ctx, 5 * S_STAGES)
+        xr = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+        dtr = rec.dt_bound(S_STAGES)
+        for k in range(5):
+            rec.step(xr, k * dtr, dtr, S_STAGES)
+        t0 = time.perf_counter()
+        lf, ll = eqs.eqs_guess_train(rec.ctx, 400, 8192, 2e-3, 1612094470)
+        train_s = time.perf_counter() - t0
+        theta = eqs.eqs_guess_get_params(rec.ctx)
+        rec.close()
+        S = make(eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_MLP, theta)
+        r = measure(S, short, 2)
+        variants["mixed_mlp"] = dict(summary(r[3], r[5]), train_s=train_s, loss_first=lf, loss_last=ll)
+        S.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = oracle_sample(4, args.N)
-        cpu = {"value": r["dof_stages_per_s"], "unit": "DOF-stages/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {r['stages']} stage evaluations of one RKC step "
-                         f"({r['seconds']:.1f} s, numpy/scipy FP64 AMG-PCG, single thread)"}
+        rr = oracle_sample(4, args.N)
+        cpu = {"value": rr["dof_stages_per_s"], "unit": "DOF-stages/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {rr['stages']} stage evaluations of one RKC step "
+                         f"({rr['seconds']:.1f} s, numpy/scipy FP64 AMG-PCG with previous-solution "
+                         f"start, single thread)"}
     if rank != 0:
-        solver.close()
         return
     ms_step = total_ms / args.steps
     line = {
@@ -281,13 +318,14 @@ def run_ours(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/f64 mixed", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_free": p.n_free, "stages": S_STAGES, "rtol": RTOL,
-                   "solver": SOLVER_OPTS,
-                   "precision": "mixed (FP32 element kernel and V-cycle; FP64 CG, recurrence)",
+                   "solver": dict(SOLVER_OPTS, spe_n=SPE_N),
+                   "form": "mixed precision (FP32 element kernel and V-cycle; FP64 CG, recurrence) "
+                           "+ SPE start vectors (Section IV)",
                    "m_solve_ms_per_rhs": ms_step / S_STAGES,
                    "cg_iters_per_solve": float(np.mean(iters)),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
-        "fp64_plain": fp64,
+        "forms": variants,
         "e2e": {"value": e2e_value, "unit": "DOF-stages/s", "h2d_bytes_per_step": p.n_nodes * 8,
                 "d2h_bytes_per_step": p.n_nodes * 8},
         "gpu_launches": int(launches),
@@ -296,7 +334,6 @@ def run_ours(args, rank, world):
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
-    solver.close()
     if dist is not None:
         dist.destroy_process_group()
 
@@ -340,11 +377,93 @@ def dominant_kernel_roofline(torch, eqs, solver, p, flush):
             "peak_kind": f"{kind} hbm_gbs (burst: kernel timed alone, L2 flushed before each launch)"}
 
 
+def run_batch(args, rank, world):
+    """Batched serving: all instances advance together, one cooperative launch
+    per stage (rows per CTA autotuned); the same instances stepped one after
+    another with the single-instance graphs are measured beside it."""
+    import torch
+
+    import eqs_inputs as ei
+    from paper_1612_09447_gb300 import autotune, eqs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    eqs.lib()
+    s = 10
+    probs = [ei.config_problem(4, instance=i) for i in range(64)]
+    solvers = [eqs.Solver(p, precision=eqs.EQS_PREC_MIXED, rtol=RTOL, **SOLVER_OPTS) for p in probs]
+    nfree = sum(S.nf for S in solvers)
+    best, tuning = autotune.tune_batch(eqs, solvers, candidates=(256, 512, 1024, 2048), s=s, steps=2)
+    b = eqs.eqs_batch_create([S.ctx for S in solvers], best)
+    ctas, rows_used = eqs.eqs_batch_info(b)
+    dt = solvers[0].dt_bound(s)
+    xs = [torch.zeros(S.n, dtype=torch.float64, device="cuda") for S in solvers]
+    t = 0.0
+    for _ in range(args.warmup):
+        eqs.eqs_batch_rkc_step(b, xs, t, dt, s)
+        t += dt
+    flushbuf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    times, iters = [], 0
+    for _ in range(args.steps):
+        flushbuf.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        eqs.eqs_batch_rkc_step(b, xs, t, dt, s, want_stats=False)
+        e1.record()
+        st, _ = eqs.eqs_batch_get_stats(b, len(solvers))
+        times.append(e0.elapsed_time(e1))
+        iters += st.total_iters
+        t += dt
+    clocks = clk.stop()
+    launches = st.launches * args.steps
+    total_ms = sum(times)
+    value = nfree * s * args.steps / (total_ms / 1e3)
+    # the same instances one after another (single-instance step graphs)
+    xsolo = [torch.zeros(S.n, dtype=torch.float64, device="cuda") for S in solvers]
+    ts = 0.0
+    for S, x in zip(solvers, xsolo):
+        S.step(x, 0.0, dt, s)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(2):
+        for S, x in zip(solvers, xsolo):
+            S.step(x, dt * (k + 1), dt, s, stats=False)
+    e1.record()
+    e1.synchronize()
+    seq_value = nfree * s * 2 / (e0.elapsed_time(e1) / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF-stages/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/f64 mixed", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances": len(solvers), "n_free_total": nfree,
+                   "stages": s, "rtol": RTOL, "rows_per_block": rows_used, "ctas": ctas,
+                   "autotune_ms_per_step": {str(k): v[0] for k, v in tuning.items()},
+                   "cg_iters_per_solve": iters / (args.steps * s * len(solvers)),
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "sequential_single_instance": {"value": seq_value, "unit": "DOF-stages/s"},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    eqs.eqs_batch_destroy(b)
+    for S in solvers:
+        S.close()
+
+
 def main():
     global CONFIG_INDEX, WORKLOAD
     args = parse()
     CONFIG_INDEX = args.config
     WORKLOAD = WORKLOADS[CONFIG_INDEX]
+    if args.config == 4 and args.impl == "ours":
+        run_batch(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
