@@ -35,6 +35,9 @@ WORKLOADS = {
     2: "cube128_jitter_spheres: 128^3-cell Kuhn cube with interior nodes jittered by +-0.2h, "
        "2146689 nodes (2113407 free), 12582912 P1 tets, two varistor spheres, s=20, "
        "dt=beta_s/rho, rtol=1e-8",
+    3: "learned start vector on cube128_jitter_spheres (2113407 free rows, s=20, rtol=1e-8): "
+       "trained on the GPU on 400 stage solutions of 20 FP64 steps, then mixed precision with "
+       "the learned guess against the previous-solution guess",
     4: "batch64: 64 independent Kuhn cubes of seeded 16^3..48^3 cells, seeded block varistor "
        "(0.2-0.5 of the edge) and drive 5e3-2e4 V, s=10, dt=beta_s/rho, rtol=1e-8, "
        "mixed precision, one cooperative launch per stage",
@@ -62,9 +65,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--N", type=int, default=None, help="override mesh size (testing)")
-    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 4],
+    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3, 4],
                     help="workload: 1 = 64^3 block cube (default), 2 = 128^3 jittered spheres, "
-                         "4 = batched serving of 64 instances")
+                         "3 = learned guess on the 128^3 mesh, 4 = batched serving of 64 instances")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the CG loops from the host (same kernels; for ncu launch lists)")
     return ap.parse_args()
@@ -456,11 +459,76 @@ def run_batch(args, rank, world):
         S.close()
 
 
+def run_learned(args):
+    """Record 20 FP64 steps (400 stage solutions) on the 128^3 jittered mesh,
+    train the start-vector network on the GPU, then run mixed-precision steps
+    with the learned guess and with the previous-solution guess."""
+    import numpy as np
+    import torch
+
+    import eqs_inputs as ei
+    from paper_1612_09447_gb300 import eqs
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    p = ei.config_problem(3, N=args.N)
+    rec = eqs.Solver(p, precision=eqs.EQS_PREC_FP64, rtol=RTOL, **SOLVER_OPTS)
+    eqs.eqs_guess_set_params(rec.ctx, ei.mlp_init())
+    eqs.eqs_guess_record(rec.ctx, 20 * S_STAGES)
+    x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+    dt = rec.dt_bound(S_STAGES)
+    for k in range(20):
+        rec.step(x, k * dt, dt, S_STAGES)
+    x_start, t_start = x.clone(), 20 * dt
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lf, ll = eqs.eqs_guess_train(rec.ctx, 2000, 16384, 2e-3, 1612094470)
+    train_s = time.perf_counter() - t0
+    theta = eqs.eqs_guess_get_params(rec.ctx)
+    rec.close()
+    out = {}
+    for name, guess in (("previous_solution", eqs.EQS_GUESS_PREV), ("learned", eqs.EQS_GUESS_MLP)):
+        S = eqs.Solver(p, precision=eqs.EQS_PREC_MIXED, rtol=RTOL, **SOLVER_OPTS)
+        eqs.eqs_guess_set_params(S.ctx, theta)
+        eqs.eqs_set_guess(S.ctx, guess)
+        x.copy_(x_start)
+        t = t_start
+        for _ in range(2):  # the history ring refills
+            S.step(x, t, dt, S_STAGES)
+            t += dt
+        times, iters, kept = [], 0, 0
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            S.step(x, t, dt, S_STAGES, stats=False)
+            e1.record()
+            st = S.last_stats()
+            times.append(e0.elapsed_time(e1))
+            iters += st.total_iters
+            kept += st.guess_kept
+            t += dt
+        out[name] = {"ms_per_step": float(np.mean(times)), "cg_iters_per_solve": iters / (args.steps * S_STAGES),
+                     "value": p.n_free * S_STAGES * args.steps / (sum(times) / 1e3),
+                     "learned_guess_kept": kept / (args.steps * S_STAGES)}
+        S.close()
+    line = {"metric": METRIC, "value": out["learned"]["value"], "unit": "DOF-stages/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": 2, "ms_per_step": out["learned"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_free": p.n_free, "train_iters": 2000, "batch": 16384,
+                       "train_s": train_s, "loss_first": lf, "loss_last": ll},
+            "forms": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global CONFIG_INDEX, WORKLOAD
     args = parse()
     CONFIG_INDEX = args.config
     WORKLOAD = WORKLOADS[CONFIG_INDEX]
+    if args.config == 3 and args.impl == "ours":
+        run_learned(args)
+        return
     if args.config == 4 and args.impl == "ours":
         run_batch(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
         return

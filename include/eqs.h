@@ -95,6 +95,10 @@ typedef struct {
                           convergence flag after every iteration) instead of
                           replaying a graph; for profilers that cannot enter
                           graph loops.  Default 0.                            */
+  long long barrier_polls; /* wait budget of one grid barrier of the persistent
+                          solve, in polls: 0 = default (2^22, about a second),
+                          < 0 = no waiting at all (every wait gives up at
+                          once; for testing the EQS_ERR_TIMEOUT path)        */
 } eqs_opts;
 
 #define EQS_MAX_STAGES 64

@@ -67,6 +67,7 @@ __device__ __forceinline__ GridCtx batch_group(const BatchInst* insts, const int
   g.stride = (int64_t)g.nblocks * blockDim.x;
   g.bar = insts[b].bar;
   g.partials = insts[b].partials;
+  g.max_spins = kMaxSpins;
   return g;
 }
 
@@ -111,15 +112,15 @@ __global__ void __launch_bounds__(kPBlock) k_batch_stage(
   const BatchInst& I = insts[b];
   const double gj = gtab[b * (s + 1) + j], gpj = gptab[b * (s + 1) + j];
   batch_stage_vector(I, g, j, s, c0, mu, nu, mut, gt, prm->dt, gj, xmesh[b], nullptr);
-  if (!grid_barrier(g.bar, g.nblocks)) return;
+  if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return;
   for (int64_t e = g.tid; e < I.nt; e += g.stride)
     elem32_tet(e, I.conn, I.mat, I.mats, I.xh, I.xl, I.Y32, I.nf, I.y32);
-  if (!grid_barrier(g.bar, g.nblocks)) return;
+  if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return;
   for (int64_t i = g.tid; i < I.nf; i += g.stride) {
     I.R[i] = -(double)I.y32[i] - gpj * I.mtop[i];
     I.y32[i] = 0.0f;
   }
-  if (!grid_barrier(g.bar, g.nblocks)) return;
+  if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return;
   pcg_group_solve(*I.plan, g, I.R, bF(I, j), tol2, I.iters + j, I.relres + j, I.zero + j);
 }
 

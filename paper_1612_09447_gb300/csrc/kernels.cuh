@@ -256,16 +256,29 @@ __global__ void k_axpy1(int n, T* __restrict__ x, const T* __restrict__ d) {
   for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] += d[i];
 }
 
-// Coarsest level: x = A_c^-1 b with the dense FP64 inverse; one warp per row.
+// Coarsest level: x = A_c^-1 b with the dense FP64 inverse; one warp per
+// row.  b is staged once per block in shared memory as FP64 (dynamic shared
+// memory of n doubles), so the inner loop has no conversions; two
+// accumulation chains per lane.
 template <typename T>
 __global__ void k_coarse_solve(int n, const double* __restrict__ inv, const T* __restrict__ b,
                                T* __restrict__ x) {
+  extern __shared__ double sb[];
   pdl_enter();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) sb[j] = (double)b[j];
+  __syncthreads();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
-  double acc = 0.0;
-  for (int j = lane; j < n; j += 32) acc = fma(inv[(int64_t)warp * n + j], (double)b[j], acc);
+  const double* __restrict__ row = inv + (int64_t)warp * n;
+  double a0 = 0.0, a1 = 0.0;
+  int j = lane;
+  for (; j + 32 < n; j += 64) {
+    a0 = fma(__ldg(row + j), sb[j], a0);
+    a1 = fma(__ldg(row + j + 32), sb[j + 32], a1);
+  }
+  if (j < n) a0 = fma(__ldg(row + j), sb[j], a0);
+  double acc = a0 + a1;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) x[warp] = (T)acc;
@@ -868,6 +881,7 @@ struct PLevel {
 template <typename T>
 struct PPlan {
   int nl, deg, nf, maxit, flexible, pad;
+  long long max_spins;  // wait budget of one grid barrier (polls)
   const double* coarse_inv;
   DevSell<double> M;
   double *r, *rprev, *pA, *pB, *q, *zd;
@@ -884,9 +898,11 @@ struct GridCtx {
   unsigned int rank;        // this CTA's index in the group
   GridBarrier* bar;         // the group's barrier
   double* partials;         // the group's reduction slots (8 x nblocks)
+  long long max_spins;      // wait budget of one barrier (polls)
 };
 
-__device__ __forceinline__ bool grid_barrier(GridBarrier* b, unsigned int nblocks) {
+__device__ __forceinline__ bool grid_barrier(GridBarrier* b, unsigned int nblocks,
+                                             long long max_spins = kMaxSpins) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -901,7 +917,7 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* b, unsigned int nblock
     } else {
       long long spins = 0;
       while (*vgen == g) {
-        if (*(volatile int*)&b->err || ++spins > kMaxSpins) {
+        if (*(volatile int*)&b->err || ++spins > max_spins) {
           atomicExch(&b->err, 1);
           ok = 0;
           break;
@@ -1075,7 +1091,7 @@ __device__ bool vcycle_persistent(const PPlan<T>& P, const GridCtx& g) {
     const T* rin = L.b;
     for (int k = 2; k <= deg; ++k) {
       ph_cheb(L, rin, din, L.r, dout, L.c1[k], L.c2[k], 0, g);
-      if (!grid_barrier(g.bar, g.nblocks)) return false;
+      if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return false;
       rin = L.r;
       T* tmp = din;
       din = dout;
@@ -1085,30 +1101,30 @@ __device__ bool vcycle_persistent(const PPlan<T>& P, const GridCtx& g) {
       ph_resid_update(L, din, g);
     else
       ph_resid(L, g);
-    if (!grid_barrier(g.bar, g.nblocks)) return false;
+    if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return false;
     ph_restrict(L, P.lev[l + 1], l + 1 < nl - 1, g);
-    if (!grid_barrier(g.bar, g.nblocks)) return false;
+    if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return false;
   }
   ph_coarse(P.lev[nl - 1], P.coarse_inv, g);
-  if (!grid_barrier(g.bar, g.nblocks)) return false;
+  if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return false;
   for (int l = nl - 2; l >= 0; --l) {
     const PLevel<T>& L = P.lev[l];
     ph_prolong(L, P.lev[l + 1], g);
-    if (!grid_barrier(g.bar, g.nblocks)) return false;
+    if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return false;
     ph_post_first(L, g);
-    if (!grid_barrier(g.bar, g.nblocks)) return false;
+    if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return false;
     T* din = L.dA;
     T* dout = L.dB;
     for (int k = 2; k <= deg; ++k) {
       ph_cheb(L, L.r, din, L.r, dout, L.c1[k], L.c2[k], k == 2, g);
-      if (!grid_barrier(g.bar, g.nblocks)) return false;
+      if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return false;
       T* tmp = din;
       din = dout;
       dout = tmp;
     }
     if (deg == 1) {
       for (int64_t i = g.tid; i < L.n; i += g.stride) L.x[i] += L.dA[i];
-      if (!grid_barrier(g.bar, g.nblocks)) return false;
+      if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return false;
     }
   }
   return true;
@@ -1143,7 +1159,7 @@ __device__ bool pcg_group_solve(const PPlan<T>& P, const GridCtx& g, const doubl
     }
     put_partials<2>(v, g.partials, 0, nb, g.rank);
   }
-  if (!grid_barrier(g.bar, nb)) return false;
+  if (!grid_barrier(g.bar, nb, g.max_spins)) return false;
   const double bnorm2 = get_total(g.partials, 0, nb);
   double rnorm2 = get_total(g.partials, 1, nb);
   const int zero = bnorm2 == 0.0;
@@ -1162,7 +1178,7 @@ __device__ bool pcg_group_solve(const PPlan<T>& P, const GridCtx& g, const doubl
       }
       put_partials<2>(v, g.partials, 2, nb, g.rank);
     }
-    if (!grid_barrier(g.bar, nb)) return false;
+    if (!grid_barrier(g.bar, nb, g.max_spins)) return false;
     const double rz = get_total(g.partials, 2, nb);
     const double zrp = get_total(g.partials, 3, nb);
     const double beta = it == 0 ? 0.0 : (P.flexible ? (rz - zrp) / rz_old : rz / rz_old);
@@ -1188,7 +1204,7 @@ __device__ bool pcg_group_solve(const PPlan<T>& P, const GridCtx& g, const doubl
       }
       put_partials<1>(v, g.partials, 4, nb, g.rank);
     }
-    if (!grid_barrier(g.bar, nb)) return false;
+    if (!grid_barrier(g.bar, nb, g.max_spins)) return false;
     const double alpha = rz / get_total(g.partials, 4, nb);
     {
       double v[1] = {0.0};
@@ -1209,7 +1225,7 @@ __device__ bool pcg_group_solve(const PPlan<T>& P, const GridCtx& g, const doubl
       }
       put_partials<1>(v, g.partials, 5, nb, g.rank);
     }
-    if (!grid_barrier(g.bar, nb)) return false;
+    if (!grid_barrier(g.bar, nb, g.max_spins)) return false;
     rnorm2 = get_total(g.partials, 5, nb);
     ++it;
     conv = !(rnorm2 > tol2 * bnorm2);
@@ -1236,6 +1252,7 @@ __global__ void __launch_bounds__(kPBlock) k_pcg_persistent(const PPlan<T>* __re
   g.rank = blockIdx.x;
   g.bar = P.bar;
   g.partials = P.partials;
+  g.max_spins = P.max_spins;
   pcg_group_solve(P, g, R, x, tol2, iters_out, relres_out, zero_out);
 }
 

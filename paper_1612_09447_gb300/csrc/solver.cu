@@ -67,6 +67,25 @@ static void launch(void (*k)(KArgs...), int grid, int block, cudaStream_t st, Ar
   cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
 }
 
+// launch() with dynamic shared memory.
+template <typename... KArgs, typename... Args>
+static void launch_smem(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+  ++g_launches;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute a[1];
+  a[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  a[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = a;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
+}
+
+
 // ---------------------------------------------------------- device memory
 static void free_all(eqs_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
@@ -255,7 +274,8 @@ static void vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStr
   const int nl = (int)L.size();
   DevLevel<T>& V = L[l];
   if (l == nl - 1) {
-    launch(k_coarse_solve<T>, nblk((int64_t)V.n * 32), kBlock, st, V.n, c->d_coarse_inv, V.b, V.x);
+    launch_smem(k_coarse_solve<T>, nblk((int64_t)V.n * 32), kBlock, (size_t)V.n * sizeof(double), st, V.n,
+                c->d_coarse_inv, (const T*)V.b, V.x);
     return;
   }
   const int deg = c->opts.cheb_degree;
@@ -397,6 +417,8 @@ static eqs_status build_plan(eqs_ctx* c, std::vector<DevLevel<T>>& L) {
   P.nf = (int)c->n_free;
   P.maxit = c->opts.max_iter;
   P.flexible = c->opts.flexible;
+  P.max_spins = c->opts.barrier_polls > 0 ? (long long)c->opts.barrier_polls
+                                          : (c->opts.barrier_polls == 0 ? kMaxSpins : 0);
   P.coarse_inv = c->d_coarse_inv;
   P.M = c->M64;
   P.r = c->d_r;
@@ -513,7 +535,7 @@ static void spe_launch_n(eqs_ctx* c, cudaStream_t st, int s, int j, double* x0) 
   const int nf = (int)c->n_free;
   launch(k_spe_mx<NH>, nblk(nf), kBlock, st, c->M64, nf, (const double*)c->d_spe_X, c->d_spe_R,
          (const long long*)c->d_stepcount, s, j);
-  launch(k_spe_gram<NH>, vec_grid(c, nf), kBlock, st, nf, (const double*)c->d_spe_X, (const double*)c->d_spe_R,
+  launch(k_spe_gram<NH>, std::max(1, std::min(nblk(nf), c->sms)), kBlock, st, nf, (const double*)c->d_spe_X, (const double*)c->d_spe_R,
          (const double*)c->d_R, (const long long*)c->d_stepcount, s, j, c->d_spe_partials, c->red.counter,
          c->red.max_blocks, 1e-12, c->d_spe_y);
   launch(k_spe_combine<NH>, vec_grid(c, nf), kBlock, st, nf, (const double*)c->d_spe_X,
@@ -715,6 +737,7 @@ void eqs_opts_default(eqs_opts* o) {
   o->blocks_per_sm = 1;
   o->spe_n = 4;
   o->host_loop = 0;
+  o->barrier_polls = 0;
 }
 
 eqs_status eqs_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,

@@ -52,6 +52,8 @@ __global__ void k_spe_gram(int nf, const double* __restrict__ X, const double* _
     xs[k] = X + (size_t)slot * nf;
     ws[k] = Rr + (size_t)slot * nf;
   }
+  // few blocks with many rows each: the block reductions of NS values cost
+  // FP64 adds in every lane, so they must stay rare next to the row work
   for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x) {
     double xv[NH], wv[NH];
 #pragma unroll
@@ -64,10 +66,10 @@ __global__ void k_spe_gram(int nf, const double* __restrict__ X, const double* _
 #pragma unroll
     for (int k = 0; k < NH; ++k) {
 #pragma unroll
-      for (int l = k; l < NH; ++l) v[q++] += xv[k] * wv[l];
+      for (int l = k; l < NH; ++l) v[q] = fma(xv[k], wv[l], v[q]), ++q;
     }
 #pragma unroll
-    for (int k = 0; k < NH; ++k) v[q++] += xv[k] * bi;
+    for (int k = 0; k < NH; ++k) v[q] = fma(xv[k], bi, v[q]), ++q;
   }
   double tot[NS];
   if (grid_sum<NS>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {

@@ -38,7 +38,7 @@ class eqs_opts(C.Structure):
                 ("max_levels", C.c_int), ("cheb_degree", C.c_int), ("cheb_alpha", C.c_double),
                 ("rtol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int),
                 ("flexible", C.c_int), ("persistent", C.c_int), ("blocks_per_sm", C.c_int),
-                ("spe_n", C.c_int), ("host_loop", C.c_int)]
+                ("spe_n", C.c_int), ("host_loop", C.c_int), ("barrier_polls", C.c_longlong)]
 
 
 class eqs_batch_stats(C.Structure):

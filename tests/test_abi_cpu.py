@@ -94,3 +94,13 @@ def test_host_amg_matches_oracle(E, cfg, N):
         assert np.array_equal(agg, H.levels[l].agg)
     assert nnz[0] == H.levels[0].A.nnz
     E.eqs_destroy(ctx)
+
+
+def test_call_order_errors(E):
+    p = ei.make_problem(2)
+    ctx = E.eqs_mesh_create(p.xyz, p.tets, p.node_tag)
+    for call in (lambda: E.eqs_apply_K(ctx, None, None), lambda: E.eqs_get_step_stats(ctx)):
+        with pytest.raises(E.EqsError) as ex:
+            call()
+        assert ex.value.status == E.EQS_ERR_STATE
+    E.eqs_destroy(ctx)
