@@ -27,8 +27,15 @@ __device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(
 // (A x)_row, accumulation in T.  Thread `tid` serves row tid >> A.logG; with
 // G > 1 every lane of the row's group returns the full sum (all lanes of a
 // warp must call this, also those past the last row).
-template <typename T>
-__device__ __forceinline__ T mat_row(const DevSell<T>& A, int64_t tid, int n, const T* __restrict__ x) {
+// x_j (+ xadd_j when ADD: a pending update not yet added to x).
+template <typename T, bool ADD>
+__device__ __forceinline__ T xv(const T* __restrict__ x, const T* __restrict__ xadd, int j) {
+  return ADD ? __ldg(x + j) + __ldg(xadd + j) : __ldg(x + j);
+}
+
+template <typename T, bool ADD>
+__device__ __forceinline__ T mat_row_impl(const DevSell<T>& A, int64_t tid, int n, const T* __restrict__ x,
+                                          const T* __restrict__ xadd) {
   const int row = (int)(tid >> A.logG);
   T acc = T(0);
   if (A.G == 0) {  // DIA: independent, coalesced loads; two accumulation chains
@@ -40,13 +47,13 @@ __device__ __forceinline__ T mat_row(const DevSell<T>& A, int64_t tid, int n, co
     for (; d + 1 < A.ndiag; d += 2) {
       const int j0 = row + A.off[d], j1 = row + A.off[d + 1];
       const T a0 = __ldg(v + (int64_t)d * n), a1 = __ldg(v + (int64_t)(d + 1) * n);
-      if ((unsigned)j0 < (unsigned)A.n_cols) acc = fmadd(a0, __ldg(x + j0), acc);
-      if ((unsigned)j1 < (unsigned)A.n_cols) acc1 = fmadd(a1, __ldg(x + j1), acc1);
+      if ((unsigned)j0 < (unsigned)A.n_cols) acc = fmadd(a0, xv<T, ADD>(x, xadd, j0), acc);
+      if ((unsigned)j1 < (unsigned)A.n_cols) acc1 = fmadd(a1, xv<T, ADD>(x, xadd, j1), acc1);
     }
     if (d < A.ndiag) {
       const int j = row + A.off[d];
       const T a = __ldg(v + (int64_t)d * n);
-      if ((unsigned)j < (unsigned)A.n_cols) acc = fmadd(a, __ldg(x + j), acc);
+      if ((unsigned)j < (unsigned)A.n_cols) acc = fmadd(a, xv<T, ADD>(x, xadd, j), acc);
     }
     return acc + acc1;
   }
@@ -65,7 +72,7 @@ __device__ __forceinline__ T mat_row(const DevSell<T>& A, int64_t tid, int n, co
         a[u] = kk < end ? __ldg(A.val + kk) : T(0);
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) acc = fmadd(a[u], __ldg(x + c[u]), acc);
+      for (int u = 0; u < 8; ++u) acc = fmadd(a[u], xv<T, ADD>(x, xadd, c[u]), acc);
     }
     return acc;
   }
@@ -85,10 +92,22 @@ __device__ __forceinline__ T mat_row(const DevSell<T>& A, int64_t tid, int n, co
       a[u] = kk < end ? __ldg(A.val + kk) : T(0);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc = fmadd(a[u], __ldg(x + c[u]), acc);
+    for (int u = 0; u < 4; ++u) acc = fmadd(a[u], xv<T, ADD>(x, xadd, c[u]), acc);
   }
   for (int o = A.G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T mat_row(const DevSell<T>& A, int64_t tid, int n, const T* __restrict__ x) {
+  return mat_row_impl<T, false>(A, tid, n, x, nullptr);
+}
+
+// (A (x + xadd))_row
+template <typename T>
+__device__ __forceinline__ T mat_row_add(const DevSell<T>& A, int64_t tid, int n, const T* __restrict__ x,
+                                         const T* __restrict__ xadd) {
+  return mat_row_impl<T, true>(A, tid, n, x, xadd);
 }
 
 // (A (x1 + beta x2))_row for a one-thread-per-row matrix (DIA or SELL-32).
@@ -216,13 +235,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_restrict(DevSell<T> R, int nc, co
   })
 }
 
-// x_f += P x_c
+// x_f += P x_c, or P (x_c + d_c) when the coarse level's last Chebyshev
+// direction d_c is still pending
 template <typename T>
-__global__ void __launch_bounds__(kBlock, 4) k_prolong(DevSell<T> P, int nf, const T* __restrict__ xc, T* __restrict__ xf) {
+__global__ void __launch_bounds__(kBlock, 4) k_prolong(DevSell<T> P, int nf, const T* __restrict__ xc,
+                                                       const T* __restrict__ dc, T* __restrict__ xf) {
   pdl_enter();
   EQS_ROWS2(P, nf, {
-    const T p0 = mat_row(P, t0, nf, xc);
-    const T p1 = mat_row(P, t1, nf, xc);
+    const T p0 = dc ? mat_row_add(P, t0, nf, xc, dc) : mat_row(P, t0, nf, xc);
+    const T p1 = dc ? mat_row_add(P, t1, nf, xc, dc) : mat_row(P, t1, nf, xc);
     if (row_leader(P, t0, nf)) xf[t0 >> P.logG] += p0;
     if (row_leader(P, t1, nf)) xf[t1 >> P.logG] += p1;
   })
@@ -469,12 +490,13 @@ __global__ void k_pcg_select(int n, double* __restrict__ x, const double* __rest
 // beta (Fletcher-Reeves, or Polak-Ribiere when flexible).
 template <typename T>
 __global__ void k_pcg_dots(int n, const double* __restrict__ r, const double* __restrict__ rprev,
-                           const T* __restrict__ z, double* __restrict__ zd, PcgScalars* sc,
-                           double* partials, unsigned int* counter, int max_blocks, int flexible) {
+                           const T* __restrict__ z, const T* __restrict__ zpend, double* __restrict__ zd,
+                           PcgScalars* sc, double* partials, unsigned int* counter, int max_blocks,
+                           int flexible) {
   pdl_enter();
   double v[2] = {0.0, 0.0};
   for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double zi = (double)z[i];
+    const double zi = zpend ? (double)(z[i] + zpend[i]) : (double)z[i];
     zd[i] = zi;
     v[0] += r[i] * zi;
     v[1] += rprev[i] * zi;

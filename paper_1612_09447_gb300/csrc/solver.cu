@@ -269,14 +269,16 @@ static cudaError_t upload_levels(eqs_ctx* c, std::vector<DevLevel<T>>& L) {
 }
 
 // ------------------------------------------------------------ V-cycle
+// Returns the Chebyshev direction still to be added to the level's x (the
+// degree-1 post-smoother's d, folded into the consumer of x), or nullptr.
 template <typename T>
-static void vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStream_t st) {
+static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStream_t st) {
   const int nl = (int)L.size();
   DevLevel<T>& V = L[l];
   if (l == nl - 1) {
     launch_smem(k_coarse_solve<T>, nblk((int64_t)V.n * 32), kBlock, (size_t)V.n * sizeof(double), st, V.n,
                 c->d_coarse_inv, (const T*)V.b, V.x);
-    return;
+    return nullptr;
   }
   const int deg = c->opts.cheb_degree;
   std::vector<double> c1, c2;
@@ -287,8 +289,7 @@ static void vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStr
   T* dout = V.dB;
   const T* rin = V.b;
   for (int k = 2; k <= deg; ++k) {
-    launch(k_cheb_step<T>, g, kBlock, st, V.A, V.n, rin, din, V.dinv, (T)c1[k], (T)c2[k], V.r, dout,
-                                         V.x, 0);
+    launch(k_cheb_step<T>, g, kBlock, st, V.A, V.n, rin, din, V.dinv, (T)c1[k], (T)c2[k], V.r, dout, V.x, 0);
     rin = V.r;
     std::swap(din, dout);
   }
@@ -298,19 +299,20 @@ static void vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStr
     launch(k_resid<T>, g, kBlock, st, V.A, V.n, V.b, V.x, V.r);
   DevLevel<T>& C = L[l + 1];
   const int first = (l + 1 < nl - 1) ? 1 : 0;
-  launch(k_restrict<T>, rows_grid(c, (int64_t)C.n * std::max(V.R.G, 1)), kBlock, st, V.R, C.n, V.r, C.b, C.dinv, (T)C.inv_theta, C.x, C.dA,
-                                               first);
-  vcycle_level(c, L, l + 1, st);
-  launch(k_prolong<T>, rows_grid(c, (int64_t)V.n * std::max(V.P.G, 1)), kBlock, st, V.P, V.n, C.x, V.x);
+  launch(k_restrict<T>, rows_grid(c, (int64_t)C.n * std::max(V.R.G, 1)), kBlock, st, V.R, C.n, V.r, C.b,
+         C.dinv, (T)C.inv_theta, C.x, C.dA, first);
+  T* cpend = vcycle_level(c, L, l + 1, st);
+  launch(k_prolong<T>, rows_grid(c, (int64_t)V.n * std::max(V.P.G, 1)), kBlock, st, V.P, V.n, C.x,
+         (const T*)cpend, V.x);
   launch(k_post_first<T>, g, kBlock, st, V.A, V.n, V.b, V.x, V.dinv, (T)V.inv_theta, V.r, V.dA);
   din = V.dA;
   dout = V.dB;
   for (int k = 2; k <= deg; ++k) {
-    launch(k_cheb_step<T>, g, kBlock, st, V.A, V.n, V.r, din, V.dinv, (T)c1[k], (T)c2[k], V.r, dout,
-                                         V.x, k == 2 ? 1 : 0);
+    launch(k_cheb_step<T>, g, kBlock, st, V.A, V.n, V.r, din, V.dinv, (T)c1[k], (T)c2[k], V.r, dout, V.x,
+           k == 2 ? 1 : 0);
     std::swap(din, dout);
   }
-  if (deg == 1) launch(k_axpy1<T>, nblk(V.n), kBlock, st, V.n, V.x, V.dA);
+  return deg == 1 ? V.dA : nullptr;
 }
 
 // ------------------------------------------------------------- PCG
@@ -347,9 +349,9 @@ static void pcg_body_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_
   DevLevel<T>& V = L[0];
   const int n = (int)c->n_free;
   const int g = vec_grid(c, n);
-  vcycle_level(c, L, 0, st);
-  launch(k_pcg_dots<T>, g, kBlock, st, n, c->d_r, c->d_rprev, V.x, c->d_zd, c->d_sc, c->red.partials,
-         c->red.counter, c->red.max_blocks, c->opts.flexible);
+  T* zpend = vcycle_level(c, L, 0, st);
+  launch(k_pcg_dots<T>, g, kBlock, st, n, c->d_r, c->d_rprev, V.x, (const T*)zpend, c->d_zd, c->d_sc,
+         c->red.partials, c->red.counter, c->red.max_blocks, c->opts.flexible);
   launch(k_pcg_pq, g, kBlock, st, c->M64, n, c->d_zd, c->d_p, c->d_q, c->d_sc, c->red.partials,
          c->red.counter, c->red.max_blocks);
   launch(k_pcg_update<T>, g, kBlock, st, n, x, c->d_r, c->d_rprev, c->d_p, c->d_q, V.dinv,
@@ -682,7 +684,8 @@ static eqs_status vcycle_impl(eqs_ctx* c, std::vector<DevLevel<T>>& L, const dou
   DevLevel<T>& V = L[0];
   launch(k_to_T<T>, nblk(nf), kBlock, st, nf, r, V.b);
   if (L.size() > 1) launch(k_first_step<T>, nblk(nf), kBlock, st, nf, V.b, V.dinv, (T)V.inv_theta, V.x, V.dA);
-  vcycle_level(c, L, 0, st);
+  T* zpend = vcycle_level(c, L, 0, st);
+  if (zpend) launch(k_axpy1<T>, nblk(nf), kBlock, st, nf, V.x, (const T*)zpend);
   launch(k_from_T<T>, nblk(nf), kBlock, st, nf, V.x, z);
   CK(cudaGetLastError());
   return EQS_OK;
