@@ -99,6 +99,12 @@ typedef struct {
                           solve, in polls: 0 = default (2^22, about a second),
                           < 0 = no waiting at all (every wait gives up at
                           once; for testing the EQS_ERR_TIMEOUT path)        */
+  int split_m;         /* EQS_PREC_MIXED only: 1 (default) forms the CG
+                          operator product M z of the FP32 preconditioned
+                          residual z with M held as two FP32 parts and an
+                          error-free FP32-pair row sum (accuracy a few
+                          2^-48 of sum |m_ij z_j|, no FP64 multiply per
+                          non-zero); 0 uses FP64 M.  Ignored in FP64 mode.  */
 } eqs_opts;
 
 #define EQS_MAX_STAGES 64
@@ -120,7 +126,8 @@ typedef struct {
 
 /* Fill *o with the defaults (precision FP64, theta 0.08, coarse_max 500,
  * max_levels 10, degree 2, alpha 30, rtol 1e-8, max_iter 500, GUESS_PREV,
- * flexible 1, persistent 1, blocks_per_sm 1, spe_n 4, host_loop 0). */
+ * flexible 1, persistent 0, blocks_per_sm 1, spe_n 4, host_loop 0,
+ * barrier_polls 0, split_m 1). */
 void eqs_opts_default(eqs_opts* o);
 
 /* Create a context from a tetrahedral mesh (Eq. 2 discretisation input).
@@ -190,6 +197,12 @@ eqs_status eqs_vcycle(eqs_ctx* ctx, const double* r, double* z);
 
 /* y = M_ff x (device, n_free doubles each). */
 eqs_status eqs_spmv_M(eqs_ctx* ctx, const double* x, double* y);
+
+/* y = M_ff x for an FP32 x (device, n_free floats) through the split-M
+ * product of the mixed CG operator (see eqs_opts.split_m); y: device,
+ * n_free doubles.  EQS_ERR_STATE unless the context was set up in
+ * EQS_PREC_MIXED with split_m 1. */
+eqs_status eqs_spmv_M32(eqs_ctx* ctx, const float* x, double* y);
 
 /* One RKC step of s stages (Sec. II; scheme of its ref. [9], damping 2/13)
  * from time t to t + dt.  x: device, n_nodes doubles, mesh order: on entry
@@ -264,6 +277,51 @@ eqs_status eqs_guess_grad(eqs_ctx* ctx, const float* X, const float* T, int B, f
  * into z0 (device, n_free doubles); synchronises. */
 eqs_status eqs_guess_eval(eqs_ctx* ctx, const double* H, double* z0);
 
+/* ---- Ensemble: EQS_ENS_W trajectories on one mesh that differ only in the
+ * amplitude of their drive (column c is driven by v0_scale[c] g(t)).  Every
+ * stage solves the EQS_ENS_W right-hand sides together: Sec. IV's multiple
+ * right-hand-side problem with the constant M, here as a blocked CG in
+ * which each matrix entry of M, of the AMG operators and of the transfer
+ * matrices is read once for all columns (sparse matrix times a block of
+ * vectors), while every column keeps its own CG coefficients and stopping
+ * test (||R_c - M z_c|| <= rtol ||R_c||; a converged column is frozen).
+ * Needs a context set up in EQS_PREC_MIXED with split_m 1; starts every
+ * solve from the column's previous solution.  Device memory for the
+ * ensemble is allocated by the first ensemble call. */
+#define EQS_ENS_W 4
+
+typedef struct {
+  int s;
+  int total_iters[EQS_ENS_W];  /* CG iterations of each column, summed over the s solves */
+  int passes;                  /* CG loop passes summed over the solves (per solve:
+                                  the largest column count)                     */
+  int max_iters;               /* largest pass count of one solve                */
+  double max_relres;           /* largest final ||r||/||R|| of all columns       */
+  int status;                  /* EQS_OK, EQS_ERR_NOCONV or EQS_ERR_NAN          */
+  int64_t launches;            /* kernels of the step (graph kernel nodes outside
+                                  loops + loop-body kernel nodes x passes)      */
+} eqs_ens_stats;
+
+/* One RKC step of s stages (as eqs_rkc_step) for the EQS_ENS_W trajectories.
+ * x: device, EQS_ENS_W x n_nodes doubles, column-major (trajectory c at
+ *   x + c n_nodes), mesh order; in x(t), out x(t + dt), Dirichlet entries
+ *   replaced by v0_scale[c] g(t).
+ * v0_scale: host, EQS_ENS_W finite doubles.
+ * The step is one CUDA graph per (s, x); stats: host or NULL (then the call
+ * is asynchronous).  EQS_ERR_STATE if the context is not mixed / split. */
+eqs_status eqs_ens_rkc_step(eqs_ctx* ctx, double* x, const double* v0_scale, double t, double dt,
+                            int s, eqs_ens_stats* stats);
+
+/* Statistics of the last ensemble step (synchronises). */
+eqs_status eqs_ens_get_step_stats(eqs_ctx* ctx, eqs_ens_stats* stats);
+
+/* Solve M_ff z_c = rhs_c for the EQS_ENS_W columns together with the blocked
+ * CG of the ensemble at the setup's rtol.  rhs, z: device, n_free x
+ * EQS_ENS_W doubles, column-major; z holds the start vectors on entry and
+ * the solutions on exit.  iters_out: host, EQS_ENS_W ints or NULL.
+ * Synchronises; EQS_ERR_NOCONV if a column hit max_iter. */
+eqs_status eqs_ens_solve_M(eqs_ctx* ctx, const double* rhs, double* z, int* iters_out);
+
 /* ---- Batched serving: many independent instances advance together.
  * Every RKC stage of all instances is one cooperative launch in which each
  * instance owns a group of CTAs proportional to its free rows (at least
@@ -304,14 +362,14 @@ eqs_status eqs_batch_info(const eqs_batch* b, int* total_blocks, int* rows_per_b
 eqs_status eqs_batch_destroy(eqs_batch* b);
 const char* eqs_batch_last_error(const eqs_batch* b);
 
-/* SPE start vector x0 = V (V^T M V)^-1 V^T b (Sec. IV, Eq. 4-5) for given
- * history X (device, n x n_free doubles, most recent first), Rh = M X
- * (device, same shape; the newest column's product is recomputed on the
- * device), b and x0 (device, n_free).
- * n must equal the setup's spe_n.  Overwrites the context's SPE history;
+/* SPE start vector x0 = V (V^T M V)^-1 V^T b (Sec. IV, Eq. 4-5) for a given
+ * history X (device, n x n_free doubles, most recent first), right-hand side
+ * b and result x0 (device, n_free doubles).  The history is pushed oldest
+ * first through the same kernels the step uses (M x of each pushed solution,
+ * incremental Gram matrix), then x0 is formed.  n must equal the setup's
+ * spe_n.  Overwrites the context's SPE history and right-hand side buffer;
  * synchronises.  For checking the projection. */
-eqs_status eqs_spe_eval(eqs_ctx* ctx, const double* X, const double* Rh, const double* b, int n,
-                        double* x0);
+eqs_status eqs_spe_eval(eqs_ctx* ctx, const double* X, const double* b, int n, double* x0);
 
 /* Release everything owned by ctx (NULL is accepted). */
 eqs_status eqs_destroy(eqs_ctx* ctx);

@@ -1,0 +1,748 @@
+// Ensemble of kEnsW = 4 trajectories on one mesh (the same M, AMG hierarchy
+// and materials; each column has its own drive amplitude).  Every stage
+// solves its four right-hand sides together: the multiple right-hand-side
+// problem of Section IV with the constant M read once per four columns.
+//
+// Layout: every ensemble vector is row-interleaved, element (i, c) at
+// 4 i + c, so a row's four columns are one 16-byte (FP32) or 32-byte (FP64)
+// load and the matrix entry of a row is read once for all four columns
+// (SpMM).  Mixed precision only: FP32 element kernel and V-cycle, FP64
+// recurrence, CG residuals and dot products; the CG operator product uses
+// the split-M FP32-pair form (df_acc); the coarsest level applies the dense
+// inverse in split FP32 parts with FP32-pair sums.
+//
+// CG runs per column with its own alpha, beta and convergence flag; a
+// converged column is frozen (its x and r no longer change) while the
+// others iterate.  The loop runs while any column is active.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace eqs {
+
+constexpr int kEnsW = 4;
+
+// ------------------------------------------------------------ float4 ops
+__device__ __forceinline__ float4 operator+(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 operator-(float4 a, float4 b) {
+  return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+__device__ __forceinline__ float4 operator*(float a, float4 b) {
+  return make_float4(a * b.x, a * b.y, a * b.z, a * b.w);
+}
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 acc) {
+  return make_float4(fmaf(a, x.x, acc.x), fmaf(a, x.y, acc.y), fmaf(a, x.z, acc.z), fmaf(a, x.w, acc.w));
+}
+__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float4 shfl_xor4(float4 v, int o) {
+  return make_float4(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o),
+                     __shfl_xor_sync(0xffffffffu, v.z, o), __shfl_xor_sync(0xffffffffu, v.w, o));
+}
+__device__ __forceinline__ float comp(const float4& v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+template <bool ADD>
+__device__ __forceinline__ float4 xv4(const float4* __restrict__ x, const float4* __restrict__ xadd, int j) {
+  return ADD ? __ldg(x + j) + __ldg(xadd + j) : __ldg(x + j);
+}
+
+// (A X)_row for four interleaved columns (A in FP32, any of the three
+// layouts); same lane conventions as mat_row_impl.
+template <bool ADD>
+__device__ __forceinline__ float4 mat_row4_impl(const DevSell<float>& A, int64_t tid, int n,
+                                                const float4* __restrict__ x, const float4* __restrict__ xadd) {
+  const int row = (int)(tid >> A.logG);
+  float4 acc = zero4();
+  if (A.G == 0) {  // DIA
+    if (row >= n) return acc;
+    const float* __restrict__ v = A.val + row;
+    float4 acc1 = zero4();
+    int d = 0;
+#pragma unroll 4
+    for (; d + 1 < A.ndiag; d += 2) {
+      const int j0 = row + A.off[d], j1 = row + A.off[d + 1];
+      const float a0 = __ldg(v + (int64_t)d * n), a1 = __ldg(v + (int64_t)(d + 1) * n);
+      if ((unsigned)j0 < (unsigned)A.n_cols) acc = fma4(a0, xv4<ADD>(x, xadd, j0), acc);
+      if ((unsigned)j1 < (unsigned)A.n_cols) acc1 = fma4(a1, xv4<ADD>(x, xadd, j1), acc1);
+    }
+    if (d < A.ndiag) {
+      const int j = row + A.off[d];
+      const float a = __ldg(v + (int64_t)d * n);
+      if ((unsigned)j < (unsigned)A.n_cols) acc = fma4(a, xv4<ADD>(x, xadd, j), acc);
+    }
+    return acc + acc1;
+  }
+  if (A.G == 1) {  // SELL-32
+    if (row >= n) return acc;
+    const int s = row >> 5, lane = row & 31;
+    const int64_t end = A.slice_ptr[s + 1];
+    for (int64_t k = A.slice_ptr[s] + lane; k < end; k += 32 * 4) {
+      int c[4];
+      float a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t kk = k + 32 * u;
+        c[u] = kk < end ? __ldg(A.col + kk) : 0;
+        a[u] = kk < end ? __ldg(A.val + kk) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc = fma4(a[u], xv4<ADD>(x, xadd, c[u]), acc);
+    }
+    return acc;
+  }
+  const int g = (int)(tid & (A.G - 1));
+  int64_t k = 0, end = 0;
+  if (row < n) {
+    k = A.slice_ptr[row] + g;
+    end = A.slice_ptr[row + 1];
+  }
+  for (; k < end; k += (int64_t)A.G * 2) {
+    int c[2];
+    float a[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t kk = k + (int64_t)A.G * u;
+      c[u] = kk < end ? __ldg(A.col + kk) : 0;
+      a[u] = kk < end ? __ldg(A.val + kk) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) acc = fma4(a[u], xv4<ADD>(x, xadd, c[u]), acc);
+  }
+  for (int o = A.G >> 1; o > 0; o >>= 1) acc = acc + shfl_xor4(acc, o);
+  return acc;
+}
+
+__device__ __forceinline__ float4 mat_row4(const DevSell<float>& A, int64_t tid, int n, const float4* x) {
+  return mat_row4_impl<false>(A, tid, n, x, nullptr);
+}
+
+// ------------------------------------------------------- V-cycle (4 cols)
+__global__ void __launch_bounds__(kBlock, 4)
+k4_cheb_step(DevSell<float> A, int n, const float4* r_in, const float4* __restrict__ d_in,
+             const float* __restrict__ dinv, float c1, float c2, float4* r_out, float4* __restrict__ d_out,
+             float4* __restrict__ x, int add_pending) {
+  pdl_enter();
+  EQS_ROWS2(A, n, {
+    const float4 a0 = mat_row4(A, t0, n, d_in);
+    const float4 a1 = mat_row4(A, t1, n, d_in);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t t = h ? t1 : t0;
+      if (!row_leader(A, t, n)) continue;
+      const int i = (int)(t >> A.logG);
+      const float4 di = d_in[i];
+      const float4 r = r_in[i] - (h ? a1 : a0);
+      const float4 dn = c1 * di + (c2 * dinv[i]) * r;
+      r_out[i] = r;
+      d_out[i] = dn;
+      x[i] = x[i] + (add_pending ? dn + di : dn);
+    }
+  })
+}
+
+__global__ void __launch_bounds__(kBlock, 4) k4_resid_update(DevSell<float> A, int n, float4* r,
+                                                             const float4* __restrict__ d) {
+  pdl_enter();
+  EQS_ROWS2(A, n, {
+    const float4 a0 = mat_row4(A, t0, n, d);
+    const float4 a1 = mat_row4(A, t1, n, d);
+    if (row_leader(A, t0, n)) r[t0 >> A.logG] = r[t0 >> A.logG] - a0;
+    if (row_leader(A, t1, n)) r[t1 >> A.logG] = r[t1 >> A.logG] - a1;
+  })
+}
+
+__global__ void __launch_bounds__(kBlock, 4) k4_resid(DevSell<float> A, int n, const float4* __restrict__ b,
+                                                      const float4* __restrict__ x, float4* __restrict__ out) {
+  pdl_enter();
+  EQS_ROWS2(A, n, {
+    const float4 a0 = mat_row4(A, t0, n, x);
+    const float4 a1 = mat_row4(A, t1, n, x);
+    if (row_leader(A, t0, n)) out[t0 >> A.logG] = b[t0 >> A.logG] - a0;
+    if (row_leader(A, t1, n)) out[t1 >> A.logG] = b[t1 >> A.logG] - a1;
+  })
+}
+
+__global__ void __launch_bounds__(kBlock, 4) k4_restrict(DevSell<float> R, int nc, const float4* __restrict__ rf,
+                                                         float4* __restrict__ bc, const float* __restrict__ dinv_c,
+                                                         float inv_theta_c, float4* __restrict__ xc,
+                                                         float4* __restrict__ dc, int first_step) {
+  pdl_enter();
+  EQS_ROWS2(R, nc, {
+    const float4 b0 = mat_row4(R, t0, nc, rf);
+    const float4 b1 = mat_row4(R, t1, nc, rf);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t t = h ? t1 : t0;
+      if (!row_leader(R, t, nc)) continue;
+      const int i = (int)(t >> R.logG);
+      const float4 b = h ? b1 : b0;
+      bc[i] = b;
+      if (first_step) {
+        const float4 d = (dinv_c[i] * inv_theta_c) * b;
+        xc[i] = d;
+        dc[i] = d;
+      }
+    }
+  })
+}
+
+__global__ void __launch_bounds__(kBlock, 4) k4_prolong(DevSell<float> P, int nf, const float4* __restrict__ xc,
+                                                        const float4* __restrict__ dc, float4* __restrict__ xf) {
+  pdl_enter();
+  EQS_ROWS2(P, nf, {
+    const float4 p0 = dc ? mat_row4_impl<true>(P, t0, nf, xc, dc) : mat_row4(P, t0, nf, xc);
+    const float4 p1 = dc ? mat_row4_impl<true>(P, t1, nf, xc, dc) : mat_row4(P, t1, nf, xc);
+    if (row_leader(P, t0, nf)) xf[t0 >> P.logG] = xf[t0 >> P.logG] + p0;
+    if (row_leader(P, t1, nf)) xf[t1 >> P.logG] = xf[t1 >> P.logG] + p1;
+  })
+}
+
+__global__ void __launch_bounds__(kBlock, 4) k4_post_first(DevSell<float> A, int n, const float4* __restrict__ b,
+                                                           const float4* __restrict__ x, const float* __restrict__ dinv,
+                                                           float inv_theta, float4* __restrict__ r_out,
+                                                           float4* __restrict__ d_out) {
+  pdl_enter();
+  EQS_ROWS2(A, n, {
+    const float4 a0 = mat_row4(A, t0, n, x);
+    const float4 a1 = mat_row4(A, t1, n, x);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t t = h ? t1 : t0;
+      if (!row_leader(A, t, n)) continue;
+      const int i = (int)(t >> A.logG);
+      const float4 r = b[i] - (h ? a1 : a0);
+      r_out[i] = r;
+      d_out[i] = (dinv[i] * inv_theta) * r;
+    }
+  })
+}
+
+__global__ void k4_axpy1(int n, float4* __restrict__ x, const float4* __restrict__ d) {
+  pdl_enter();
+  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = x[i] + d[i];
+}
+
+// Error-free sum of two FP32 pairs into (S, s).
+__device__ __forceinline__ void df_add(float& S, float& s, float S2, float s2) {
+  const float S1 = __fadd_rn(S, S2);
+  const float bv = __fsub_rn(S1, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(S1, bv)), __fsub_rn(S2, bv));
+  S = S1;
+  s = __fadd_rn(s, __fadd_rn(s2, err));
+}
+
+// Coarsest level, W interleaved columns: x = A_c^-1 b with the dense inverse
+// held as two FP32 parts (hi + lo) and FP32-pair row sums (df_acc), one warp
+// per row; b (FP32) is staged once per block in shared memory (W = 4: one
+// 16-byte element per row, conflict-free).
+template <int W>
+__global__ void k_coarse_solve_df(int n, const float* __restrict__ ihi, const float* __restrict__ ilo,
+                                  const float* __restrict__ b, float* __restrict__ x) {
+  extern __shared__ float4 sb4[];
+  float* sbf = reinterpret_cast<float*>(sb4);
+  pdl_enter();
+  for (int j = threadIdx.x; j < n * W; j += blockDim.x) sbf[j] = b[j];
+  __syncthreads();
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const float* __restrict__ rh = ihi + (int64_t)warp * n;
+  const float* __restrict__ rl = ilo + (int64_t)warp * n;
+  float S[W], s[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) S[c] = s[c] = 0.f;
+  for (int j = lane; j < n; j += 32) {
+    const float ah = __ldg(rh + j), al = __ldg(rl + j);
+    if constexpr (W == 4) {
+      const float4 bj = sb4[j];
+      df_acc(S[0], s[0], ah, al, bj.x);
+      df_acc(S[1], s[1], ah, al, bj.y);
+      df_acc(S[2], s[2], ah, al, bj.z);
+      df_acc(S[3], s[3], ah, al, bj.w);
+    } else {
+#pragma unroll
+      for (int c = 0; c < W; ++c) df_acc(S[c], s[c], ah, al, sbf[j * W + c]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      const float S2 = __shfl_xor_sync(0xffffffffu, S[c], o);
+      const float s2 = __shfl_xor_sync(0xffffffffu, s[c], o);
+      df_add(S[c], s[c], S2, s2);
+    }
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < W; ++c) x[(int64_t)warp * W + c] = (float)((double)S[c] + (double)s[c]);
+}
+
+// Interleave four column-major FP64 columns (column c at src + c n) into
+// rows of four, and back.
+__global__ void k4_interleave(int n, const double* __restrict__ src, double4_32a* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double4_32a v;
+  v.x = src[i];
+  v.y = src[(int64_t)n + i];
+  v.z = src[2 * (int64_t)n + i];
+  v.w = src[3 * (int64_t)n + i];
+  dst[i] = v;
+}
+
+__global__ void k4_deinterleave(int n, const double4_32a* __restrict__ src, double* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double4_32a v = src[i];
+  dst[i] = v.x;
+  dst[(int64_t)n + i] = v.y;
+  dst[2 * (int64_t)n + i] = v.z;
+  dst[3 * (int64_t)n + i] = v.w;
+}
+
+// ------------------------------------------------------------- CG (4 cols)
+// Per-column solve state; conv = 1 freezes the column.
+struct EnsScalars {
+  double bnorm2[kEnsW], rnorm2[kEnsW], rz[kEnsW], rz_old[kEnsW], alpha[kEnsW], beta[kEnsW];
+  int it[kEnsW], conv[kEnsW];
+  int pass;  // CG loop passes of the current solve
+};
+
+__device__ __forceinline__ float4 to_f4(const double4_32a& v) {
+  return make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
+}
+__device__ __forceinline__ double dc4(const double4_32a& v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void set4(double4_32a& v, int c, double a) {
+  if (c == 0) v.x = a; else if (c == 1) v.y = a; else if (c == 2) v.z = a; else v.w = a;
+}
+
+// (M X)_row in FP64 for four interleaved FP64 columns (one thread per row).
+__device__ __forceinline__ double4_32a mat_row_d4(const DevSell<double>& A, int64_t row, int n,
+                                                  const double4_32a* __restrict__ x) {
+  double4_32a acc = {0.0, 0.0, 0.0, 0.0};
+  if (row >= n) return acc;
+  if (A.G == 0) {
+#pragma unroll 5
+    for (int d = 0; d < A.ndiag; ++d) {
+      const int j = (int)row + A.off[d];
+      if ((unsigned)j >= (unsigned)A.n_cols) continue;
+      const double a = __ldg(A.val + (int64_t)d * n + row);
+      const double4_32a v = x[j];
+      acc.x = fma(a, v.x, acc.x);
+      acc.y = fma(a, v.y, acc.y);
+      acc.z = fma(a, v.z, acc.z);
+      acc.w = fma(a, v.w, acc.w);
+    }
+    return acc;
+  }
+  const int64_t sl = row >> 5, lane = row & 31;
+  const int64_t end = A.slice_ptr[sl + 1];
+  for (int64_t k = A.slice_ptr[sl] + lane; k < end; k += 32) {
+    const double a = __ldg(A.val + k);
+    const double4_32a v = x[__ldg(A.col + k)];
+    acc.x = fma(a, v.x, acc.x);
+    acc.y = fma(a, v.y, acc.y);
+    acc.z = fma(a, v.z, acc.z);
+    acc.w = fma(a, v.w, acc.w);
+  }
+  return acc;
+}
+
+// The V-cycle input of a row from its four FP64 residuals.
+__device__ __forceinline__ void vc_input4(int64_t i, const double4_32a& r, const float* __restrict__ dinv0,
+                                          float inv_theta0, float4* __restrict__ b0, float4* __restrict__ x0,
+                                          float4* __restrict__ d0) {
+  const float4 bi = to_f4(r);
+  b0[i] = bi;
+  const float4 d = (dinv0[i] * inv_theta0) * bi;
+  x0[i] = d;
+  d0[i] = d;
+}
+
+// r = R - M x for the four columns (FP64), norms of R and r per column, the
+// first V-cycle input; the last block sets the per-column flags and the
+// loop condition (any column active).
+__global__ void k4_pcg_init(DevSell<double> M, int n, const double4_32a* __restrict__ R,
+                            const double4_32a* __restrict__ x, double4_32a* __restrict__ r,
+                            const float* __restrict__ dinv0, float inv_theta0, float4* __restrict__ b0,
+                            float4* __restrict__ x0, float4* __restrict__ d0, EnsScalars* sc,
+                            double* partials, unsigned int* counter, int max_blocks, double tol2, int maxit,
+                            cudaGraphConditionalHandle h, int use_handle, int* iters_out,
+                            double* relres_out, int* zero_out) {
+  pdl_enter();
+  double v[2 * kEnsW];
+#pragma unroll
+  for (int k = 0; k < 2 * kEnsW; ++k) v[k] = 0.0;
+  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double4_32a Ri = R[i];
+    const double4_32a mx = mat_row_d4(M, i, n, x);
+    double4_32a ri;
+    ri.x = Ri.x - mx.x;
+    ri.y = Ri.y - mx.y;
+    ri.z = Ri.z - mx.z;
+    ri.w = Ri.w - mx.w;
+    r[i] = ri;
+    vc_input4(i, ri, dinv0, inv_theta0, b0, x0, d0);
+#pragma unroll
+    for (int c = 0; c < kEnsW; ++c) {
+      v[c] = fma(dc4(Ri, c), dc4(Ri, c), v[c]);
+      v[kEnsW + c] = fma(dc4(ri, c), dc4(ri, c), v[kEnsW + c]);
+    }
+  }
+  double tot[2 * kEnsW];
+  if (grid_sum<2 * kEnsW>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    int go = 0;
+    for (int c = 0; c < kEnsW; ++c) {
+      sc->bnorm2[c] = tot[c];
+      sc->rnorm2[c] = tot[kEnsW + c];
+      sc->it[c] = 0;
+      sc->rz_old[c] = 0.0;
+      sc->beta[c] = 0.0;
+      sc->alpha[c] = 0.0;
+      const int zero = tot[c] == 0.0;
+      const int gc = !zero && tot[kEnsW + c] > tol2 * tot[c] && maxit > 0;
+      sc->conv[c] = !gc;
+      go |= gc;
+      if (iters_out) iters_out[c] = 0;
+      if (relres_out) relres_out[c] = zero ? 0.0 : sqrt(tot[kEnsW + c] / tot[c]);
+      if (zero_out) zero_out[c] = zero;
+    }
+    sc->pass = 0;
+    if (use_handle) cudaGraphSetConditional(h, go ? 1u : 0u);
+  }
+}
+
+// z = V-cycle output (+ pending direction) kept in FP32; r.z and r_prev.z
+// per column; the last block forms beta per active column (Polak-Ribiere or
+// Fletcher-Reeves).
+__global__ void k4_pcg_dots(int n, const double4_32a* __restrict__ r, const double4_32a* __restrict__ rprev,
+                            const float4* __restrict__ z, const float4* __restrict__ zpend,
+                            float4* __restrict__ z32, EnsScalars* sc, double* partials, unsigned int* counter,
+                            int max_blocks, int flexible) {
+  pdl_enter();
+  double v[2 * kEnsW];
+#pragma unroll
+  for (int k = 0; k < 2 * kEnsW; ++k) v[k] = 0.0;
+  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 zt = zpend ? z[i] + zpend[i] : z[i];
+    z32[i] = zt;
+    const double4_32a ri = r[i], pi = rprev[i];
+#pragma unroll
+    for (int c = 0; c < kEnsW; ++c) {
+      const double zc = (double)comp(zt, c);
+      v[c] = fma(dc4(ri, c), zc, v[c]);
+      v[kEnsW + c] = fma(dc4(pi, c), zc, v[kEnsW + c]);
+    }
+  }
+  double tot[2 * kEnsW];
+  if (grid_sum<2 * kEnsW>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    for (int c = 0; c < kEnsW; ++c) {
+      if (sc->conv[c]) {
+        sc->beta[c] = 0.0;
+        continue;
+      }
+      const double rz = tot[c];
+      double beta = 0.0;
+      if (sc->it[c] > 0 && sc->rz_old[c] != 0.0)
+        beta = flexible ? (rz - tot[kEnsW + c]) / sc->rz_old[c] : rz / sc->rz_old[c];
+      sc->beta[c] = beta;
+      sc->rz[c] = rz;
+      sc->rz_old[c] = rz;
+    }
+  }
+}
+
+// q = M z + beta q, p = z + beta p per active column (split-M product of the
+// FP32 z: four columns per matrix entry), p.q and alpha.
+__global__ void k4_pcg_pq(DevSell<double> M, const float* __restrict__ Mhi, const float* __restrict__ Mlo, int n,
+                          const float4* __restrict__ z32, double4_32a* __restrict__ p, double4_32a* __restrict__ q,
+                          EnsScalars* sc, double* partials, unsigned int* counter, int max_blocks) {
+  pdl_enter();
+  double beta[kEnsW];
+  int act[kEnsW];
+#pragma unroll
+  for (int c = 0; c < kEnsW; ++c) {
+    beta[c] = sc->beta[c];
+    act[c] = !sc->conv[c];
+  }
+  double v[kEnsW];
+#pragma unroll
+  for (int c = 0; c < kEnsW; ++c) v[c] = 0.0;
+  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float S[kEnsW] = {0.f, 0.f, 0.f, 0.f}, s[kEnsW] = {0.f, 0.f, 0.f, 0.f};
+    if (M.G == 0) {
+#pragma unroll 5
+      for (int d = 0; d < M.ndiag; ++d) {
+        const int j = (int)i + M.off[d];
+        if ((unsigned)j >= (unsigned)M.n_cols) continue;
+        const int64_t k = (int64_t)d * n + i;
+        const float ah = __ldg(Mhi + k), al = __ldg(Mlo + k);
+        const float4 zj = __ldg(z32 + j);
+        df_acc(S[0], s[0], ah, al, zj.x);
+        df_acc(S[1], s[1], ah, al, zj.y);
+        df_acc(S[2], s[2], ah, al, zj.z);
+        df_acc(S[3], s[3], ah, al, zj.w);
+      }
+    } else {
+      const int64_t sl = i >> 5, lane = i & 31;
+      const int64_t end = M.slice_ptr[sl + 1];
+      for (int64_t k = M.slice_ptr[sl] + lane; k < end; k += 32) {
+        const float ah = __ldg(Mhi + k), al = __ldg(Mlo + k);
+        const float4 zj = __ldg(z32 + __ldg(M.col + k));
+        df_acc(S[0], s[0], ah, al, zj.x);
+        df_acc(S[1], s[1], ah, al, zj.y);
+        df_acc(S[2], s[2], ah, al, zj.z);
+        df_acc(S[3], s[3], ah, al, zj.w);
+      }
+    }
+    const float4 zi = z32[i];
+    double4_32a pi = p[i], qi = q[i];
+#pragma unroll
+    for (int c = 0; c < kEnsW; ++c) {
+      if (!act[c]) continue;
+      const double w = (double)S[c] + (double)s[c];
+      const double zc = (double)comp(zi, c);
+      const double qn = fma(beta[c], dc4(qi, c), w);
+      const double pn = fma(beta[c], dc4(pi, c), zc);
+      set4(qi, c, qn);
+      set4(pi, c, pn);
+      v[c] = fma(pn, qn, v[c]);
+    }
+    p[i] = pi;
+    q[i] = qi;
+  }
+  double tot[kEnsW];
+  if (grid_sum<kEnsW>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    for (int c = 0; c < kEnsW; ++c)
+      sc->alpha[c] = (!sc->conv[c] && tot[c] != 0.0) ? sc->rz[c] / tot[c] : 0.0;
+  }
+}
+
+// x += alpha p ; r_prev = r ; r -= alpha q (active columns), ||r||^2 per
+// column, the next V-cycle input; the last block updates the flags, the
+// per-column iteration counts and the loop condition.
+__global__ void k4_pcg_update(int n, double4_32a* __restrict__ x, double4_32a* __restrict__ r,
+                              double4_32a* __restrict__ rprev, const double4_32a* __restrict__ p,
+                              const double4_32a* __restrict__ q, const float* __restrict__ dinv0,
+                              float inv_theta0, float4* __restrict__ b0, float4* __restrict__ x0,
+                              float4* __restrict__ d0, EnsScalars* sc, double* partials,
+                              unsigned int* counter, int max_blocks, double tol2, int maxit,
+                              cudaGraphConditionalHandle h, int use_handle, int* iters_out,
+                              double* relres_out) {
+  pdl_enter();
+  double a[kEnsW];
+  int act[kEnsW];
+#pragma unroll
+  for (int c = 0; c < kEnsW; ++c) {
+    act[c] = !sc->conv[c];
+    a[c] = sc->alpha[c];
+  }
+  double v[kEnsW];
+#pragma unroll
+  for (int c = 0; c < kEnsW; ++c) v[c] = 0.0;
+  for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double4_32a xi = x[i], ri = r[i];
+    const double4_32a pi = p[i], qi = q[i];
+    rprev[i] = ri;
+#pragma unroll
+    for (int c = 0; c < kEnsW; ++c) {
+      if (act[c]) {
+        set4(xi, c, fma(a[c], dc4(pi, c), dc4(xi, c)));
+        set4(ri, c, fma(-a[c], dc4(qi, c), dc4(ri, c)));
+      }
+      v[c] = fma(dc4(ri, c), dc4(ri, c), v[c]);
+    }
+    x[i] = xi;
+    r[i] = ri;
+    vc_input4(i, ri, dinv0, inv_theta0, b0, x0, d0);
+  }
+  double tot[kEnsW];
+  if (grid_sum<kEnsW>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    const int pass = sc->pass + 1;
+    sc->pass = pass;
+    int go = 0;
+    for (int c = 0; c < kEnsW; ++c) {
+      if (sc->conv[c]) continue;
+      sc->rnorm2[c] = tot[c];
+      sc->it[c] += 1;
+      const int conv = tot[c] <= tol2 * sc->bnorm2[c];
+      sc->conv[c] = conv;
+      go |= !conv;
+      if (iters_out) iters_out[c] = sc->it[c];
+      if (relres_out) relres_out[c] = sqrt(tot[c] / sc->bnorm2[c]);
+    }
+    if (use_handle) cudaGraphSetConditional(h, (go && pass < maxit) ? 1u : 0u);
+  }
+}
+
+// --------------------------------------------------- element and stages
+// K(x)x for four columns: the tet's geometry once, four gradients, kappas
+// and local residuals, scattered with one 16-byte vector atomic per vertex.
+// Y2: per node the four columns as (hi, lo) FP32 pairs (two float4).
+__global__ void k4_elem32(int64_t nt, const int4* __restrict__ conn, const uint8_t* __restrict__ mat,
+                          const MaterialDev* __restrict__ mats, const float4* __restrict__ xh,
+                          const float4* __restrict__ xl, const float4* __restrict__ Y2, int n_limit,
+                          float4* __restrict__ y) {
+  pdl_enter();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt) return;
+  const int4 t = conn[e];
+  const float4 h0 = xh[t.x], h1 = xh[t.y], h2 = xh[t.z], h3 = xh[t.w];
+  const float4 l0 = xl[t.x], l1 = xl[t.y], l2 = xl[t.z], l3 = xl[t.w];
+  const float e1x = (h1.x - h0.x) + (l1.x - l0.x), e1y = (h1.y - h0.y) + (l1.y - l0.y),
+              e1z = (h1.z - h0.z) + (l1.z - l0.z);
+  const float e2x = (h2.x - h0.x) + (l2.x - l0.x), e2y = (h2.y - h0.y) + (l2.y - l0.y),
+              e2z = (h2.z - h0.z) + (l2.z - l0.z);
+  const float e3x = (h3.x - h0.x) + (l3.x - l0.x), e3y = (h3.y - h0.y) + (l3.y - l0.y),
+              e3z = (h3.z - h0.z) + (l3.z - l0.z);
+  const float c1x = e2y * e3z - e2z * e3y, c1y = e2z * e3x - e2x * e3z, c1z = e2x * e3y - e2y * e3x;
+  const float c2x = e3y * e1z - e3z * e1y, c2y = e3z * e1x - e3x * e1z, c2z = e3x * e1y - e3y * e1x;
+  const float c3x = e1y * e2z - e1z * e2y, c3y = e1z * e2x - e1x * e2z, c3z = e1x * e2y - e1y * e2x;
+  const float D = e1x * c1x + e1y * c1y + e1z * c1z;
+  const MaterialDev m = mats[mat[e]];
+  // potentials: node v holds columns 0,1 in Y2[2v] and 2,3 in Y2[2v+1]
+  const float4 a0 = Y2[2 * (int64_t)t.x], b0 = Y2[2 * (int64_t)t.x + 1];
+  const float4 a1 = Y2[2 * (int64_t)t.y], b1 = Y2[2 * (int64_t)t.y + 1];
+  const float4 a2 = Y2[2 * (int64_t)t.z], b2 = Y2[2 * (int64_t)t.z + 1];
+  const float4 a3 = Y2[2 * (int64_t)t.w], b3 = Y2[2 * (int64_t)t.w + 1];
+  float r0[kEnsW], r1[kEnsW], r2[kEnsW], r3[kEnsW];
+#pragma unroll
+  for (int c = 0; c < kEnsW; ++c) {
+    // (hi, lo) of column c at the four vertices
+    const float2 f0 = c == 0 ? make_float2(a0.x, a0.y) : c == 1 ? make_float2(a0.z, a0.w)
+                    : c == 2 ? make_float2(b0.x, b0.y) : make_float2(b0.z, b0.w);
+    const float2 f1 = c == 0 ? make_float2(a1.x, a1.y) : c == 1 ? make_float2(a1.z, a1.w)
+                    : c == 2 ? make_float2(b1.x, b1.y) : make_float2(b1.z, b1.w);
+    const float2 f2 = c == 0 ? make_float2(a2.x, a2.y) : c == 1 ? make_float2(a2.z, a2.w)
+                    : c == 2 ? make_float2(b2.x, b2.y) : make_float2(b2.z, b2.w);
+    const float2 f3 = c == 0 ? make_float2(a3.x, a3.y) : c == 1 ? make_float2(a3.z, a3.w)
+                    : c == 2 ? make_float2(b3.x, b3.y) : make_float2(b3.z, b3.w);
+    const float d1 = (f1.x - f0.x) + (f1.y - f0.y);
+    const float d2 = (f2.x - f0.x) + (f2.y - f0.y);
+    const float d3 = (f3.x - f0.x) + (f3.y - f0.y);
+    const float gx = d1 * c1x + d2 * c2x + d3 * c3x;
+    const float gy = d1 * c1y + d2 * c2y + d3 * c3y;
+    const float gz = d1 * c1z + d2 * c2z + d3 * c3z;
+    float kap;
+    if (m.is_const) {
+      kap = (float)m.klo;
+    } else {
+      const float E = sqrtf(gx * gx + gy * gy + gz * gz) / D;
+      kap = kappa32(m, E);
+    }
+    const float sc = kap / (6.0f * D);
+    r1[c] = sc * (c1x * gx + c1y * gy + c1z * gz);
+    r2[c] = sc * (c2x * gx + c2y * gy + c2z * gz);
+    r3[c] = sc * (c3x * gx + c3y * gy + c3z * gz);
+    r0[c] = -(r1[c] + r2[c] + r3[c]);
+  }
+  if (t.x < n_limit) atomicAdd(y + t.x, make_float4(r0[0], r0[1], r0[2], r0[3]));
+  if (t.y < n_limit) atomicAdd(y + t.y, make_float4(r1[0], r1[1], r1[2], r1[3]));
+  if (t.z < n_limit) atomicAdd(y + t.z, make_float4(r2[0], r2[1], r2[2], r2[3]));
+  if (t.w < n_limit) atomicAdd(y + t.w, make_float4(r3[0], r3[1], r3[2], r3[3]));
+}
+
+__device__ __forceinline__ void store_split4(float4* __restrict__ Y2, int64_t i, const double4_32a& v) {
+  const float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z, hw = (float)v.w;
+  Y2[2 * i] = make_float4(hx, (float)(v.x - (double)hx), hy, (float)(v.y - (double)hy));
+  Y2[2 * i + 1] = make_float4(hz, (float)(v.z - (double)hz), hw, (float)(v.w - (double)hw));
+}
+
+// Y0 (interleaved, internal order) from the caller's column-major mesh-order
+// X (column c at X + c n), Dirichlet rows = g(t) times the column's drive
+// scale; the start vector of the first solve (previous solution).
+__global__ void k4_gather_state(int n, int nf, const double* __restrict__ X, const int32_t* __restrict__ noi,
+                                const double* __restrict__ dir_scale, const double* __restrict__ g,
+                                const double* __restrict__ colv, double4_32a* __restrict__ Y0,
+                                float4* __restrict__ Y2, const double4_32a* __restrict__ Fsrc,
+                                double4_32a* __restrict__ Fdst) {
+  pdl_enter();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double4_32a v;
+  if (i < nf) {
+    const int64_t m = noi[i];
+    v.x = X[m];
+    v.y = X[(int64_t)n + m];
+    v.z = X[2 * (int64_t)n + m];
+    v.w = X[3 * (int64_t)n + m];
+    Fdst[i] = Fsrc[i];
+  } else {
+    const double gd = dir_scale[i - nf] * g[0];
+    v.x = gd * colv[0];
+    v.y = gd * colv[1];
+    v.z = gd * colv[2];
+    v.w = gd * colv[3];
+  }
+  Y0[i] = v;
+  store_split4(Y2, i, v);
+}
+
+// Stage recurrence for the four columns (same coefficients; a column whose
+// right-hand side was zero contributes F = 0), the next start vector and,
+// after the last stage, x(t + dt) back to the caller's column-major layout.
+__global__ void k4_recurrence(int n, int nf, double c0, double mu, double nu, double mut, double gt,
+                              const StepParams* prm, const double4_32a* __restrict__ Y0,
+                              const double4_32a* __restrict__ Yjm1, const double4_32a* __restrict__ Yjm2,
+                              const double4_32a* __restrict__ Fjm1, const double4_32a* __restrict__ F0,
+                              const int* __restrict__ zero_flags, int jm1, const double* __restrict__ dir_scale,
+                              const double* __restrict__ gj, const double* __restrict__ colv,
+                              double4_32a* __restrict__ Yj, float4* __restrict__ Y2,
+                              double4_32a* __restrict__ Fguess, double* __restrict__ X,
+                              const int32_t* __restrict__ noi) {
+  pdl_enter();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double4_32a v;
+  if (i < nf) {
+    const double dt = prm->dt;
+    const double4_32a y0 = Y0[i], y1 = Yjm1[i], y2 = Yjm2[i], f1 = Fjm1[i], f0 = F0[i];
+#pragma unroll
+    for (int c = 0; c < kEnsW; ++c) {
+      const double fj = zero_flags[jm1 * kEnsW + c] ? 0.0 : dc4(f1, c);
+      const double ff = zero_flags[c] ? 0.0 : dc4(f0, c);
+      set4(v, c, c0 * dc4(y0, c) + mu * dc4(y1, c) + nu * dc4(y2, c) + (mut * dt) * fj + (gt * dt) * ff);
+    }
+    if (Fguess) Fguess[i] = f1;
+  } else {
+    const double gd = dir_scale[i - nf] * (*gj);
+    v.x = gd * colv[0];
+    v.y = gd * colv[1];
+    v.z = gd * colv[2];
+    v.w = gd * colv[3];
+  }
+  Yj[i] = v;
+  if (Y2) store_split4(Y2, i, v);
+  if (X) {
+    const int64_t m = noi[i];
+    X[m] = v.x;
+    X[(int64_t)n + m] = v.y;
+    X[2 * (int64_t)n + m] = v.z;
+    X[3 * (int64_t)n + m] = v.w;
+  }
+}
+
+// R = -y - g'(t_j) v_c M_fd 1_top per column in FP64, and clear y.
+__global__ void k4_rhs(int nf, float4* __restrict__ y32, const double* __restrict__ gpj,
+                       const double* __restrict__ colv, const double* __restrict__ mtop,
+                       double4_32a* __restrict__ R) {
+  pdl_enter();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nf) return;
+  const float4 y = y32[i];
+  const double gm = (*gpj) * mtop[i];
+  double4_32a r;
+  r.x = -(double)y.x - gm * colv[0];
+  r.y = -(double)y.y - gm * colv[1];
+  r.z = -(double)y.z - gm * colv[2];
+  r.w = -(double)y.w - gm * colv[3];
+  R[i] = r;
+  y32[i] = zero4();
+}
+
+}  // namespace eqs

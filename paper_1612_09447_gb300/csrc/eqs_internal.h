@@ -144,6 +144,9 @@ struct eqs_ctx {
 
   // ---- device matrices
   eqs::DevSell<double> M64;          // M_ff in FP64 (CG operator)
+  float* d_M_hi = nullptr;           // split M_ff = hi + lo (FP32 parts, M64's layout;
+  float* d_M_lo = nullptr;           //   mixed path with split_m)
+  float* d_z32 = nullptr;            // FP32 preconditioned residual (split operator pass)
   std::vector<eqs::DevLevel<double>> lev64;
   std::vector<eqs::DevLevel<float>> lev32;
   double* d_coarse_inv = nullptr;    // dense inverse of the coarsest matrix
@@ -197,11 +200,43 @@ struct eqs_ctx {
   bool recording = false;
   double* d_rtmp = nullptr;          // residual of the fallback start vector
   double* d_spe_X = nullptr;         // SPE: last solutions (spe_max x n_free)
-  double* d_spe_R = nullptr;         // SPE: W = M X of the stored solutions
+  double* d_spe_W = nullptr;         // SPE: W = M X of the stored solutions
+  double* d_spe_G = nullptr;         // SPE: Gram matrix x_a . w_b by ring slot (6 x 6)
   double* d_spe_y = nullptr;         // SPE: projection coefficients
   double* d_spe_partials = nullptr;  // SPE: reduction slots
   bool mlp_ready = false;
   bool direct = false;               // enqueue_step launches directly (host-driven CG loop)
+
+  // ---- split coarse inverse (mixed precision): inv = hi + lo, FP32 parts
+  float* d_cinv_hi = nullptr;
+  float* d_cinv_lo = nullptr;
+
+  // ---- ensemble of 4 trajectories (allocated by the first ensemble call;
+  // every vector row-interleaved, 4 columns per row)
+  bool ens_ready = false;
+  struct EnsLevel {
+    float4 *b = nullptr, *x = nullptr, *r = nullptr, *dA = nullptr, *dB = nullptr;
+  };
+  std::vector<EnsLevel> elev;
+  double4_32a* d_eY[4] = {nullptr, nullptr, nullptr, nullptr};  // Y0 + 3 rotating (n_nodes)
+  float4* d_eY2 = nullptr;           // (hi, lo) FP32 pairs of the current stage (2 per node)
+  double4_32a* d_eF[3] = {nullptr, nullptr, nullptr};  // stage solutions (n_free)
+  double4_32a* d_eR = nullptr;       // stage right-hand sides
+  float4* d_ey32 = nullptr;          // FP32 accumulation of K(x)x (n_nodes)
+  double4_32a *d_er = nullptr, *d_erprev = nullptr, *d_ep = nullptr, *d_eq = nullptr;
+  double4_32a* d_esol = nullptr;     // eqs_ens_solve_M work solution
+  float4* d_ez32 = nullptr;          // FP32 preconditioned residual
+  void* d_esc = nullptr;             // per-column CG scalars
+  double* d_epart = nullptr;         // reduction slots (8 per block)
+  int* d_eiters = nullptr;           // per stage and column: CG iterations
+  double* d_erelres = nullptr;       // per stage and column: final relative residual
+  int* d_ezero = nullptr;            // per stage and column: zero right-hand side
+  double* d_ecolv = nullptr;         // drive scale of each column
+  int64_t ens_body_kernels = 0;
+  std::map<std::pair<int, uintptr_t>, eqs::GraphEntry> ens_graphs;   // key: (s, x)
+  const eqs::GraphEntry* ens_last = nullptr;
+  eqs::GraphEntry ens_solve_graph;   // eqs_ens_solve_M (rtol of the setup)
+  double ens_solve_tol = -1.0;
 
   std::map<std::pair<int, uintptr_t>, eqs::GraphEntry> step_graphs;  // key: (s, x)
   const eqs::GraphEntry* last_step = nullptr;                       // graph of the last step

@@ -486,18 +486,23 @@ __global__ void k_pcg_select(int n, double* __restrict__ x, const double* __rest
   }
 }
 
-// z (from the V-cycle, in T) to FP64, r.z and r_prev.z; the last block forms
-// beta (Fletcher-Reeves, or Polak-Ribiere when flexible).
+// z (from the V-cycle, in T) to FP64 (zd) or, for the split-M operator
+// pass, kept in FP32 (z32); r.z and r_prev.z; the last block forms beta
+// (Fletcher-Reeves, or Polak-Ribiere when flexible).
 template <typename T>
 __global__ void k_pcg_dots(int n, const double* __restrict__ r, const double* __restrict__ rprev,
                            const T* __restrict__ z, const T* __restrict__ zpend, double* __restrict__ zd,
-                           PcgScalars* sc, double* partials, unsigned int* counter, int max_blocks,
-                           int flexible) {
+                           float* __restrict__ z32, PcgScalars* sc, double* partials, unsigned int* counter,
+                           int max_blocks, int flexible) {
   pdl_enter();
   double v[2] = {0.0, 0.0};
   for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double zi = zpend ? (double)(z[i] + zpend[i]) : (double)z[i];
-    zd[i] = zi;
+    const T zt = zpend ? z[i] + zpend[i] : z[i];
+    const double zi = (double)zt;
+    if (z32)
+      z32[i] = (float)zt;
+    else
+      zd[i] = zi;
     v[0] += r[i] * zi;
     v[1] += rprev[i] * zi;
   }
@@ -532,6 +537,81 @@ __global__ void k_pcg_pq(DevSell<double> M, int n, const double* __restrict__ zd
       const double w = h ? w1 : w0;
       const double qi = beta == 0.0 ? w : fma(beta, q[i], w);
       const double pi = beta == 0.0 ? zd[i] : fma(beta, p[i], zd[i]);
+      p[i] = pi;
+      q[i] = qi;
+      v[0] += pi * qi;
+    }
+  }
+  double tot[1];
+  if (grid_sum<1>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    sc->pq = tot[0];
+    sc->alpha = sc->rz / tot[0];
+  }
+}
+
+// ------------------------------------------------ split-M operator pass
+// M z with M stored as two FP32 parts (M = M_hi + M_lo to about 2^-48) and z
+// exactly FP32 (the V-cycle output of the mixed path): every product M_hi z
+// is split exactly into p + e by an FMA, M_lo z is rounded to FP32 (it is
+// 2^-24 smaller), and the row sum is carried as an unevaluated FP32 pair
+// (S, s) with an error-free two-sum per term.  The result is accurate to a
+// few units of 2^-48 of sum |m_ij z_j| -- FP64-class for the CG operator --
+// but uses the FP32 pipe, 62x faster than FP64 on GB300.  The __f*_rn forms
+// keep the compiler from contracting the error-free steps.
+__device__ __forceinline__ void df_acc(float& S, float& s, float ah, float al, float z) {
+  const float p = __fmul_rn(ah, z);
+  const float e = __fmaf_rn(ah, z, -p);  // ah z = p + e exactly
+  const float t = __fmaf_rn(al, z, e);
+  const float S1 = __fadd_rn(S, p);
+  const float bv = __fsub_rn(S1, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(S1, bv)), __fsub_rn(p, bv));  // S + p = S1 + err
+  S = S1;
+  s = __fadd_rn(s, __fadd_rn(err, t));
+}
+
+__device__ __forceinline__ double mat_row_split(const DevSell<double>& A, const float* __restrict__ hi,
+                                                const float* __restrict__ lo, int64_t row, int n,
+                                                const float* __restrict__ z) {
+  float S = 0.0f, s = 0.0f;
+  if (row >= n) return 0.0;
+  if (A.G == 0) {
+#pragma unroll 5
+    for (int d = 0; d < A.ndiag; ++d) {
+      const int j = (int)row + A.off[d];
+      const int64_t k = (int64_t)d * n + row;
+      if ((unsigned)j < (unsigned)A.n_cols) df_acc(S, s, __ldg(hi + k), __ldg(lo + k), __ldg(z + j));
+    }
+  } else {
+    const int64_t sl = row >> 5, lane = row & 31;
+    const int64_t end = A.slice_ptr[sl + 1];
+    for (int64_t k = A.slice_ptr[sl] + lane; k < end; k += 32)
+      df_acc(S, s, __ldg(hi + k), __ldg(lo + k), __ldg(z + __ldg(A.col + k)));
+  }
+  return (double)S + (double)s;
+}
+
+// k_pcg_pq with the split-M product: q = M z + beta q_old, p = z + beta p,
+// p.q and alpha (z in FP32).
+__global__ void k_pcg_pq_split(DevSell<double> M, const float* __restrict__ Mhi,
+                               const float* __restrict__ Mlo, int n, const float* __restrict__ z32,
+                               double* __restrict__ p, double* __restrict__ q, PcgScalars* sc,
+                               double* partials, unsigned int* counter, int max_blocks) {
+  pdl_enter();
+  const double beta = sc->beta;
+  double v[1] = {0.0};
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = gtid(); i0 < n; i0 += 2 * st) {  // two rows in flight per thread
+    const int64_t i1 = i0 + st;
+    const double w0 = mat_row_split(M, Mhi, Mlo, i0, n, z32);
+    const double w1 = mat_row_split(M, Mhi, Mlo, i1, n, z32);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t i = h ? i1 : i0;
+      if (i >= n) continue;
+      const double w = h ? w1 : w0;
+      const double zi = (double)z32[i];
+      const double qi = beta == 0.0 ? w : fma(beta, q[i], w);
+      const double pi = beta == 0.0 ? zi : fma(beta, p[i], zi);
       p[i] = pi;
       q[i] = qi;
       v[0] += pi * qi;
@@ -862,6 +942,15 @@ __global__ void k_first_step(int n, const T* __restrict__ b, const T* __restrict
   const T v = dinv[i] * b[i] * inv_theta;
   x[i] = v;
   d[i] = v;
+}
+
+// y = M x for FP32 x through the split-M product (the CG operator pass of
+// the mixed path without its vector updates).
+__global__ void k_spmv_split(DevSell<double> A, const float* __restrict__ hi, const float* __restrict__ lo,
+                             int n, const float* __restrict__ x, double* __restrict__ y) {
+  pdl_enter();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = mat_row_split(A, hi, lo, i, n, x);
 }
 
 __global__ void k_spmv64(DevSell<double> A, int n, const double* __restrict__ x, double* __restrict__ y) {

@@ -16,7 +16,10 @@
 #include "kernels.cuh"
 #include "mlp_kernels.cuh"
 #include "batch_kernels.cuh"
+#include <type_traits>
+
 #include "spe_kernels.cuh"
+#include "ens_kernels.cuh"
 
 using namespace eqs;
 
@@ -276,6 +279,13 @@ static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStrea
   const int nl = (int)L.size();
   DevLevel<T>& V = L[l];
   if (l == nl - 1) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (c->d_cinv_hi) {  // FP32-pair application of the split inverse
+        launch_smem(k_coarse_solve_df<1>, nblk((int64_t)V.n * 32), kBlock, (size_t)V.n * sizeof(float), st, V.n,
+                    (const float*)c->d_cinv_hi, (const float*)c->d_cinv_lo, (const float*)V.b, (float*)V.x);
+        return nullptr;
+      }
+    }
     launch_smem(k_coarse_solve<T>, nblk((int64_t)V.n * 32), kBlock, (size_t)V.n * sizeof(double), st, V.n,
                 c->d_coarse_inv, (const T*)V.b, V.x);
     return nullptr;
@@ -322,13 +332,73 @@ struct SolveSlots {
   int* zero;
 };
 
+// Stage whose solve starts from the SPE vector (solve index stepcount*s + j).
+struct SpeAt {
+  int s, j;
+};
+
+// SPE projection of solve j (templated on the history length): the newest
+// solution's product with M, the Gram column and the coefficients y.
+template <int NH>
+static void spe_gram_n(eqs_ctx* c, cudaStream_t st, int s, int j) {
+  const int nf = (int)c->n_free;
+  launch(k_spe_gram<NH>, std::max(1, std::min(nblk(nf), c->sms)), kBlock, st, c->M64, nf,
+         (const double*)c->d_spe_X, c->d_spe_W, (const double*)c->d_R, (const long long*)c->d_stepcount, s, j,
+         c->d_spe_G, c->d_spe_partials, c->red.counter, c->red.max_blocks, 1e-12, c->d_spe_y);
+}
+
+static void spe_gram(eqs_ctx* c, cudaStream_t st, int s, int j) {
+  switch (c->opts.spe_n) {
+    case 1: spe_gram_n<1>(c, st, s, j); break;
+    case 2: spe_gram_n<2>(c, st, s, j); break;
+    case 3: spe_gram_n<3>(c, st, s, j); break;
+    case 4: spe_gram_n<4>(c, st, s, j); break;
+    case 5: spe_gram_n<5>(c, st, s, j); break;
+    default: spe_gram_n<6>(c, st, s, j); break;
+  }
+}
+
+// x0 = X y and, unless R is null, r0 = R - W y with the first V-cycle input
+// and the loop condition (the CG start of an SPE solve).
+template <typename T, int NH>
+static void spe_start_n(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st, int s, int j,
+                        const double* R, double* x, double tol2, cudaGraphConditionalHandle h,
+                        int use_handle, SolveSlots sl) {
+  DevLevel<T>& V = L[0];
+  const int nf = (int)c->n_free;
+  launch(k_spe_start<T, NH>, vec_grid(c, nf), kBlock, st, c->M64, nf, (const double*)c->d_spe_X,
+         (const double*)c->d_spe_W, (const double*)c->d_spe_y, (const long long*)c->d_stepcount, s, j, R, x,
+         R ? c->d_r : nullptr, V.dinv, (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials,
+         c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres,
+         sl.zero);
+}
+
+template <typename T>
+static void spe_start(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st, int s, int j,
+                      const double* R, double* x, double tol2, cudaGraphConditionalHandle h,
+                      int use_handle, SolveSlots sl) {
+  switch (c->opts.spe_n) {
+    case 1: spe_start_n<T, 1>(c, L, st, s, j, R, x, tol2, h, use_handle, sl); break;
+    case 2: spe_start_n<T, 2>(c, L, st, s, j, R, x, tol2, h, use_handle, sl); break;
+    case 3: spe_start_n<T, 3>(c, L, st, s, j, R, x, tol2, h, use_handle, sl); break;
+    case 4: spe_start_n<T, 4>(c, L, st, s, j, R, x, tol2, h, use_handle, sl); break;
+    case 5: spe_start_n<T, 5>(c, L, st, s, j, R, x, tol2, h, use_handle, sl); break;
+    default: spe_start_n<T, 6>(c, L, st, s, j, R, x, tol2, h, use_handle, sl); break;
+  }
+}
+
+
 template <typename T>
 static void pcg_init_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st,
                             const double* R, double* x, double tol2, cudaGraphConditionalHandle h,
                             int use_handle, SolveSlots sl, const double* h1 = nullptr,
-                            int* kept = nullptr) {
+                            int* kept = nullptr, const SpeAt* spe = nullptr) {
   DevLevel<T>& V = L[0];
   const int n = (int)c->n_free;
+  if (spe) {  // SPE start vector: x0 = X y, r0 = R - W y (no SpMV)
+    spe_start<T>(c, L, st, spe->s, spe->j, R, x, tol2, h, use_handle, sl);
+    return;
+  }
   if (h1) {  // learned start vector with the previous solution as fallback
     launch(k_pcg_init_dual<T>, vec_grid(c, n), kBlock, st, c->M64, n, R, x, h1, c->d_r, c->d_rtmp, V.dinv,
            (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials, c->red.counter,
@@ -350,10 +420,14 @@ static void pcg_body_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_
   const int n = (int)c->n_free;
   const int g = vec_grid(c, n);
   T* zpend = vcycle_level(c, L, 0, st);
-  launch(k_pcg_dots<T>, g, kBlock, st, n, c->d_r, c->d_rprev, V.x, (const T*)zpend, c->d_zd, c->d_sc,
-         c->red.partials, c->red.counter, c->red.max_blocks, c->opts.flexible);
-  launch(k_pcg_pq, g, kBlock, st, c->M64, n, c->d_zd, c->d_p, c->d_q, c->d_sc, c->red.partials,
-         c->red.counter, c->red.max_blocks);
+  launch(k_pcg_dots<T>, g, kBlock, st, n, c->d_r, c->d_rprev, V.x, (const T*)zpend, c->d_zd, c->d_z32,
+         c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks, c->opts.flexible);
+  if (c->d_z32)  // mixed path: FP32 z, split-M operator pass
+    launch(k_pcg_pq_split, g, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo, n,
+           (const float*)c->d_z32, c->d_p, c->d_q, c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks);
+  else
+    launch(k_pcg_pq, g, kBlock, st, c->M64, n, c->d_zd, c->d_p, c->d_q, c->d_sc, c->red.partials,
+           c->red.counter, c->red.max_blocks);
   launch(k_pcg_update<T>, g, kBlock, st, n, x, c->d_r, c->d_rprev, c->d_p, c->d_q, V.dinv,
          (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials, c->red.counter,
          c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres);
@@ -378,7 +452,8 @@ static int64_t count_kernel_nodes(cudaGraph_t g) {
 // c->cap_stream; the loop body is captured on c->cap_stream2.
 template <typename T>
 static eqs_status pcg_capture(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* R, double* x,
-                              double tol2, SolveSlots sl, const double* h1 = nullptr, int* kept = nullptr) {
+                              double tol2, SolveSlots sl, const double* h1 = nullptr, int* kept = nullptr,
+                              const SpeAt* spe = nullptr) {
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -386,7 +461,7 @@ static eqs_status pcg_capture(eqs_ctx* c, std::vector<DevLevel<T>>& L, const dou
   CK(cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphConditionalHandle h;
   CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
-  pcg_init_launch<T>(c, L, c->cap_stream, R, x, tol2, h, 1, sl, h1, kept);
+  pcg_init_launch<T>(c, L, c->cap_stream, R, x, tol2, h, 1, sl, h1, kept, spe);
   CK(cudaGetLastError());
   CK(cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
@@ -492,9 +567,9 @@ static eqs_status persistent_launch(eqs_ctx* c, cudaStream_t st, const double* R
 // back after every iteration).  Used by the host-loop execution mode.
 template <typename T>
 static eqs_status pcg_direct(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* R, double* x,
-                             double tol2, SolveSlots sl, const double* h1, int* kept) {
+                             double tol2, SolveSlots sl, const double* h1, int* kept, const SpeAt* spe) {
   cudaStream_t st = c->stream;
-  pcg_init_launch<T>(c, L, st, R, x, tol2, 0, 0, sl, h1, kept);
+  pcg_init_launch<T>(c, L, st, R, x, tol2, 0, 0, sl, h1, kept, spe);
   for (int it = 0; it < c->opts.max_iter; ++it) {
     int conv = 0;
     CK(cudaMemcpyAsync(&conv, &c->d_sc->conv, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -508,10 +583,15 @@ static eqs_status pcg_direct(eqs_ctx* c, std::vector<DevLevel<T>>& L, const doub
 
 template <typename T>
 static eqs_status solve_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* R, double* x,
-                               double tol2, SolveSlots sl, const double* h1 = nullptr, int* kept = nullptr) {
-  if (c->direct) return pcg_direct<T>(c, L, R, x, tol2, sl, h1, kept);
-  if (c->opts.persistent && !h1) return persistent_launch<T>(c, c->cap_stream, R, x, tol2, sl);
-  return pcg_capture<T>(c, L, R, x, tol2, sl, h1, kept);
+                               double tol2, SolveSlots sl, const double* h1 = nullptr, int* kept = nullptr,
+                               const SpeAt* spe = nullptr) {
+  if (c->direct) return pcg_direct<T>(c, L, R, x, tol2, sl, h1, kept, spe);
+  if (c->opts.persistent && !h1) {
+    // the persistent kernel forms its own initial residual: only x0 here
+    if (spe) spe_start<T>(c, L, c->cap_stream, spe->s, spe->j, nullptr, x, tol2, 0, 0, sl);
+    return persistent_launch<T>(c, c->cap_stream, R, x, tol2, sl);
+  }
+  return pcg_capture<T>(c, L, R, x, tol2, sl, h1, kept, spe);
 }
 
 static bool mixed(const eqs_ctx* c) { return c->opts.precision == EQS_PREC_MIXED; }
@@ -530,30 +610,6 @@ static void elem_launch(eqs_ctx* c, cudaStream_t st, const double* Y, int n_limi
 // -------------------------------------------------------- step graph
 static double* Ybuf(eqs_ctx* c, int j) { return j == 0 ? c->d_Y[0] : c->d_Y[1 + (j - 1) % 3]; }
 static double* Fbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_F[0] : c->d_F[1 + (j - 1) % 2]; }
-
-// SPE start vector of solve j into x0 (templated on the history length).
-template <int NH>
-static void spe_launch_n(eqs_ctx* c, cudaStream_t st, int s, int j, double* x0) {
-  const int nf = (int)c->n_free;
-  launch(k_spe_mx<NH>, nblk(nf), kBlock, st, c->M64, nf, (const double*)c->d_spe_X, c->d_spe_R,
-         (const long long*)c->d_stepcount, s, j);
-  launch(k_spe_gram<NH>, std::max(1, std::min(nblk(nf), c->sms)), kBlock, st, nf, (const double*)c->d_spe_X, (const double*)c->d_spe_R,
-         (const double*)c->d_R, (const long long*)c->d_stepcount, s, j, c->d_spe_partials, c->red.counter,
-         c->red.max_blocks, 1e-12, c->d_spe_y);
-  launch(k_spe_combine<NH>, vec_grid(c, nf), kBlock, st, nf, (const double*)c->d_spe_X,
-         (const double*)c->d_spe_y, (const long long*)c->d_stepcount, s, j, x0);
-}
-
-static void spe_launch(eqs_ctx* c, cudaStream_t st, int s, int j, double* x0) {
-  switch (c->opts.spe_n) {
-    case 1: spe_launch_n<1>(c, st, s, j, x0); break;
-    case 2: spe_launch_n<2>(c, st, s, j, x0); break;
-    case 3: spe_launch_n<3>(c, st, s, j, x0); break;
-    case 4: spe_launch_n<4>(c, st, s, j, x0); break;
-    case 5: spe_launch_n<5>(c, st, s, j, x0); break;
-    default: spe_launch_n<6>(c, st, s, j, x0); break;
-  }
-}
 
 // Enqueue one RKC step on st: captured into a graph (c->direct false) or
 // launched directly with a host-driven CG loop (c->direct true).
@@ -605,8 +661,9 @@ static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
              (const __nv_bfloat16*)c->d_theta_bf16, (const double*)c->d_sh, Fbuf(c, j));
       stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, h1, c->d_mlp_used + j);
     } else if (c->opts.guess == EQS_GUESS_SPE) {
-      spe_launch(c, st, s, j, Fbuf(c, j));
-      stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl);
+      spe_gram(c, st, s, j);
+      const SpeAt at{s, j};
+      stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, nullptr, nullptr, &at);
     } else {
       if (c->opts.guess == EQS_GUESS_ZERO && cudaMemsetAsync(Fbuf(c, j), 0, nf * sizeof(double), st) != cudaSuccess)
         stt = fail(c, EQS_ERR_CUDA, "cudaMemsetAsync failed during capture");
@@ -675,6 +732,11 @@ static void destroy_graphs(eqs_ctx* c) {
   c->step_graphs.clear();
   for (auto& kv : c->solve_graphs) destroy_graph(kv.second);
   c->solve_graphs.clear();
+  c->ens_last = nullptr;
+  for (auto& kv : c->ens_graphs) destroy_graph(kv.second);
+  c->ens_graphs.clear();
+  destroy_graph(c->ens_solve_graph);
+  c->ens_solve_tol = -1.0;
 }
 
 template <typename T>
@@ -688,6 +750,240 @@ static eqs_status vcycle_impl(eqs_ctx* c, std::vector<DevLevel<T>>& L, const dou
   if (zpend) launch(k_axpy1<T>, nblk(nf), kBlock, st, nf, V.x, (const T*)zpend);
   launch(k_from_T<T>, nblk(nf), kBlock, st, nf, V.x, z);
   CK(cudaGetLastError());
+  return EQS_OK;
+}
+
+// ------------------------------------------------------------ ensemble
+// Four trajectories on one context (row-interleaved vectors); mixed
+// precision with the previous-solution start vector.
+static eqs_status ens_alloc(eqs_ctx* c) {
+  if (c->ens_ready) return EQS_OK;
+  if (!mixed(c) || !c->d_M_hi || !c->d_cinv_hi)
+    return fail(c, EQS_ERR_STATE, "the ensemble needs a context set up in EQS_PREC_MIXED with split_m 1");
+  const int64_t n = c->n_nodes, nf = c->n_free;
+  c->elev.assign(c->lev32.size(), eqs_ctx::EnsLevel());
+  for (size_t l = 0; l < c->lev32.size(); ++l) {
+    const int nl = c->lev32[l].n;
+    eqs_ctx::EnsLevel& E = c->elev[l];
+    for (float4** v : {&E.b, &E.x, &E.r, &E.dA, &E.dB}) CK(dalloc(c, v, nl));
+  }
+  for (auto& y : c->d_eY) CK(dalloc(c, &y, n));
+  CK(dalloc(c, &c->d_eY2, 2 * n));
+  for (auto& f : c->d_eF) CK(dalloc(c, &f, nf));
+  for (double4_32a** v : {&c->d_eR, &c->d_er, &c->d_erprev, &c->d_ep, &c->d_eq, &c->d_esol}) CK(dalloc(c, v, nf));
+  CK(dalloc(c, &c->d_ey32, n));
+  CK(dalloc(c, &c->d_ez32, nf));
+  EnsScalars* sc = nullptr;
+  CK(dalloc(c, &sc, 1));
+  c->d_esc = sc;
+  CK(dalloc(c, &c->d_epart, 2 * kEnsW * (size_t)c->red.max_blocks));
+  CK(dalloc(c, &c->d_eiters, (EQS_MAX_STAGES + 1) * kEnsW));
+  CK(dalloc(c, &c->d_erelres, (EQS_MAX_STAGES + 1) * kEnsW));
+  CK(dalloc(c, &c->d_ezero, (EQS_MAX_STAGES + 1) * kEnsW));
+  CK(dalloc(c, &c->d_ecolv, kEnsW));
+  c->ens_ready = true;
+  return EQS_OK;
+}
+
+// V-cycle of the four columns from level l (returns the pending direction of
+// a degree-1 post-smoother, like vcycle_level).
+static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st) {
+  std::vector<DevLevel<float>>& L = c->lev32;
+  const int nl = (int)L.size();
+  DevLevel<float>& V = L[l];
+  eqs_ctx::EnsLevel& E = c->elev[l];
+  if (l == nl - 1) {
+    launch_smem(k_coarse_solve_df<4>, nblk((int64_t)V.n * 32), kBlock, (size_t)V.n * sizeof(float4), st, V.n,
+                (const float*)c->d_cinv_hi, (const float*)c->d_cinv_lo, (const float*)E.b, (float*)E.x);
+    return nullptr;
+  }
+  const int deg = c->opts.cheb_degree;
+  std::vector<double> c1, c2;
+  cheb_coeffs(V.sigma, V.delta, deg, c1, c2);
+  const int g = rows_grid(c, (int64_t)V.n * std::max(V.A.G, 1));
+  float4* din = E.dA;
+  float4* dout = E.dB;
+  const float4* rin = E.b;
+  for (int k = 2; k <= deg; ++k) {
+    launch(k4_cheb_step, g, kBlock, st, V.A, V.n, rin, (const float4*)din, (const float*)V.dinv, (float)c1[k],
+           (float)c2[k], E.r, dout, E.x, 0);
+    rin = E.r;
+    std::swap(din, dout);
+  }
+  if (deg >= 2)
+    launch(k4_resid_update, g, kBlock, st, V.A, V.n, E.r, (const float4*)din);
+  else
+    launch(k4_resid, g, kBlock, st, V.A, V.n, (const float4*)E.b, (const float4*)E.x, E.r);
+  DevLevel<float>& C = L[l + 1];
+  eqs_ctx::EnsLevel& EC = c->elev[l + 1];
+  const int first = (l + 1 < nl - 1) ? 1 : 0;
+  launch(k4_restrict, rows_grid(c, (int64_t)C.n * std::max(V.R.G, 1)), kBlock, st, V.R, C.n, (const float4*)E.r,
+         EC.b, (const float*)C.dinv, (float)C.inv_theta, EC.x, EC.dA, first);
+  float4* cpend = ens_vcycle_level(c, l + 1, st);
+  launch(k4_prolong, rows_grid(c, (int64_t)V.n * std::max(V.P.G, 1)), kBlock, st, V.P, V.n, (const float4*)EC.x,
+         (const float4*)cpend, E.x);
+  launch(k4_post_first, g, kBlock, st, V.A, V.n, (const float4*)E.b, (const float4*)E.x, (const float*)V.dinv,
+         (float)V.inv_theta, E.r, E.dA);
+  din = E.dA;
+  dout = E.dB;
+  for (int k = 2; k <= deg; ++k) {
+    launch(k4_cheb_step, g, kBlock, st, V.A, V.n, (const float4*)E.r, (const float4*)din, (const float*)V.dinv,
+           (float)c1[k], (float)c2[k], E.r, dout, E.x, k == 2 ? 1 : 0);
+    std::swap(din, dout);
+  }
+  return deg == 1 ? E.dA : nullptr;
+}
+
+struct EnsSlots {
+  int* iters;      // 4 per stage
+  double* relres;  // 4 per stage
+  int* zero;       // 4 per stage
+};
+
+static void ens_init_launch(eqs_ctx* c, cudaStream_t st, const double4_32a* R, double4_32a* x, double tol2,
+                            cudaGraphConditionalHandle h, int use_handle, EnsSlots sl) {
+  DevLevel<float>& V = c->lev32[0];
+  eqs_ctx::EnsLevel& E = c->elev[0];
+  const int n = (int)c->n_free;
+  launch(k4_pcg_init, vec_grid(c, n), kBlock, st, c->M64, n, R, (const double4_32a*)x, c->d_er,
+         (const float*)V.dinv, (float)V.inv_theta, E.b, E.x, E.dA, (EnsScalars*)c->d_esc, c->d_epart,
+         c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres, sl.zero);
+}
+
+static void ens_body_launch(eqs_ctx* c, cudaStream_t st, double4_32a* x, double tol2,
+                            cudaGraphConditionalHandle h, int use_handle, EnsSlots sl) {
+  DevLevel<float>& V = c->lev32[0];
+  eqs_ctx::EnsLevel& E = c->elev[0];
+  const int n = (int)c->n_free;
+  const int g = vec_grid(c, n);
+  EnsScalars* sc = (EnsScalars*)c->d_esc;
+  float4* zpend = ens_vcycle_level(c, 0, st);
+  launch(k4_pcg_dots, g, kBlock, st, n, (const double4_32a*)c->d_er, (const double4_32a*)c->d_erprev,
+         (const float4*)E.x, (const float4*)zpend, c->d_ez32, sc, c->d_epart, c->red.counter, c->red.max_blocks,
+         c->opts.flexible);
+  launch(k4_pcg_pq, g, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo, n,
+         (const float4*)c->d_ez32, c->d_ep, c->d_eq, sc, c->d_epart, c->red.counter, c->red.max_blocks);
+  launch(k4_pcg_update, g, kBlock, st, n, x, c->d_er, c->d_erprev, (const double4_32a*)c->d_ep,
+         (const double4_32a*)c->d_eq, (const float*)V.dinv, (float)V.inv_theta, E.b, E.x, E.dA, sc, c->d_epart,
+         c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres);
+}
+
+// "init; while (any column active) body" captured into the graph of c->cap_stream.
+static eqs_status ens_pcg_capture(eqs_ctx* c, const double4_32a* R, double4_32a* x, double tol2, EnsSlots sl) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  ens_init_launch(c, c->cap_stream, R, x, tol2, h, 1, sl);
+  CK(cudaGetLastError());
+  CK(cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(c->cap_stream2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  ens_body_launch(c, c->cap_stream2, x, tol2, h, 1, sl);
+  cudaError_t le = cudaGetLastError();
+  cudaGraph_t body_out = nullptr;
+  CK(cudaStreamEndCapture(c->cap_stream2, &body_out));
+  CK(le);
+  c->ens_body_kernels = count_kernel_nodes(body_out);
+  CK(cudaStreamUpdateCaptureDependencies(c->cap_stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return EQS_OK;
+}
+
+// Host-driven loop (host_loop option): same kernels, the flags are read back
+// after every pass.
+static eqs_status ens_pcg_direct(eqs_ctx* c, const double4_32a* R, double4_32a* x, double tol2, EnsSlots sl) {
+  cudaStream_t st = c->stream;
+  ens_init_launch(c, st, R, x, tol2, 0, 0, sl);
+  EnsScalars* sc = (EnsScalars*)c->d_esc;
+  for (int it = 0; it < c->opts.max_iter; ++it) {
+    int conv[kEnsW];
+    CK(cudaMemcpyAsync(conv, sc->conv, sizeof(conv), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int k = 0; k < kEnsW; ++k) any |= !conv[k];
+    if (!any) break;
+    ens_body_launch(c, st, x, tol2, 0, 0, sl);
+  }
+  CK(cudaGetLastError());
+  return EQS_OK;
+}
+
+static double4_32a* eYbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_eY[0] : c->d_eY[1 + (j - 1) % 3]; }
+static double4_32a* eFbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_eF[0] : c->d_eF[1 + (j - 1) % 2]; }
+
+static eqs_status ens_enqueue_step(eqs_ctx* c, int s, double* X, const double* d_cj, cudaStream_t st) {
+  std::vector<double> mu, nu, mut, gt, cj;
+  double beta;
+  rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
+  const int n = (int)c->n_nodes, nf = (int)c->n_free;
+  const double tol2 = c->opts.rtol * c->opts.rtol;
+  const double w = 2.0 * M_PI * c->freq;
+  launch(k_stage_scalars, 1, 64, st, s + 1, d_cj, c->d_params, c->V0, w, c->phase, c->d_g, c->d_gp,
+         c->d_stepcount);
+  launch(k4_gather_state, nblk(n), kBlock, st, n, nf, (const double*)X, (const int32_t*)c->d_node_of_internal,
+         (const double*)c->d_dir_scale, (const double*)c->d_g, (const double*)c->d_ecolv, eYbuf(c, 0), c->d_eY2,
+         (const double4_32a*)eFbuf(c, s - 1), eFbuf(c, 0));
+  eqs_status stt = EQS_OK;
+  for (int j = 0; j <= s && stt == EQS_OK; ++j) {
+    if (j >= 1) {
+      const bool first = (j == 1);
+      const bool last = (j == s);
+      const double c0 = first ? 1.0 : 1.0 - mu[j] - nu[j];
+      launch(k4_recurrence, nblk(n), kBlock, st, n, nf, c0, first ? 0.0 : mu[j], first ? 0.0 : nu[j], mut[j],
+             first ? 0.0 : gt[j], (const StepParams*)c->d_params, (const double4_32a*)eYbuf(c, 0),
+             (const double4_32a*)eYbuf(c, j - 1), (const double4_32a*)eYbuf(c, j >= 2 ? j - 2 : 0),
+             (const double4_32a*)eFbuf(c, j - 1), (const double4_32a*)eFbuf(c, 0), (const int*)c->d_ezero, j - 1,
+             (const double*)c->d_dir_scale, (const double*)(c->d_g + j), (const double*)c->d_ecolv, eYbuf(c, j),
+             last ? nullptr : c->d_eY2, last ? nullptr : eFbuf(c, j), last ? X : nullptr,
+             (const int32_t*)c->d_node_of_internal);
+      if (last) break;
+    }
+    launch(k4_elem32, nblk(c->n_tets), kBlock, st, c->n_tets, (const int4*)c->d_conn, (const uint8_t*)c->d_mat,
+           (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi, (const float4*)c->d_xyz_lo,
+           (const float4*)c->d_eY2, nf, c->d_ey32);
+    launch(k4_rhs, nblk(nf), kBlock, st, nf, c->d_ey32, (const double*)(c->d_gp + j), (const double*)c->d_ecolv,
+           (const double*)c->d_mtop, c->d_eR);
+    EnsSlots sl{c->d_eiters + kEnsW * j, c->d_erelres + kEnsW * j, c->d_ezero + kEnsW * j};
+    if (c->direct)
+      stt = ens_pcg_direct(c, c->d_eR, eFbuf(c, j), tol2, sl);
+    else
+      stt = ens_pcg_capture(c, c->d_eR, eFbuf(c, j), tol2, sl);
+  }
+  return stt;
+}
+
+static eqs_status ens_capture_step(eqs_ctx* c, int s, double* X, GraphEntry& ge) {
+  std::vector<double> mu, nu, mut, gt, cj;
+  double beta;
+  rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
+  CK(upload(c, &ge.d_cj, cj.data(), cj.size()));
+  cudaStream_t st = c->cap_stream;
+  c->direct = false;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  eqs_status stt = ens_enqueue_step(c, s, X, ge.d_cj, st);
+  cudaError_t le = cudaGetLastError();
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  if (stt != EQS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return stt;
+  }
+  CK(le);
+  CK(ee);
+  ge.graph = graph;
+  ge.s = s;
+  ge.fixed_kernels = count_kernel_nodes(graph);
+  ge.per_iter_kernels = c->ens_body_kernels;
+  CK(cudaGraphInstantiate(&ge.exec, graph, 0));
   return EQS_OK;
 }
 
@@ -736,11 +1032,12 @@ void eqs_opts_default(eqs_opts* o) {
   o->max_iter = 500;
   o->guess = EQS_GUESS_PREV;
   o->flexible = 1;
-  o->persistent = 1;
+  o->persistent = 0;
   o->blocks_per_sm = 1;
   o->spe_n = 4;
   o->host_loop = 0;
   o->barrier_polls = 0;
+  o->split_m = 1;
 }
 
 eqs_status eqs_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
@@ -814,6 +1111,8 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
   destroy_graphs(c);
   free_all(c);
   c->setup_done = false;
+  c->ens_ready = false;
+  c->elev.clear();
   c->opts = o;
   c->hier_ready = false;
 
@@ -884,7 +1183,35 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
   CK(upload(c, &c->d_dir_scale, dir_scale.data(), dir_scale.size()));
   CK(upload(c, &c->d_mtop, mtop.data(), mtop.size()));
   CK(upload_sell(c, Mff, c->M64, false));  // CG kernels use one thread per row (DIA or SELL)
+  c->d_M_hi = c->d_M_lo = nullptr;
+  c->d_z32 = nullptr;
+  if (mixed(c) && c->opts.split_m) {  // M_ff = hi + lo in FP32 parts, same layout
+    std::vector<double> mv((size_t)c->M64.stored);
+    CK(cudaMemcpy(mv.data(), c->M64.val, mv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<float> mh(mv.size()), ml(mv.size());
+    for (size_t k = 0; k < mv.size(); ++k) {
+      mh[k] = (float)mv[k];
+      ml[k] = (float)(mv[k] - (double)mh[k]);
+    }
+    CK(upload(c, &c->d_M_hi, mh.data(), mh.size()));
+    CK(upload(c, &c->d_M_lo, ml.data(), ml.size()));
+    CK(dalloc(c, &c->d_z32, std::max<int64_t>(nf, 1)));
+  }
   CK(upload(c, &c->d_coarse_inv, inv.data(), inv.size()));
+  c->d_cinv_hi = c->d_cinv_lo = nullptr;
+  if (mixed(c)) {  // the FP32-pair coarse solve of the mixed V-cycle
+    std::vector<float> ih(inv.size()), il(inv.size());
+    for (size_t k = 0; k < inv.size(); ++k) {
+      ih[k] = (float)inv[k];
+      il[k] = (float)(inv[k] - (double)ih[k]);
+    }
+    CK(upload(c, &c->d_cinv_hi, ih.data(), ih.size()));
+    CK(upload(c, &c->d_cinv_lo, il.data(), il.size()));
+    const size_t smem = (size_t)c->coarse_n * 4 * sizeof(float);
+    if (smem > 227 * 1024) return fail(c, EQS_ERR_ARG, "coarsest level too large for the shared-memory coarse solve");
+    CK(cudaFuncSetAttribute(k_coarse_solve_df<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
+    CK(cudaFuncSetAttribute(k_coarse_solve_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
+  }
   c->lev64.clear();
   c->lev32.clear();
   if (mixed(c))
@@ -943,8 +1270,9 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     CK(dalloc(c, &c->d_mlp_used, EQS_MAX_STAGES + 1));
     CK(dalloc(c, &c->d_rtmp, nf));
     CK(dalloc(c, &c->d_spe_X, (size_t)kSpeMax * nf));
-    CK(dalloc(c, &c->d_spe_R, (size_t)kSpeMax * nf));
+    CK(dalloc(c, &c->d_spe_W, (size_t)kSpeMax * nf));
     CK(dalloc(c, &c->d_spe_y, kSpeMax));
+    CK(dalloc(c, &c->d_spe_G, (size_t)kSpeMax * kSpeMax));
     CK(dalloc(c, &c->d_spe_partials, (size_t)kSpeSums * c->red.max_blocks));
     c->adam_t = 0;
     c->d_store = nullptr;
@@ -1026,6 +1354,16 @@ eqs_status eqs_spmv_M(eqs_ctx* c, const double* x, double* y) {
   if (!x || !y) return fail(c, EQS_ERR_ARG, "null vector");
   const int nf = (int)c->n_free;
   k_spmv64<<<nblk(nf), kBlock, 0, c->stream>>>(c->M64, nf, x, y);
+  CK(cudaGetLastError());
+  return EQS_OK;
+}
+
+eqs_status eqs_spmv_M32(eqs_ctx* c, const float* x, double* y) {
+  REQUIRE_SETUP(c);
+  if (!x || !y) return fail(c, EQS_ERR_ARG, "null vector");
+  if (!c->d_M_hi) return fail(c, EQS_ERR_STATE, "set up in EQS_PREC_MIXED with split_m 1 first");
+  const int nf = (int)c->n_free;
+  k_spmv_split<<<nblk(nf), kBlock, 0, c->stream>>>(c->M64, c->d_M_hi, c->d_M_lo, nf, x, y);
   CK(cudaGetLastError());
   return EQS_OK;
 }
@@ -1161,6 +1499,131 @@ eqs_status eqs_get_step_stats(eqs_ctx* c, eqs_step_stats* stats) {
   if (res == EQS_ERR_NOCONV) return fail(c, res, "a stage solve reached max_iter");
   if (res == EQS_ERR_NAN) return fail(c, res, "non-finite residual in a stage solve");
   return EQS_OK;
+}
+
+// ------------------------------------------------------------- ensemble
+eqs_status eqs_ens_rkc_step(eqs_ctx* c, double* x, const double* v0_scale, double t, double dt, int s,
+                            eqs_ens_stats* stats) {
+  REQUIRE_SETUP(c);
+  if (!x || !v0_scale) return fail(c, EQS_ERR_ARG, "x or v0_scale is NULL");
+  if (s < 2 || s > EQS_MAX_STAGES) return fail(c, EQS_ERR_ARG, "s out of range [2, 64]");
+  if (!std::isfinite(t) || !(dt > 0) || !std::isfinite(dt)) return fail(c, EQS_ERR_ARG, "bad t or dt");
+  for (int k = 0; k < EQS_ENS_W; ++k)
+    if (!std::isfinite(v0_scale[k])) return fail(c, EQS_ERR_ARG, "non-finite drive scale");
+  const eqs_status as = ens_alloc(c);
+  if (as != EQS_OK) return as;
+  StepParams prm{t, dt};
+  CK(cudaMemcpyAsync(c->d_params, &prm, sizeof(prm), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_ecolv, v0_scale, EQS_ENS_W * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (c->opts.host_loop) {
+    const std::pair<int, uintptr_t> dkey(-s, 0);
+    auto dit = c->ens_graphs.find(dkey);
+    if (dit == c->ens_graphs.end()) {
+      GraphEntry ge;
+      std::vector<double> mu, nu, mut, gt, cj;
+      double beta;
+      rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
+      CK(upload(c, &ge.d_cj, cj.data(), cj.size()));
+      ge.s = s;
+      dit = c->ens_graphs.emplace(dkey, ge).first;
+    }
+    c->direct = true;
+    g_launches = 0;
+    const eqs_status st = ens_enqueue_step(c, s, x, dit->second.d_cj, c->stream);
+    c->direct = false;
+    if (st != EQS_OK) return st;
+    dit->second.fixed_kernels = g_launches;
+    dit->second.per_iter_kernels = 0;
+    c->ens_last = &dit->second;
+  } else {
+    const std::pair<int, uintptr_t> key(s, (uintptr_t)x);
+    auto it = c->ens_graphs.find(key);
+    if (it == c->ens_graphs.end()) {
+      GraphEntry ge;
+      const eqs_status st = ens_capture_step(c, s, x, ge);
+      if (st != EQS_OK) return st;
+      it = c->ens_graphs.emplace(key, ge).first;
+    }
+    CK(cudaGraphLaunch(it->second.exec, c->stream));
+    c->ens_last = &it->second;
+  }
+  return stats ? eqs_ens_get_step_stats(c, stats) : EQS_OK;
+}
+
+eqs_status eqs_ens_get_step_stats(eqs_ctx* c, eqs_ens_stats* stats) {
+  REQUIRE_SETUP(c);
+  if (!stats) return fail(c, EQS_ERR_ARG, "stats is NULL");
+  if (!c->ens_last) return fail(c, EQS_ERR_STATE, "no ensemble step has run");
+  const int s = c->ens_last->s;
+  std::vector<int> iters((size_t)s * kEnsW);
+  std::vector<double> rr((size_t)s * kEnsW);
+  CK(cudaMemcpyAsync(iters.data(), c->d_eiters, iters.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(rr.data(), c->d_erelres, rr.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::memset(stats, 0, sizeof(*stats));
+  stats->s = s;
+  eqs_status res = EQS_OK;
+  for (int j = 0; j < s; ++j) {
+    int pass = 0;
+    for (int k = 0; k < kEnsW; ++k) {
+      const int it = iters[(size_t)j * kEnsW + k];
+      const double r = rr[(size_t)j * kEnsW + k];
+      stats->total_iters[k] += it;
+      pass = std::max(pass, it);
+      stats->max_relres = std::max(stats->max_relres, r);
+      if (!std::isfinite(r)) res = EQS_ERR_NAN;
+      else if (r > c->opts.rtol && res == EQS_OK) res = EQS_ERR_NOCONV;
+    }
+    stats->passes += pass;
+    stats->max_iters = std::max(stats->max_iters, pass);
+  }
+  stats->launches = c->ens_last->fixed_kernels + c->ens_last->per_iter_kernels * stats->passes;
+  stats->status = res;
+  if (res == EQS_ERR_NOCONV) return fail(c, res, "an ensemble stage solve reached max_iter");
+  if (res == EQS_ERR_NAN) return fail(c, res, "non-finite residual in an ensemble stage solve");
+  return EQS_OK;
+}
+
+eqs_status eqs_ens_solve_M(eqs_ctx* c, const double* rhs, double* z, int* iters_out) {
+  REQUIRE_SETUP(c);
+  if (!rhs || !z) return fail(c, EQS_ERR_ARG, "null vector");
+  const eqs_status as = ens_alloc(c);
+  if (as != EQS_OK) return as;
+  const int nf = (int)c->n_free;
+  cudaStream_t st = c->stream;
+  if (!c->ens_solve_graph.exec) {
+    cudaStream_t cs = c->cap_stream;
+    c->direct = false;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    EnsSlots sl{c->d_eiters, c->d_erelres, c->d_ezero};
+    const double tol = c->opts.rtol;
+    const eqs_status stt = ens_pcg_capture(c, c->d_eR, c->d_esol, tol * tol, sl);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+    if (stt != EQS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return stt;
+    }
+    CK(ee);
+    c->ens_solve_graph.graph = graph;
+    CK(cudaGraphInstantiate(&c->ens_solve_graph.exec, graph, 0));
+  }
+  k4_interleave<<<nblk(nf), kBlock, 0, st>>>(nf, rhs, c->d_eR);
+  k4_interleave<<<nblk(nf), kBlock, 0, st>>>(nf, z, c->d_esol);
+  CK(cudaGraphLaunch(c->ens_solve_graph.exec, st));
+  k4_deinterleave<<<nblk(nf), kBlock, 0, st>>>(nf, c->d_esol, z);
+  int it[kEnsW];
+  double rr[kEnsW];
+  CK(cudaMemcpyAsync(it, c->d_eiters, sizeof(it), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(rr, c->d_erelres, sizeof(rr), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  eqs_status res = EQS_OK;
+  for (int k = 0; k < kEnsW; ++k) {
+    if (iters_out) iters_out[k] = it[k];
+    if (!std::isfinite(rr[k])) res = fail(c, EQS_ERR_NAN, "non-finite residual in the ensemble solve");
+    else if (rr[k] > c->opts.rtol && res == EQS_OK) res = fail(c, EQS_ERR_NOCONV, "ensemble CG reached max_iter");
+  }
+  return res;
 }
 
 double eqs_rkc_dt_bound(const eqs_ctx* c, int s) {
@@ -1338,26 +1801,31 @@ eqs_status eqs_guess_grad(eqs_ctx* c, const float* X, const float* T, int B, flo
   return st;
 }
 
-eqs_status eqs_spe_eval(eqs_ctx* c, const double* X, const double* Rh, const double* b, int n, double* x0) {
+eqs_status eqs_spe_eval(eqs_ctx* c, const double* X, const double* b, int n, double* x0) {
   REQUIRE_SETUP(c);
-  if (!X || !Rh || !b || !x0) return fail(c, EQS_ERR_ARG, "null vector");
+  if (!X || !b || !x0) return fail(c, EQS_ERR_ARG, "null vector");
   if (n != c->opts.spe_n) return fail(c, EQS_ERR_ARG, "n must equal the context's spe_n");
   const int64_t nf = c->n_free;
   cudaStream_t st = c->stream;
   long long* cnt = nullptr;
   CK(cudaMalloc(&cnt, 2 * sizeof(long long)));
-  const long long gn[2] = {n, n + 1};  // solve index g = n: column k sits in slot n-1-k
-  cudaMemcpyAsync(cnt, gn, sizeof(gn), cudaMemcpyHostToDevice, st);
-  for (int k = 0; k < n; ++k) {
-    cudaMemcpyAsync(c->d_spe_X + (size_t)(n - 1 - k) * nf, X + (size_t)k * nf, nf * sizeof(double),
-                    cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(c->d_spe_R + (size_t)(n - 1 - k) * nf, Rh + (size_t)k * nf, nf * sizeof(double),
-                    cudaMemcpyDeviceToDevice, st);
-  }
-  cudaMemcpyAsync(c->d_R, b, nf * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  const long long zero2[2] = {0, 1};  // stepcount 0: solve index g = j
+  CK(cudaMemcpyAsync(cnt, zero2, sizeof(zero2), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(c->d_R, b, nf * sizeof(double), cudaMemcpyDeviceToDevice, st));
   long long* saved = c->d_stepcount;
   c->d_stepcount = cnt;
-  spe_launch(c, st, 1, 0, x0);
+  // push the history oldest first (solution q into slot q % n), updating the
+  // Gram matrix as the step does, then form x0 for the solve g = n
+  for (int q = 0; q < n; ++q) {
+    CK(cudaMemcpyAsync(c->d_spe_X + (size_t)(q % n) * nf, X + (size_t)(n - 1 - q) * nf, nf * sizeof(double),
+                       cudaMemcpyDeviceToDevice, st));
+    spe_gram(c, st, 1, q + 1);
+  }
+  SolveSlots sl{nullptr, nullptr, nullptr};
+  if (mixed(c))
+    spe_start<float>(c, c->lev32, st, 1, n, nullptr, x0, 0.0, 0, 0, sl);
+  else
+    spe_start<double>(c, c->lev64, st, 1, n, nullptr, x0, 0.0, 0, 0, sl);
   c->d_stepcount = saved;
   cudaError_t e = cudaStreamSynchronize(st);
   cudaFree(cnt);

@@ -1,14 +1,19 @@
 // Subspace projection extrapolation (SPE) start vector, Section IV, Eq. 4-5:
 // x0 = V (V^T M V)^-1 V^T b with V spanning the last n solutions.
 //
-// The history rings hold the last n solutions X (FP64) and W = M X; each
-// solve adds one product (M times the newest solution), so V^T M V costs one
-// SpMV per solve: A = X^T W (upper triangle, mirrored).  The basis is formed in the M
-// inner product by a Cholesky factorisation of A that skips a column whose
-// remaining M-norm is below sqrt(drop2) of its own (a nearly dependent
-// history vector) -- the projection of Eq. 5 over the same span that
-// Euclidean Gram-Schmidt would keep.  Solution k of the sequence is stored in
-// ring slot k % n.
+// The history rings hold the last n solutions X (FP64, solution q in ring
+// slot q % n) and W = M X.  The Gram matrix G[a][b] = x_a . w_b (by slot) is
+// kept on the device and updated incrementally: when solution q becomes the
+// newest, one pass computes w_q = M x_q, the new Gram column x_k . w_q for
+// every stored solution k and the projections c_k = x_k . b of the current
+// right-hand side (2n sums instead of n(n+1)/2 + n).  The basis is formed in
+// the M inner product by a Cholesky factorisation of the Gram matrix that
+// skips a column whose remaining M-norm is below sqrt(drop2) of its own (a
+// nearly dependent history vector) -- the projection of Eq. 5 over the same
+// span that Euclidean Gram-Schmidt would keep.
+//
+// Because M x0 = W y, the initial CG residual r0 = b - W y needs no SpMV:
+// k_spe_start forms x0, r0 and the first V-cycle input in one row-local pass.
 #pragma once
 
 #include "kernels.cuh"
@@ -16,77 +21,63 @@
 namespace eqs {
 
 constexpr int kSpeMax = 6;
-constexpr int kSpeSums = kSpeMax * (kSpeMax + 1) / 2 + kSpeMax;  // 27
+constexpr int kSpeSums = 2 * kSpeMax;  // Gram column + projections of b
 
-// W slot of the newest solution x_{g-1}: w = M x_{g-1}.
+__device__ __forceinline__ int spe_slot(long long q, int NH) { return (int)(((q % NH) + NH) % NH); }
+
+// Solve index g = stepcount[0] * s + j: solutions 0..g-1 exist, the newest
+// m = min(g, NH) of them are in the rings.  One pass: w_{g-1} = M x_{g-1},
+// the Gram column G[k][g-1] over the stored solutions k and c_k = x_k . b.
+// The last block updates G and solves (L L^T) y = c with column dropping;
+// y_out[k] is the coefficient of the k-th most recent solution.
 template <int NH>
-__global__ void k_spe_mx(DevSell<double> M, int nf, const double* __restrict__ X, double* __restrict__ W,
-                         const long long* __restrict__ stepcount, int s, int j) {
+__global__ void k_spe_gram(DevSell<double> M, int nf, const double* __restrict__ X, double* __restrict__ W,
+                           const double* __restrict__ b, const long long* __restrict__ stepcount, int s,
+                           int j, double* __restrict__ G, double* partials, unsigned int* counter,
+                           int max_blocks, double drop2, double* __restrict__ y_out) {
   pdl_enter();
   const long long g = stepcount[0] * (long long)s + j;
-  if (g == 0) return;
-  const size_t slot = (size_t)((g - 1) % NH) * nf;
-  for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x)
-    W[slot + i] = mat_row<double>(M, i, nf, X + slot);
-}
-
-// Sums A_kl (k <= l) = x_{g-1-k} . w_{g-1-l} and c_k = x_{g-1-k} . b over the
-// rows; the last block solves for y (y_out[0..n)).
-template <int NH>
-__global__ void k_spe_gram(int nf, const double* __restrict__ X, const double* __restrict__ Rr,
-                           const double* __restrict__ b,
-                           const long long* __restrict__ stepcount, int s, int j, double* partials,
-                           unsigned int* counter, int max_blocks, double drop2, double* y_out) {
-  pdl_enter();
-  const long long g = stepcount[0] * (long long)s + j;
+  if (g == 0) return;  // uniform over the grid: no history, no reduction
   const int m = (int)(g < NH ? g : NH);
-  constexpr int NS = NH * (NH + 1) / 2 + NH;
+  const int sn = spe_slot(g - 1, NH);
+  constexpr int NS = 2 * NH;
   double v[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) v[k] = 0.0;
   const double* xs[NH];
-  const double* ws[NH];
 #pragma unroll
-  for (int k = 0; k < NH; ++k) {
-    const long long slot = ((g - 1 - k) % NH + NH) % NH;
-    xs[k] = X + (size_t)slot * nf;
-    ws[k] = Rr + (size_t)slot * nf;
-  }
-  // few blocks with many rows each: the block reductions of NS values cost
-  // FP64 adds in every lane, so they must stay rare next to the row work
+  for (int k = 0; k < NH; ++k) xs[k] = X + (size_t)spe_slot(g - 1 - k, NH) * nf;
+  const double* __restrict__ xn = X + (size_t)sn * nf;
+  double* __restrict__ wn = W + (size_t)sn * nf;
   for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x) {
-    double xv[NH], wv[NH];
-#pragma unroll
-    for (int k = 0; k < NH; ++k) {
-      xv[k] = k < m ? xs[k][i] : 0.0;
-      wv[k] = k < m ? ws[k][i] : 0.0;
-    }
+    const double w = mat_row<double>(M, i, nf, xn);
+    wn[i] = w;
     const double bi = b[i];
-    int q = 0;
 #pragma unroll
     for (int k = 0; k < NH; ++k) {
-#pragma unroll
-      for (int l = k; l < NH; ++l) v[q] = fma(xv[k], wv[l], v[q]), ++q;
+      const double xk = k < m ? xs[k][i] : 0.0;
+      v[k] = fma(xk, w, v[k]);
+      v[NH + k] = fma(xk, bi, v[NH + k]);
     }
-#pragma unroll
-    for (int k = 0; k < NH; ++k) v[q] = fma(xv[k], bi, v[q]), ++q;
   }
   double tot[NS];
   if (grid_sum<NS>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    int slot[NH];
+    for (int k = 0; k < NH; ++k) slot[k] = spe_slot(g - 1 - k, NH);
+    for (int k = 0; k < m; ++k) {  // new Gram column and row of the newest slot
+      G[slot[k] * kSpeMax + sn] = tot[k];
+      G[sn * kSpeMax + slot[k]] = tot[k];
+    }
     double A[NH][NH], c[NH], L[NH][NH], y[NH];
-    int q = 0;
-    for (int k = 0; k < NH; ++k)
-      for (int l = k; l < NH; ++l) {
-        A[k][l] = tot[q];
-        A[l][k] = tot[q];
-        ++q;
-      }
-    for (int k = 0; k < NH; ++k) c[k] = tot[q++];
     bool keep[NH];
     for (int k = 0; k < NH; ++k) {
+      c[k] = tot[NH + k];
       keep[k] = false;
       y[k] = 0.0;
-      for (int l = 0; l < NH; ++l) L[k][l] = 0.0;
+      for (int l = 0; l < NH; ++l) {
+        A[k][l] = (k < m && l < m) ? G[slot[k] * kSpeMax + slot[l]] : 0.0;
+        L[k][l] = 0.0;
+      }
     }
     // Cholesky with column dropping, most recent solution first
     for (int k = 0; k < m; ++k) {
@@ -123,27 +114,76 @@ __global__ void k_spe_gram(int nf, const double* __restrict__ X, const double* _
   }
 }
 
-// x0 = sum_k y_k x_{g-1-k} (x0 is left as it is when there is no history).
-template <int NH>
-__global__ void k_spe_combine(int nf, const double* __restrict__ X, const double* __restrict__ y,
-                              const long long* __restrict__ stepcount, int s, int j, double* __restrict__ x0) {
+// Start of the CG solve from the SPE vector: x0 = X y, r0 = R - W y (= R -
+// M x0), the norms of R and r0, and the first V-cycle input (b0 = r0 in T,
+// x = d = D0^-1 b0 / theta0); the last block decides whether the CG loop
+// runs.  Without history (g == 0) x keeps the caller's start vector and
+// r0 = R - M x.  With r == nullptr only x0 is written (no reduction).
+template <typename T, int NH>
+__global__ void k_spe_start(DevSell<double> M, int nf, const double* __restrict__ X,
+                            const double* __restrict__ W, const double* __restrict__ yc,
+                            const long long* __restrict__ stepcount, int s, int j,
+                            const double* __restrict__ R, double* __restrict__ x, double* __restrict__ r,
+                            const T* __restrict__ dinv0, T inv_theta0, T* __restrict__ b0,
+                            T* __restrict__ x0, T* __restrict__ d0, PcgScalars* sc, double* partials,
+                            unsigned int* counter, int max_blocks, double tol2, int maxit,
+                            cudaGraphConditionalHandle h, int use_handle, int* iters_out,
+                            double* relres_out, int* zero_out) {
   pdl_enter();
   const long long g = stepcount[0] * (long long)s + j;
   const int m = (int)(g < NH ? g : NH);
-  if (m == 0) return;  // no history yet: keep the previous-solution start vector
-  double yc[NH];
+  double y[NH];
   const double* xs[NH];
+  const double* ws[NH];
 #pragma unroll
   for (int k = 0; k < NH; ++k) {
-    yc[k] = k < m ? y[k] : 0.0;
-    xs[k] = X + (size_t)(((g - 1 - k) % NH + NH) % NH) * nf;
+    y[k] = k < m ? yc[k] : 0.0;
+    const size_t off = (size_t)spe_slot(g - 1 - k, NH) * nf;
+    xs[k] = X + off;
+    ws[k] = W + off;
   }
+  double v[2] = {0.0, 0.0};
   for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
+    double xi, mx;
+    if (m > 0) {
+      xi = 0.0;
+      mx = 0.0;
 #pragma unroll
-    for (int k = 0; k < NH; ++k)
-      if (k < m) acc = fma(yc[k], xs[k][i], acc);
-    x0[i] = acc;
+      for (int k = 0; k < NH; ++k)
+        if (k < m) {
+          xi = fma(y[k], xs[k][i], xi);
+          mx = fma(y[k], ws[k][i], mx);
+        }
+      x[i] = xi;
+    } else {
+      mx = r ? mat_row<double>(M, i, nf, x) : 0.0;
+    }
+    if (!r) continue;
+    const double Ri = R[i];
+    const double ri = Ri - mx;
+    r[i] = ri;
+    const T bi = (T)ri;
+    b0[i] = bi;
+    const T d = dinv0[i] * bi * inv_theta0;
+    x0[i] = d;
+    d0[i] = d;
+    v[0] += Ri * Ri;
+    v[1] += ri * ri;
+  }
+  if (!r) return;
+  double tot[2];
+  if (grid_sum<2>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    sc->bnorm2 = tot[0];
+    sc->rnorm2 = tot[1];
+    sc->it = 0;
+    sc->parity = 0;
+    const int zero = tot[0] == 0.0;
+    const int go = !zero && tot[1] > tol2 * tot[0] && maxit > 0;
+    sc->conv = !go;
+    if (use_handle) cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = zero ? 0.0 : sqrt(tot[1] / tot[0]);
+    if (zero_out) *zero_out = zero;
   }
 }
 

@@ -38,11 +38,21 @@ class eqs_opts(C.Structure):
                 ("max_levels", C.c_int), ("cheb_degree", C.c_int), ("cheb_alpha", C.c_double),
                 ("rtol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int),
                 ("flexible", C.c_int), ("persistent", C.c_int), ("blocks_per_sm", C.c_int),
-                ("spe_n", C.c_int), ("host_loop", C.c_int), ("barrier_polls", C.c_longlong)]
+                ("spe_n", C.c_int), ("host_loop", C.c_int), ("barrier_polls", C.c_longlong),
+                ("split_m", C.c_int)]
 
 
 class eqs_batch_stats(C.Structure):
     _fields_ = [("n_inst", C.c_int), ("s", C.c_int), ("total_iters", C.c_int64),
+                ("max_iters", C.c_int), ("max_relres", C.c_double), ("status", C.c_int),
+                ("launches", C.c_int64)]
+
+
+EQS_ENS_W = 4
+
+
+class eqs_ens_stats(C.Structure):
+    _fields_ = [("s", C.c_int), ("total_iters", C.c_int * EQS_ENS_W), ("passes", C.c_int),
                 ("max_iters", C.c_int), ("max_relres", C.c_double), ("status", C.c_int),
                 ("launches", C.c_int64)]
 
@@ -80,6 +90,7 @@ def _declare(L):
         "eqs_solve_M": (I, [P, P, P, I, D, P]),
         "eqs_vcycle": (I, [P, P, P]),
         "eqs_spmv_M": (I, [P, P, P]),
+        "eqs_spmv_M32": (I, [P, P, P]),
         "eqs_rkc_step": (I, [P, P, D, D, I, C.POINTER(eqs_step_stats)]),
         "eqs_rkc_dt_bound": (D, [P, I]),
         "eqs_get_step_stats": (I, [P, C.POINTER(eqs_step_stats)]),
@@ -94,13 +105,16 @@ def _declare(L):
         "eqs_guess_train": (I, [P, I, I, C.c_float, C.c_uint64, P, P]),
         "eqs_guess_grad": (I, [P, P, P, I, P, P]),
         "eqs_guess_eval": (I, [P, P, P]),
-        "eqs_spe_eval": (I, [P, P, P, P, I, P]),
+        "eqs_spe_eval": (I, [P, P, P, I, P]),
         "eqs_batch_create": (I, [P, I, I, C.POINTER(C.c_void_p)]),
         "eqs_batch_rkc_step": (I, [P, P, D, D, I, C.POINTER(eqs_batch_stats)]),
         "eqs_batch_get_stats": (I, [P, C.POINTER(eqs_batch_stats), P]),
         "eqs_batch_info": (I, [P, P, P]),
         "eqs_batch_destroy": (I, [P]),
         "eqs_batch_last_error": (C.c_char_p, [P]),
+        "eqs_ens_rkc_step": (I, [P, P, P, D, D, I, C.POINTER(eqs_ens_stats)]),
+        "eqs_ens_get_step_stats": (I, [P, C.POINTER(eqs_ens_stats)]),
+        "eqs_ens_solve_M": (I, [P, P, P, P]),
         "eqs_destroy": (I, [P]),
         "eqs_last_error": (C.c_char_p, [P]),
     }
@@ -183,6 +197,10 @@ def eqs_vcycle(ctx, r, z):
 
 def eqs_spmv_M(ctx, x, y):
     _check(lib().eqs_spmv_M(ctx, _dev(x), _dev(y)), ctx)
+
+
+def eqs_spmv_M32(ctx, x, y):
+    _check(lib().eqs_spmv_M32(ctx, _dev(x), _dev(y)), ctx)
 
 
 def eqs_rkc_step(ctx, x, t, dt, s, want_stats=True):
@@ -300,8 +318,33 @@ def eqs_batch_destroy(b):
         lib().eqs_batch_destroy(b)
 
 
-def eqs_spe_eval(ctx, X, Rh, b, n, x0):
-    _check(lib().eqs_spe_eval(ctx, _dev(X), _dev(Rh), _dev(b), n, _dev(x0)), ctx)
+def eqs_spe_eval(ctx, X, b, n, x0):
+    _check(lib().eqs_spe_eval(ctx, _dev(X), _dev(b), n, _dev(x0)), ctx)
+
+
+def eqs_ens_rkc_step(ctx, x, v0_scale, t, dt, s, want_stats=True):
+    """One RKC step of the 4-trajectory ensemble; x: CUDA float64 tensor of
+    shape (4, n_nodes) (trajectory c in row c), v0_scale: 4 drive scales."""
+    st = eqs_ens_stats() if want_stats else None
+    v, vp = _host(v0_scale, np.float64)
+    if v.size != EQS_ENS_W:
+        raise ValueError("v0_scale needs 4 values")
+    _check(lib().eqs_ens_rkc_step(ctx, _dev(x), vp, t, dt, s, C.byref(st) if st is not None else None), ctx)
+    return st
+
+
+def eqs_ens_get_step_stats(ctx):
+    st = eqs_ens_stats()
+    _check(lib().eqs_ens_get_step_stats(ctx, C.byref(st)), ctx)
+    return st
+
+
+def eqs_ens_solve_M(ctx, rhs, z):
+    """Blocked solve of 4 columns: rhs, z CUDA float64 tensors (4, n_free);
+    z holds the start vectors and receives the solutions."""
+    it = (C.c_int * EQS_ENS_W)()
+    _check(lib().eqs_ens_solve_M(ctx, _dev(rhs), _dev(z), it), ctx)
+    return list(it)
 
 
 def eqs_destroy(ctx):

@@ -1,0 +1,137 @@
+"""Four-trajectory ensemble (blocked multiple right-hand-side solves,
+Section IV) on the GPU: each column against its own solo run and the oracle."""
+import dataclasses
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import eqs_inputs as ei
+from oracle import rkc, system
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64, MIXED = 0, 1
+SCALES = (0.5, 1.0, 1.5, 2.0)
+
+
+@pytest.fixture(scope="module")
+def E():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_09447_gb300 import build, eqs
+    if not os.path.exists(build.LIB):
+        build.build()
+    return eqs
+
+
+def _oracle_run(p, s, steps, dt):
+    Sy = system.EQSSystem(p)
+    coef = rkc.RKCCoefficients(s)
+    xf, t, out = np.zeros(p.n_free), 0.0, []
+    for _ in range(steps):
+        xf, _ = rkc.rkc_step(Sy.F, t, xf, dt, coef)
+        t += dt
+        out.append(Sy.full(t, xf))
+    return np.array(out)
+
+
+def _ens_run(E, p, scales, s, steps, rtol, host_loop=0):
+    S = E.Solver(p, precision=MIXED, rtol=rtol, persistent=0, host_loop=host_loop)
+    dt = S.dt_bound(s)
+    x = torch.zeros((4, p.n_nodes), dtype=torch.float64, device="cuda")
+    traj, stats, t = [], [], 0.0
+    for _ in range(steps):
+        st = E.eqs_ens_rkc_step(S.ctx, x, scales, t, dt, s)
+        stats.append(st)
+        t += dt
+        traj.append(x.cpu().numpy().copy())
+    S.close()
+    return np.array(traj), stats, dt
+
+
+def _err(a, b):
+    return np.linalg.norm(a - b, axis=-1).max() / np.linalg.norm(b, axis=-1).max()
+
+
+@pytest.mark.parametrize("name,V0,steps", [("cube12", 1e4, 8), ("jitter10", 2e5, 4)])
+def test_ensemble_matches_solo_and_oracle(E, name, V0, steps):
+    """Every column equals its own single-trajectory run (drive V0 * scale)
+    and the FP64 oracle; V0 = 2e5 drives the varistor into switching, so
+    the columns see different conductivities."""
+    p0 = ei.config_problem(0) if name == "cube12" else ei.config_problem(2, N=10)
+    p = dataclasses.replace(p0, V0=V0)
+    s = 10
+    traj, stats, dt = _ens_run(E, p, SCALES, s, steps, rtol=1e-12)
+    for st in stats:
+        assert st.status == 0 and st.max_relres <= 1e-12
+        assert st.passes >= max(st.total_iters) // s
+    for c, sc in enumerate(SCALES):
+        pc = dataclasses.replace(p, V0=V0 * sc)
+        solo = E.Solver(pc, precision=MIXED, rtol=1e-12, persistent=0)
+        x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+        got, t = [], 0.0
+        for _ in range(steps):
+            solo.step(x, t, dt, s)
+            t += dt
+            got.append(x.cpu().numpy())
+        solo.close()
+        assert _err(traj[:, c], np.array(got)) <= 1e-7, c
+        ref = _oracle_run(pc, s, steps, dt)
+        assert _err(traj[:, c], ref) <= 1e-6, c
+
+
+def test_ensemble_zero_column_and_counts(E):
+    """A column with zero drive stays exactly zero (its right-hand sides are
+    zero: no iterations) while the others iterate; per-column counts add up."""
+    p = ei.config_problem(0)
+    traj, stats, _ = _ens_run(E, p, (0.0, 1.0, 2.0, 0.0), 10, 3, rtol=1e-10)
+    assert not traj[:, 0].any() and not traj[:, 3].any()
+    assert np.abs(traj[:, 1]).max() > 0
+    for st in stats:
+        assert st.total_iters[0] == 0 and st.total_iters[3] == 0
+        assert st.total_iters[1] > 0 and st.total_iters[2] > 0
+        assert st.passes >= max(st.total_iters) // st.s
+        assert st.launches > 0
+
+
+def test_ensemble_host_loop_matches_graph(E):
+    p = ei.config_problem(2, N=10)
+    a, sa, _ = _ens_run(E, p, SCALES, 10, 3, rtol=1e-10, host_loop=0)
+    b, sb, _ = _ens_run(E, p, SCALES, 10, 3, rtol=1e-10, host_loop=1)
+    assert [list(x.total_iters) for x in sa] == [list(x.total_iters) for x in sb]
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-7 * np.abs(a).max())
+
+
+def test_ensemble_solve_blocked(E):
+    """eqs_ens_solve_M: four right-hand sides at once, each column as the
+    direct solve; the per-column iteration counts match single solves."""
+    p = ei.config_problem(2, N=10)
+    S = E.Solver(p, precision=MIXED, rtol=1e-10, persistent=0)
+    Sy = system.EQSSystem(p)
+    rng = np.random.default_rng(7)
+    R = rng.standard_normal((4, p.n_free))
+    R[2] *= 1e-3  # columns of very different size converge independently
+    rhs = torch.tensor(R, dtype=torch.float64, device="cuda")
+    z = torch.zeros_like(rhs)
+    its = E.eqs_ens_solve_M(S.ctx, rhs, z)
+    zs = z.cpu().numpy()
+    for c in range(4):
+        zd = spla.spsolve(Sy.Mff.tocsc(), R[c])
+        assert np.linalg.norm(zs[c] - zd) / np.linalg.norm(zd) <= 1e-7
+        assert np.linalg.norm(R[c] - Sy.Mff @ zs[c]) / np.linalg.norm(R[c]) <= 2e-10
+        _, it1 = S.solve_M(torch.tensor(R[c], device="cuda"), rtol=1e-10)
+        assert abs(its[c] - it1[0]) <= 1, (c, its, it1)
+    S.close()
+
+
+def test_ensemble_requires_mixed(E):
+    p = ei.make_problem(3)
+    S = E.Solver(p, precision=FP64)
+    x = torch.zeros((4, p.n_nodes), dtype=torch.float64, device="cuda")
+    with pytest.raises(E.EqsError) as ex:
+        E.eqs_ens_rkc_step(S.ctx, x, SCALES, 0.0, 1e-3, 10)
+    assert ex.value.status == E.EQS_ERR_STATE
+    S.close()

@@ -69,6 +69,38 @@ def test_spmv_M(E, name):
     S.close()
 
 
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_spmv_M_split(E, name):
+    """The mixed CG operator product (FP32 parts of M, FP32-pair row sums)
+    against FP64 M x for FP32 x: every row within 1e-13 of sum |m_ij x_j|,
+    far below what an FP32 product would give (about 6e-8)."""
+    p = PROBLEMS[name]()
+    S = E.Solver(p, precision=MIXED)
+    Sy = system.EQSSystem(p)
+    rng = np.random.default_rng(5)
+    # a smooth field plus noise: strong cancellation in the Laplace rows
+    x = (np.sin(np.arange(p.n_free) / 50.0) + 1e-3 * rng.standard_normal(p.n_free)).astype(np.float32)
+    y = torch.empty(p.n_free, dtype=torch.float64, device="cuda")
+    E.eqs_spmv_M32(S.ctx, torch.tensor(x, device="cuda"), y)
+    xd = x.astype(np.float64)
+    ref = Sy.Mff @ xd
+    scale = abs(Sy.Mff) @ np.abs(xd)
+    err = np.abs(y.cpu().numpy() - ref) / np.maximum(scale, 1e-300)
+    assert err.max() <= 1e-13, err.max()
+    S.close()
+
+
+def test_spmv_M_split_requires_mixed(E):
+    p = PROBLEMS["cube2"]()
+    S = E.Solver(p, precision=FP64)
+    x = torch.zeros(p.n_free, dtype=torch.float32, device="cuda")
+    y = torch.empty(p.n_free, dtype=torch.float64, device="cuda")
+    with pytest.raises(E.EqsError) as ex:
+        E.eqs_spmv_M32(S.ctx, x, y)
+    assert ex.value.status == E.EQS_ERR_STATE
+    S.close()
+
+
 @pytest.mark.parametrize("name", ["cube12", "jitter10", "cube2"])
 @pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-4)])
 def test_vcycle(E, name, prec, tol):
@@ -121,9 +153,10 @@ def _oracle_run(p, s, steps, dt):
 
 @pytest.mark.parametrize("name,s,steps", [("cube12", 10, 12), ("jitter10", 20, 4), ("batch7", 10, 6)])
 @pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6)])
-def test_rkc_trajectory(E, name, s, steps, prec, tol):
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_rkc_trajectory(E, name, s, steps, prec, tol, persistent):
     p = PROBLEMS[name]()
-    S = E.Solver(p, precision=prec, rtol=1e-13)
+    S = E.Solver(p, precision=prec, rtol=1e-13, persistent=persistent)
     dt = S.dt_bound(s)
     ref = _oracle_run(p, s, steps, dt)
     x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")

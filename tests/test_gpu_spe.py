@@ -34,9 +34,8 @@ def test_spe_projection_matches_oracle(E, n):
     base = np.sin(np.linspace(0, 5, p.n_free))
     H = [base * (1 + 0.3 * k) + 0.2 * rng.standard_normal(p.n_free) for k in range(n)]
     b = Sy.Mff @ (0.7 * H[0] + 0.2 * rng.standard_normal(p.n_free))
-    Rh = [Sy.Mff @ h for h in H]
     x0 = torch.empty(p.n_free, dtype=torch.float64, device="cuda")
-    E.eqs_spe_eval(S.ctx, _cuda(np.concatenate(H)), _cuda(np.concatenate(Rh)), _cuda(b), n, x0)
+    E.eqs_spe_eval(S.ctx, _cuda(np.concatenate(H)), _cuda(b), n, x0)
     ref = spe.spe_start(Sy.Mff, H, b)
     got = x0.cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
