@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--N", type=int, default=None, help="override mesh size (testing)")
     ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3, 4],
                     help="workload: 1 = 64^3 block cube (default), 2 = 128^3 jittered spheres, "
@@ -305,6 +306,17 @@ def run_ours(args, rank, world):
         variants["mixed_mlp"] = dict(summary(r[3], r[5]), train_s=train_s, loss_first=lf, loss_last=ll)
         S.close()
 
+    if not args.no_ensemble:
+        # 4-member ensemble (drive V0 x {0.5, 1, 1.5, 2}) on the same mesh:
+        # every stage's four right-hand sides solved together (blocked CG)
+        variants["ensemble4_mixed_prev"] = measure_ensemble(torch, eqs, p, make, flush,
+                                                            max(3, args.steps // 4), 2)
+        if "mixed_prev" not in variants:
+            S = make(eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_PREV)
+            r = measure(S, max(3, args.steps // 4), 2)
+            variants["mixed_prev"] = summary(r[3], r[5])
+            S.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rr = oracle_sample(4, args.N)
@@ -339,6 +351,45 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+ENS_SCALES = (0.5, 1.0, 1.5, 2.0)
+
+
+def measure_ensemble(torch, eqs, p, make, flush, steps, warmup):
+    """Timed RKC steps of the 4-trajectory ensemble (mixed precision,
+    previous-solution start): DOF-stages count all four trajectories."""
+    import numpy as np
+
+    S = make(eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_PREV)
+    dt = S.dt_bound(S_STAGES)
+    x = torch.zeros((4, p.n_nodes), dtype=torch.float64, device="cuda")
+    t = 0.0
+    for _ in range(warmup):
+        eqs.eqs_ens_rkc_step(S.ctx, x, ENS_SCALES, t, dt, S_STAGES)
+        t += dt
+    torch.cuda.synchronize()
+    times, iters, passes, launches = [], [], 0, 0
+    for _ in range(steps):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        eqs.eqs_ens_rkc_step(S.ctx, x, ENS_SCALES, t, dt, S_STAGES, want_stats=False)
+        e1.record()
+        st = eqs.eqs_ens_get_step_stats(S.ctx)
+        times.append(e0.elapsed_time(e1))
+        iters.append([v / S_STAGES for v in st.total_iters])
+        passes += st.passes
+        launches += st.launches
+        t += dt
+    S.close()
+    ms = sum(times) / len(times)
+    return {"value": 4 * p.n_free * S_STAGES * len(times) / (sum(times) / 1e3), "ms_per_step": ms,
+            "m_solve_ms_per_rhs": ms / (4 * S_STAGES),
+            "cg_iters_per_solve_by_column": [float(v) for v in np.mean(iters, axis=0)],
+            "cg_passes_per_stage": passes / (steps * S_STAGES), "drive_scales": list(ENS_SCALES),
+            "gpu_launches_per_step": launches / steps}
 
 
 def _peaks():

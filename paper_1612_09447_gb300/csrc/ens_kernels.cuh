@@ -56,22 +56,27 @@ __device__ __forceinline__ float4 mat_row4_impl(const DevSell<float>& A, int64_t
                                                 const float4* __restrict__ x, const float4* __restrict__ xadd) {
   const int row = (int)(tid >> A.logG);
   float4 acc = zero4();
-  if (A.G == 0) {  // DIA
+  if (A.G == 0) {  // DIA, chunks of loads issued before use (as mat_row_impl)
     if (row >= n) return acc;
     const float* __restrict__ v = A.val + row;
     float4 acc1 = zero4();
-    int d = 0;
-#pragma unroll 4
-    for (; d + 1 < A.ndiag; d += 2) {
-      const int j0 = row + A.off[d], j1 = row + A.off[d + 1];
-      const float a0 = __ldg(v + (int64_t)d * n), a1 = __ldg(v + (int64_t)(d + 1) * n);
-      if ((unsigned)j0 < (unsigned)A.n_cols) acc = fma4(a0, xv4<ADD>(x, xadd, j0), acc);
-      if ((unsigned)j1 < (unsigned)A.n_cols) acc1 = fma4(a1, xv4<ADD>(x, xadd, j1), acc1);
-    }
-    if (d < A.ndiag) {
-      const int j = row + A.off[d];
-      const float a = __ldg(v + (int64_t)d * n);
-      if ((unsigned)j < (unsigned)A.n_cols) acc = fma4(a, xv4<ADD>(x, xadd, j), acc);
+    constexpr int C = kDiaChunk / 2;
+    for (int d0 = 0; d0 < A.ndiag; d0 += C) {
+      float a[C];
+      float4 xs[C];
+#pragma unroll
+      for (int u = 0; u < C; ++u) {
+        const int d = d0 + u;
+        const int j = row + A.off[d < kMaxDiag ? d : 0];
+        const bool ok = d < A.ndiag && (unsigned)j < (unsigned)A.n_cols;
+        a[u] = ok ? __ldg(v + (int64_t)d * n) : 0.f;
+        xs[u] = ok ? xv4<ADD>(x, xadd, j) : zero4();
+      }
+#pragma unroll
+      for (int u = 0; u < C; u += 2) {
+        acc = fma4(a[u], xs[u], acc);
+        acc1 = fma4(a[u + 1], xs[u + 1], acc1);
+      }
     }
     return acc + acc1;
   }
@@ -476,17 +481,27 @@ __global__ void k4_pcg_pq(DevSell<double> M, const float* __restrict__ Mhi, cons
   for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float S[kEnsW] = {0.f, 0.f, 0.f, 0.f}, s[kEnsW] = {0.f, 0.f, 0.f, 0.f};
     if (M.G == 0) {
-#pragma unroll 5
-      for (int d = 0; d < M.ndiag; ++d) {
-        const int j = (int)i + M.off[d];
-        if ((unsigned)j >= (unsigned)M.n_cols) continue;
-        const int64_t k = (int64_t)d * n + i;
-        const float ah = __ldg(Mhi + k), al = __ldg(Mlo + k);
-        const float4 zj = __ldg(z32 + j);
-        df_acc(S[0], s[0], ah, al, zj.x);
-        df_acc(S[1], s[1], ah, al, zj.y);
-        df_acc(S[2], s[2], ah, al, zj.z);
-        df_acc(S[3], s[3], ah, al, zj.w);
+      constexpr int C = kDiaChunk / 2;
+      for (int d0 = 0; d0 < M.ndiag; d0 += C) {
+        float ah[C], al[C];
+        float4 zz[C];
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+          const int d = d0 + u;
+          const int j = (int)i + M.off[d < kMaxDiag ? d : 0];
+          const bool ok = d < M.ndiag && (unsigned)j < (unsigned)M.n_cols;
+          const int64_t k = (int64_t)d * n + i;
+          ah[u] = ok ? __ldg(Mhi + k) : 0.f;
+          al[u] = ok ? __ldg(Mlo + k) : 0.f;
+          zz[u] = ok ? __ldg(z32 + j) : zero4();
+        }
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+          df_acc(S[0], s[0], ah[u], al[u], zz[u].x);
+          df_acc(S[1], s[1], ah[u], al[u], zz[u].y);
+          df_acc(S[2], s[2], ah[u], al[u], zz[u].z);
+          df_acc(S[3], s[3], ah[u], al[u], zz[u].w);
+        }
       }
     } else {
       const int64_t sl = i >> 5, lane = i & 31;

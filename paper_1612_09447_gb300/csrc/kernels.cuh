@@ -12,6 +12,7 @@
 namespace eqs {
 
 constexpr int kBlock = 256;
+constexpr int kDiaChunk = 8;  // DIA diagonals whose loads are issued together
 
 // Programmatic dependent launch: wait until the preceding kernel of the
 // stream has completed (its writes visible), then allow the next kernel to
@@ -38,22 +39,27 @@ __device__ __forceinline__ T mat_row_impl(const DevSell<T>& A, int64_t tid, int 
                                           const T* __restrict__ xadd) {
   const int row = (int)(tid >> A.logG);
   T acc = T(0);
-  if (A.G == 0) {  // DIA: independent, coalesced loads; two accumulation chains
+  if (A.G == 0) {  // DIA: coalesced loads, no indices; chunks of kDiaChunk
+    // diagonals whose loads are all issued before the first use (memory-level
+    // parallelism for these latency-bound row kernels), two accumulation chains
     if (row >= n) return acc;
     const T* __restrict__ v = A.val + row;
     T acc1 = T(0);
-    int d = 0;
-#pragma unroll 4
-    for (; d + 1 < A.ndiag; d += 2) {
-      const int j0 = row + A.off[d], j1 = row + A.off[d + 1];
-      const T a0 = __ldg(v + (int64_t)d * n), a1 = __ldg(v + (int64_t)(d + 1) * n);
-      if ((unsigned)j0 < (unsigned)A.n_cols) acc = fmadd(a0, xv<T, ADD>(x, xadd, j0), acc);
-      if ((unsigned)j1 < (unsigned)A.n_cols) acc1 = fmadd(a1, xv<T, ADD>(x, xadd, j1), acc1);
-    }
-    if (d < A.ndiag) {
-      const int j = row + A.off[d];
-      const T a = __ldg(v + (int64_t)d * n);
-      if ((unsigned)j < (unsigned)A.n_cols) acc = fmadd(a, xv<T, ADD>(x, xadd, j), acc);
+    for (int d0 = 0; d0 < A.ndiag; d0 += kDiaChunk) {
+      T a[kDiaChunk], xs[kDiaChunk];
+#pragma unroll
+      for (int u = 0; u < kDiaChunk; ++u) {
+        const int d = d0 + u;
+        const int j = row + A.off[d < kMaxDiag ? d : 0];
+        const bool ok = d < A.ndiag && (unsigned)j < (unsigned)A.n_cols;
+        a[u] = ok ? __ldg(v + (int64_t)d * n) : T(0);
+        xs[u] = ok ? xv<T, ADD>(x, xadd, j) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kDiaChunk; u += 2) {
+        acc = fmadd(a[u], xs[u], acc);
+        acc1 = fmadd(a[u + 1], xs[u + 1], acc1);
+      }
     }
     return acc + acc1;
   }
@@ -306,17 +312,80 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ inv, const T* _
 }
 
 // ---------------------------------------------------------------- reductions
+// Warp sum of NV doubles by recursive halving: at offset o every lane keeps
+// half of its remaining values (the upper half when bit o of its lane is
+// set) and adds the partner's copy of that half, so the warp spends about
+// NV shuffles and adds instead of 5 NV.  Afterwards every lane holds the full
+// sum of value scatter_index(lane) and stores it to out[] (lanes that hold
+// the same index store the same value).
+__host__ __device__ constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
+
+__device__ __forceinline__ int scatter_index(int lane, int P) {
+  int idx = 0, half = P / 2;
+  for (int o = 16; o >= 1 && half >= 1; o >>= 1, half >>= 1)
+    if (lane & o) idx += half;
+  return idx;
+}
+
+template <int NV>
+__device__ __forceinline__ void warp_sum_scatter(const double (&v)[NV], double* out) {
+  constexpr int P = pow2_at_least(NV) < 32 ? pow2_at_least(NV) : 32;
+  static_assert(NV <= 32, "warp_sum_scatter handles up to 32 values");
+  const int lane = threadIdx.x & 31;
+  double w[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) w[k] = k < NV ? v[k] : 0.0;
+  int cnt = P;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    if (cnt > 1) {
+      const int half = cnt / 2;
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int k = 0; k < P / 2; ++k) {
+        if (k >= half) break;
+        const double send = up ? w[k] : w[k + half];
+        const double keep = up ? w[k + half] : w[k];
+        w[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+      cnt = half;
+    } else {
+      w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
+    }
+  }
+  const int idx = scatter_index(lane, P);
+  if (idx < NV) out[idx] = w[0];  // lanes of a group write the same value
+}
+
 // Block sum of NV doubles (any block size up to 1024 threads, a multiple of
 // 32); result valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   __shared__ double sh[NV][32];
+  __shared__ double tot_s[NV];
   const int nw = (int)(blockDim.x >> 5);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if constexpr (NV >= 4) {
+    __shared__ double part[32][NV];
+    warp_sum_scatter<NV>(v, part[w]);
+    __syncthreads();
+    if (w == 0) {
+      double t[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) t[k] = lane < nw ? part[lane][k] : 0.0;
+      warp_sum_scatter<NV>(t, tot_s);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) v[k] = tot_s[k];
+    __syncthreads();
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < NV; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0)
 #pragma unroll
     for (int k = 0; k < NV; ++k) sh[k][w] = v[k];
@@ -574,12 +643,21 @@ __device__ __forceinline__ double mat_row_split(const DevSell<double>& A, const 
                                                 const float* __restrict__ z) {
   float S = 0.0f, s = 0.0f;
   if (row >= n) return 0.0;
-  if (A.G == 0) {
-#pragma unroll 5
-    for (int d = 0; d < A.ndiag; ++d) {
-      const int j = (int)row + A.off[d];
-      const int64_t k = (int64_t)d * n + row;
-      if ((unsigned)j < (unsigned)A.n_cols) df_acc(S, s, __ldg(hi + k), __ldg(lo + k), __ldg(z + j));
+  if (A.G == 0) {  // chunks of kDiaChunk diagonals: all loads before the sums
+    for (int d0 = 0; d0 < A.ndiag; d0 += kDiaChunk) {
+      float ah[kDiaChunk], al[kDiaChunk], zz[kDiaChunk];
+#pragma unroll
+      for (int u = 0; u < kDiaChunk; ++u) {
+        const int d = d0 + u;
+        const int j = (int)row + A.off[d < kMaxDiag ? d : 0];
+        const bool ok = d < A.ndiag && (unsigned)j < (unsigned)A.n_cols;
+        const int64_t k = (int64_t)d * n + row;
+        ah[u] = ok ? __ldg(hi + k) : 0.0f;
+        al[u] = ok ? __ldg(lo + k) : 0.0f;
+        zz[u] = ok ? __ldg(z + j) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < kDiaChunk; ++u) df_acc(S, s, ah[u], al[u], zz[u]);
     }
   } else {
     const int64_t sl = row >> 5, lane = row & 31;
