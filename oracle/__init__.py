@@ -21,6 +21,10 @@ Time Integration Methods for Electro-Quasistatic Fields"):
 * ``pcg``      - preconditioned conjugate gradients (Section IV, ref. [3]);
 * ``dtbound``  - a-priori bound of the spectral radius of M^-1 dK/dx and the
                  RKC step at the stability boundary;
+* ``spe``      - subspace projection extrapolation start vector (Section IV,
+                 Eq. 4-5);
+* ``pod``      - POD-MOR start vectors, fixed (MOR) and rolling (MOR2)
+                 snapshot sets (Section IV);
 * ``mlp``      - the per-node initial-guess network (a project addition with
                  no counterpart in the paper): forward, backward, Adam.
 
