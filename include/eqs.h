@@ -69,8 +69,16 @@ typedef enum {
   EQS_GUESS_PREV = 0, /* start vector = previous M-solve solution           */
   EQS_GUESS_MLP = 1,  /* learned per-node network (eqs_guess_* calls)       */
   EQS_GUESS_ZERO = 2, /* start vector = 0                                   */
-  EQS_GUESS_SPE = 3   /* subspace projection extrapolation over the last
+  EQS_GUESS_SPE = 3,  /* subspace projection extrapolation over the last
                          spe_n solutions (Sec. IV, Eq. 4-5)                 */
+  EQS_GUESS_POD = 4,  /* POD-MOR (Sec. IV, "MOR"): the first pod_k
+                         solutions are the snapshots, their leading pod_m
+                         POD modes span the projection of Eq. 5, computed
+                         once; earlier solves start from the previous one  */
+  EQS_GUESS_POD2 = 5  /* rolling POD-MOR (Sec. IV, "MOR2"): a solution whose
+                         solve took more than pod_min_iters iterations
+                         replaces the oldest of pod_k snapshots and the
+                         basis is recomputed                                */
 } eqs_guess_mode;
 
 /* Options of eqs_amg_setup (fill with eqs_opts_default). */
@@ -105,6 +113,11 @@ typedef struct {
                           error-free FP32-pair row sum (accuracy a few
                           2^-48 of sum |m_ij z_j|, no FP64 multiply per
                           non-zero); 0 uses FP64 M.  Ignored in FP64 mode.  */
+  int pod_k;           /* POD snapshots (1..16, default 12)                  */
+  int pod_m;           /* POD modes kept (1..pod_k, default 6); fewer when
+                          the snapshots have lower numerical rank           */
+  int pod_min_iters;   /* EQS_GUESS_POD2: a solution becomes a snapshot when
+                          its solve needed more CG iterations (default 3)   */
 } eqs_opts;
 
 #define EQS_MAX_STAGES 64
@@ -127,7 +140,7 @@ typedef struct {
 /* Fill *o with the defaults (precision FP64, theta 0.08, coarse_max 500,
  * max_levels 10, degree 2, alpha 30, rtol 1e-8, max_iter 500, GUESS_PREV,
  * flexible 1, persistent 0, blocks_per_sm 1, spe_n 4, host_loop 0,
- * barrier_polls 0, split_m 1). */
+ * barrier_polls 0, split_m 1, pod_k 12, pod_m 6, pod_min_iters 3). */
 void eqs_opts_default(eqs_opts* o);
 
 /* Create a context from a tetrahedral mesh (Eq. 2 discretisation input).
@@ -370,6 +383,20 @@ const char* eqs_batch_last_error(const eqs_batch* b);
  * spe_n.  Overwrites the context's SPE history and right-hand side buffer;
  * synchronises.  For checking the projection. */
 eqs_status eqs_spe_eval(eqs_ctx* ctx, const double* X, const double* b, int n, double* x0);
+
+/* POD-MOR start vector (Sec. IV) for K given snapshots X (device, K x
+ * n_free doubles, oldest first, K <= pod_k): the basis of the leading
+ * pod_m POD modes is built by the kernels of the step (Gram matrices,
+ * Jacobi eigendecomposition, reduced system) and x0 = V (V^T M V)^-1 V^T b
+ * is written (b, x0: device, n_free doubles).  Replaces the context's
+ * snapshot set by X (eqs_pod_info then describes this basis); synchronises.
+ * For checking the projection. */
+eqs_status eqs_pod_eval(eqs_ctx* ctx, const double* X, int K, const double* b, double* x0);
+
+/* POD state of the context (synchronises): snapshots stored, modes kept,
+ * bases computed, snapshots added, and (host, 16 doubles, nullable) the
+ * eigenvalues of X^T X of the last basis, descending. */
+eqs_status eqs_pod_info(eqs_ctx* ctx, int* count, int* modes, int* rebuilds, int* adds, double* lam);
 
 /* Release everything owned by ctx (NULL is accepted). */
 eqs_status eqs_destroy(eqs_ctx* ctx);

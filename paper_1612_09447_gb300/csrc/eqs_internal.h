@@ -204,6 +204,13 @@ struct eqs_ctx {
   double* d_spe_G = nullptr;         // SPE: Gram matrix x_a . w_b by ring slot (6 x 6)
   double* d_spe_y = nullptr;         // SPE: projection coefficients
   double* d_spe_partials = nullptr;  // SPE: reduction slots
+  double* d_pod_X = nullptr;         // POD: snapshots (pod_k x n_free)
+  double* d_pod_W = nullptr;         // POD: W = M X
+  double* d_pod_GE = nullptr;        // POD: X^T X by slot (16 x 16)
+  double* d_pod_GM = nullptr;        // POD: X^T M X by slot
+  double* d_pod_a = nullptr;         // POD: projection coefficients by slot
+  double* d_pod_partials = nullptr;  // POD: reduction slots
+  void* d_pod_state = nullptr;       // POD: snapshot count, kept modes, reduced factor
   bool mlp_ready = false;
   bool direct = false;               // enqueue_step launches directly (host-driven CG loop)
 

@@ -19,6 +19,7 @@
 #include <type_traits>
 
 #include "spe_kernels.cuh"
+#include "pod_kernels.cuh"
 #include "ens_kernels.cuh"
 
 using namespace eqs;
@@ -332,9 +333,11 @@ struct SolveSlots {
   int* zero;
 };
 
-// Stage whose solve starts from the SPE vector (solve index stepcount*s + j).
+// A solve that starts from a projection start vector: SPE (stage j of an
+// s-stage step) or POD (coefficients of the current basis).
 struct SpeAt {
   int s, j;
+  bool pod;
 };
 
 // SPE projection of solve j (templated on the history length): the newest
@@ -366,8 +369,8 @@ static void spe_start_n(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st
                         int use_handle, SolveSlots sl) {
   DevLevel<T>& V = L[0];
   const int nf = (int)c->n_free;
-  launch(k_spe_start<T, NH>, vec_grid(c, nf), kBlock, st, c->M64, nf, (const double*)c->d_spe_X,
-         (const double*)c->d_spe_W, (const double*)c->d_spe_y, (const long long*)c->d_stepcount, s, j, R, x,
+  launch(k_proj_start<T, NH>, vec_grid(c, nf), kBlock, st, c->M64, nf, (const double*)c->d_spe_X,
+         (const double*)c->d_spe_W, (const double*)c->d_spe_y, (const int*)(c->d_spe_y + kSpeMax), R, x,
          R ? c->d_r : nullptr, V.dinv, (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials,
          c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres,
          sl.zero);
@@ -388,6 +391,37 @@ static void spe_start(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st, 
 }
 
 
+// POD start vector (Section IV): snapshot rule, basis rebuild when flagged,
+// projection coefficients of the current right-hand side.  xnew is the
+// newest solution, prev_iters / prev_zero the counters of its solve.
+static void pod_prepare(eqs_ctx* c, cudaStream_t st, int s, int j, const double* xnew, const int* prev_iters,
+                        const int* prev_zero, const long long* stepcount) {
+  const int nf = (int)c->n_free;
+  PodState* ps = (PodState*)c->d_pod_state;
+  const int mode = c->opts.guess == EQS_GUESS_POD2 ? 1 : 0;
+  launch(k_pod_add<kPodMax>, vec_grid(c, nf), kBlock, st, c->M64, nf, c->d_pod_X, c->d_pod_W, c->d_pod_GE,
+         c->d_pod_GM, xnew, prev_iters, prev_zero, stepcount, s, j, mode, c->opts.pod_k, c->opts.pod_min_iters,
+         ps, c->d_pod_partials, c->red.counter, c->red.max_blocks);
+  launch(k_pod_rebuild<kPodMax>, 1, kBlock, st, (const double*)c->d_pod_GE, (const double*)c->d_pod_GM,
+         c->opts.pod_m, kPodDrop2, ps);
+  launch(k_pod_gram<kPodMax>, std::max(1, std::min(nblk(nf), c->sms)), kBlock, st, nf,
+         (const double*)c->d_pod_X, (const double*)c->d_R, ps, c->d_pod_a, c->d_pod_partials, c->red.counter,
+         c->red.max_blocks);
+}
+
+template <typename T>
+static void pod_start(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st, const double* R, double* x,
+                      double tol2, cudaGraphConditionalHandle h, int use_handle, SolveSlots sl) {
+  DevLevel<T>& V = L[0];
+  const int nf = (int)c->n_free;
+  PodState* ps = (PodState*)c->d_pod_state;
+  launch(k_proj_start<T, kPodMax>, vec_grid(c, nf), kBlock, st, c->M64, nf, (const double*)c->d_pod_X,
+         (const double*)c->d_pod_W, (const double*)c->d_pod_a, (const int*)&ps->nuse, R, x,
+         R ? c->d_r : nullptr, V.dinv, (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials,
+         c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres,
+         sl.zero);
+}
+
 template <typename T>
 static void pcg_init_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st,
                             const double* R, double* x, double tol2, cudaGraphConditionalHandle h,
@@ -395,8 +429,11 @@ static void pcg_init_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_
                             int* kept = nullptr, const SpeAt* spe = nullptr) {
   DevLevel<T>& V = L[0];
   const int n = (int)c->n_free;
-  if (spe) {  // SPE start vector: x0 = X y, r0 = R - W y (no SpMV)
-    spe_start<T>(c, L, st, spe->s, spe->j, R, x, tol2, h, use_handle, sl);
+  if (spe) {  // projection start vector: x0 = X y, r0 = R - W y (no SpMV)
+    if (spe->pod)
+      pod_start<T>(c, L, st, R, x, tol2, h, use_handle, sl);
+    else
+      spe_start<T>(c, L, st, spe->s, spe->j, R, x, tol2, h, use_handle, sl);
     return;
   }
   if (h1) {  // learned start vector with the previous solution as fallback
@@ -588,7 +625,8 @@ static eqs_status solve_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, const do
   if (c->direct) return pcg_direct<T>(c, L, R, x, tol2, sl, h1, kept, spe);
   if (c->opts.persistent && !h1) {
     // the persistent kernel forms its own initial residual: only x0 here
-    if (spe) spe_start<T>(c, L, c->cap_stream, spe->s, spe->j, nullptr, x, tol2, 0, 0, sl);
+    if (spe && spe->pod) pod_start<T>(c, L, c->cap_stream, nullptr, x, tol2, 0, 0, sl);
+    else if (spe) spe_start<T>(c, L, c->cap_stream, spe->s, spe->j, nullptr, x, tol2, 0, 0, sl);
     return persistent_launch<T>(c, c->cap_stream, R, x, tol2, sl);
   }
   return pcg_capture<T>(c, L, R, x, tol2, sl, h1, kept, spe);
@@ -662,7 +700,12 @@ static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
       stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, h1, c->d_mlp_used + j);
     } else if (c->opts.guess == EQS_GUESS_SPE) {
       spe_gram(c, st, s, j);
-      const SpeAt at{s, j};
+      const SpeAt at{s, j, false};
+      stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, nullptr, nullptr, &at);
+    } else if (c->opts.guess == EQS_GUESS_POD || c->opts.guess == EQS_GUESS_POD2) {
+      const int jp = j == 0 ? s - 1 : j - 1;  // the solve that produced the newest solution
+      pod_prepare(c, st, s, j, Fbuf(c, jp), c->d_iters + jp, c->d_zero + jp, (const long long*)c->d_stepcount);
+      const SpeAt at{s, j, true};
       stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, nullptr, nullptr, &at);
     } else {
       if (c->opts.guess == EQS_GUESS_ZERO && cudaMemsetAsync(Fbuf(c, j), 0, nf * sizeof(double), st) != cudaSuccess)
@@ -1038,6 +1081,9 @@ void eqs_opts_default(eqs_opts* o) {
   o->host_loop = 0;
   o->barrier_polls = 0;
   o->split_m = 1;
+  o->pod_k = 12;
+  o->pod_m = 6;
+  o->pod_min_iters = 3;
 }
 
 eqs_status eqs_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
@@ -1104,6 +1150,7 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
   else
     eqs_opts_default(&o);
   if (o.cheb_degree < 1 || o.cheb_degree > 4 || o.blocks_per_sm < 0 || o.spe_n < 1 || o.spe_n > kSpeMax || o.max_levels < 1 || o.coarse_max < 1 ||
+      o.pod_k < 1 || o.pod_k > kPodMax || o.pod_m < 1 || o.pod_m > o.pod_k || o.pod_min_iters < 0 ||
       !(o.theta >= 0) || !(o.cheb_alpha > 1) || !(o.rtol > 0) || o.max_iter < 1 ||
       (o.precision != EQS_PREC_FP64 && o.precision != EQS_PREC_MIXED))
     return fail(c, EQS_ERR_ARG, "invalid eqs_opts");
@@ -1271,9 +1318,18 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     CK(dalloc(c, &c->d_rtmp, nf));
     CK(dalloc(c, &c->d_spe_X, (size_t)kSpeMax * nf));
     CK(dalloc(c, &c->d_spe_W, (size_t)kSpeMax * nf));
-    CK(dalloc(c, &c->d_spe_y, kSpeMax));
+    CK(dalloc(c, &c->d_spe_y, kSpeMax + 1));  // coefficients + slots in use
     CK(dalloc(c, &c->d_spe_G, (size_t)kSpeMax * kSpeMax));
     CK(dalloc(c, &c->d_spe_partials, (size_t)kSpeSums * c->red.max_blocks));
+    CK(dalloc(c, &c->d_pod_X, (size_t)c->opts.pod_k * nf));
+    CK(dalloc(c, &c->d_pod_W, (size_t)c->opts.pod_k * nf));
+    CK(dalloc(c, &c->d_pod_GE, (size_t)kPodMax * kPodMax));
+    CK(dalloc(c, &c->d_pod_GM, (size_t)kPodMax * kPodMax));
+    CK(dalloc(c, &c->d_pod_a, kPodMax));
+    CK(dalloc(c, &c->d_pod_partials, 2 * (size_t)kPodMax * c->red.max_blocks));
+    PodState* ps = nullptr;
+    CK(dalloc(c, &ps, 1));
+    c->d_pod_state = ps;
     c->adam_t = 0;
     c->d_store = nullptr;
     c->d_store_rms = nullptr;
@@ -1672,13 +1728,16 @@ eqs_status eqs_amg_aggregates(const eqs_ctx* c, int level, int32_t* agg_out) {
 
 eqs_status eqs_set_guess(eqs_ctx* c, int mode) {
   REQUIRE_SETUP(c);
-  if (mode != EQS_GUESS_PREV && mode != EQS_GUESS_MLP && mode != EQS_GUESS_ZERO && mode != EQS_GUESS_SPE)
+  if (mode != EQS_GUESS_PREV && mode != EQS_GUESS_MLP && mode != EQS_GUESS_ZERO && mode != EQS_GUESS_SPE &&
+      mode != EQS_GUESS_POD && mode != EQS_GUESS_POD2)
     return fail(c, EQS_ERR_ARG, "unknown guess mode");
   if (mode != c->opts.guess) {
     destroy_graphs(c);
-    if (mode == EQS_GUESS_SPE) {  // the right-hand-side ring starts empty: restart the history
+    if (mode == EQS_GUESS_SPE || mode == EQS_GUESS_POD || mode == EQS_GUESS_POD2) {
+      // the solution rings / snapshot set start empty: restart the history
       CK(cudaStreamSynchronize(c->stream));
       CK(cudaMemset(c->d_stepcount, 0, 2 * sizeof(long long)));
+      CK(cudaMemset(c->d_pod_state, 0, sizeof(PodState)));
     }
   }
   c->opts.guess = mode;
@@ -1830,6 +1889,60 @@ eqs_status eqs_spe_eval(eqs_ctx* c, const double* X, const double* b, int n, dou
   cudaError_t e = cudaStreamSynchronize(st);
   cudaFree(cnt);
   if (e != cudaSuccess) return fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
+  return EQS_OK;
+}
+
+eqs_status eqs_pod_eval(eqs_ctx* c, const double* X, int K, const double* b, double* x0) {
+  REQUIRE_SETUP(c);
+  if (!X || !b || !x0) return fail(c, EQS_ERR_ARG, "null vector");
+  if (K < 1 || K > c->opts.pod_k) return fail(c, EQS_ERR_ARG, "K must be in [1, pod_k]");
+  const int64_t nf = c->n_free;
+  cudaStream_t st = c->stream;
+  long long* cnt = nullptr;
+  int* zero = nullptr;
+  CK(cudaMalloc(&cnt, 2 * sizeof(long long)));
+  CK(cudaMalloc(&zero, sizeof(int)));
+  const long long one2[2] = {1, 2};  // solve index g = 1: a previous solution exists
+  CK(cudaMemcpyAsync(cnt, one2, sizeof(one2), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(zero, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(c->d_pod_state, 0, sizeof(PodState), st));
+  CK(cudaMemcpyAsync(c->d_R, b, nf * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  PodState* ps = (PodState*)c->d_pod_state;
+  const int nfi = (int)nf;
+  // the K snapshots enter by the fixed-set rule with capacity K, oldest first;
+  // the basis is built when the set is full
+  for (int q = 0; q < K; ++q) {
+    k_pod_add<kPodMax><<<vec_grid(c, nfi), kBlock, 0, st>>>(c->M64, nfi, c->d_pod_X, c->d_pod_W, c->d_pod_GE,
+                                                            c->d_pod_GM, X + (size_t)q * nf, zero, zero, cnt, 1,
+                                                            0, 0, K, 0, ps, c->d_pod_partials, c->red.counter,
+                                                            c->red.max_blocks);
+    k_pod_rebuild<kPodMax><<<1, kBlock, 0, st>>>(c->d_pod_GE, c->d_pod_GM, c->opts.pod_m, kPodDrop2, ps);
+  }
+  k_pod_gram<kPodMax><<<std::max(1, std::min(nblk(nf), c->sms)), kBlock, 0, st>>>(
+      nfi, c->d_pod_X, c->d_R, ps, c->d_pod_a, c->d_pod_partials, c->red.counter, c->red.max_blocks);
+  SolveSlots sl{nullptr, nullptr, nullptr};
+  if (mixed(c))
+    pod_start<float>(c, c->lev32, st, nullptr, x0, 0.0, 0, 0, sl);
+  else
+    pod_start<double>(c, c->lev64, st, nullptr, x0, 0.0, 0, 0, sl);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(cnt);
+  cudaFree(zero);
+  if (e != cudaSuccess) return fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
+  return EQS_OK;
+}
+
+eqs_status eqs_pod_info(eqs_ctx* c, int* count, int* modes, int* rebuilds, int* adds, double* lam) {
+  REQUIRE_SETUP(c);
+  PodState ps;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(&ps, c->d_pod_state, sizeof(ps), cudaMemcpyDeviceToHost));
+  if (count) *count = ps.count;
+  if (modes) *modes = ps.m_used;
+  if (rebuilds) *rebuilds = ps.rebuilds;
+  if (adds) *adds = ps.adds;
+  if (lam)
+    for (int k = 0; k < kPodMax; ++k) lam[k] = k < ps.count ? ps.lam[k] : 0.0;
   return EQS_OK;
 }
 

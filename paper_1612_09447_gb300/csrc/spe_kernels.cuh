@@ -13,7 +13,7 @@
 // span that Euclidean Gram-Schmidt would keep.
 //
 // Because M x0 = W y, the initial CG residual r0 = b - W y needs no SpMV:
-// k_spe_start forms x0, r0 and the first V-cycle input in one row-local pass.
+// k_proj_start forms x0, r0 and the first V-cycle input in one row-local pass.
 #pragma once
 
 #include "kernels.cuh"
@@ -29,7 +29,8 @@ __device__ __forceinline__ int spe_slot(long long q, int NH) { return (int)(((q 
 // m = min(g, NH) of them are in the rings.  One pass: w_{g-1} = M x_{g-1},
 // the Gram column G[k][g-1] over the stored solutions k and c_k = x_k . b.
 // The last block updates G and solves (L L^T) y = c with column dropping;
-// y_out[k] is the coefficient of the k-th most recent solution.
+// y_out[slot] is the coefficient of the solution in that ring slot and
+// y_out[kSpeMax] (as int) the number of slots in use.
 template <int NH>
 __global__ void k_spe_gram(DevSell<double> M, int nf, const double* __restrict__ X, double* __restrict__ W,
                            const double* __restrict__ b, const long long* __restrict__ stepcount, int s,
@@ -37,7 +38,10 @@ __global__ void k_spe_gram(DevSell<double> M, int nf, const double* __restrict__
                            int max_blocks, double drop2, double* __restrict__ y_out) {
   pdl_enter();
   const long long g = stepcount[0] * (long long)s + j;
-  if (g == 0) return;  // uniform over the grid: no history, no reduction
+  if (g == 0) {  // uniform over the grid: no history, no reduction
+    if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<int*>(y_out + kSpeMax)[0] = 0;
+    return;
+  }
   const int m = (int)(g < NH ? g : NH);
   const int sn = spe_slot(g - 1, NH);
   constexpr int NS = 2 * NH;
@@ -110,38 +114,34 @@ __global__ void k_spe_gram(DevSell<double> M, int nf, const double* __restrict__
         if (keep[r]) e -= L[r][k] * y[r];
       y[k] = e / L[k][k];
     }
-    for (int k = 0; k < NH; ++k) y_out[k] = y[k];
+    // coefficients by ring slot for k_proj_start; y_out[kSpeMax] = slots in use
+    for (int k = 0; k < NH; ++k) y_out[k] = 0.0;
+    for (int k = 0; k < m; ++k) y_out[slot[k]] = y[k];
+    reinterpret_cast<int*>(y_out + kSpeMax)[0] = m;
   }
 }
 
-// Start of the CG solve from the SPE vector: x0 = X y, r0 = R - W y (= R -
-// M x0), the norms of R and r0, and the first V-cycle input (b0 = r0 in T,
-// x = d = D0^-1 b0 / theta0); the last block decides whether the CG loop
-// runs.  Without history (g == 0) x keeps the caller's start vector and
+// Start of the CG solve from a projection start vector (SPE or POD): with
+// coefficients a (by ring slot, *nuse > 0 slots in use) x0 = X a and
+// r0 = R - W a (= R - M x0: W = M X, so no SpMV), the norms of R and r0, and
+// the first V-cycle input (b0 = r0 in T, x = d = D0^-1 b0 / theta0); the
+// last block decides whether the CG loop runs.  With *nuse == 0 (no
+// history or no basis yet) x keeps the caller's start vector and
 // r0 = R - M x.  With r == nullptr only x0 is written (no reduction).
 template <typename T, int NH>
-__global__ void k_spe_start(DevSell<double> M, int nf, const double* __restrict__ X,
-                            const double* __restrict__ W, const double* __restrict__ yc,
-                            const long long* __restrict__ stepcount, int s, int j,
-                            const double* __restrict__ R, double* __restrict__ x, double* __restrict__ r,
-                            const T* __restrict__ dinv0, T inv_theta0, T* __restrict__ b0,
-                            T* __restrict__ x0, T* __restrict__ d0, PcgScalars* sc, double* partials,
-                            unsigned int* counter, int max_blocks, double tol2, int maxit,
-                            cudaGraphConditionalHandle h, int use_handle, int* iters_out,
-                            double* relres_out, int* zero_out) {
+__global__ void k_proj_start(DevSell<double> M, int nf, const double* __restrict__ X,
+                             const double* __restrict__ W, const double* __restrict__ coef,
+                             const int* __restrict__ nuse, const double* __restrict__ R,
+                             double* __restrict__ x, double* __restrict__ r, const T* __restrict__ dinv0,
+                             T inv_theta0, T* __restrict__ b0, T* __restrict__ x0, T* __restrict__ d0,
+                             PcgScalars* sc, double* partials, unsigned int* counter, int max_blocks,
+                             double tol2, int maxit, cudaGraphConditionalHandle h, int use_handle,
+                             int* iters_out, double* relres_out, int* zero_out) {
   pdl_enter();
-  const long long g = stepcount[0] * (long long)s + j;
-  const int m = (int)(g < NH ? g : NH);
+  const int m = *nuse;
   double y[NH];
-  const double* xs[NH];
-  const double* ws[NH];
 #pragma unroll
-  for (int k = 0; k < NH; ++k) {
-    y[k] = k < m ? yc[k] : 0.0;
-    const size_t off = (size_t)spe_slot(g - 1 - k, NH) * nf;
-    xs[k] = X + off;
-    ws[k] = W + off;
-  }
+  for (int k = 0; k < NH; ++k) y[k] = k < m ? coef[k] : 0.0;
   double v[2] = {0.0, 0.0};
   for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x) {
     double xi, mx;
@@ -151,8 +151,8 @@ __global__ void k_spe_start(DevSell<double> M, int nf, const double* __restrict_
 #pragma unroll
       for (int k = 0; k < NH; ++k)
         if (k < m) {
-          xi = fma(y[k], xs[k][i], xi);
-          mx = fma(y[k], ws[k][i], mx);
+          xi = fma(y[k], X[(size_t)k * nf + i], xi);
+          mx = fma(y[k], W[(size_t)k * nf + i], mx);
         }
       x[i] = xi;
     } else {

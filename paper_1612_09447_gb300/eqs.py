@@ -19,6 +19,7 @@ EQS_OK, EQS_ERR_ARG, EQS_ERR_MESH, EQS_ERR_CUDA = 0, -1, -2, -3
 EQS_ERR_NOCONV, EQS_ERR_TIMEOUT, EQS_ERR_NAN, EQS_ERR_STATE = -4, -5, -6, -7
 EQS_PREC_FP64, EQS_PREC_MIXED = 0, 1
 EQS_GUESS_PREV, EQS_GUESS_MLP, EQS_GUESS_ZERO, EQS_GUESS_SPE = 0, 1, 2, 3
+EQS_GUESS_POD, EQS_GUESS_POD2 = 4, 5
 EQS_MAX_STAGES = 64
 
 
@@ -39,7 +40,8 @@ class eqs_opts(C.Structure):
                 ("rtol", C.c_double), ("max_iter", C.c_int), ("guess", C.c_int),
                 ("flexible", C.c_int), ("persistent", C.c_int), ("blocks_per_sm", C.c_int),
                 ("spe_n", C.c_int), ("host_loop", C.c_int), ("barrier_polls", C.c_longlong),
-                ("split_m", C.c_int)]
+                ("split_m", C.c_int), ("pod_k", C.c_int), ("pod_m", C.c_int),
+                ("pod_min_iters", C.c_int)]
 
 
 class eqs_batch_stats(C.Structure):
@@ -115,6 +117,8 @@ def _declare(L):
         "eqs_ens_rkc_step": (I, [P, P, P, D, D, I, C.POINTER(eqs_ens_stats)]),
         "eqs_ens_get_step_stats": (I, [P, C.POINTER(eqs_ens_stats)]),
         "eqs_ens_solve_M": (I, [P, P, P, P]),
+        "eqs_pod_eval": (I, [P, P, I, P, P]),
+        "eqs_pod_info": (I, [P, P, P, P, P, P]),
         "eqs_destroy": (I, [P]),
         "eqs_last_error": (C.c_char_p, [P]),
     }
@@ -316,6 +320,18 @@ def eqs_batch_info(b):
 def eqs_batch_destroy(b):
     if b:
         lib().eqs_batch_destroy(b)
+
+
+def eqs_pod_eval(ctx, X, K, b, x0):
+    _check(lib().eqs_pod_eval(ctx, _dev(X), K, _dev(b), _dev(x0)), ctx)
+
+
+def eqs_pod_info(ctx):
+    cnt, m, rb, ad = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    lam = (C.c_double * 16)()
+    _check(lib().eqs_pod_info(ctx, C.byref(cnt), C.byref(m), C.byref(rb), C.byref(ad), lam), ctx)
+    return {"count": cnt.value, "modes": m.value, "rebuilds": rb.value, "adds": ad.value,
+            "lam": list(lam)}
 
 
 def eqs_spe_eval(ctx, X, b, n, x0):
