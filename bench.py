@@ -281,10 +281,13 @@ def run_ours(args, rank, world):
     variants = {}
     if not args.no_fp64:
         short = max(3, args.steps // 4)
-        # fp64_plain is the metric's baseline: plain FP64 AMG-PCG, previous-solution start
+        # fp64_plain is the metric's baseline: plain FP64 AMG-PCG, previous-solution start;
+        # mixed_pod / mixed_pod2 are the paper's POD-MOR estimators (fixed / rolling set)
         for name, prec, guess in (("fp64_plain", eqs.EQS_PREC_FP64, eqs.EQS_GUESS_PREV),
                                   ("mixed_prev", eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_PREV),
-                                  ("fp64_spe", eqs.EQS_PREC_FP64, eqs.EQS_GUESS_SPE)):
+                                  ("fp64_spe", eqs.EQS_PREC_FP64, eqs.EQS_GUESS_SPE),
+                                  ("mixed_pod", eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_POD),
+                                  ("mixed_pod2", eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_POD2)):
             S = make(prec, guess)
             r = measure(S, short, 2)
             variants[name] = summary(r[3], r[5])

@@ -48,6 +48,11 @@ static inline int nblk(int64_t n, int b = kBlock) { return (int)((n + b - 1) / b
 static inline int rows_grid(const eqs_ctx* c, int64_t lanes) {
   return std::max(1, std::min(nblk((lanes + 1) / 2), 4 * c->sms));
 }
+// Grid of a row kernel on matrix A (rows_grid over its lanes).
+template <typename T>
+static inline int mat_grid(const eqs_ctx* c, const DevSell<T>& A, int64_t rows) {
+  return rows_grid(c, rows * std::max(A.G, 1));
+}
 // Grid of a CG vector kernel (grid-stride, one reduction ticket per block).
 static inline int vec_grid(const eqs_ctx* c, int64_t n) { return std::max(1, std::min(nblk(n), 4 * c->sms)); }
 
@@ -294,7 +299,7 @@ static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStrea
   const int deg = c->opts.cheb_degree;
   std::vector<double> c1, c2;
   cheb_coeffs(V.sigma, V.delta, deg, c1, c2);
-  const int g = rows_grid(c, (int64_t)V.n * std::max(V.A.G, 1));
+  const int g = mat_grid(c, V.A, V.n);
   // pre-smoothing: x = d = D^-1 b / theta was set by the producer of b
   T* din = V.dA;
   T* dout = V.dB;
@@ -310,10 +315,10 @@ static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStrea
     launch(k_resid<T>, g, kBlock, st, V.A, V.n, V.b, V.x, V.r);
   DevLevel<T>& C = L[l + 1];
   const int first = (l + 1 < nl - 1) ? 1 : 0;
-  launch(k_restrict<T>, rows_grid(c, (int64_t)C.n * std::max(V.R.G, 1)), kBlock, st, V.R, C.n, V.r, C.b,
+  launch(k_restrict<T>, mat_grid(c, V.R, C.n), kBlock, st, V.R, C.n, V.r, C.b,
          C.dinv, (T)C.inv_theta, C.x, C.dA, first);
   T* cpend = vcycle_level(c, L, l + 1, st);
-  launch(k_prolong<T>, rows_grid(c, (int64_t)V.n * std::max(V.P.G, 1)), kBlock, st, V.P, V.n, C.x,
+  launch(k_prolong<T>, mat_grid(c, V.P, V.n), kBlock, st, V.P, V.n, C.x,
          (const T*)cpend, V.x);
   launch(k_post_first<T>, g, kBlock, st, V.A, V.n, V.b, V.x, V.dinv, (T)V.inv_theta, V.r, V.dA);
   din = V.dA;
@@ -843,7 +848,7 @@ static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st) {
   const int deg = c->opts.cheb_degree;
   std::vector<double> c1, c2;
   cheb_coeffs(V.sigma, V.delta, deg, c1, c2);
-  const int g = rows_grid(c, (int64_t)V.n * std::max(V.A.G, 1));
+  const int g = mat_grid(c, V.A, V.n);
   float4* din = E.dA;
   float4* dout = E.dB;
   const float4* rin = E.b;
@@ -860,10 +865,10 @@ static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st) {
   DevLevel<float>& C = L[l + 1];
   eqs_ctx::EnsLevel& EC = c->elev[l + 1];
   const int first = (l + 1 < nl - 1) ? 1 : 0;
-  launch(k4_restrict, rows_grid(c, (int64_t)C.n * std::max(V.R.G, 1)), kBlock, st, V.R, C.n, (const float4*)E.r,
+  launch(k4_restrict, mat_grid(c, V.R, C.n), kBlock, st, V.R, C.n, (const float4*)E.r,
          EC.b, (const float*)C.dinv, (float)C.inv_theta, EC.x, EC.dA, first);
   float4* cpend = ens_vcycle_level(c, l + 1, st);
-  launch(k4_prolong, rows_grid(c, (int64_t)V.n * std::max(V.P.G, 1)), kBlock, st, V.P, V.n, (const float4*)EC.x,
+  launch(k4_prolong, mat_grid(c, V.P, V.n), kBlock, st, V.P, V.n, (const float4*)EC.x,
          (const float4*)cpend, E.x);
   launch(k4_post_first, g, kBlock, st, V.A, V.n, (const float4*)E.b, (const float4*)E.x, (const float*)V.dinv,
          (float)V.inv_theta, E.r, E.dA);
