@@ -326,27 +326,20 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ inv, const T* _
 // Warp sum of NV doubles by recursive halving: at offset o every lane keeps
 // half of its remaining values (the upper half when bit o of its lane is
 // set) and adds the partner's copy of that half, so the warp spends about
-// NV shuffles and adds instead of 5 NV.  Afterwards every lane holds the full
-// sum of value scatter_index(lane) and stores it to out[] (lanes that hold
-// the same index store the same value).
+// NV shuffles and adds instead of 5 NV.  Afterwards every lane holds full
+// sums of a run of values and stores them to out[] (lanes that hold the same
+// values store the same sums).
 __host__ __device__ constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
-
-__device__ __forceinline__ int scatter_index(int lane, int P) {
-  int idx = 0, half = P / 2;
-  for (int o = 16; o >= 1 && half >= 1; o >>= 1, half >>= 1)
-    if (lane & o) idx += half;
-  return idx;
-}
 
 template <int NV>
 __device__ __forceinline__ void warp_sum_scatter(const double (&v)[NV], double* out) {
-  constexpr int P = pow2_at_least(NV) < 32 ? pow2_at_least(NV) : 32;
-  static_assert(NV <= 32, "warp_sum_scatter handles up to 32 values");
+  constexpr int P = pow2_at_least(NV);
+  static_assert(NV <= 64, "warp_sum_scatter handles up to 64 values");
   const int lane = threadIdx.x & 31;
   double w[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) w[k] = k < NV ? v[k] : 0.0;
-  int cnt = P;
+  int cnt = P, base = 0;
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
     if (cnt > 1) {
@@ -359,13 +352,16 @@ __device__ __forceinline__ void warp_sum_scatter(const double (&v)[NV], double* 
         const double keep = up ? w[k + half] : w[k];
         w[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
       }
+      if (up) base += half;
       cnt = half;
     } else {
       w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
     }
   }
-  const int idx = scatter_index(lane, P);
-  if (idx < NV) out[idx] = w[0];  // lanes of a group write the same value
+  // each lane now holds the full sums of values base .. base + cnt - 1
+#pragma unroll
+  for (int k = 0; k < (P > 32 ? P / 32 : 1); ++k)
+    if (base + k < NV) out[base + k] = w[k];  // lanes of a group write the same value
 }
 
 // Block sum of NV doubles (any block size up to 1024 threads, a multiple of

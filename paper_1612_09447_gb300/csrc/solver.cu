@@ -1881,8 +1881,9 @@ eqs_status eqs_spe_eval(eqs_ctx* c, const double* X, const double* b, int n, dou
   // push the history oldest first (solution q into slot q % n), updating the
   // Gram matrix as the step does, then form x0 for the solve g = n
   for (int q = 0; q < n; ++q) {
-    CK(cudaMemcpyAsync(c->d_spe_X + (size_t)(q % n) * nf, X + (size_t)(n - 1 - q) * nf, nf * sizeof(double),
-                       cudaMemcpyDeviceToDevice, st));
+    const double* col = X + (size_t)(n - 1 - q) * nf;
+    CK(cudaMemcpyAsync(c->d_spe_X + (size_t)(q % n) * nf, col, nf * sizeof(double), cudaMemcpyDeviceToDevice,
+                       st));
     spe_gram(c, st, 1, q + 1);
   }
   SolveSlots sl{nullptr, nullptr, nullptr};

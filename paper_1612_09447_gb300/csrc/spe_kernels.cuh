@@ -25,6 +25,64 @@ constexpr int kSpeSums = 2 * kSpeMax;  // Gram column + projections of b
 
 __device__ __forceinline__ int spe_slot(long long q, int NH) { return (int)(((q % NH) + NH) % NH); }
 
+// Last block of a Gram pass: store the new Gram column of slot sn (tot[0..m)),
+// solve (L L^T) y = c (c = tot[NH..NH+m)) by Cholesky with column dropping
+// (most recent first) and write y by ring slot plus the slots in use.
+template <int NH>
+__device__ void spe_solve(const double* tot, long long g, int m, int sn, double* __restrict__ G, double drop2,
+                          double* __restrict__ y_out) {
+  int slot[NH];
+  for (int k = 0; k < NH; ++k) slot[k] = spe_slot(g - 1 - k, NH);
+  for (int k = 0; k < m; ++k) {  // new Gram column and row of the newest slot
+    G[slot[k] * kSpeMax + sn] = tot[k];
+    G[sn * kSpeMax + slot[k]] = tot[k];
+  }
+  double A[NH][NH], c[NH], L[NH][NH], y[NH];
+  bool keep[NH];
+  for (int k = 0; k < NH; ++k) {
+    c[k] = tot[NH + k];
+    keep[k] = false;
+    y[k] = 0.0;
+    for (int l = 0; l < NH; ++l) {
+      A[k][l] = (k < m && l < m) ? G[slot[k] * kSpeMax + slot[l]] : 0.0;
+      L[k][l] = 0.0;
+    }
+  }
+  for (int k = 0; k < m; ++k) {
+    double d = A[k][k];
+    for (int p = 0; p < k; ++p)
+      if (keep[p]) d -= L[k][p] * L[k][p];
+    if (!(A[k][k] > 0.0) || !(d > drop2 * A[k][k])) continue;
+    keep[k] = true;
+    L[k][k] = sqrt(d);
+    for (int r = k + 1; r < m; ++r) {
+      double e = A[r][k];
+      for (int p = 0; p < k; ++p)
+        if (keep[p]) e -= L[r][p] * L[k][p];
+      L[r][k] = e / L[k][k];
+    }
+  }
+  double z[NH];
+  for (int k = 0; k < m; ++k) {  // L z = c (kept rows)
+    z[k] = 0.0;
+    if (!keep[k]) continue;
+    double e = c[k];
+    for (int p = 0; p < k; ++p)
+      if (keep[p]) e -= L[k][p] * z[p];
+    z[k] = e / L[k][k];
+  }
+  for (int k = m - 1; k >= 0; --k) {  // L^T y = z
+    if (!keep[k]) continue;
+    double e = z[k];
+    for (int r = k + 1; r < m; ++r)
+      if (keep[r]) e -= L[r][k] * y[r];
+    y[k] = e / L[k][k];
+  }
+  for (int k = 0; k < NH; ++k) y_out[k] = 0.0;
+  for (int k = 0; k < m; ++k) y_out[slot[k]] = y[k];
+  reinterpret_cast<int*>(y_out + kSpeMax)[0] = m;
+}
+
 // Solve index g = stepcount[0] * s + j: solutions 0..g-1 exist, the newest
 // m = min(g, NH) of them are in the rings.  One pass: w_{g-1} = M x_{g-1},
 // the Gram column G[k][g-1] over the stored solutions k and c_k = x_k . b.
@@ -65,60 +123,8 @@ __global__ void k_spe_gram(DevSell<double> M, int nf, const double* __restrict__
     }
   }
   double tot[NS];
-  if (grid_sum<NS>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
-    int slot[NH];
-    for (int k = 0; k < NH; ++k) slot[k] = spe_slot(g - 1 - k, NH);
-    for (int k = 0; k < m; ++k) {  // new Gram column and row of the newest slot
-      G[slot[k] * kSpeMax + sn] = tot[k];
-      G[sn * kSpeMax + slot[k]] = tot[k];
-    }
-    double A[NH][NH], c[NH], L[NH][NH], y[NH];
-    bool keep[NH];
-    for (int k = 0; k < NH; ++k) {
-      c[k] = tot[NH + k];
-      keep[k] = false;
-      y[k] = 0.0;
-      for (int l = 0; l < NH; ++l) {
-        A[k][l] = (k < m && l < m) ? G[slot[k] * kSpeMax + slot[l]] : 0.0;
-        L[k][l] = 0.0;
-      }
-    }
-    // Cholesky with column dropping, most recent solution first
-    for (int k = 0; k < m; ++k) {
-      double d = A[k][k];
-      for (int p = 0; p < k; ++p)
-        if (keep[p]) d -= L[k][p] * L[k][p];
-      if (!(A[k][k] > 0.0) || !(d > drop2 * A[k][k])) continue;
-      keep[k] = true;
-      L[k][k] = sqrt(d);
-      for (int r = k + 1; r < m; ++r) {
-        double e = A[r][k];
-        for (int p = 0; p < k; ++p)
-          if (keep[p]) e -= L[r][p] * L[k][p];
-        L[r][k] = e / L[k][k];
-      }
-    }
-    double z[NH];
-    for (int k = 0; k < m; ++k) {  // L z = c (kept rows)
-      z[k] = 0.0;
-      if (!keep[k]) continue;
-      double e = c[k];
-      for (int p = 0; p < k; ++p)
-        if (keep[p]) e -= L[k][p] * z[p];
-      z[k] = e / L[k][k];
-    }
-    for (int k = m - 1; k >= 0; --k) {  // L^T y = z
-      if (!keep[k]) continue;
-      double e = z[k];
-      for (int r = k + 1; r < m; ++r)
-        if (keep[r]) e -= L[r][k] * y[r];
-      y[k] = e / L[k][k];
-    }
-    // coefficients by ring slot for k_proj_start; y_out[kSpeMax] = slots in use
-    for (int k = 0; k < NH; ++k) y_out[k] = 0.0;
-    for (int k = 0; k < m; ++k) y_out[slot[k]] = y[k];
-    reinterpret_cast<int*>(y_out + kSpeMax)[0] = m;
-  }
+  if (grid_sum<NS>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0)
+    spe_solve<NH>(tot, g, m, sn, G, drop2, y_out);
 }
 
 // Start of the CG solve from a projection start vector (SPE or POD): with
