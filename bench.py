@@ -314,6 +314,8 @@ def run_ours(args, rank, world):
         # every stage's four right-hand sides solved together (blocked CG)
         variants["ensemble4_mixed_prev"] = measure_ensemble(torch, eqs, p, make, flush,
                                                             max(3, args.steps // 4), 2)
+        variants["ensemble4_mixed_spe"] = measure_ensemble(torch, eqs, p, make, flush,
+                                                           max(3, args.steps // 4), 2, eqs.EQS_GUESS_SPE)
         if "mixed_prev" not in variants:
             S = make(eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_PREV)
             r = measure(S, max(3, args.steps // 4), 2)
@@ -359,12 +361,13 @@ def run_ours(args, rank, world):
 ENS_SCALES = (0.5, 1.0, 1.5, 2.0)
 
 
-def measure_ensemble(torch, eqs, p, make, flush, steps, warmup):
-    """Timed RKC steps of the 4-trajectory ensemble (mixed precision,
-    previous-solution start): DOF-stages count all four trajectories."""
+def measure_ensemble(torch, eqs, p, make, flush, steps, warmup, guess=None):
+    """Timed RKC steps of the 4-trajectory ensemble (mixed precision; start
+    vector: previous solution or SPE): DOF-stages count all four
+    trajectories."""
     import numpy as np
 
-    S = make(eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_PREV)
+    S = make(eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_PREV if guess is None else guess)
     dt = S.dt_bound(S_STAGES)
     x = torch.zeros((4, p.n_nodes), dtype=torch.float64, device="cuda")
     t = 0.0

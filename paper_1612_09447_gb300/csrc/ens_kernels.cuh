@@ -16,11 +16,12 @@
 // others iterate.  The loop runs while any column is active.
 #pragma once
 
-#include "kernels.cuh"
+#include "spe_kernels.cuh"
 
 namespace eqs {
 
 constexpr int kEnsW = 4;
+constexpr int kEnsSpe = 4;  // SPE history length of the ensemble (32 sums per Gram pass)
 
 // ------------------------------------------------------------ float4 ops
 __device__ __forceinline__ float4 operator+(float4 a, float4 b) {
@@ -369,6 +370,31 @@ __device__ __forceinline__ void vc_input4(int64_t i, const double4_32a& r, const
   d0[i] = d;
 }
 
+// Last block of a CG start: per-column norms (tot: ||R_c||^2, then ||r_c||^2),
+// flags and the loop condition (any column active).
+__device__ __forceinline__ void ens_init_tail(const double* tot, EnsScalars* sc, double tol2, int maxit,
+                                              cudaGraphConditionalHandle h, int use_handle, int* iters_out,
+                                              double* relres_out, int* zero_out) {
+  int go = 0;
+  for (int c = 0; c < kEnsW; ++c) {
+    sc->bnorm2[c] = tot[c];
+    sc->rnorm2[c] = tot[kEnsW + c];
+    sc->it[c] = 0;
+    sc->rz_old[c] = 0.0;
+    sc->beta[c] = 0.0;
+    sc->alpha[c] = 0.0;
+    const int zero = tot[c] == 0.0;
+    const int gc = !zero && tot[kEnsW + c] > tol2 * tot[c] && maxit > 0;
+    sc->conv[c] = !gc;
+    go |= gc;
+    if (iters_out) iters_out[c] = 0;
+    if (relres_out) relres_out[c] = zero ? 0.0 : sqrt(tot[kEnsW + c] / tot[c]);
+    if (zero_out) zero_out[c] = zero;
+  }
+  sc->pass = 0;
+  if (use_handle) cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 // r = R - M x for the four columns (FP64), norms of R and r per column, the
 // first V-cycle input; the last block sets the per-column flags and the
 // loop condition (any column active).
@@ -400,26 +426,8 @@ __global__ void k4_pcg_init(DevSell<double> M, int n, const double4_32a* __restr
     }
   }
   double tot[2 * kEnsW];
-  if (grid_sum<2 * kEnsW>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
-    int go = 0;
-    for (int c = 0; c < kEnsW; ++c) {
-      sc->bnorm2[c] = tot[c];
-      sc->rnorm2[c] = tot[kEnsW + c];
-      sc->it[c] = 0;
-      sc->rz_old[c] = 0.0;
-      sc->beta[c] = 0.0;
-      sc->alpha[c] = 0.0;
-      const int zero = tot[c] == 0.0;
-      const int gc = !zero && tot[kEnsW + c] > tol2 * tot[c] && maxit > 0;
-      sc->conv[c] = !gc;
-      go |= gc;
-      if (iters_out) iters_out[c] = 0;
-      if (relres_out) relres_out[c] = zero ? 0.0 : sqrt(tot[kEnsW + c] / tot[c]);
-      if (zero_out) zero_out[c] = zero;
-    }
-    sc->pass = 0;
-    if (use_handle) cudaGraphSetConditional(h, go ? 1u : 0u);
-  }
+  if (grid_sum<2 * kEnsW>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0)
+    ens_init_tail(tot, sc, tol2, maxit, h, use_handle, iters_out, relres_out, zero_out);
 }
 
 // z = V-cycle output (+ pending direction) kept in FP32; r.z and r_prev.z
@@ -595,6 +603,115 @@ __global__ void k4_pcg_update(int n, double4_32a* __restrict__ x, double4_32a* _
   }
 }
 
+// ------------------------------------------------------- SPE (4 cols)
+// Section IV, Eq. 4-5 per column: the rings hold the last NH solutions of
+// all four columns (row-interleaved) and W = M X; column c has its own Gram
+// matrix G[c] and coefficients.  One pass: w = M x_newest (four columns per
+// matrix entry), the Gram column and c_k = x_k . b of every column; the last
+// block solves the four small systems.  coef: per column kSpeMax + 1 doubles
+// (coefficients by slot, then the slots in use).
+template <int NH>
+__global__ void k4_spe_gram(DevSell<double> M, int nf, const double4_32a* __restrict__ X,
+                            double4_32a* __restrict__ W, const double4_32a* __restrict__ b,
+                            const long long* __restrict__ stepcount, int s, int j, double* __restrict__ G,
+                            double* partials, unsigned int* counter, int max_blocks, double drop2,
+                            double* __restrict__ coef) {
+  pdl_enter();
+  const long long g = stepcount[0] * (long long)s + j;
+  if (g == 0) {
+    if (blockIdx.x == 0 && threadIdx.x < kEnsW)
+      reinterpret_cast<int*>(coef + threadIdx.x * (kSpeMax + 1) + kSpeMax)[0] = 0;
+    return;
+  }
+  const int m = (int)(g < NH ? g : NH);
+  const int sn = spe_slot(g - 1, NH);
+  constexpr int NS = 2 * NH * kEnsW;  // per column: Gram column (NH), projections (NH)
+  double v[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) v[k] = 0.0;
+  const double4_32a* xs[NH];
+#pragma unroll
+  for (int k = 0; k < NH; ++k) xs[k] = X + (size_t)spe_slot(g - 1 - k, NH) * nf;
+  const double4_32a* __restrict__ xn = X + (size_t)sn * nf;
+  double4_32a* __restrict__ wn = W + (size_t)sn * nf;
+  for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+    const double4_32a w = mat_row_d4(M, i, nf, xn);
+    wn[i] = w;
+    const double4_32a bi = b[i];
+#pragma unroll
+    for (int k = 0; k < NH; ++k) {
+      if (k >= m) break;
+      const double4_32a xk = xs[k][i];
+#pragma unroll
+      for (int c = 0; c < kEnsW; ++c) {
+        v[c * 2 * NH + k] = fma(dc4(xk, c), dc4(w, c), v[c * 2 * NH + k]);
+        v[c * 2 * NH + NH + k] = fma(dc4(xk, c), dc4(bi, c), v[c * 2 * NH + NH + k]);
+      }
+    }
+  }
+  double tot[NS];
+  if (grid_sum<NS>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0)
+    for (int c = 0; c < kEnsW; ++c)
+      spe_solve<NH>(tot + c * 2 * NH, g, m, sn, G + c * kSpeMax * kSpeMax, drop2, coef + c * (kSpeMax + 1));
+}
+
+// CG start of the four columns from their SPE vectors: x0 = X a_c,
+// r0 = R - W a_c (no SpMV), norms, V-cycle input and flags (as
+// k4_pcg_init); without history r0 = R - M x.
+template <int NH>
+__global__ void k4_spe_start(DevSell<double> M, int nf, const double4_32a* __restrict__ X,
+                             const double4_32a* __restrict__ W, const double* __restrict__ coef,
+                             const double4_32a* __restrict__ R, double4_32a* __restrict__ x,
+                             double4_32a* __restrict__ r, const float* __restrict__ dinv0, float inv_theta0,
+                             float4* __restrict__ b0, float4* __restrict__ x0, float4* __restrict__ d0,
+                             EnsScalars* sc, double* partials, unsigned int* counter, int max_blocks,
+                             double tol2, int maxit, cudaGraphConditionalHandle h, int use_handle,
+                             int* iters_out, double* relres_out, int* zero_out) {
+  pdl_enter();
+  const int m = reinterpret_cast<const int*>(coef + kSpeMax)[0];  // same for every column
+  double y[kEnsW][NH];
+#pragma unroll
+  for (int c = 0; c < kEnsW; ++c)
+#pragma unroll
+    for (int k = 0; k < NH; ++k) y[c][k] = k < m ? coef[c * (kSpeMax + 1) + k] : 0.0;
+  double v[2 * kEnsW];
+#pragma unroll
+  for (int k = 0; k < 2 * kEnsW; ++k) v[k] = 0.0;
+  for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+    double4_32a mx;
+    if (m > 0) {
+      double4_32a xi = {0.0, 0.0, 0.0, 0.0};
+      mx = xi;
+#pragma unroll
+      for (int k = 0; k < NH; ++k) {
+        if (k >= m) break;
+        const double4_32a xk = X[(size_t)k * nf + i], wk = W[(size_t)k * nf + i];
+#pragma unroll
+        for (int c = 0; c < kEnsW; ++c) {
+          set4(xi, c, fma(y[c][k], dc4(xk, c), dc4(xi, c)));
+          set4(mx, c, fma(y[c][k], dc4(wk, c), dc4(mx, c)));
+        }
+      }
+      x[i] = xi;
+    } else {
+      mx = mat_row_d4(M, i, nf, x);
+    }
+    const double4_32a Ri = R[i];
+    double4_32a ri;
+#pragma unroll
+    for (int c = 0; c < kEnsW; ++c) {
+      set4(ri, c, dc4(Ri, c) - dc4(mx, c));
+      v[c] = fma(dc4(Ri, c), dc4(Ri, c), v[c]);
+      v[kEnsW + c] = fma(dc4(ri, c), dc4(ri, c), v[kEnsW + c]);
+    }
+    r[i] = ri;
+    vc_input4(i, ri, dinv0, inv_theta0, b0, x0, d0);
+  }
+  double tot[2 * kEnsW];
+  if (grid_sum<2 * kEnsW>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0)
+    ens_init_tail(tot, sc, tol2, maxit, h, use_handle, iters_out, relres_out, zero_out);
+}
+
 // --------------------------------------------------- element and stages
 // K(x)x for four columns: the tet's geometry once, four gradients, kappas
 // and local residuals, scattered with one 16-byte vector atomic per vertex.
@@ -709,7 +826,8 @@ __global__ void k4_recurrence(int n, int nf, double c0, double mu, double nu, do
                               const double* __restrict__ gj, const double* __restrict__ colv,
                               double4_32a* __restrict__ Yj, float4* __restrict__ Y2,
                               double4_32a* __restrict__ Fguess, double* __restrict__ X,
-                              const int32_t* __restrict__ noi) {
+                              const int32_t* __restrict__ noi, const long long* __restrict__ stepcount, int s,
+                              double4_32a* __restrict__ ring, int nh) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -717,6 +835,7 @@ __global__ void k4_recurrence(int n, int nf, double c0, double mu, double nu, do
   if (i < nf) {
     const double dt = prm->dt;
     const double4_32a y0 = Y0[i], y1 = Yjm1[i], y2 = Yjm2[i], f1 = Fjm1[i], f0 = F0[i];
+    if (ring) ring[(size_t)((stepcount[0] * (long long)s + jm1) % nh) * nf + i] = f1;  // SPE history
 #pragma unroll
     for (int c = 0; c < kEnsW; ++c) {
       const double fj = zero_flags[jm1 * kEnsW + c] ? 0.0 : dc4(f1, c);

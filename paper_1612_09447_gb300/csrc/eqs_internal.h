@@ -239,6 +239,12 @@ struct eqs_ctx {
   double* d_erelres = nullptr;       // per stage and column: final relative residual
   int* d_ezero = nullptr;            // per stage and column: zero right-hand side
   double* d_ecolv = nullptr;         // drive scale of each column
+  double4_32a* d_eX = nullptr;       // SPE history of the four columns (row-interleaved rings)
+  double4_32a* d_eW = nullptr;       // W = M X
+  double* d_eG = nullptr;            // per-column Gram matrices (4 x 6 x 6)
+  double* d_ecoef = nullptr;         // per-column coefficients (+ slots in use)
+  double* d_espart = nullptr;        // reduction slots of the ensemble Gram pass
+  long long* d_estepcount = nullptr; // ensemble step counter (history index)
   int64_t ens_body_kernels = 0;
   std::map<std::pair<int, uintptr_t>, eqs::GraphEntry> ens_graphs;   // key: (s, x)
   const eqs::GraphEntry* ens_last = nullptr;

@@ -808,6 +808,8 @@ static eqs_status ens_alloc(eqs_ctx* c) {
   if (c->ens_ready) return EQS_OK;
   if (!mixed(c) || !c->d_M_hi || !c->d_cinv_hi)
     return fail(c, EQS_ERR_STATE, "the ensemble needs a context set up in EQS_PREC_MIXED with split_m 1");
+  if (c->opts.guess != EQS_GUESS_PREV && c->opts.guess != EQS_GUESS_SPE)
+    return fail(c, EQS_ERR_STATE, "the ensemble starts from EQS_GUESS_PREV or EQS_GUESS_SPE");
   const int64_t n = c->n_nodes, nf = c->n_free;
   c->elev.assign(c->lev32.size(), eqs_ctx::EnsLevel());
   for (size_t l = 0; l < c->lev32.size(); ++l) {
@@ -829,6 +831,12 @@ static eqs_status ens_alloc(eqs_ctx* c) {
   CK(dalloc(c, &c->d_erelres, (EQS_MAX_STAGES + 1) * kEnsW));
   CK(dalloc(c, &c->d_ezero, (EQS_MAX_STAGES + 1) * kEnsW));
   CK(dalloc(c, &c->d_ecolv, kEnsW));
+  CK(dalloc(c, &c->d_eX, (size_t)kEnsSpe * nf));
+  CK(dalloc(c, &c->d_eW, (size_t)kEnsSpe * nf));
+  CK(dalloc(c, &c->d_eG, (size_t)kEnsW * kSpeMax * kSpeMax));
+  CK(dalloc(c, &c->d_ecoef, (size_t)kEnsW * (kSpeMax + 1)));
+  CK(dalloc(c, &c->d_espart, 2 * (size_t)kEnsSpe * kEnsW * c->red.max_blocks));
+  CK(dalloc(c, &c->d_estepcount, 2));
   c->ens_ready = true;
   return EQS_OK;
 }
@@ -889,10 +897,17 @@ struct EnsSlots {
 };
 
 static void ens_init_launch(eqs_ctx* c, cudaStream_t st, const double4_32a* R, double4_32a* x, double tol2,
-                            cudaGraphConditionalHandle h, int use_handle, EnsSlots sl) {
+                            cudaGraphConditionalHandle h, int use_handle, EnsSlots sl, bool spe = false) {
   DevLevel<float>& V = c->lev32[0];
   eqs_ctx::EnsLevel& E = c->elev[0];
   const int n = (int)c->n_free;
+  if (spe) {  // SPE start: x0 = X a_c, r0 = R - W a_c
+    launch(k4_spe_start<kEnsSpe>, vec_grid(c, n), kBlock, st, c->M64, n, (const double4_32a*)c->d_eX,
+           (const double4_32a*)c->d_eW, (const double*)c->d_ecoef, R, x, c->d_er, (const float*)V.dinv,
+           (float)V.inv_theta, E.b, E.x, E.dA, (EnsScalars*)c->d_esc, c->d_epart, c->red.counter,
+           c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres, sl.zero);
+    return;
+  }
   launch(k4_pcg_init, vec_grid(c, n), kBlock, st, c->M64, n, R, (const double4_32a*)x, c->d_er,
          (const float*)V.dinv, (float)V.inv_theta, E.b, E.x, E.dA, (EnsScalars*)c->d_esc, c->d_epart,
          c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres, sl.zero);
@@ -917,7 +932,8 @@ static void ens_body_launch(eqs_ctx* c, cudaStream_t st, double4_32a* x, double 
 }
 
 // "init; while (any column active) body" captured into the graph of c->cap_stream.
-static eqs_status ens_pcg_capture(eqs_ctx* c, const double4_32a* R, double4_32a* x, double tol2, EnsSlots sl) {
+static eqs_status ens_pcg_capture(eqs_ctx* c, const double4_32a* R, double4_32a* x, double tol2, EnsSlots sl,
+                                  bool spe = false) {
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -925,7 +941,7 @@ static eqs_status ens_pcg_capture(eqs_ctx* c, const double4_32a* R, double4_32a*
   CK(cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphConditionalHandle h;
   CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
-  ens_init_launch(c, c->cap_stream, R, x, tol2, h, 1, sl);
+  ens_init_launch(c, c->cap_stream, R, x, tol2, h, 1, sl, spe);
   CK(cudaGetLastError());
   CK(cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
@@ -948,9 +964,10 @@ static eqs_status ens_pcg_capture(eqs_ctx* c, const double4_32a* R, double4_32a*
 
 // Host-driven loop (host_loop option): same kernels, the flags are read back
 // after every pass.
-static eqs_status ens_pcg_direct(eqs_ctx* c, const double4_32a* R, double4_32a* x, double tol2, EnsSlots sl) {
+static eqs_status ens_pcg_direct(eqs_ctx* c, const double4_32a* R, double4_32a* x, double tol2, EnsSlots sl,
+                                 bool spe = false) {
   cudaStream_t st = c->stream;
-  ens_init_launch(c, st, R, x, tol2, 0, 0, sl);
+  ens_init_launch(c, st, R, x, tol2, 0, 0, sl, spe);
   EnsScalars* sc = (EnsScalars*)c->d_esc;
   for (int it = 0; it < c->opts.max_iter; ++it) {
     int conv[kEnsW];
@@ -975,8 +992,9 @@ static eqs_status ens_enqueue_step(eqs_ctx* c, int s, double* X, const double* d
   const int n = (int)c->n_nodes, nf = (int)c->n_free;
   const double tol2 = c->opts.rtol * c->opts.rtol;
   const double w = 2.0 * M_PI * c->freq;
+  const bool spe = c->opts.guess == EQS_GUESS_SPE;
   launch(k_stage_scalars, 1, 64, st, s + 1, d_cj, c->d_params, c->V0, w, c->phase, c->d_g, c->d_gp,
-         c->d_stepcount);
+         c->d_estepcount);
   launch(k4_gather_state, nblk(n), kBlock, st, n, nf, (const double*)X, (const int32_t*)c->d_node_of_internal,
          (const double*)c->d_dir_scale, (const double*)c->d_g, (const double*)c->d_ecolv, eYbuf(c, 0), c->d_eY2,
          (const double4_32a*)eFbuf(c, s - 1), eFbuf(c, 0));
@@ -992,7 +1010,8 @@ static eqs_status ens_enqueue_step(eqs_ctx* c, int s, double* X, const double* d
              (const double4_32a*)eFbuf(c, j - 1), (const double4_32a*)eFbuf(c, 0), (const int*)c->d_ezero, j - 1,
              (const double*)c->d_dir_scale, (const double*)(c->d_g + j), (const double*)c->d_ecolv, eYbuf(c, j),
              last ? nullptr : c->d_eY2, last ? nullptr : eFbuf(c, j), last ? X : nullptr,
-             (const int32_t*)c->d_node_of_internal);
+             (const int32_t*)c->d_node_of_internal, (const long long*)c->d_estepcount, s,
+             spe ? c->d_eX : nullptr, kEnsSpe);
       if (last) break;
     }
     launch(k4_elem32, nblk(c->n_tets), kBlock, st, c->n_tets, (const int4*)c->d_conn, (const uint8_t*)c->d_mat,
@@ -1001,10 +1020,14 @@ static eqs_status ens_enqueue_step(eqs_ctx* c, int s, double* X, const double* d
     launch(k4_rhs, nblk(nf), kBlock, st, nf, c->d_ey32, (const double*)(c->d_gp + j), (const double*)c->d_ecolv,
            (const double*)c->d_mtop, c->d_eR);
     EnsSlots sl{c->d_eiters + kEnsW * j, c->d_erelres + kEnsW * j, c->d_ezero + kEnsW * j};
+    if (spe)
+      launch(k4_spe_gram<kEnsSpe>, std::max(1, std::min(nblk(nf), c->sms)), kBlock, st, c->M64, nf,
+             (const double4_32a*)c->d_eX, c->d_eW, (const double4_32a*)c->d_eR, (const long long*)c->d_estepcount,
+             s, j, c->d_eG, c->d_espart, c->red.counter, c->red.max_blocks, 1e-12, c->d_ecoef);
     if (c->direct)
-      stt = ens_pcg_direct(c, c->d_eR, eFbuf(c, j), tol2, sl);
+      stt = ens_pcg_direct(c, c->d_eR, eFbuf(c, j), tol2, sl, spe);
     else
-      stt = ens_pcg_capture(c, c->d_eR, eFbuf(c, j), tol2, sl);
+      stt = ens_pcg_capture(c, c->d_eR, eFbuf(c, j), tol2, sl, spe);
   }
   return stt;
 }
@@ -1571,6 +1594,8 @@ eqs_status eqs_ens_rkc_step(eqs_ctx* c, double* x, const double* v0_scale, doubl
   if (!std::isfinite(t) || !(dt > 0) || !std::isfinite(dt)) return fail(c, EQS_ERR_ARG, "bad t or dt");
   for (int k = 0; k < EQS_ENS_W; ++k)
     if (!std::isfinite(v0_scale[k])) return fail(c, EQS_ERR_ARG, "non-finite drive scale");
+  if (c->opts.guess != EQS_GUESS_PREV && c->opts.guess != EQS_GUESS_SPE)
+    return fail(c, EQS_ERR_STATE, "the ensemble starts from EQS_GUESS_PREV or EQS_GUESS_SPE");
   const eqs_status as = ens_alloc(c);
   if (as != EQS_OK) return as;
   StepParams prm{t, dt};
@@ -1743,6 +1768,7 @@ eqs_status eqs_set_guess(eqs_ctx* c, int mode) {
       CK(cudaStreamSynchronize(c->stream));
       CK(cudaMemset(c->d_stepcount, 0, 2 * sizeof(long long)));
       CK(cudaMemset(c->d_pod_state, 0, sizeof(PodState)));
+      if (c->d_estepcount) CK(cudaMemset(c->d_estepcount, 0, 2 * sizeof(long long)));
     }
   }
   c->opts.guess = mode;

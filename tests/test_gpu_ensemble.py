@@ -38,8 +38,9 @@ def _oracle_run(p, s, steps, dt):
     return np.array(out)
 
 
-def _ens_run(E, p, scales, s, steps, rtol, host_loop=0):
+def _ens_run(E, p, scales, s, steps, rtol, host_loop=0, guess=0):
     S = E.Solver(p, precision=MIXED, rtol=rtol, persistent=0, host_loop=host_loop)
+    E.eqs_set_guess(S.ctx, guess)
     dt = S.dt_bound(s)
     x = torch.zeros((4, p.n_nodes), dtype=torch.float64, device="cuda")
     traj, stats, t = [], [], 0.0
@@ -130,6 +131,37 @@ def test_ensemble_solve_blocked(E):
 def test_ensemble_requires_mixed(E):
     p = ei.make_problem(3)
     S = E.Solver(p, precision=FP64)
+    x = torch.zeros((4, p.n_nodes), dtype=torch.float64, device="cuda")
+    with pytest.raises(E.EqsError) as ex:
+        E.eqs_ens_rkc_step(S.ctx, x, SCALES, 0.0, 1e-3, 10)
+    assert ex.value.status == E.EQS_ERR_STATE
+    S.close()
+
+
+def test_ensemble_spe_start(E):
+    """Per-column SPE start vectors (Section IV, Eq. 4-5) in the ensemble:
+    same trajectories as the oracle, far fewer CG iterations than starting
+    from the previous solutions."""
+    p = ei.config_problem(0)
+    s, steps = 10, 6
+    a, sa, dt = _ens_run(E, p, SCALES, s, steps, rtol=1e-12, guess=E.EQS_GUESS_PREV)
+    b, sb, _ = _ens_run(E, p, SCALES, s, steps, rtol=1e-12, guess=E.EQS_GUESS_SPE)
+    for c, sc in enumerate(SCALES):
+        ref = _oracle_run(dataclasses.replace(p, V0=p.V0 * sc), s, steps, dt)
+        assert _err(b[:, c], ref) <= 1e-6, c
+    it_prev = [sum(st.total_iters[c] for st in sa[2:]) for c in range(4)]
+    it_spe = [sum(st.total_iters[c] for st in sb[2:]) for c in range(4)]
+    print("ensemble iterations per column, previous solution", it_prev, "SPE", it_spe)
+    for c in range(4):
+        assert it_spe[c] * 1.5 < it_prev[c]
+    for st in sb:
+        assert st.status == 0 and st.max_relres <= 1e-12
+
+
+def test_ensemble_rejects_other_guess_modes(E):
+    p = ei.make_problem(3)
+    S = E.Solver(p, precision=MIXED)
+    E.eqs_set_guess(S.ctx, E.EQS_GUESS_POD)
     x = torch.zeros((4, p.n_nodes), dtype=torch.float64, device="cuda")
     with pytest.raises(E.EqsError) as ex:
         E.eqs_ens_rkc_step(S.ctx, x, SCALES, 0.0, 1e-3, 10)
