@@ -34,7 +34,8 @@ WORKLOADS = {
        "block varistor, s=20, dt=beta_s/rho, rtol=1e-8",
     2: "cube128_jitter_spheres: 128^3-cell Kuhn cube with interior nodes jittered by +-0.2h, "
        "2146689 nodes (2113407 free), 12582912 P1 tets, two varistor spheres, s=20, "
-       "dt=beta_s/rho, rtol=1e-8",
+       "dt=beta_s/rho, rtol=1e-8, 4-member ensemble (V0 x 0.5/1/1.5/2), M-solve right-hand "
+       "sides blocked 4 at a time (SpMM)",
     3: "learned start vector on cube128_jitter_spheres (2113407 free rows, s=20, rtol=1e-8): "
        "trained on the GPU on 400 stage solutions of 20 FP64 steps, then mixed precision with "
        "the learned guess against the previous-solution guess",
@@ -578,6 +579,145 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble_headline(args, rank, world):
+    """Config 2: the 4-member ensemble (drive V0 x {0.5, 1, 1.5, 2}) on the
+    128^3 jittered mesh, every stage's four right-hand sides solved together
+    (blocked CG, SpMM), mixed precision, per-column SPE start vectors."""
+    import numpy as np
+    import torch
+
+    import eqs_inputs as ei
+    from paper_1612_09447_gb300 import eqs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    eqs.lib()
+    p = ei.config_problem(CONFIG_INDEX, N=args.N)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    flushbuf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def flush():
+        flushbuf.zero_()
+
+    def make(precision, guess):
+        S = eqs.Solver(p, precision=precision, rtol=RTOL, host_loop=int(args.host_loop), spe_n=SPE_N,
+                       **SOLVER_OPTS)
+        eqs.eqs_set_guess(S.ctx, guess)
+        return S
+
+    S = make(eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_SPE)
+    dt = S.dt_bound(S_STAGES)
+    x = torch.zeros((4, p.n_nodes), dtype=torch.float64, device="cuda")
+    t = 0.0
+    for _ in range(args.warmup):
+        eqs.eqs_ens_rkc_step(S.ctx, x, ENS_SCALES, t, dt, S_STAGES)
+        t += dt
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = ClockSampler(local)
+    times, iters, launches = [], [], 0
+    for _ in range(args.steps):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        eqs.eqs_ens_rkc_step(S.ctx, x, ENS_SCALES, t, dt, S_STAGES, want_stats=False)
+        e1.record()
+        st = eqs.eqs_ens_get_step_stats(S.ctx)
+        times.append(e0.elapsed_time(e1))
+        iters.append([v / S_STAGES for v in st.total_iters])
+        launches += st.launches
+        t += dt
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    total_ms = sum(times)
+    if dist is not None:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    units = world * 4 * p.n_free * S_STAGES * args.steps
+    value = units / (total_ms / 1e3)
+    # end to end: pinned host x (4 trajectories) in, step, x back to host
+    xh = torch.zeros((4, p.n_nodes), dtype=torch.float64).pin_memory()
+    xh.copy_(x.cpu())
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t_host = time.perf_counter()
+        e0.record()
+        x.copy_(xh, non_blocking=True)
+        eqs.eqs_ens_rkc_step(S.ctx, x, ENS_SCALES, t, dt, S_STAGES, want_stats=False)
+        xh.copy_(x, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        e2e_ms += max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_host))
+        t += dt
+    if dist is not None:
+        tt = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    roof = dominant_kernel_roofline(torch, eqs, S, p, flush)
+    S.close()
+    forms = {}
+    if not args.no_fp64:
+        short = max(3, args.steps // 4)
+        forms["ensemble4_mixed_prev"] = measure_ensemble(torch, eqs, p, make, flush, short, 2)
+        for name, guess in (("single_mixed_spe", eqs.EQS_GUESS_SPE), ("single_mixed_prev", eqs.EQS_GUESS_PREV)):
+            T = make(eqs.EQS_PREC_MIXED, guess)
+            xs = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+            ts = 0.0
+            for _ in range(2):
+                T.step(xs, ts, dt, S_STAGES)
+                ts += dt
+            tm, it = [], []
+            for _ in range(short):
+                flush()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                T.step(xs, ts, dt, S_STAGES, stats=False)
+                e1.record()
+                stt = T.last_stats()
+                tm.append(e0.elapsed_time(e1))
+                it.append(stt.total_iters / S_STAGES)
+                ts += dt
+            T.close()
+            forms[name] = {"value": p.n_free * S_STAGES * len(tm) / (sum(tm) / 1e3),
+                           "ms_per_step": sum(tm) / len(tm), "cg_iters_per_solve": float(np.mean(it))}
+    if rank != 0:
+        return
+    ms_step = total_ms / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF-stages/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/f64 mixed", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_free": p.n_free, "trajectories": 4,
+                   "drive_scales": list(ENS_SCALES), "stages": S_STAGES, "rtol": RTOL,
+                   "solver": dict(SOLVER_OPTS, spe_n=4),
+                   "form": "4-member ensemble, blocked CG (SpMM over the four right-hand sides of a "
+                           "stage), mixed precision, per-column SPE start vectors (Section IV)",
+                   "m_solve_ms_per_rhs": ms_step / (4 * S_STAGES),
+                   "cg_iters_per_solve_by_column": [float(v) for v in np.mean(iters, axis=0)],
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "forms": forms,
+        "e2e": {"value": units / (e2e_ms / 1e3), "unit": "DOF-stages/s",
+                "h2d_bytes_per_step": 4 * p.n_nodes * 8, "d2h_bytes_per_step": 4 * p.n_nodes * 8},
+        "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": None, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     global CONFIG_INDEX, WORKLOAD
     args = parse()
@@ -588,6 +728,9 @@ def main():
         return
     if args.config == 4 and args.impl == "ours":
         run_batch(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
+        return
+    if args.config == 2 and args.impl == "ours":
+        run_ensemble_headline(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

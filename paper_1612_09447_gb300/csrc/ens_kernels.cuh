@@ -21,7 +21,7 @@
 namespace eqs {
 
 constexpr int kEnsW = 4;
-constexpr int kEnsSpe = 4;  // SPE history length of the ensemble (32 sums per Gram pass)
+constexpr int kEnsSpe = 6;  // SPE history length of the ensemble (48 sums per Gram pass)
 
 // ------------------------------------------------------------ float4 ops
 __device__ __forceinline__ float4 operator+(float4 a, float4 b) {
