@@ -30,6 +30,19 @@ closed forms cosh(j acosh x), j sinh(j t)/sinh(t); the stage recurrence on
 y' = lambda y against the closed-form P_j; P_s(z) = 1 + z + z^2/2 + O(z^3);
 |P_s| <= 1 on [-beta_s, 0]; beta_s against (2/3)(s^2-1)(1-2 eps/15);
 second-order convergence under step refinement.
+
+Adaptive stepping (the paper runs with a local time-integration error below
+1e-2; ref. [9] controls it): per step the number of stages is the smallest
+s with beta_s >= h rho, the local error estimate is
+Est = (12 (y_n - y_{n+1}) + 6 h (F_n + F_{n+1})) / 15 in a weighted RMS
+norm, a step is accepted when that norm is <= 1 and the next step is
+h 0.8 err^(-1/3) within [0.1 h, 10 h].  Readings: rho is the a-priori bound
+of dtbound (the paper does not say how it is estimated); the simple
+(non-PI) step controller.  Pins (tests/test_oracle_rkc_adaptive.py): the
+estimate vanishes where the scheme is exact and equals h^3 y3/15 - 12/15
+of the local error to leading order (y3 the third derivative); the stage
+choice against brute force; global error and step counts scale with the
+tolerance like a second-order method; a rejected step shrinks.
 """
 
 from __future__ import annotations
@@ -117,3 +130,51 @@ def rkc_step(F, t: float, y: np.ndarray, dt: float, coef: RKCCoefficients):
               + coef.mut[j] * dt * Fjm1 + coef.gt[j] * dt * F0)
         Yjm2, Yjm1 = Yjm1, Yj
     return Yjm1, calls
+
+
+# ------------------------------------------------------- adaptive stepping
+def stages_for(h: float, rho: float, s_max: int = 64):
+    """Smallest s >= 2 whose stability interval covers h*rho (beta_s >= h rho);
+    (s_max, beta_smax / rho) when even s_max does not: the step is cut."""
+    for s in range(2, s_max + 1):
+        if RKCCoefficients(s).beta >= h * rho:
+            return s, h
+    return s_max, RKCCoefficients(s_max).beta / rho
+
+
+def error_estimate(h, y0, y1, F0, F1):
+    """Local error estimate of the RKC scheme (ref. [9]):
+    Est = (12 (y_n - y_{n+1}) + 6 h (F(t_n, y_n) + F(t_{n+1}, y_{n+1}))) / 15."""
+    return (12.0 * (y0 - y1) + 6.0 * h * (F0 + F1)) / 15.0
+
+
+def error_norm(est, y0, y1, atol, rtol):
+    """Weighted RMS norm: sqrt(mean((Est_i / (atol + rtol max(|y0_i|, |y1_i|)))^2))."""
+    w = atol + rtol * np.maximum(np.abs(y0), np.abs(y1))
+    return float(np.sqrt(np.mean((est / w) ** 2)))
+
+
+def step_factor(err: float) -> float:
+    """Step size factor 0.8 err^(-1/3), kept in [0.1, 10] (second-order
+    scheme: the local error scales like h^3)."""
+    if err == 0.0:
+        return 10.0
+    return min(10.0, max(0.1, 0.8 * err ** (-1.0 / 3.0)))
+
+
+def rkc_adaptive_step(F, t, y, F0, h, rho, atol, rtol, s_max=64, max_tries=50):
+    """One accepted adaptive RKC step from (t, y) with F0 = F(t, y), trying
+    step h first.  Each try: s from stages_for(h, rho), one RKC step,
+    F1 = F(t + h, y1), the error norm of error_estimate; accept when
+    err <= 1, else retry with h * step_factor(err).
+
+    Returns (y1, F1, h_used, s, err, h_next, tries)."""
+    for tries in range(1, max_tries + 1):
+        s, h = stages_for(h, rho, s_max)
+        y1, _ = rkc_step(F, t, y, h, RKCCoefficients(s))
+        F1 = F(t + h, y1)
+        err = error_norm(error_estimate(h, y, y1, F0, F1), y, y1, atol, rtol)
+        if err <= 1.0:
+            return y1, F1, h, s, err, h * step_factor(err), tries
+        h = h * step_factor(err)
+    raise RuntimeError("adaptive RKC: too many rejected steps")
