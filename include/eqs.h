@@ -227,6 +227,31 @@ eqs_status eqs_spmv_M32(eqs_ctx* ctx, const float* x, double* y);
 eqs_status eqs_rkc_step(eqs_ctx* ctx, double* x, double t, double dt, int s,
                         eqs_step_stats* stats);
 
+/* ---- Adaptive stepping (the paper runs RKC with a local time-integration
+ * error below 1e-2; ref. [9] controls it).  One accepted step from t: the
+ * number of stages is the smallest s <= s_max with beta_s >= h rho (rho the
+ * a-priori stiffness bound of eqs_rkc_dt_bound; h is cut when s_max does
+ * not suffice), the step runs as eqs_rkc_step, then F(t + h, x_new) is
+ * evaluated and the local error estimate
+ *   Est = (12 (x_n - x_n+1) + 6 h (F_n + F_n+1)) / 15
+ * is measured in the weighted RMS norm with weights atol + rtol
+ * max(|x_n|, |x_n+1|) over the free nodes.  err <= 1 accepts; otherwise x
+ * is restored and the step retried with h 0.8 err^(-1/3) (factor kept in
+ * [0.1, 10]).  x: device, n_nodes doubles, mesh order, in x(t), out
+ * x(t + h_used).  Synchronises.  EQS_ERR_NOCONV after 50 rejected tries (x
+ * restored), or when a stage solve did not converge. */
+typedef struct {
+  double h_used;     /* accepted step                                        */
+  double h_next;     /* proposed next step (h_used 0.8 err^(-1/3), clipped)  */
+  double err;        /* error norm of the accepted step (<= 1)                */
+  int s;             /* stages of the accepted step                          */
+  int tries;         /* 1 + rejected tries                                   */
+  int total_iters;   /* CG iterations of all tries and error evaluations     */
+} eqs_adapt_stats;
+
+eqs_status eqs_rkc_adaptive_step(eqs_ctx* ctx, double* x, double t, double h_try, double atol,
+                                 double rtol, int s_max, eqs_adapt_stats* out);
+
 /* Statistics of the last eqs_rkc_step on ctx (synchronises the stream). */
 eqs_status eqs_get_step_stats(eqs_ctx* ctx, eqs_step_stats* stats);
 

@@ -617,7 +617,7 @@ __global__ void k4_spe_gram(DevSell<double> M, int nf, const double4_32a* __rest
                             double* partials, unsigned int* counter, int max_blocks, double drop2,
                             double* __restrict__ coef) {
   pdl_enter();
-  const long long g = stepcount[0] * (long long)s + j;
+  const long long g = stepcount[0] + j;
   if (g == 0) {
     if (blockIdx.x == 0 && threadIdx.x < kEnsW)
       reinterpret_cast<int*>(coef + threadIdx.x * (kSpeMax + 1) + kSpeMax)[0] = 0;
@@ -835,7 +835,7 @@ __global__ void k4_recurrence(int n, int nf, double c0, double mu, double nu, do
   if (i < nf) {
     const double dt = prm->dt;
     const double4_32a y0 = Y0[i], y1 = Yjm1[i], y2 = Yjm2[i], f1 = Fjm1[i], f0 = F0[i];
-    if (ring) ring[(size_t)((stepcount[0] * (long long)s + jm1) % nh) * nf + i] = f1;  // SPE history
+    if (ring) ring[(size_t)((stepcount[0] + jm1) % nh) * nf + i] = f1;  // SPE history
 #pragma unroll
     for (int c = 0; c < kEnsW; ++c) {
       const double fj = zero_flags[jm1 * kEnsW + c] ? 0.0 : dc4(f1, c);

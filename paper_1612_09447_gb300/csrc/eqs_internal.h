@@ -251,6 +251,14 @@ struct eqs_ctx {
   eqs::GraphEntry ens_solve_graph;   // eqs_ens_solve_M (rtol of the setup)
   double ens_solve_tol = -1.0;
 
+  // ---- adaptive stepping: F(t, x) evaluation graphs (key: x) and scratch
+  std::map<uintptr_t, eqs::GraphEntry> eval_graphs;
+  double* d_xsave = nullptr;         // x(t_n) of the step being tried (n_nodes, mesh order)
+  double* d_Fnew = nullptr;          // F(t_n+1, x_n+1) (n_free, internal order)
+  double* d_err = nullptr;           // error norm of the last try
+  long long* d_evalcount = nullptr;  // dummy history counter of the evaluations
+  double* d_cj0 = nullptr;           // {0}: stage abscissa of an evaluation
+
   std::map<std::pair<int, uintptr_t>, eqs::GraphEntry> step_graphs;  // key: (s, x)
   const eqs::GraphEntry* last_step = nullptr;                       // graph of the last step
   int64_t body_kernels = 0;  // kernel nodes of the last captured CG loop body

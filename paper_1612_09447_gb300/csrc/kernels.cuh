@@ -897,9 +897,9 @@ __global__ void k_stage_scalars(int s1, const double* __restrict__ cj, const Ste
                                 double* __restrict__ gp, long long* stepcount) {
   pdl_enter();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j == 0) {  // [0]: index of this step in the solution history, [1]: next
-    stepcount[0] = stepcount[1];
-    stepcount[1] += 1;
+  if (j == 0) {  // [0]: solves before this step (history index of its first
+    stepcount[0] = stepcount[1];  // solve), [1]: after it; steps may differ in s
+    stepcount[1] += s1 - 1;
   }
   if (j >= s1) return;
   const double tj = prm->t + cj[j] * prm->dt;
@@ -957,7 +957,7 @@ __global__ void k_recurrence(int n, int nf, double c0, double mu, double nu, dou
   double v;
   if (i < nf) {
     // F_{j-1} enters the solution history (ring slot g % 4; recorded copy)
-    const long long gidx = stepcount[0] * (long long)s + jm1;
+    const long long gidx = stepcount[0] + jm1;
     const float f32 = (float)Fjm1[i];
     ring[(size_t)(gidx & 3) * nf + i] = f32;
     if (store && gidx < store_cap) store[(size_t)gidx * nf + i] = f32;
@@ -984,6 +984,28 @@ __global__ void k_rhs_from_y32(int nf, float* __restrict__ y32, const double* __
   if (i >= nf) return;
   R[i] = -(double)y32[i] - (*gpj) * mtop[i];
   y32[i] = 0.0f;
+}
+
+// Weighted RMS norm of the local error estimate of the RKC scheme (ref. [9]),
+// Est_i = (12 (y_n,i - y_n+1,i) + 6 h (F_n,i + F_n+1,i)) / 15 with weights
+// atol + rtol max(|y_n,i|, |y_n+1,i|) over the free rows; the last block
+// writes sqrt(mean((Est / w)^2)) to *out.  y in mesh order, F internal.
+__global__ void k_rkc_errnorm(int nf, const double* __restrict__ y0, const double* __restrict__ y1,
+                              const int32_t* __restrict__ node_of_internal, const double* __restrict__ F0,
+                              const double* __restrict__ F1, double h, double atol, double rtol,
+                              double* partials, unsigned int* counter, int max_blocks, double* out) {
+  pdl_enter();
+  double v[1] = {0.0};
+  for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+    const int m = node_of_internal[i];
+    const double a = y0[m], b = y1[m];
+    const double est = (12.0 * (a - b) + 6.0 * h * (F0[i] + F1[i])) * (1.0 / 15.0);
+    const double w = atol + rtol * fmax(fabs(a), fabs(b));
+    const double q = est / w;
+    v[0] = fma(q, q, v[0]);
+  }
+  double tot[1];
+  if (grid_sum<1>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) *out = sqrt(tot[0] / nf);
 }
 
 // ------------------------------------------------------- small utilities

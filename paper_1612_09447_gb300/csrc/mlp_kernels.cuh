@@ -98,7 +98,8 @@ __global__ void k_rms(int n, const double* __restrict__ h, double* sh, double* p
 }
 
 // z0 = h1 + s_h MLP(features) for the solve with global index
-// g = stepcount[0] * s + j; the history ring holds solution k in slot k % 4.
+// g = stepcount[0] + j (solves before this step + stage); the history ring
+// holds solution k in slot k % 4.
 // With fewer than four earlier solutions (or s_h = 0) z0 = h1.
 __global__ void k_mlp_guess(int nf, const double* __restrict__ h1d, const float* __restrict__ ring,
                             const long long* __restrict__ stepcount, int s, int j,
@@ -108,7 +109,7 @@ __global__ void k_mlp_guess(int nf, const double* __restrict__ h1d, const float*
   pdl_enter();
   __shared__ float sw[kNP + 3];
   load_weights(wb, sw);
-  const long long g = stepcount[0] * (long long)s + j;
+  const long long g = stepcount[0] + j;
   const double s_h = *sh;
   const bool use = g >= 4 && s_h > 0.0;
   const float* hr[4];

@@ -56,7 +56,7 @@ __global__ void k_pod_add(DevSell<double> M, int nf, double* __restrict__ X, dou
                           int min_iters, PodState* st, double* partials, unsigned int* counter,
                           int max_blocks) {
   pdl_enter();
-  const long long g = stepcount[0] * (long long)s + j;
+  const long long g = stepcount[0] + j;
   if (g == 0 || *prev_zero) return;  // no solution yet / a zero solve is not a snapshot
   const int add = mode == 0 ? st->count < cap : *prev_iters > min_iters;
   if (!add) return;  // uniform over the grid

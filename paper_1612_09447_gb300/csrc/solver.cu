@@ -749,6 +749,53 @@ static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
   return EQS_OK;
 }
 
+// F(t, x) = M_ff^-1 (-[K(x~)x~]_f - g'(t) M_fd 1_top) into Fout (internal
+// order; its content is the CG start vector): the stage evaluation of a step
+// as a graph of its own (time from the device parameters).
+template <typename T>
+static eqs_status enqueue_eval_F(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* xmesh, double* Fout,
+                                 cudaStream_t st) {
+  const int n = (int)c->n_nodes, nf = (int)c->n_free;
+  const bool mx = mixed(c);
+  const double w = 2.0 * M_PI * c->freq;
+  launch(k_stage_scalars, 1, 64, st, 1, (const double*)c->d_cj0, (const StepParams*)c->d_params, c->V0, w,
+         c->phase, c->d_g, c->d_gp, c->d_evalcount);
+  launch(k_gather_state, nblk(n), kBlock, st, n, nf, xmesh, (const int32_t*)c->d_node_of_internal,
+         (const double*)c->d_dir_scale, (const double*)c->d_g, (const double*)c->d_gp, (const double*)c->d_mtop,
+         c->d_tmpn, mx ? c->d_Y32 : nullptr, (const double*)nullptr, (double*)nullptr, mx ? nullptr : c->d_R);
+  if (mx) {
+    elem_launch(c, st, nullptr, nf, nullptr, c->d_y32);
+    launch(k_rhs_from_y32, nblk(nf), kBlock, st, nf, c->d_y32, (const double*)c->d_gp, (const double*)c->d_mtop,
+           c->d_R);
+  } else {
+    elem_launch(c, st, c->d_tmpn, nf, c->d_R, nullptr);
+  }
+  SolveSlots sl{c->d_iters + EQS_MAX_STAGES, c->d_relres + EQS_MAX_STAGES, c->d_zero + EQS_MAX_STAGES};
+  const double tol2 = c->opts.rtol * c->opts.rtol;
+  return solve_launch<T>(c, L, c->d_R, Fout, tol2, sl);
+}
+
+template <typename T>
+static eqs_status capture_eval_F(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* xmesh, double* Fout,
+                                 GraphEntry& ge) {
+  cudaStream_t st = c->cap_stream;
+  c->direct = false;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  const eqs_status stt = enqueue_eval_F<T>(c, L, xmesh, Fout, st);
+  cudaError_t le = cudaGetLastError();
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  if (stt != EQS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return stt;
+  }
+  CK(le);
+  CK(ee);
+  ge.graph = graph;
+  CK(cudaGraphInstantiate(&ge.exec, graph, 0));
+  return EQS_OK;
+}
+
 template <typename T>
 static eqs_status capture_solve(eqs_ctx* c, std::vector<DevLevel<T>>& L, double rtol, GraphEntry& ge) {
   cudaStream_t st = c->cap_stream;
@@ -780,6 +827,8 @@ static void destroy_graphs(eqs_ctx* c) {
   c->step_graphs.clear();
   for (auto& kv : c->solve_graphs) destroy_graph(kv.second);
   c->solve_graphs.clear();
+  for (auto& kv : c->eval_graphs) destroy_graph(kv.second);
+  c->eval_graphs.clear();
   c->ens_last = nullptr;
   for (auto& kv : c->ens_graphs) destroy_graph(kv.second);
   c->ens_graphs.clear();
@@ -1344,6 +1393,11 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     CK(dalloc(c, &c->d_sh, 1));
     CK(dalloc(c, &c->d_mlp_used, EQS_MAX_STAGES + 1));
     CK(dalloc(c, &c->d_rtmp, nf));
+    CK(dalloc(c, &c->d_xsave, n));
+    CK(dalloc(c, &c->d_Fnew, nf));
+    CK(dalloc(c, &c->d_err, 1));
+    CK(dalloc(c, &c->d_evalcount, 2));
+    CK(dalloc(c, &c->d_cj0, 1));
     CK(dalloc(c, &c->d_spe_X, (size_t)kSpeMax * nf));
     CK(dalloc(c, &c->d_spe_W, (size_t)kSpeMax * nf));
     CK(dalloc(c, &c->d_spe_y, kSpeMax + 1));  // coefficients + slots in use
@@ -1583,6 +1637,77 @@ eqs_status eqs_get_step_stats(eqs_ctx* c, eqs_step_stats* stats) {
   if (res == EQS_ERR_NOCONV) return fail(c, res, "a stage solve reached max_iter");
   if (res == EQS_ERR_NAN) return fail(c, res, "non-finite residual in a stage solve");
   return EQS_OK;
+}
+
+eqs_status eqs_rkc_adaptive_step(eqs_ctx* c, double* x, double t, double h_try, double atol, double rtol,
+                                 int s_max, eqs_adapt_stats* out) {
+  REQUIRE_SETUP(c);
+  if (!x || !out) return fail(c, EQS_ERR_ARG, "x or out is NULL");
+  if (!std::isfinite(t) || !(h_try > 0) || !std::isfinite(h_try) || !(atol >= 0) || !(rtol >= 0) ||
+      !(atol + rtol > 0) || s_max < 2 || s_max > EQS_MAX_STAGES)
+    return fail(c, EQS_ERR_ARG, "bad adaptive step arguments");
+  if (c->opts.host_loop) return fail(c, EQS_ERR_STATE, "adaptive stepping runs the step graphs (host_loop 0)");
+  const double rho = rho_bound(c->mats);
+  std::vector<double> beta(EQS_MAX_STAGES + 1, 0.0);
+  for (int s = 2; s <= s_max; ++s) {
+    std::vector<double> mu, nu, mut, gt, cj;
+    rkc_coefficients(s, mu, nu, mut, gt, cj, beta[s]);
+  }
+  const double zero = 0.0;
+  CK(cudaMemcpyAsync(c->d_cj0, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_xsave, x, c->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  std::memset(out, 0, sizeof(*out));
+  double h = h_try;
+  const int nf = (int)c->n_free;
+  for (int tries = 1; tries <= 50; ++tries) {
+    int s = 2;  // smallest s with beta_s >= h rho; cut h when s_max does not suffice
+    while (s < s_max && beta[s] < h * rho) ++s;
+    if (beta[s] < h * rho) h = beta[s] / rho;
+    if (tries > 1)
+      CK(cudaMemcpyAsync(x, c->d_xsave, c->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    eqs_step_stats st;
+    const eqs_status ss = eqs_rkc_step(c, x, t, h, s, &st);
+    if (ss != EQS_OK) return ss;
+    out->total_iters += st.total_iters;
+    // F(t + h, x_new), started from F(t, x_old) (the step's first stage)
+    CK(cudaMemcpyAsync(c->d_Fnew, c->d_F[0], nf * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    auto it = c->eval_graphs.find((uintptr_t)x);
+    if (it == c->eval_graphs.end()) {
+      GraphEntry ge;
+      const eqs_status es = mixed(c) ? capture_eval_F(c, c->lev32, x, c->d_Fnew, ge)
+                                     : capture_eval_F(c, c->lev64, x, c->d_Fnew, ge);
+      if (es != EQS_OK) return es;
+      it = c->eval_graphs.emplace((uintptr_t)x, ge).first;
+    }
+    StepParams prm{t + h, h};
+    CK(cudaMemcpyAsync(c->d_params, &prm, sizeof(prm), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaGraphLaunch(it->second.exec, c->stream));
+    k_rkc_errnorm<<<vec_grid(c, nf), kBlock, 0, c->stream>>>(
+        nf, c->d_xsave, x, c->d_node_of_internal, c->d_F[0], c->d_Fnew, h, atol, rtol, c->red.partials,
+        c->red.counter, c->red.max_blocks, c->d_err);
+    double err = 0.0;
+    int eit = 0;
+    double err_rr = 0.0;
+    CK(cudaMemcpyAsync(&err, c->d_err, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&eit, c->d_iters + EQS_MAX_STAGES, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&err_rr, c->d_relres + EQS_MAX_STAGES, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out->total_iters += eit;
+    if (!std::isfinite(err) || !std::isfinite(err_rr)) return fail(c, EQS_ERR_NAN, "non-finite error estimate");
+    const double fac = err == 0.0 ? 10.0 : std::min(10.0, std::max(0.1, 0.8 * std::pow(err, -1.0 / 3.0)));
+    if (err <= 1.0) {
+      out->h_used = h;
+      out->h_next = h * fac;
+      out->err = err;
+      out->s = s;
+      out->tries = tries;
+      return EQS_OK;
+    }
+    h *= fac;
+  }
+  CK(cudaMemcpyAsync(x, c->d_xsave, c->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return fail(c, EQS_ERR_NOCONV, "adaptive step: 50 rejected tries");
 }
 
 // ------------------------------------------------------------- ensemble

@@ -83,7 +83,7 @@ __device__ void spe_solve(const double* tot, long long g, int m, int sn, double*
   reinterpret_cast<int*>(y_out + kSpeMax)[0] = m;
 }
 
-// Solve index g = stepcount[0] * s + j: solutions 0..g-1 exist, the newest
+// Solve index g = stepcount[0] + j: solutions 0..g-1 exist, the newest
 // m = min(g, NH) of them are in the rings.  One pass: w_{g-1} = M x_{g-1},
 // the Gram column G[k][g-1] over the stored solutions k and c_k = x_k . b.
 // The last block updates G and solves (L L^T) y = c with column dropping;
@@ -95,7 +95,7 @@ __global__ void k_spe_gram(DevSell<double> M, int nf, const double* __restrict__
                            int j, double* __restrict__ G, double* partials, unsigned int* counter,
                            int max_blocks, double drop2, double* __restrict__ y_out) {
   pdl_enter();
-  const long long g = stepcount[0] * (long long)s + j;
+  const long long g = stepcount[0] + j;
   if (g == 0) {  // uniform over the grid: no history, no reduction
     if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<int*>(y_out + kSpeMax)[0] = 0;
     return;

@@ -59,6 +59,11 @@ class eqs_ens_stats(C.Structure):
                 ("launches", C.c_int64)]
 
 
+class eqs_adapt_stats(C.Structure):
+    _fields_ = [("h_used", C.c_double), ("h_next", C.c_double), ("err", C.c_double), ("s", C.c_int),
+                ("tries", C.c_int), ("total_iters", C.c_int)]
+
+
 class eqs_step_stats(C.Structure):
     _fields_ = [("s", C.c_int), ("total_iters", C.c_int), ("max_iters", C.c_int),
                 ("iters", C.c_int * EQS_MAX_STAGES), ("max_relres", C.c_double),
@@ -119,6 +124,7 @@ def _declare(L):
         "eqs_ens_solve_M": (I, [P, P, P, P]),
         "eqs_pod_eval": (I, [P, P, I, P, P]),
         "eqs_pod_info": (I, [P, P, P, P, P, P]),
+        "eqs_rkc_adaptive_step": (I, [P, P, D, D, D, D, I, C.POINTER(eqs_adapt_stats)]),
         "eqs_destroy": (I, [P]),
         "eqs_last_error": (C.c_char_p, [P]),
     }
@@ -210,6 +216,13 @@ def eqs_spmv_M32(ctx, x, y):
 def eqs_rkc_step(ctx, x, t, dt, s, want_stats=True):
     st = eqs_step_stats() if want_stats else None
     _check(lib().eqs_rkc_step(ctx, _dev(x), t, dt, s, C.byref(st) if st is not None else None), ctx)
+    return st
+
+
+def eqs_rkc_adaptive_step(ctx, x, t, h_try, atol, rtol, s_max=EQS_MAX_STAGES):
+    """One accepted adaptive RKC step from t (x: CUDA float64 node vector)."""
+    st = eqs_adapt_stats()
+    _check(lib().eqs_rkc_adaptive_step(ctx, _dev(x), t, h_try, atol, rtol, s_max, C.byref(st)), ctx)
     return st
 
 
