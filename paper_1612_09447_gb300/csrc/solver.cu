@@ -165,7 +165,14 @@ static cudaError_t upload_sell(eqs_ctx* c, const HostCSR& A, DevSell<T>& S, bool
       return upload(c, &S.val, val.data(), val.size());
     }
   }
-  S.G = allow_groups ? lanes_for(A.n_rows ? (double)A.nnz() / (double)A.n_rows : 0.0) : 1;
+  const double mean_row = A.n_rows ? (double)A.nnz() / (double)A.n_rows : 0.0;
+  S.G = allow_groups ? lanes_for(mean_row) : 1;
+  // small levels: more lanes per row until the rows fill the resident
+  // threads (latency of long rows shared by a lane group, not serialised)
+  if (allow_groups) {
+    const int64_t resident = (int64_t)std::max(c->sms, 1) * 2048;
+    while (S.G < 32 && S.G < mean_row && A.n_rows * (int64_t)S.G * 2 <= resident) S.G *= 2;
+  }
   S.logG = 0;
   while ((1 << S.logG) < S.G) ++S.logG;
   if (S.G > 1) {  // CSR, G lanes per row
