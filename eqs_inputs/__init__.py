@@ -19,6 +19,10 @@ from .mesh import (  # noqa: F401
     splitmix64,
     uniform01,
     kuhn_cube,
+    kuhn_cube_p2,
+    P2_EDGES,
+    dirichlet_tags_p2,
+    make_problem_p2,
     tag_materials_block,
     tag_materials_spheres,
     dirichlet_tags,

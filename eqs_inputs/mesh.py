@@ -105,6 +105,47 @@ def kuhn_cube(N: int, L: float = L_CUBE, jitter: float = 0.0, seed: int = 0):
     return xyz, tets.reshape(-1, 4).astype(np.int32)
 
 
+# P2 (10-node) tets: vertex order as kuhn_cube, then the midpoints of the
+# edges (0,1), (0,2), (0,3), (1,2), (1,3), (2,3).
+P2_EDGES = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
+
+
+def kuhn_cube_p2(N: int, L: float = L_CUBE, jitter: float = 0.0, seed: int = 0):
+    """Return (xyz[(2N+1)^3, 3], tets[6 N^3, 10]) of the quadratic mesh.
+
+    Every node of the (2N+1)^3 refined grid is a vertex (even refined
+    coordinates) or the midpoint of exactly one edge of the Kuhn split.
+    Vertices sit where ``kuhn_cube`` puts them (same jitter draws), edges are
+    straight: a midpoint node is the mean of its edge's two vertices.  Node
+    index I + R (J + R K), R = 2N + 1, refined coordinates (I, J, K).
+    """
+    xyz1, tets1 = kuhn_cube(N, L, jitter, seed)
+    n1, R = N + 1, 2 * N + 1
+    v = tets1.astype(np.int64)
+    vi, vj, vk = v % n1, (v // n1) % n1, v // (n1 * n1)
+    ref = np.stack([2 * vi, 2 * vj, 2 * vk], axis=2)  # (T, 4, 3) refined coordinates
+    ids = np.empty((len(tets1), 10), dtype=np.int64)
+    ids[:, :4] = ref[:, :, 0] + R * (ref[:, :, 1] + R * ref[:, :, 2])
+    xyz = np.full((R ** 3, 3), np.nan)
+    xyz[ids[:, :4].reshape(-1)] = xyz1[v.reshape(-1)]
+    for e, (a, b) in enumerate(P2_EDGES):
+        m = (ref[:, a] + ref[:, b]) // 2
+        ids[:, 4 + e] = m[:, 0] + R * (m[:, 1] + R * m[:, 2])
+        xyz[ids[:, 4 + e]] = 0.5 * (xyz1[v[:, a]] + xyz1[v[:, b]])
+    if np.isnan(xyz).any():
+        raise AssertionError("refined grid node without an edge")
+    return xyz, ids.astype(np.int32)
+
+
+def dirichlet_tags_p2(N: int) -> np.ndarray:
+    """Refined-grid tags: 1 on z = 0, 2 on z = L, 0 elsewhere."""
+    R = 2 * N + 1
+    tag = np.zeros(R ** 3, dtype=np.uint8)
+    tag[: R * R] = 1
+    tag[-R * R:] = 2
+    return tag
+
+
 def _centroids(xyz, tets):
     return xyz[tets].mean(axis=1)
 
@@ -183,6 +224,16 @@ def make_problem(N, *, jitter=0.0, seed=CONFIG_SEED, varistor="block", block=(1 
         raise ValueError(varistor)
     return Problem(N, xyz, tets, mat, dirichlet_tags(N), (BACKGROUND, VARISTOR),
                    V0, freq, phase, s, steps, name)
+
+
+def make_problem_p2(N, *, jitter=0.0, seed=CONFIG_SEED, block=(1 / 3, 2 / 3), V0=1e4, freq=50.0,
+                    phase=0.0, s=10, steps=1, name=""):
+    """Quadratic (P2) problem on the N^3-cell Kuhn cube with the block
+    varistor (material by the centroid of the tet's four vertices)."""
+    xyz, tets = kuhn_cube_p2(N, L_CUBE, jitter, seed)
+    mat = tag_materials_block(xyz, tets[:, :4], block[0] * L_CUBE, block[1] * L_CUBE)
+    return Problem(N, xyz, tets, mat, dirichlet_tags_p2(N), (BACKGROUND, VARISTOR),
+                   V0, freq, phase, s, steps, name or f"p2_cube{N}")
 
 
 def sphere_centres(seed: int, count: int = 2, radius: float = 0.02):

@@ -87,7 +87,11 @@ def local_matrices(G, V, coef):
 
 
 def apply_K(xyz, tets, tet_mat, materials, x):
-    """y = K(x) x, formed tet by tet and scattered into y (Section III)."""
+    """y = K(x) x, formed tet by tet and scattered into y (Section III).
+    10-node tets go to the P2 element (oracle.fem_p2)."""
+    if tets.shape[1] == 10:
+        from . import fem_p2
+        return fem_p2.apply_K(xyz, tets, tet_mat, materials, x)
     G, V = tet_geometry(xyz, tets)
     kap, _ = tet_kappa(xyz, tets, tet_mat, materials, x, G)
     Ke = local_matrices(G, V, kap)
@@ -108,6 +112,9 @@ def _assemble(n, tets, Ke):
 
 def assemble_K(xyz, tets, tet_mat, materials, x):
     """Global CSR K(x) (classical assembly), all nodes, before Dirichlet BCs."""
+    if tets.shape[1] == 10:
+        from . import fem_p2
+        return fem_p2.assemble_K(xyz, tets, tet_mat, materials, x)
     G, V = tet_geometry(xyz, tets)
     kap, _ = tet_kappa(xyz, tets, tet_mat, materials, x, G)
     return _assemble(len(xyz), tets, local_matrices(G, V, kap))
@@ -121,6 +128,9 @@ def tet_eps(tet_mat, materials):
 
 def assemble_M(xyz, tets, tet_mat, materials):
     """Global CSR M (eps-weighted Laplace-type "mass" matrix of Eq. 2)."""
+    if tets.shape[1] == 10:
+        from . import fem_p2
+        return fem_p2.assemble_M(xyz, tets, tet_mat, materials)
     G, V = tet_geometry(xyz, tets)
     return _assemble(len(xyz), tets, local_matrices(G, V, tet_eps(tet_mat, materials)))
 
