@@ -156,6 +156,18 @@ void eqs_opts_default(eqs_opts* o);
 eqs_status eqs_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets,
                            int64_t n_tets, const uint8_t* node_tag, eqs_ctx** out);
 
+/* Quadratic (P2) mesh (Section V's 2nd order ansatz functions): as
+ * eqs_mesh_create with tets10: host, n_tets x 10 int32 node indices, the
+ * four vertices (positively oriented) followed by the midpoint nodes of the
+ * edges (0,1), (0,2), (0,3), (1,2), (1,3), (2,3) (straight edges).  K(x)x
+ * and M use the ten quadratic shape functions with the symmetric 4-point
+ * quadrature rule of degree 2 (the conductivity is evaluated at each
+ * quadrature point).  The single-trajectory paths (apply, solve, step,
+ * adaptive step, start vectors) accept it; the ensemble and batched serving
+ * take linear tets only. */
+eqs_status eqs_mesh_create_p2(const double* xyz, int64_t n_nodes, const int32_t* tets10,
+                              int64_t n_tets, const uint8_t* node_tag, eqs_ctx** out);
+
 /* Material of every tet (Eq. 1 coefficients).  tet_mat: host, n_tets bytes,
  * values < n_mat; mats: host array of n_mat (1..255) laws.
  * Errors: EQS_ERR_ARG, EQS_ERR_MESH (id out of range), EQS_ERR_STATE. */

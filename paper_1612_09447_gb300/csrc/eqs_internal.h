@@ -114,7 +114,9 @@ struct eqs_ctx {
   // ---- mesh (host copies)
   int64_t n_nodes = 0, n_tets = 0, n_free = 0;
   std::vector<double> xyz;          // mesh order, n x 3
-  std::vector<int32_t> tets;        // mesh order, oriented (positive volume)
+  std::vector<int32_t> tets;        // mesh order, npe nodes per tet (vertices first)
+  int npe = 4;                       // nodes per tet: 4 (P1) or 10 (P2: + edge midpoints)
+  int32_t* d_conn10 = nullptr;       // P2: 10 x n_tets internal node ids (node-major)
   std::vector<uint8_t> tag;         // mesh order
   std::vector<int32_t> internal_of_node, node_of_internal;  // free first
   std::vector<uint8_t> tet_mat;

@@ -1,6 +1,7 @@
 // Host-side, run-once setup of the EQS RKC library:
 //  - mesh validation and the internal node numbering (free nodes first);
-//  - assembly of the constant matrix M of Eq. 2 (eps-weighted P1 Laplacian)
+//  - assembly of the constant matrix M of Eq. 2 (eps-weighted Laplacian of
+//    the P1 or P2 elements)
 //    restricted to free nodes, and M_fd 1_top (the Dirichlet coupling that
 //    carries the drive into the right-hand side b of Eq. 2);
 //  - the smoothed-aggregation AMG hierarchy of M_ff, built once and reused
@@ -39,9 +40,10 @@ eqs_status validate_and_orient(eqs_ctx* c) {
     return EQS_ERR_MESH;
   }
   c->n_free = n_free;
+  const int npe = c->npe;
   for (int64_t e = 0; e < c->n_tets; ++e) {
-    const int32_t* t = &c->tets[4 * e];
-    for (int k = 0; k < 4; ++k)
+    const int32_t* t = &c->tets[(int64_t)npe * e];
+    for (int k = 0; k < npe; ++k)
       if (t[k] < 0 || t[k] >= n) {
         c->err = "tet " + std::to_string(e) + " has node index out of range";
         return EQS_ERR_MESH;
@@ -105,20 +107,54 @@ static void tet_gradients(const double* xyz, const int32_t* t, double G[4][3], d
   V = det / 6.0;
 }
 
-// M = sum_e eps_e V_e G_e G_e^T; rows/cols of free nodes in internal
-// numbering (= ascending mesh order); mtop = M_fd 1_top.
+// Row a of the local matrix integral of grad N_a . grad N_b over a P2 tet
+// (vertices first, then the edges (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)),
+// times w: the symmetric 4-point rule of degree 2 (exact: the integrand is
+// quadratic).  grad N of vertex k = (4 l_k - 1) grad l_k, of edge (k, l) =
+// 4 (l_k grad l_l + l_l grad l_k).
+static const int kP2Edge[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+static void p2_grad(const double G[4][3], const double lam[4], int i, double g[3]) {
+  if (i < 4) {
+    for (int d = 0; d < 3; ++d) g[d] = (4.0 * lam[i] - 1.0) * G[i][d];
+  } else {
+    const int k = kP2Edge[i - 4][0], l = kP2Edge[i - 4][1];
+    for (int d = 0; d < 3; ++d) g[d] = 4.0 * (lam[k] * G[l][d] + lam[l] * G[k][d]);
+  }
+}
+
+static void p2_row(const double G[4][3], double wV, int a, double row[10]) {
+  const double qa = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, qb = (5.0 - std::sqrt(5.0)) / 20.0;
+  for (int b = 0; b < 10; ++b) row[b] = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    double lam[4] = {qb, qb, qb, qb};
+    lam[q] = qa;
+    double ga[3];
+    p2_grad(G, lam, a, ga);
+    for (int b = 0; b < 10; ++b) {
+      double gb[3];
+      p2_grad(G, lam, b, gb);
+      row[b] += 0.25 * wV * (ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2]);
+    }
+  }
+}
+
+// M = sum_e eps_e (integral of grad N_a . grad N_b): P1 eps_e V_e G_e G_e^T,
+// P2 by quadrature; rows/cols of free nodes in internal numbering
+// (= ascending mesh order); mtop = M_fd 1_top.
 void assemble_M(const eqs_ctx* c, HostCSR& Mff, std::vector<double>& mtop) {
   const int64_t n = c->n_nodes, nf = c->n_free, nt = c->n_tets;
+  const int npe = c->npe;
   // node -> tets incidence
   std::vector<int64_t> nptr(n + 1, 0);
   for (int64_t e = 0; e < nt; ++e)
-    for (int k = 0; k < 4; ++k) nptr[c->tets[4 * e + k] + 1]++;
+    for (int k = 0; k < npe; ++k) nptr[c->tets[(int64_t)npe * e + k] + 1]++;
   for (int64_t i = 0; i < n; ++i) nptr[i + 1] += nptr[i];
   std::vector<int64_t> ntet(nptr[n]);
   {
     std::vector<int64_t> fill(nptr.begin(), nptr.end() - 1);
     for (int64_t e = 0; e < nt; ++e)
-      for (int k = 0; k < 4; ++k) ntet[fill[c->tets[4 * e + k]]++] = e;
+      for (int k = 0; k < npe; ++k) ntet[fill[c->tets[(int64_t)npe * e + k]]++] = e;
   }
   std::vector<double> eps(c->mats.size());
   for (size_t m = 0; m < c->mats.size(); ++m) eps[m] = kEps0 * c->mats[m].eps_r;
@@ -140,14 +176,19 @@ void assemble_M(const eqs_ctx* c, HostCSR& Mff, std::vector<double>& mtop) {
     double top = 0.0;
     for (int64_t q = nptr[node]; q < nptr[node + 1]; ++q) {
       const int64_t e = ntet[q];
-      const int32_t* t = &c->tets[4 * e];
+      const int32_t* t = &c->tets[(int64_t)npe * e];
       double G[4][3], V;
       tet_gradients(c->xyz.data(), t, G, V);
       int a = 0;
       while (t[a] != node) ++a;
       const double w = eps[c->tet_mat[e]] * V;
-      for (int b = 0; b < 4; ++b) {
-        const double v = w * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2]);
+      double row[10];
+      if (npe == 10)
+        p2_row(G, w, a, row);
+      else
+        for (int b = 0; b < 4; ++b) row[b] = w * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2]);
+      for (int b = 0; b < npe; ++b) {
+        const double v = row[b];
         const int32_t cn = c->internal_of_node[t[b]];
         if (cn >= nf) {
           if (c->tag[t[b]] == 2) top += v;

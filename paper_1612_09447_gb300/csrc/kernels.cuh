@@ -884,6 +884,156 @@ __global__ void k_elem32(int64_t nt, const int4* __restrict__ conn, const uint8_
   elem32_tet(e, conn, mat, mats, xh, xl, x, n_limit, y);
 }
 
+// ---------------------------------------------------- P2 element kernels
+// Quadratic tets (Section V's 2nd order ansatz functions): 10 nodes, the
+// vertices then the midpoints of the edges (0,1) (0,2) (0,3) (1,2) (1,3)
+// (2,3); straight edges, so the barycentric gradients are those of the
+// vertices: grad lambda_k = c_k / D (k = 1..3), grad lambda_0 = -sum.  At each
+// point of the symmetric 4-point rule of degree 2 (weights V/4)
+//   grad phi = sum_k a_k grad lambda_k,
+//   a_k = (4 lambda_k - 1) phi_k + 4 sum_{edges (k,l)} lambda_l phi_kl,
+//   s_k = grad lambda_k . grad phi,
+//   vertex k:     r_k  += (V/4) kappa(|grad phi|) (4 lambda_k - 1) s_k,
+//   edge (k, l):  r_kl += (V/4) kappa 4 (lambda_k s_l + lambda_l s_k).
+// Potentials enter as differences to phi_0 (a constant shift moves every a_k
+// by the same amount and sum_k grad lambda_k = 0), and r_0 = -(r_1 + ... +
+// r_9) keeps the local residual's zero sum exactly.
+template <typename R>
+__device__ __forceinline__ R kappa_of(const MaterialDev& m, R E);
+template <>
+__device__ __forceinline__ double kappa_of<double>(const MaterialDev& m, double E) { return kappa64(m, E); }
+template <>
+__device__ __forceinline__ float kappa_of<float>(const MaterialDev& m, float E) { return kappa32(m, E); }
+
+template <typename R>
+__device__ __forceinline__ void p2_residual(const R (&gl)[4][3], R D, const R (&d)[10], const MaterialDev& m,
+                                            R (&r)[10]) {
+  const R QA = (R)0.5854101966249684544613760503096914353161, QB = (R)0.1381966011250105151795413165634361882280;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) r[i] = R(0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    R l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) l[k] = k == q ? QA : QB;
+    R a[4];
+    a[0] = (R(4) * l[0] - R(1)) * d[0] + R(4) * (l[1] * d[4] + l[2] * d[5] + l[3] * d[6]);
+    a[1] = (R(4) * l[1] - R(1)) * d[1] + R(4) * (l[0] * d[4] + l[2] * d[7] + l[3] * d[8]);
+    a[2] = (R(4) * l[2] - R(1)) * d[2] + R(4) * (l[0] * d[5] + l[1] * d[7] + l[3] * d[9]);
+    a[3] = (R(4) * l[3] - R(1)) * d[3] + R(4) * (l[0] * d[6] + l[1] * d[8] + l[2] * d[9]);
+    R g[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[c] = a[0] * gl[0][c] + a[1] * gl[1][c] + a[2] * gl[2][c] + a[3] * gl[3][c];
+    R kap;
+    if (m.is_const) {
+      kap = (R)m.klo;
+    } else {
+      const R E = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) / D;
+      kap = kappa_of<R>(m, E);
+    }
+    R sk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sk[k] = gl[k][0] * g[0] + gl[k][1] * g[1] + gl[k][2] * g[2];
+    const R sc = kap / (R(24) * D);  // (V/4) / D^2 with V = D/6
+#pragma unroll
+    for (int k = 1; k < 4; ++k) r[k] += sc * (R(4) * l[k] - R(1)) * sk[k];
+    r[4] += sc * R(4) * (l[0] * sk[1] + l[1] * sk[0]);
+    r[5] += sc * R(4) * (l[0] * sk[2] + l[2] * sk[0]);
+    r[6] += sc * R(4) * (l[0] * sk[3] + l[3] * sk[0]);
+    r[7] += sc * R(4) * (l[1] * sk[2] + l[2] * sk[1]);
+    r[8] += sc * R(4) * (l[1] * sk[3] + l[3] * sk[1]);
+    r[9] += sc * R(4) * (l[2] * sk[3] + l[3] * sk[2]);
+  }
+  R s0 = R(0);
+#pragma unroll
+  for (int i = 1; i < 10; ++i) s0 += r[i];
+  r[0] = -s0;
+}
+
+template <typename R>
+__device__ __forceinline__ void p2_gradients(const R (&e)[3][3], R (&gl)[4][3], R& D) {
+  // c_1 = e_2 x e_3, c_2 = e_3 x e_1, c_3 = e_1 x e_2; D = e_1 . c_1
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const R* a = e[(k + 1) % 3];
+    const R* b = e[(k + 2) % 3];
+    gl[k + 1][0] = a[1] * b[2] - a[2] * b[1];
+    gl[k + 1][1] = a[2] * b[0] - a[0] * b[2];
+    gl[k + 1][2] = a[0] * b[1] - a[1] * b[0];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) gl[0][c] = -(gl[1][c] + gl[2][c] + gl[3][c]);
+  D = e[0][0] * gl[1][0] + e[0][1] * gl[1][1] + e[0][2] * gl[1][2];
+}
+
+__global__ void k_elem64_p2(int64_t nt, const int32_t* __restrict__ conn10, const uint8_t* __restrict__ mat,
+                            const MaterialDev* __restrict__ mats, const double4* __restrict__ xyz,
+                            const double* __restrict__ x, int n_limit, double sign, double* __restrict__ y) {
+  pdl_enter();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt) return;
+  int t[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) t[k] = __ldg(conn10 + (int64_t)k * nt + e);
+  const double4 p0 = xyz[t[0]];
+  double ed[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double4 pk = xyz[t[k + 1]];
+    ed[k][0] = pk.x - p0.x;
+    ed[k][1] = pk.y - p0.y;
+    ed[k][2] = pk.z - p0.z;
+  }
+  double gl[4][3], D;
+  p2_gradients<double>(ed, gl, D);
+  const double f0 = __ldg(x + t[0]);
+  double d[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) d[k] = k == 0 ? 0.0 : __ldg(x + t[k]) - f0;
+  double r[10];
+  p2_residual<double>(gl, D, d, mats[mat[e]], r);
+#pragma unroll
+  for (int k = 0; k < 10; ++k)
+    if (t[k] < n_limit) atomicAdd(y + t[k], sign * r[k]);
+}
+
+// Mixed precision: coordinates and potentials as FP32 (hi, lo) pairs,
+// differences formed as (hi_a - hi_b) + (lo_a - lo_b), the rest in FP32.
+__global__ void k_elem32_p2(int64_t nt, const int32_t* __restrict__ conn10, const uint8_t* __restrict__ mat,
+                            const MaterialDev* __restrict__ mats, const float4* __restrict__ xh,
+                            const float4* __restrict__ xl, const float2* __restrict__ x, int n_limit,
+                            float* __restrict__ y) {
+  pdl_enter();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt) return;
+  int t[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) t[k] = __ldg(conn10 + (int64_t)k * nt + e);
+  const float4 h0 = xh[t[0]], l0 = xl[t[0]];
+  float ed[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 hk = xh[t[k + 1]], lk = xl[t[k + 1]];
+    ed[k][0] = (hk.x - h0.x) + (lk.x - l0.x);
+    ed[k][1] = (hk.y - h0.y) + (lk.y - l0.y);
+    ed[k][2] = (hk.z - h0.z) + (lk.z - l0.z);
+  }
+  float gl[4][3], D;
+  p2_gradients<float>(ed, gl, D);
+  const float2 f0 = x[t[0]];
+  float d[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    const float2 fk = x[t[k]];
+    d[k] = k == 0 ? 0.f : (fk.x - f0.x) + (fk.y - f0.y);
+  }
+  float r[10];
+  p2_residual<float>(gl, D, d, mats[mat[e]], r);
+#pragma unroll
+  for (int k = 0; k < 10; ++k)
+    if (t[k] < n_limit) atomicAdd(y + t[k], r[k]);
+}
+
 // ------------------------------------------------------------- RKC pieces
 __device__ __forceinline__ float2 split2(double v) {
   const float h = (float)v;

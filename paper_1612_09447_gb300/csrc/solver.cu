@@ -649,6 +649,17 @@ static bool mixed(const eqs_ctx* c) { return c->opts.precision == EQS_PREC_MIXED
 // ------------------------------------------------------------ element
 static void elem_launch(eqs_ctx* c, cudaStream_t st, const double* Y, int n_limit, double* y64,
                         float* y32) {
+  if (c->npe == 10) {  // quadratic tets
+    if (mixed(c))
+      launch(k_elem32_p2, nblk(c->n_tets), kBlock, st, c->n_tets, (const int32_t*)c->d_conn10,
+             (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi,
+             (const float4*)c->d_xyz_lo, (const float2*)c->d_Y32, n_limit, y32);
+    else
+      launch(k_elem64_p2, nblk(c->n_tets), kBlock, st, c->n_tets, (const int32_t*)c->d_conn10,
+             (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats, (const double4*)c->d_xyz, Y, n_limit,
+             y64 == c->d_R ? -1.0 : 1.0, y64);
+    return;
+  }
   if (mixed(c))
     launch(k_elem32, nblk(c->n_tets), kBlock, st, c->n_tets, c->d_conn, c->d_mat, c->d_mats,
                                                  c->d_xyz_hi, c->d_xyz_lo, c->d_Y32, n_limit, y32);
@@ -864,6 +875,7 @@ static eqs_status ens_alloc(eqs_ctx* c) {
   if (c->ens_ready) return EQS_OK;
   if (!mixed(c) || !c->d_M_hi || !c->d_cinv_hi)
     return fail(c, EQS_ERR_STATE, "the ensemble needs a context set up in EQS_PREC_MIXED with split_m 1");
+  if (c->npe != 4) return fail(c, EQS_ERR_STATE, "the ensemble runs linear (4-node) tets");
   if (c->opts.guess != EQS_GUESS_PREV && c->opts.guess != EQS_GUESS_SPE)
     return fail(c, EQS_ERR_STATE, "the ensemble starts from EQS_GUESS_PREV or EQS_GUESS_SPE");
   const int64_t n = c->n_nodes, nf = c->n_free;
@@ -1170,8 +1182,21 @@ void eqs_opts_default(eqs_opts* o) {
   o->pod_min_iters = 3;
 }
 
+static eqs_status mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                              int npe, const uint8_t* node_tag, eqs_ctx** out);
+
 eqs_status eqs_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
                            const uint8_t* node_tag, eqs_ctx** out) {
+  return mesh_create(xyz, n_nodes, tets, n_tets, 4, node_tag, out);
+}
+
+eqs_status eqs_mesh_create_p2(const double* xyz, int64_t n_nodes, const int32_t* tets10, int64_t n_tets,
+                              const uint8_t* node_tag, eqs_ctx** out) {
+  return mesh_create(xyz, n_nodes, tets10, n_tets, 10, node_tag, out);
+}
+
+static eqs_status mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                              int npe, const uint8_t* node_tag, eqs_ctx** out) {
   if (!out) return fail(nullptr, EQS_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!xyz || !tets || !node_tag || n_nodes <= 0 || n_tets <= 0)
@@ -1182,7 +1207,8 @@ eqs_status eqs_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* te
   c->n_nodes = n_nodes;
   c->n_tets = n_tets;
   c->xyz.assign(xyz, xyz + 3 * n_nodes);
-  c->tets.assign(tets, tets + 4 * n_tets);
+  c->npe = npe;
+  c->tets.assign(tets, tets + (int64_t)npe * n_tets);
   c->tag.assign(node_tag, node_tag + n_nodes);
   eqs_opts_default(&c->opts);
   eqs_status st = validate_and_orient(c);
@@ -1273,10 +1299,17 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
   const int64_t n = c->n_nodes, nf = c->n_free;
   // mesh data in internal numbering
   std::vector<int4> conn(c->n_tets);
+  const int npe = c->npe;
   for (int64_t e = 0; e < c->n_tets; ++e) {
-    const int32_t* t = &c->tets[4 * e];
+    const int32_t* t = &c->tets[(int64_t)npe * e];
     conn[e] = make_int4(c->internal_of_node[t[0]], c->internal_of_node[t[1]], c->internal_of_node[t[2]],
                         c->internal_of_node[t[3]]);
+  }
+  std::vector<int32_t> conn10;
+  if (npe == 10) {  // node-major: entry k of tet e at k * n_tets + e (coalesced per k)
+    conn10.resize((size_t)10 * c->n_tets);
+    for (int64_t e = 0; e < c->n_tets; ++e)
+      for (int k = 0; k < 10; ++k) conn10[(size_t)k * c->n_tets + e] = c->internal_of_node[c->tets[10 * e + k]];
   }
   std::vector<double4> xyz(n);
   std::vector<float4> xh(n), xl(n);
@@ -1305,6 +1338,8 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     md[m].pad = 0;
   }
   CK(upload(c, &c->d_conn, conn.data(), conn.size()));
+  c->d_conn10 = nullptr;
+  if (npe == 10) CK(upload(c, &c->d_conn10, conn10.data(), conn10.size()));
   CK(upload(c, &c->d_mat, c->tet_mat.data(), c->tet_mat.size()));
   CK(upload(c, &c->d_mats, md.data(), md.size()));
   CK(upload(c, &c->d_xyz, xyz.data(), xyz.size()));
@@ -1481,7 +1516,15 @@ eqs_status eqs_apply_K_static(eqs_ctx* c, const double* x, double* y) {
   k_gather_perm<<<nblk(n), kBlock, 0, st>>>(n, x, c->d_node_of_internal, xg, mx ? x2 : nullptr);
   // the accumulator keeps the previous call's contents: clear it
   CK(cudaMemsetAsync(yacc, 0, (size_t)n * (mx ? sizeof(float) : sizeof(double)), st));
-  if (mx) {
+  if (mx && c->npe == 10) {
+    k_elem32_p2<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn10, c->d_mat, c->d_mats, c->d_xyz_hi,
+                                                    c->d_xyz_lo, x2, n, (float*)yacc);
+    k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, nullptr, (const float*)yacc, c->d_node_of_internal, y);
+  } else if (c->npe == 10) {
+    k_elem64_p2<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn10, c->d_mat, c->d_mats, c->d_xyz, xg, n,
+                                                    1.0, (double*)yacc);
+    k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, (const double*)yacc, nullptr, c->d_node_of_internal, y);
+  } else if (mx) {
     k_elem32<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn, c->d_mat, c->d_mats, c->d_xyz_hi,
                                                  c->d_xyz_lo, x2, n, (float*)yacc);
     k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, nullptr, (const float*)yacc, c->d_node_of_internal, y);
@@ -2246,6 +2289,7 @@ eqs_status eqs_batch_create(eqs_ctx* const* ctxs, int n, int rows_per_block, eqs
     if (!ctxs[k] || !ctxs[k]->setup_done) return bfail(nullptr, EQS_ERR_STATE, "every context must be set up");
     if (ctxs[k]->opts.precision != EQS_PREC_MIXED)
       return bfail(nullptr, EQS_ERR_ARG, "batched stages run in mixed precision");
+    if (ctxs[k]->npe != 4) return bfail(nullptr, EQS_ERR_ARG, "batched stages run linear (4-node) tets");
     if (ctxs[k]->device != ctxs[0]->device) return bfail(nullptr, EQS_ERR_ARG, "contexts on different devices");
     if (ctxs[k]->opts.rtol != ctxs[0]->opts.rtol) return bfail(nullptr, EQS_ERR_ARG, "contexts differ in rtol");
   }

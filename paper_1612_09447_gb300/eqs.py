@@ -89,6 +89,7 @@ def _declare(L):
     sig = {
         "eqs_opts_default": (None, [C.POINTER(eqs_opts)]),
         "eqs_mesh_create": (I, [P, I64, P, I64, P, C.POINTER(C.c_void_p)]),
+        "eqs_mesh_create_p2": (I, [P, I64, P, I64, P, C.POINTER(C.c_void_p)]),
         "eqs_set_materials": (I, [P, P, I, P]),
         "eqs_set_dirichlet": (I, [P, D, D, D]),
         "eqs_amg_setup": (I, [P, C.POINTER(eqs_opts)]),
@@ -161,11 +162,13 @@ def eqs_opts_default():
 
 
 def eqs_mesh_create(xyz, tets, node_tag):
+    """Linear (n_tets x 4) or quadratic (n_tets x 10) tetrahedral mesh."""
     xyz, pxyz = _host(xyz, np.float64)
     tets, ptets = _host(tets, np.int32)
     tag, ptag = _host(node_tag, np.uint8)
     out = C.c_void_p()
-    _check(lib().eqs_mesh_create(pxyz, len(xyz), ptets, len(tets), ptag, C.byref(out)))
+    create = lib().eqs_mesh_create_p2 if tets.ndim == 2 and tets.shape[1] == 10 else lib().eqs_mesh_create
+    _check(create(pxyz, len(xyz), ptets, len(tets), ptag, C.byref(out)))
     return out
 
 

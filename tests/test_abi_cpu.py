@@ -96,6 +96,30 @@ def test_host_amg_matches_oracle(E, cfg, N):
     E.eqs_destroy(ctx)
 
 
+@pytest.mark.parametrize("N,jitter", [(4, 0.0), (5, 0.2)])
+def test_host_amg_matches_oracle_p2(E, N, jitter):
+    """Quadratic tets: the host assembly of M (10-node shape functions,
+    4-point rule) gives the oracle's matrix pattern and the same hierarchy."""
+    p = ei.make_problem_p2(N, jitter=jitter, seed=3)
+    ctx = _host_setup(E, p)
+    rows, nnz = E.eqs_amg_info(ctx)
+    H = amg.SAHierarchy(system.EQSSystem(p).Mff)
+    assert rows == [l.n for l in H.levels]
+    assert nnz[0] == H.levels[0].A.nnz
+    for l in range(len(rows) - 1):
+        assert np.array_equal(E.eqs_amg_aggregates(ctx, l, rows[l]), H.levels[l].agg)
+    E.eqs_destroy(ctx)
+
+
+def test_p2_mesh_validation(E):
+    p = ei.make_problem_p2(2)
+    bad = p.tets.copy()
+    bad[0, 7] = p.n_nodes  # a midpoint index out of range
+    with pytest.raises(E.EqsError) as ex:
+        E.eqs_mesh_create(p.xyz, bad, p.node_tag)
+    assert ex.value.status == E.EQS_ERR_MESH
+
+
 def test_call_order_errors(E):
     p = ei.make_problem(2)
     ctx = E.eqs_mesh_create(p.xyz, p.tets, p.node_tag)
