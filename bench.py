@@ -325,6 +325,8 @@ def run_ours(args, rank, world):
 
     if not args.no_fp64:
         variants["adaptive_mixed_spe"] = measure_adaptive(torch, eqs, p, make, max(4, args.steps // 2))
+        if CONFIG_INDEX == 1 and args.N is None:
+            variants["p2_cube32_mixed_spe"] = measure_p2(torch, eqs, flush, max(3, args.steps // 4))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -400,6 +402,39 @@ def measure_ensemble(torch, eqs, p, make, flush, steps, warmup, guess=None):
             "cg_iters_per_solve_by_column": [float(v) for v in np.mean(iters, axis=0)],
             "cg_passes_per_stage": passes / (steps * S_STAGES), "drive_scales": list(ENS_SCALES),
             "gpu_launches_per_step": launches / steps}
+
+
+def measure_p2(torch, eqs, flush, steps):
+    """Quadratic (P2) elements on the 32^3-cell cube: the same 274,625 nodes
+    as the 64^3 P1 cube, about twice the matrix non-zeros per row; mixed
+    precision with SPE, s = 20 at the stability bound."""
+    import eqs_inputs as ei
+
+    q = ei.make_problem_p2(32)
+    S = eqs.Solver(q, precision=eqs.EQS_PREC_MIXED, rtol=RTOL, spe_n=SPE_N, **SOLVER_OPTS)
+    eqs.eqs_set_guess(S.ctx, eqs.EQS_GUESS_SPE)
+    rows, nnz = S.amg_info()
+    dt = S.dt_bound(S_STAGES)
+    x = torch.zeros(q.n_nodes, dtype=torch.float64, device="cuda")
+    t = 0.0
+    for _ in range(2):
+        S.step(x, t, dt, S_STAGES)
+        t += dt
+    times, iters = [], 0
+    for _ in range(steps):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        S.step(x, t, dt, S_STAGES, stats=False)
+        e1.record()
+        st = S.last_stats()
+        times.append(e0.elapsed_time(e1))
+        iters += st.total_iters
+        t += dt
+    S.close()
+    return {"value": q.n_free * S_STAGES * steps / (sum(times) / 1e3), "ms_per_step": sum(times) / steps,
+            "n_free": q.n_free, "nnz_per_row": nnz[0] / rows[0], "cg_iters_per_solve": iters / (steps * S_STAGES)}
 
 
 def measure_adaptive(torch, eqs, p, make, steps):

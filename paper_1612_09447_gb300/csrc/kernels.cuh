@@ -593,6 +593,49 @@ __global__ void k_pcg_dots(int n, const double* __restrict__ r, const double* __
   }
 }
 
+// Level-0 post-smoothing step of a degree-1 V-cycle fused with the CG dot
+// products: r = b - A x, d = D^-1 r / theta, and the preconditioned residual
+// z = x + d (FP32 z32 for the split-M operator pass, else FP64 zd); sums
+// r_cg.z and r_prev.z; the last block forms beta (as k_pcg_dots).  Saves
+// one kernel per CG iteration: every value it needs is row-local.
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 4)
+k_post_first_dots(DevSell<T> A, int n, const T* __restrict__ b, const T* __restrict__ x,
+                  const T* __restrict__ dinv, T inv_theta, const double* __restrict__ rcg,
+                  const double* __restrict__ rprev, double* __restrict__ zd, float* __restrict__ z32,
+                  PcgScalars* sc, double* partials, unsigned int* counter, int max_blocks, int flexible) {
+  pdl_enter();
+  double v[2] = {0.0, 0.0};
+  EQS_ROWS2(A, n, {
+    const T a0 = mat_row(A, t0, n, x);
+    const T a1 = mat_row(A, t1, n, x);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t t = h ? t1 : t0;
+      if (!row_leader(A, t, n)) continue;
+      const int i = (int)(t >> A.logG);
+      const T r = b[i] - (h ? a1 : a0);
+      const T zt = x[i] + dinv[i] * r * inv_theta;
+      const double zi = (double)zt;
+      if (z32)
+        z32[i] = (float)zt;
+      else
+        zd[i] = zi;
+      v[0] += rcg[i] * zi;
+      v[1] += rprev[i] * zi;
+    }
+  })
+  double tot[2];
+  if (grid_sum<2>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    const double rz = tot[0];
+    double beta = 0.0;
+    if (sc->it > 0) beta = flexible ? (rz - tot[1]) / sc->rz_old : rz / sc->rz_old;
+    sc->beta = beta;
+    sc->rz = rz;
+    sc->rz_old = rz;
+  }
+}
+
 // p = z + beta p and q = M p through q = M z + beta q (M p_old = q_old), so
 // p and q stay row-local and M costs one FMA per non-zero; p.q and alpha.
 __global__ void k_pcg_pq(DevSell<double> M, int n, const double* __restrict__ zd, double* __restrict__ p,

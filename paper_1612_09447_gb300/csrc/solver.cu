@@ -288,7 +288,8 @@ static cudaError_t upload_levels(eqs_ctx* c, std::vector<DevLevel<T>>& L) {
 // Returns the Chebyshev direction still to be added to the level's x (the
 // degree-1 post-smoother's d, folded into the consumer of x), or nullptr.
 template <typename T>
-static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStream_t st) {
+static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStream_t st,
+                       bool fuse_dots = false) {
   const int nl = (int)L.size();
   DevLevel<T>& V = L[l];
   if (l == nl - 1) {
@@ -327,6 +328,12 @@ static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStrea
   T* cpend = vcycle_level(c, L, l + 1, st);
   launch(k_prolong<T>, mat_grid(c, V.P, V.n), kBlock, st, V.P, V.n, C.x,
          (const T*)cpend, V.x);
+  if (fuse_dots && l == 0 && deg == 1) {  // the CG dot products ride on the last smoothing pass
+    launch(k_post_first_dots<T>, g, kBlock, st, V.A, V.n, (const T*)V.b, (const T*)V.x, (const T*)V.dinv,
+           (T)V.inv_theta, (const double*)c->d_r, (const double*)c->d_rprev, c->d_zd, c->d_z32, c->d_sc,
+           c->red.partials, c->red.counter, c->red.max_blocks, c->opts.flexible);
+    return nullptr;
+  }
   launch(k_post_first<T>, g, kBlock, st, V.A, V.n, V.b, V.x, V.dinv, (T)V.inv_theta, V.r, V.dA);
   din = V.dA;
   dout = V.dB;
@@ -468,9 +475,11 @@ static void pcg_body_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_
   DevLevel<T>& V = L[0];
   const int n = (int)c->n_free;
   const int g = vec_grid(c, n);
-  T* zpend = vcycle_level(c, L, 0, st);
-  launch(k_pcg_dots<T>, g, kBlock, st, n, c->d_r, c->d_rprev, V.x, (const T*)zpend, c->d_zd, c->d_z32,
-         c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks, c->opts.flexible);
+  const bool fuse = c->opts.cheb_degree == 1 && L.size() > 1;
+  T* zpend = vcycle_level(c, L, 0, st, fuse);
+  if (!fuse)
+    launch(k_pcg_dots<T>, g, kBlock, st, n, c->d_r, c->d_rprev, V.x, (const T*)zpend, c->d_zd, c->d_z32,
+           c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks, c->opts.flexible);
   if (c->d_z32)  // mixed path: FP32 z, split-M operator pass
     launch(k_pcg_pq_split, g, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo, n,
            (const float*)c->d_z32, c->d_p, c->d_q, c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks);
