@@ -54,7 +54,10 @@ SOLVER_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0)
 SPE_N = 6  # solutions spanning the SPE subspace
 # DRAM bytes (read + write) of one k_spmv64 launch per workload from an ncu
 # capture (profiles/k_spmv64_cube64.md); None where not captured.
-TRAFFIC_SPMV64 = {1: 34096128, 2: None}
+TRAFFIC_SPMV64 = {1: None, 2: None}
+# DRAM bytes (read + write) of one k_spmv_split launch per workload from an
+# ncu capture (profiles/k_spmv_split.md); None where not captured.
+TRAFFIC_SPLIT = {1: None, 2: None}
 
 
 def parse():
@@ -476,34 +479,47 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def dominant_kernel_roofline(torch, eqs, solver, p, flush):
-    """FP64 M SpMV (the CG operator, the SpMV of every CG iteration) timed
-    alone: algorithmic bytes = stored SELL values/indices + x gather + y."""
-    nf = p.n_free
-    rows, nnz = solver.amg_info()
-    x = torch.randn(nf, dtype=torch.float64, device="cuda")
-    y = torch.empty_like(x)
+def _time_launches(torch, fn, flush, reps=20):
     ts = []
-    for _ in range(20):
+    for _ in range(reps):
         flush()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        eqs.eqs_spmv_M(solver.ctx, x, y)
+        fn()
         e1.record()
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
-    ms = statistics.median(ts[3:])
-    # algorithmic bytes of y = M_ff x: one FP64 value per stored non-zero plus
-    # x and y once per row (the layout needs no index loads: DIA storage)
-    bytes_alg = nnz[0] * 8 + nf * 8 * 2
+    return statistics.median(ts[3:])
+
+
+def dominant_kernel_roofline(torch, eqs, solver, p, flush):
+    """The CG operator product M z of the timed mixed path (k_spmv_split:
+    M as two FP32 parts, FP32 z, FP32-pair row sums; the same row product
+    as k_pcg_pq_split) timed alone with CUDA events on the launch stream,
+    L2 flushed before each launch.  Algorithmic bytes per launch: 8 B per
+    non-zero (hi + lo) + 4 B of z and 8 B of y per row.  The FP64 product
+    (k_spmv64, the FP64 path's operator) is reported beside it."""
+    nf = p.n_free
+    rows, nnz = solver.amg_info()
+    z = torch.randn(nf, dtype=torch.float32, device="cuda")
+    x = z.double()
+    y = torch.empty(nf, dtype=torch.float64, device="cuda")
     peak, kind = _peaks()
-    ach = bytes_alg / (ms / 1e3) / 1e9
-    return {"kernel": "k_spmv64 (FP64 DIA SpMV of M_ff, the operator of every CG iteration)",
+    ms32 = _time_launches(torch, lambda: eqs.eqs_spmv_M32(solver.ctx, z, y), flush)
+    b32 = nnz[0] * 8 + nf * (4 + 8)
+    ms64 = _time_launches(torch, lambda: eqs.eqs_spmv_M(solver.ctx, x, y), flush)
+    b64 = nnz[0] * 8 + nf * 8 * 2
+    ach = b32 / (ms32 / 1e3) / 1e9
+    a64 = b64 / (ms64 / 1e3) / 1e9
+    return {"kernel": "k_spmv_split (mixed-path CG operator product M z, as in k_pcg_pq_split)",
             "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": TRAFFIC_SPMV64.get(CONFIG_INDEX), "bytes_per_launch": bytes_alg, "ms_per_launch": ms,
-            "fp64_tflops": 2.0 * nnz[0] / (ms / 1e3) / 1e12,
-            "peak_kind": f"{kind} hbm_gbs (burst: kernel timed alone, L2 flushed before each launch)"}
+            "traffic": TRAFFIC_SPLIT.get(CONFIG_INDEX), "bytes_per_launch": b32, "ms_per_launch": ms32,
+            "peak_kind": f"{kind} hbm_gbs (burst: kernel timed alone, L2 flushed before each launch)",
+            "fp64_operator": {"kernel": "k_spmv64 (FP64 DIA SpMV of M_ff)", "achieved": a64, "frac": a64 / peak,
+                              "bytes_per_launch": b64, "ms_per_launch": ms64,
+                              "fp64_tflops": 2.0 * nnz[0] / (ms64 / 1e3) / 1e12,
+                              "traffic": TRAFFIC_SPMV64.get(CONFIG_INDEX)}}
 
 
 def run_batch(args, rank, world):
