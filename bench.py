@@ -53,11 +53,11 @@ WORKLOAD = WORKLOADS[CONFIG_INDEX]
 SOLVER_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0)
 SPE_N = 6  # solutions spanning the SPE subspace
 # DRAM bytes (read + write) of one k_spmv64 launch per workload from an ncu
-# capture (profiles/k_spmv64_cube64.md); None where not captured.
-TRAFFIC_SPMV64 = {1: None, 2: None}
+# capture (profiles/k_spmv_split_cube64.md); None where not captured.
+TRAFFIC_SPMV64 = {1: 33821696, 2: None}
 # DRAM bytes (read + write) of one k_spmv_split launch per workload from an
-# ncu capture (profiles/k_spmv_split.md); None where not captured.
-TRAFFIC_SPLIT = {1: None, 2: None}
+# ncu capture (profiles/k_spmv_split_cube64.md); None where not captured.
+TRAFFIC_SPLIT = {1: 32744704, 2: None}
 
 
 def parse():
