@@ -536,7 +536,9 @@ def run_batch(args, rank, world):
     eqs.lib()
     s = 10
     probs = [ei.config_problem(4, instance=i) for i in range(64)]
-    solvers = [eqs.Solver(p, precision=eqs.EQS_PREC_MIXED, rtol=RTOL, **SOLVER_OPTS) for p in probs]
+    # instances own a few CTAs each in the batched launch: lanes by row length only
+    solvers = [eqs.Solver(p, precision=eqs.EQS_PREC_MIXED, rtol=RTOL, fill_lanes=0, **SOLVER_OPTS)
+               for p in probs]
     nfree = sum(S.nf for S in solvers)
     best, tuning = autotune.tune_batch(eqs, solvers, candidates=(256, 512, 1024, 2048), s=s, steps=2)
     b = eqs.eqs_batch_create([S.ctx for S in solvers], best)

@@ -118,6 +118,11 @@ typedef struct {
                           the snapshots have lower numerical rank           */
   int pod_min_iters;   /* EQS_GUESS_POD2: a solution becomes a snapshot when
                           its solve needed more CG iterations (default 3)   */
+  int fill_lanes;      /* 1 (default): rows of AMG levels too small to fill
+                          the GPU get lane groups (up to 32 lanes per row)
+                          until they do; 0: lanes by row length only (for
+                          contexts that run together in a batch, where each
+                          instance owns a few CTAs)                         */
 } eqs_opts;
 
 #define EQS_MAX_STAGES 64
@@ -140,7 +145,8 @@ typedef struct {
 /* Fill *o with the defaults (precision FP64, theta 0.08, coarse_max 500,
  * max_levels 10, degree 2, alpha 30, rtol 1e-8, max_iter 500, GUESS_PREV,
  * flexible 1, persistent 0, blocks_per_sm 1, spe_n 4, host_loop 0,
- * barrier_polls 0, split_m 1, pod_k 12, pod_m 6, pod_min_iters 3). */
+ * barrier_polls 0, split_m 1, pod_k 12, pod_m 6, pod_min_iters 3,
+ * fill_lanes 1). */
 void eqs_opts_default(eqs_opts* o);
 
 /* Create a context from a tetrahedral mesh (Eq. 2 discretisation input).

@@ -169,7 +169,7 @@ static cudaError_t upload_sell(eqs_ctx* c, const HostCSR& A, DevSell<T>& S, bool
   S.G = allow_groups ? lanes_for(mean_row) : 1;
   // small levels: more lanes per row until the rows fill the resident
   // threads (latency of long rows shared by a lane group, not serialised)
-  if (allow_groups) {
+  if (allow_groups && c->opts.fill_lanes) {
     const int64_t resident = (int64_t)std::max(c->sms, 1) * 2048;
     while (S.G < 32 && S.G < mean_row && A.n_rows * (int64_t)S.G * 2 <= resident) S.G *= 2;
   }
@@ -1189,6 +1189,7 @@ void eqs_opts_default(eqs_opts* o) {
   o->pod_k = 12;
   o->pod_m = 6;
   o->pod_min_iters = 3;
+  o->fill_lanes = 1;
 }
 
 static eqs_status mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
