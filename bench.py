@@ -78,6 +78,25 @@ def parse():
     return ap.parse_args()
 
 
+# ------------------------------------------------------------ replicas
+def max_over_ranks(value, dist=None, device="cuda"):
+    """Max of a per-rank scalar over all ranks (the slowest replica's time);
+    the value itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    tt = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(units_per_rank, world, total_ms):
+    """Whole-job rate of independent replicas (weak scaling): every rank
+    processes units_per_rank; the job takes the slowest rank's time."""
+    return world * units_per_rank / (total_ms / 1e3)
+
+
 # ------------------------------------------------------------------ oracle
 ORACLE_SNIPPET = r"""
 import json, os, sys
@@ -248,13 +267,9 @@ def run_ours(args, rank, world):
     # headline: mixed precision with the SPE start vector (Section IV)
     solver = make(eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_SPE)
     x, t, dt, times, launches, iters, clocks = measure(solver, args.steps, args.warmup)
-    total_ms = sum(times)
-    if dist is not None:
-        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(times), dist)
     units = world * p.n_free * S_STAGES * args.steps
-    value = units / (total_ms / 1e3)
+    value = job_throughput(p.n_free * S_STAGES * args.steps, world, total_ms)
 
     # end to end through the public API: pinned host x in, step, x back to host
     xh = torch.zeros(p.n_nodes, dtype=torch.float64).pin_memory()
@@ -274,10 +289,7 @@ def run_ours(args, rank, world):
         e1.synchronize()
         e2e_ms += max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_host))
         t += dt
-    if dist is not None:
-        tt = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist)
     e2e_value = units / (e2e_ms / 1e3)
     roof = dominant_kernel_roofline(torch, eqs, solver, p, flush)
     solver.close()
@@ -534,6 +546,10 @@ def run_batch(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     eqs.lib()
+    dist = None
+    if world > 1:  # replicas: every rank serves the whole batch on its own GPU
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     s = 10
     probs = [ei.config_problem(4, instance=i) for i in range(64)]
     # instances own a few CTAs each in the batched launch: lanes by row length only
@@ -566,8 +582,8 @@ def run_batch(args, rank, world):
         t += dt
     clocks = clk.stop()
     launches = st.launches * args.steps
-    total_ms = sum(times)
-    value = nfree * s * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(times), dist)
+    value = job_throughput(nfree * s * args.steps, world, total_ms)
     # the same instances one after another (single-instance step graphs)
     xsolo = [torch.zeros(S.n, dtype=torch.float64, device="cuda") for S in solvers]
     ts = 0.0
@@ -601,6 +617,8 @@ def run_batch(args, rank, world):
     eqs.eqs_batch_destroy(b)
     for S in solvers:
         S.close()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def run_learned(args):
@@ -720,13 +738,9 @@ def run_ensemble_headline(args, rank, world):
         t += dt
     torch.cuda.synchronize()
     clocks = clk.stop()
-    total_ms = sum(times)
-    if dist is not None:
-        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(times), dist)
     units = world * 4 * p.n_free * S_STAGES * args.steps
-    value = units / (total_ms / 1e3)
+    value = job_throughput(4 * p.n_free * S_STAGES * args.steps, world, total_ms)
     # end to end: pinned host x (4 trajectories) in, step, x back to host
     xh = torch.zeros((4, p.n_nodes), dtype=torch.float64).pin_memory()
     xh.copy_(x.cpu())
@@ -745,10 +759,7 @@ def run_ensemble_headline(args, rank, world):
         e1.synchronize()
         e2e_ms += max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_host))
         t += dt
-    if dist is not None:
-        tt = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist)
     roof = dominant_kernel_roofline(torch, eqs, S, p, flush)
     S.close()
     forms = {}
