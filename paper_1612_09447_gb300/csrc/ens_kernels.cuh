@@ -430,6 +430,24 @@ __global__ void k4_pcg_init(DevSell<double> M, int n, const double4_32a* __restr
     ens_init_tail(tot, sc, tol2, maxit, h, use_handle, iters_out, relres_out, zero_out);
 }
 
+// Last block of the dot-product pass: beta per active column
+// (Polak-Ribiere or Fletcher-Reeves) from r.z (tot[0..4)) and r_prev.z.
+__device__ __forceinline__ void ens_beta_tail(const double* tot, EnsScalars* sc, int flexible) {
+  for (int c = 0; c < kEnsW; ++c) {
+    if (sc->conv[c]) {
+      sc->beta[c] = 0.0;
+      continue;
+    }
+    const double rz = tot[c];
+    double beta = 0.0;
+    if (sc->it[c] > 0 && sc->rz_old[c] != 0.0)
+      beta = flexible ? (rz - tot[kEnsW + c]) / sc->rz_old[c] : rz / sc->rz_old[c];
+    sc->beta[c] = beta;
+    sc->rz[c] = rz;
+    sc->rz_old[c] = rz;
+  }
+}
+
 // z = V-cycle output (+ pending direction) kept in FP32; r.z and r_prev.z
 // per column; the last block forms beta per active column (Polak-Ribiere or
 // Fletcher-Reeves).
@@ -453,21 +471,45 @@ __global__ void k4_pcg_dots(int n, const double4_32a* __restrict__ r, const doub
     }
   }
   double tot[2 * kEnsW];
-  if (grid_sum<2 * kEnsW>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
-    for (int c = 0; c < kEnsW; ++c) {
-      if (sc->conv[c]) {
-        sc->beta[c] = 0.0;
-        continue;
+  if (grid_sum<2 * kEnsW>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0)
+    ens_beta_tail(tot, sc, flexible);
+}
+
+// Level-0 post-smoothing step of a degree-1 V-cycle fused with the dot
+// products (as k_post_first_dots, four columns): z = x + D^-1 (b - A x)/theta.
+__global__ void __launch_bounds__(kBlock, 4)
+k4_post_first_dots(DevSell<float> A, int n, const float4* __restrict__ b, const float4* __restrict__ x,
+                   const float* __restrict__ dinv, float inv_theta, const double4_32a* __restrict__ rcg,
+                   const double4_32a* __restrict__ rprev, float4* __restrict__ z32, EnsScalars* sc,
+                   double* partials, unsigned int* counter, int max_blocks, int flexible) {
+  pdl_enter();
+  double v[2 * kEnsW];
+#pragma unroll
+  for (int k = 0; k < 2 * kEnsW; ++k) v[k] = 0.0;
+  EQS_ROWS2(A, n, {
+    const float4 a0 = mat_row4(A, t0, n, x);
+    const float4 a1 = mat_row4(A, t1, n, x);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t t = h ? t1 : t0;
+      if (!row_leader(A, t, n)) continue;
+      const int i = (int)(t >> A.logG);
+      const float4 r = b[i] - (h ? a1 : a0);
+      const float4 zt = x[i] + (dinv[i] * inv_theta) * r;
+      z32[i] = zt;
+      const double4_32a ri = rcg[i];
+      const double4_32a pi = rprev[i];
+#pragma unroll
+      for (int c = 0; c < kEnsW; ++c) {
+        const double zc = (double)comp(zt, c);
+        v[c] = fma(dc4(ri, c), zc, v[c]);
+        v[kEnsW + c] = fma(dc4(pi, c), zc, v[kEnsW + c]);
       }
-      const double rz = tot[c];
-      double beta = 0.0;
-      if (sc->it[c] > 0 && sc->rz_old[c] != 0.0)
-        beta = flexible ? (rz - tot[kEnsW + c]) / sc->rz_old[c] : rz / sc->rz_old[c];
-      sc->beta[c] = beta;
-      sc->rz[c] = rz;
-      sc->rz_old[c] = rz;
     }
-  }
+  })
+  double tot[2 * kEnsW];
+  if (grid_sum<2 * kEnsW>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0)
+    ens_beta_tail(tot, sc, flexible);
 }
 
 // q = M z + beta q, p = z + beta p per active column (split-M product of the

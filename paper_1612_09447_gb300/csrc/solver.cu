@@ -920,7 +920,7 @@ static eqs_status ens_alloc(eqs_ctx* c) {
 
 // V-cycle of the four columns from level l (returns the pending direction of
 // a degree-1 post-smoother, like vcycle_level).
-static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st) {
+static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st, bool fuse_dots = false) {
   std::vector<DevLevel<float>>& L = c->lev32;
   const int nl = (int)L.size();
   DevLevel<float>& V = L[l];
@@ -955,6 +955,13 @@ static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st) {
   float4* cpend = ens_vcycle_level(c, l + 1, st);
   launch(k4_prolong, mat_grid(c, V.P, V.n), kBlock, st, V.P, V.n, (const float4*)EC.x,
          (const float4*)cpend, E.x);
+  if (fuse_dots && l == 0 && deg == 1) {  // the CG dot products ride on the last smoothing pass
+    launch(k4_post_first_dots, g, kBlock, st, V.A, V.n, (const float4*)E.b, (const float4*)E.x,
+           (const float*)V.dinv, (float)V.inv_theta, (const double4_32a*)c->d_er,
+           (const double4_32a*)c->d_erprev, c->d_ez32, (EnsScalars*)c->d_esc, c->d_epart, c->red.counter,
+           c->red.max_blocks, c->opts.flexible);
+    return nullptr;
+  }
   launch(k4_post_first, g, kBlock, st, V.A, V.n, (const float4*)E.b, (const float4*)E.x, (const float*)V.dinv,
          (float)V.inv_theta, E.r, E.dA);
   din = E.dA;
@@ -997,10 +1004,12 @@ static void ens_body_launch(eqs_ctx* c, cudaStream_t st, double4_32a* x, double 
   const int n = (int)c->n_free;
   const int g = vec_grid(c, n);
   EnsScalars* sc = (EnsScalars*)c->d_esc;
-  float4* zpend = ens_vcycle_level(c, 0, st);
-  launch(k4_pcg_dots, g, kBlock, st, n, (const double4_32a*)c->d_er, (const double4_32a*)c->d_erprev,
-         (const float4*)E.x, (const float4*)zpend, c->d_ez32, sc, c->d_epart, c->red.counter, c->red.max_blocks,
-         c->opts.flexible);
+  const bool fuse = c->opts.cheb_degree == 1 && c->lev32.size() > 1;
+  float4* zpend = ens_vcycle_level(c, 0, st, fuse);
+  if (!fuse)
+    launch(k4_pcg_dots, g, kBlock, st, n, (const double4_32a*)c->d_er, (const double4_32a*)c->d_erprev,
+           (const float4*)E.x, (const float4*)zpend, c->d_ez32, sc, c->d_epart, c->red.counter,
+           c->red.max_blocks, c->opts.flexible);
   launch(k4_pcg_pq, g, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo, n,
          (const float4*)c->d_ez32, c->d_ep, c->d_eq, sc, c->d_epart, c->red.counter, c->red.max_blocks);
   launch(k4_pcg_update, g, kBlock, st, n, x, c->d_er, c->d_erprev, (const double4_32a*)c->d_ep,
