@@ -117,6 +117,8 @@ struct eqs_ctx {
   std::vector<int32_t> tets;        // mesh order, npe nodes per tet (vertices first)
   int npe = 4;                       // nodes per tet: 4 (P1) or 10 (P2: + edge midpoints)
   int32_t* d_conn10 = nullptr;       // P2: 10 x n_tets internal node ids (node-major)
+  int64_t n_cells = 0;               // > 0: the tets form Kuhn cells (6 per cell, in order)
+  int32_t* d_corner = nullptr;       // 8 x n_cells internal corner ids (corner-major)
   std::vector<uint8_t> tag;         // mesh order
   std::vector<int32_t> internal_of_node, node_of_internal;  // free first
   std::vector<uint8_t> tet_mat;

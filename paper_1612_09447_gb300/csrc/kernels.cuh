@@ -927,6 +927,155 @@ __global__ void k_elem32(int64_t nt, const int4* __restrict__ conn, const uint8_
   elem32_tet(e, conn, mat, mats, xh, xl, x, n_limit, y);
 }
 
+// kappa(|E|) in the element's working precision.
+template <typename R>
+__device__ __forceinline__ R kappa_of(const MaterialDev& m, R E);
+template <>
+__device__ __forceinline__ double kappa_of<double>(const MaterialDev& m, double E) { return kappa64(m, E); }
+template <>
+__device__ __forceinline__ float kappa_of<float>(const MaterialDev& m, float E) { return kappa32(m, E); }
+
+// ------------------------------------------------ Kuhn-cell element kernels
+// Meshes whose tets come in groups of six forming one Kuhn-split hexahedron
+// (detected at setup): one thread per cell loads the cell's 8 corners and
+// potentials once, forms the six tets' residuals (the same arithmetic as
+// the per-tet kernels) into 8 corner sums and issues 8 atomic adds instead
+// of 24.  Corner c = bx + 2 by + 4 bz; the six tets of a cell have the
+// corners (0,1,3,7), (0,1,7,5), (0,2,7,3), (0,2,6,7), (0,4,5,7), (0,4,7,6)
+// (the vertex order of the mesh: positive orientation).
+
+template <typename R>
+__device__ __forceinline__ void tet_residual(const R (&e)[3][3], R d1, R d2, R d3, const MaterialDev& m,
+                                             R sign, R (&r)[4]) {
+  const R c1x = e[1][1] * e[2][2] - e[1][2] * e[2][1], c1y = e[1][2] * e[2][0] - e[1][0] * e[2][2],
+          c1z = e[1][0] * e[2][1] - e[1][1] * e[2][0];
+  const R c2x = e[2][1] * e[0][2] - e[2][2] * e[0][1], c2y = e[2][2] * e[0][0] - e[2][0] * e[0][2],
+          c2z = e[2][0] * e[0][1] - e[2][1] * e[0][0];
+  const R c3x = e[0][1] * e[1][2] - e[0][2] * e[1][1], c3y = e[0][2] * e[1][0] - e[0][0] * e[1][2],
+          c3z = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+  const R D = e[0][0] * c1x + e[0][1] * c1y + e[0][2] * c1z;
+  const R gx = d1 * c1x + d2 * c2x + d3 * c3x;
+  const R gy = d1 * c1y + d2 * c2y + d3 * c3y;
+  const R gz = d1 * c1z + d2 * c2z + d3 * c3z;
+  R kap;
+  if (m.is_const) {
+    kap = (R)m.klo;
+  } else {
+    const R E = sqrt(gx * gx + gy * gy + gz * gz) / D;
+    kap = kappa_of<R>(m, E);
+  }
+  const R sc = sign * kap / (R(6) * D);
+  r[1] = sc * (c1x * gx + c1y * gy + c1z * gz);
+  r[2] = sc * (c2x * gx + c2y * gy + c2z * gz);
+  r[3] = sc * (c3x * gx + c3y * gy + c3z * gz);
+  r[0] = -(r[1] + r[2] + r[3]);
+}
+
+// One tet (corners A, B, C, D of the cell; compile-time indices keep the
+// corner arrays in registers) into the cell's corner sums.
+template <int A, int B, int C, int D>
+__device__ __forceinline__ void cell_tet64(const double (&px)[8][3], const double (&f)[8], const MaterialDev& m,
+                                           double sign, double (&acc)[8]) {
+  double e[3][3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    e[0][q] = px[B][q] - px[A][q];
+    e[1][q] = px[C][q] - px[A][q];
+    e[2][q] = px[D][q] - px[A][q];
+  }
+  double r[4];
+  tet_residual<double>(e, f[B] - f[A], f[C] - f[A], f[D] - f[A], m, sign, r);
+  acc[A] += r[0];
+  acc[B] += r[1];
+  acc[C] += r[2];
+  acc[D] += r[3];
+}
+
+template <int A, int B, int C, int D>
+__device__ __forceinline__ void cell_tet32(const float4 (&h)[8], const float4 (&l)[8], const float2 (&f)[8],
+                                           const MaterialDev& m, float (&acc)[8]) {
+  float e[3][3];
+  e[0][0] = (h[B].x - h[A].x) + (l[B].x - l[A].x);
+  e[0][1] = (h[B].y - h[A].y) + (l[B].y - l[A].y);
+  e[0][2] = (h[B].z - h[A].z) + (l[B].z - l[A].z);
+  e[1][0] = (h[C].x - h[A].x) + (l[C].x - l[A].x);
+  e[1][1] = (h[C].y - h[A].y) + (l[C].y - l[A].y);
+  e[1][2] = (h[C].z - h[A].z) + (l[C].z - l[A].z);
+  e[2][0] = (h[D].x - h[A].x) + (l[D].x - l[A].x);
+  e[2][1] = (h[D].y - h[A].y) + (l[D].y - l[A].y);
+  e[2][2] = (h[D].z - h[A].z) + (l[D].z - l[A].z);
+  const float d1 = (f[B].x - f[A].x) + (f[B].y - f[A].y);
+  const float d2 = (f[C].x - f[A].x) + (f[C].y - f[A].y);
+  const float d3 = (f[D].x - f[A].x) + (f[D].y - f[A].y);
+  float r[4];
+  tet_residual<float>(e, d1, d2, d3, m, 1.0f, r);
+  acc[A] += r[0];
+  acc[B] += r[1];
+  acc[C] += r[2];
+  acc[D] += r[3];
+}
+
+__global__ void k_elem64_cell(int64_t ncell, const int32_t* __restrict__ corner, const uint8_t* __restrict__ mat,
+                              const MaterialDev* __restrict__ mats, const double4* __restrict__ xyz,
+                              const double* __restrict__ x, int n_limit, double sign, double* __restrict__ y) {
+  pdl_enter();
+  const int64_t cidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cidx >= ncell) return;
+  int v[8];
+  double px[8][3], f[8], acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = __ldg(corner + (int64_t)k * ncell + cidx);
+    const double4 p = xyz[v[k]];
+    px[k][0] = p.x;
+    px[k][1] = p.y;
+    px[k][2] = p.z;
+    f[k] = __ldg(x + v[k]);
+    acc[k] = 0.0;
+  }
+  const uint8_t* mt = mat + 6 * cidx;
+  cell_tet64<0, 1, 3, 7>(px, f, mats[mt[0]], sign, acc);
+  cell_tet64<0, 1, 7, 5>(px, f, mats[mt[1]], sign, acc);
+  cell_tet64<0, 2, 7, 3>(px, f, mats[mt[2]], sign, acc);
+  cell_tet64<0, 2, 6, 7>(px, f, mats[mt[3]], sign, acc);
+  cell_tet64<0, 4, 5, 7>(px, f, mats[mt[4]], sign, acc);
+  cell_tet64<0, 4, 7, 6>(px, f, mats[mt[5]], sign, acc);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (v[k] < n_limit) atomicAdd(y + v[k], acc[k]);
+}
+
+__global__ void k_elem32_cell(int64_t ncell, const int32_t* __restrict__ corner, const uint8_t* __restrict__ mat,
+                              const MaterialDev* __restrict__ mats, const float4* __restrict__ xh,
+                              const float4* __restrict__ xl, const float2* __restrict__ x, int n_limit,
+                              float* __restrict__ y) {
+  pdl_enter();
+  const int64_t cidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cidx >= ncell) return;
+  int v[8];
+  float4 h[8], l[8];
+  float2 f[8];
+  float acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = __ldg(corner + (int64_t)k * ncell + cidx);
+    h[k] = xh[v[k]];
+    l[k] = xl[v[k]];
+    f[k] = x[v[k]];
+    acc[k] = 0.f;
+  }
+  const uint8_t* mt = mat + 6 * cidx;
+  cell_tet32<0, 1, 3, 7>(h, l, f, mats[mt[0]], acc);
+  cell_tet32<0, 1, 7, 5>(h, l, f, mats[mt[1]], acc);
+  cell_tet32<0, 2, 7, 3>(h, l, f, mats[mt[2]], acc);
+  cell_tet32<0, 2, 6, 7>(h, l, f, mats[mt[3]], acc);
+  cell_tet32<0, 4, 5, 7>(h, l, f, mats[mt[4]], acc);
+  cell_tet32<0, 4, 7, 6>(h, l, f, mats[mt[5]], acc);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (v[k] < n_limit) atomicAdd(y + v[k], acc[k]);
+}
+
 // ---------------------------------------------------- P2 element kernels
 // Quadratic tets (Section V's 2nd order ansatz functions): 10 nodes, the
 // vertices then the midpoints of the edges (0,1) (0,2) (0,3) (1,2) (1,3)
@@ -941,12 +1090,6 @@ __global__ void k_elem32(int64_t nt, const int4* __restrict__ conn, const uint8_
 // Potentials enter as differences to phi_0 (a constant shift moves every a_k
 // by the same amount and sum_k grad lambda_k = 0), and r_0 = -(r_1 + ... +
 // r_9) keeps the local residual's zero sum exactly.
-template <typename R>
-__device__ __forceinline__ R kappa_of(const MaterialDev& m, R E);
-template <>
-__device__ __forceinline__ double kappa_of<double>(const MaterialDev& m, double E) { return kappa64(m, E); }
-template <>
-__device__ __forceinline__ float kappa_of<float>(const MaterialDev& m, float E) { return kappa32(m, E); }
 
 template <typename R>
 __device__ __forceinline__ void p2_residual(const R (&gl)[4][3], R D, const R (&d)[10], const MaterialDev& m,

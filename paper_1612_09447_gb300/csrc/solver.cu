@@ -669,6 +669,17 @@ static void elem_launch(eqs_ctx* c, cudaStream_t st, const double* Y, int n_limi
              y64 == c->d_R ? -1.0 : 1.0, y64);
     return;
   }
+  if (c->n_cells > 0) {  // Kuhn cells: 8 atomic adds per six tets
+    if (mixed(c))
+      launch(k_elem32_cell, nblk(c->n_cells), kBlock, st, c->n_cells, (const int32_t*)c->d_corner,
+             (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi,
+             (const float4*)c->d_xyz_lo, (const float2*)c->d_Y32, n_limit, y32);
+    else
+      launch(k_elem64_cell, nblk(c->n_cells), kBlock, st, c->n_cells, (const int32_t*)c->d_corner,
+             (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats, (const double4*)c->d_xyz, Y, n_limit,
+             y64 == c->d_R ? -1.0 : 1.0, y64);
+    return;
+  }
   if (mixed(c))
     launch(k_elem32, nblk(c->n_tets), kBlock, st, c->n_tets, c->d_conn, c->d_mat, c->d_mats,
                                                  c->d_xyz_hi, c->d_xyz_lo, c->d_Y32, n_limit, y32);
@@ -1324,6 +1335,34 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     conn[e] = make_int4(c->internal_of_node[t[0]], c->internal_of_node[t[1]], c->internal_of_node[t[2]],
                         c->internal_of_node[t[3]]);
   }
+  // Kuhn cells: every group of six consecutive tets is the split of one
+  // hexahedron (corner c = bx + 2 by + 4 bz, tet p with corners
+  // kKuhnTetHost[p]); then the element kernel works per cell
+  static const int kKuhnTetHost[6][4] = {{0, 1, 3, 7}, {0, 1, 7, 5}, {0, 2, 7, 3},
+                                         {0, 2, 6, 7}, {0, 4, 5, 7}, {0, 4, 7, 6}};
+  std::vector<int32_t> corner;
+  c->n_cells = 0;
+  if (npe == 4 && c->n_tets % 6 == 0) {
+    const int64_t nc = c->n_tets / 6;
+    corner.resize((size_t)8 * nc);
+    bool ok = true;
+    for (int64_t q = 0; q < nc && ok; ++q) {
+      const int32_t* t = &c->tets[24 * q];
+      int32_t cn[8];
+      cn[0] = t[0];
+      cn[1] = t[1];
+      cn[3] = t[2];
+      cn[7] = t[3];
+      cn[5] = t[4 + 3];
+      cn[2] = t[8 + 1];
+      cn[6] = t[12 + 2];
+      cn[4] = t[16 + 1];
+      for (int p = 0; p < 6 && ok; ++p)
+        for (int k = 0; k < 4 && ok; ++k) ok = t[4 * p + k] == cn[kKuhnTetHost[p][k]];
+      for (int k = 0; k < 8; ++k) corner[(size_t)k * nc + q] = c->internal_of_node[cn[k]];
+    }
+    if (ok) c->n_cells = nc;
+  }
   std::vector<int32_t> conn10;
   if (npe == 10) {  // node-major: entry k of tet e at k * n_tets + e (coalesced per k)
     conn10.resize((size_t)10 * c->n_tets);
@@ -1359,6 +1398,8 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
   CK(upload(c, &c->d_conn, conn.data(), conn.size()));
   c->d_conn10 = nullptr;
   if (npe == 10) CK(upload(c, &c->d_conn10, conn10.data(), conn10.size()));
+  c->d_corner = nullptr;
+  if (c->n_cells > 0) CK(upload(c, &c->d_corner, corner.data(), corner.size()));
   CK(upload(c, &c->d_mat, c->tet_mat.data(), c->tet_mat.size()));
   CK(upload(c, &c->d_mats, md.data(), md.size()));
   CK(upload(c, &c->d_xyz, xyz.data(), xyz.size()));
