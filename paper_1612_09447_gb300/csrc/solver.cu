@@ -119,6 +119,28 @@ static cudaError_t upload(eqs_ctx* c, T** p, const T* h, size_t n) {
   return cudaMemcpy(*p, h, n * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+// Device buffer owned by one call (the checking / evaluation entry points
+// that need a few bytes of their own); freed on every return path.
+template <typename T>
+struct TmpBuf {
+  T* p = nullptr;
+  TmpBuf() = default;
+  TmpBuf(const TmpBuf&) = delete;
+  TmpBuf& operator=(const TmpBuf&) = delete;
+  ~TmpBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t n) { return cudaMalloc((void**)&p, n * sizeof(T)); }
+};
+
+// Puts a swapped pointer member back on every return path.
+template <typename T>
+struct PtrRestore {
+  T** slot;
+  T* saved;
+  ~PtrRestore() { *slot = saved; }
+};
+
 // Lanes per row for a mean row length: 1 selects SELL-32 (thread per row).
 static int lanes_for(double mean_row) {
   if (mean_row <= 16.0) return 1;
@@ -2107,13 +2129,15 @@ eqs_status eqs_guess_train(eqs_ctx* c, int iters, int batch, float lr, uint64_t 
 eqs_status eqs_guess_grad(eqs_ctx* c, const float* X, const float* T, int B, float* grad, float* loss) {
   REQUIRE_SETUP(c);
   if (!X || !T || !grad || B < 1) return fail(c, EQS_ERR_ARG, "bad gradient arguments");
-  float *dX = nullptr, *dT = nullptr;
-  CK(cudaMalloc(&dX, (size_t)B * 8 * sizeof(float)));
-  CK(cudaMalloc(&dT, (size_t)B * sizeof(float)));
-  cudaMemcpy(dX, X, (size_t)B * 8 * sizeof(float), cudaMemcpyHostToDevice);
-  cudaMemcpy(dT, T, (size_t)B * sizeof(float), cudaMemcpyHostToDevice);
-  cudaMemset(c->d_grad, 0, kNP * sizeof(float));
-  cudaMemset(c->d_loss, 0, sizeof(float));
+  TmpBuf<float> tX, tT;
+  CK(tX.alloc((size_t)B * 8));
+  CK(tT.alloc((size_t)B));
+  float* dX = tX.p;
+  float* dT = tT.p;
+  CK(cudaMemcpy(dX, X, (size_t)B * 8 * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dT, T, (size_t)B * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemset(c->d_grad, 0, kNP * sizeof(float)));
+  CK(cudaMemset(c->d_loss, 0, sizeof(float)));
   eqs_status st = train_batch(c, 5, B, 0ull, 0, dX, dT);
   if (st == EQS_OK) {
     cudaError_t e = cudaMemcpy(grad, c->d_grad, kNP * sizeof(float), cudaMemcpyDeviceToHost);
@@ -2121,8 +2145,6 @@ eqs_status eqs_guess_grad(eqs_ctx* c, const float* X, const float* T, int B, flo
     if (e == cudaSuccess) e = cudaMemset(c->d_grad, 0, kNP * sizeof(float));
     if (e != cudaSuccess) st = fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
   }
-  cudaFree(dX);
-  cudaFree(dT);
   return st;
 }
 
@@ -2132,12 +2154,13 @@ eqs_status eqs_spe_eval(eqs_ctx* c, const double* X, const double* b, int n, dou
   if (n != c->opts.spe_n) return fail(c, EQS_ERR_ARG, "n must equal the context's spe_n");
   const int64_t nf = c->n_free;
   cudaStream_t st = c->stream;
-  long long* cnt = nullptr;
-  CK(cudaMalloc(&cnt, 2 * sizeof(long long)));
+  TmpBuf<long long> tcnt;
+  CK(tcnt.alloc(2));
+  long long* cnt = tcnt.p;
   const long long zero2[2] = {0, 1};  // stepcount 0: solve index g = j
   CK(cudaMemcpyAsync(cnt, zero2, sizeof(zero2), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(c->d_R, b, nf * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  long long* saved = c->d_stepcount;
+  PtrRestore<long long> restore{&c->d_stepcount, c->d_stepcount};
   c->d_stepcount = cnt;
   // push the history oldest first (solution q into slot q % n), updating the
   // Gram matrix as the step does, then form x0 for the solve g = n
@@ -2152,9 +2175,7 @@ eqs_status eqs_spe_eval(eqs_ctx* c, const double* X, const double* b, int n, dou
     spe_start<float>(c, c->lev32, st, 1, n, nullptr, x0, 0.0, 0, 0, sl);
   else
     spe_start<double>(c, c->lev64, st, 1, n, nullptr, x0, 0.0, 0, 0, sl);
-  c->d_stepcount = saved;
   cudaError_t e = cudaStreamSynchronize(st);
-  cudaFree(cnt);
   if (e != cudaSuccess) return fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
   return EQS_OK;
 }
@@ -2165,10 +2186,12 @@ eqs_status eqs_pod_eval(eqs_ctx* c, const double* X, int K, const double* b, dou
   if (K < 1 || K > c->opts.pod_k) return fail(c, EQS_ERR_ARG, "K must be in [1, pod_k]");
   const int64_t nf = c->n_free;
   cudaStream_t st = c->stream;
-  long long* cnt = nullptr;
-  int* zero = nullptr;
-  CK(cudaMalloc(&cnt, 2 * sizeof(long long)));
-  CK(cudaMalloc(&zero, sizeof(int)));
+  TmpBuf<long long> tcnt;
+  TmpBuf<int> tzero;
+  CK(tcnt.alloc(2));
+  CK(tzero.alloc(1));
+  long long* cnt = tcnt.p;
+  int* zero = tzero.p;
   const long long one2[2] = {1, 2};  // solve index g = 1: a previous solution exists
   CK(cudaMemcpyAsync(cnt, one2, sizeof(one2), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(zero, 0, sizeof(int), st));
@@ -2193,8 +2216,6 @@ eqs_status eqs_pod_eval(eqs_ctx* c, const double* X, int K, const double* b, dou
   else
     pod_start<double>(c, c->lev64, st, nullptr, x0, 0.0, 0, 0, sl);
   cudaError_t e = cudaStreamSynchronize(st);
-  cudaFree(cnt);
-  cudaFree(zero);
   if (e != cudaSuccess) return fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
   return EQS_OK;
 }
@@ -2218,22 +2239,22 @@ eqs_status eqs_guess_eval(eqs_ctx* c, const double* H, double* z0) {
   if (!H || !z0) return fail(c, EQS_ERR_ARG, "null vector");
   const int nf = (int)c->n_free;
   cudaStream_t st = c->stream;
-  float* ring = nullptr;
-  long long* cnt = nullptr;
-  CK(cudaMalloc(&ring, 4 * (size_t)nf * sizeof(float)));
-  CK(cudaMalloc(&cnt, 2 * sizeof(long long)));
+  TmpBuf<float> tring;
+  TmpBuf<long long> tcnt;
+  CK(tring.alloc(4 * (size_t)nf));
+  CK(tcnt.alloc(2));
+  float* ring = tring.p;
+  long long* cnt = tcnt.p;
   // solve index g = 4: h_l (l = 1..4) goes to slot (4 - l) % 4
   for (int l = 0; l < 4; ++l)
     k_push_solution<<<nblk(nf), kBlock, 0, st>>>(nf, H + (size_t)l * nf, ring + (size_t)((3 - l) & 3) * nf);
   const long long four[2] = {4, 5};
-  cudaMemcpyAsync(cnt, four, sizeof(four), cudaMemcpyHostToDevice, st);
+  CK(cudaMemcpyAsync(cnt, four, sizeof(four), cudaMemcpyHostToDevice, st));
   k_rms<<<vec_grid(c, nf), kBlock, 0, st>>>(nf, H, c->d_sh, c->red.partials, c->red.counter,
                                            c->red.max_blocks);
   k_mlp_guess<<<nblk(nf), kBlock, 0, st>>>(nf, H, ring, cnt, 1, 0, c->d_adj_ptr, c->d_adj_col, c->d_inv_deg,
                                          (const __nv_bfloat16*)c->d_theta_bf16, c->d_sh, z0);
   cudaError_t e = cudaStreamSynchronize(st);
-  cudaFree(ring);
-  cudaFree(cnt);
   if (e != cudaSuccess) return fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
   return EQS_OK;
 }

@@ -120,6 +120,21 @@ def test_p2_mesh_validation(E):
     assert ex.value.status == E.EQS_ERR_MESH
 
 
+@pytest.mark.parametrize("field,value", [("pod_k", 0), ("pod_k", 17), ("pod_m", 0), ("pod_m", 13),
+                                         ("pod_min_iters", -1), ("spe_n", 7), ("cheb_degree", 5),
+                                         ("rtol", 0.0), ("precision", 2)])
+def test_invalid_options_are_rejected_before_any_device_work(E, field, value):
+    p = ei.make_problem(2)
+    ctx = E.eqs_mesh_create(p.xyz, p.tets, p.node_tag)
+    E.eqs_set_materials(ctx, p.tet_mat, p.materials)
+    o = E.eqs_opts_default()
+    setattr(o, field, value)
+    with pytest.raises(E.EqsError) as ex:
+        E.eqs_amg_setup(ctx, o)
+    assert ex.value.status == E.EQS_ERR_ARG
+    E.eqs_destroy(ctx)
+
+
 def test_call_order_errors(E):
     p = ei.make_problem(2)
     ctx = E.eqs_mesh_create(p.xyz, p.tets, p.node_tag)

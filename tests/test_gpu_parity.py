@@ -58,6 +58,22 @@ def test_apply_K(E, name, prec, tol):
     S.close()
 
 
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-12), (MIXED, 2e-5)])
+def test_apply_K_cell_and_tet_paths_agree(E, prec, tol):
+    """Kuhn-ordered tets take the per-cell element kernel; the same mesh with
+    its tets shuffled takes the per-tet kernel: both equal the oracle."""
+    p = ei.config_problem(2, N=6)
+    perm = np.random.default_rng(1).permutation(p.n_tets)
+    x = _state(p, seed=4)
+    ref = fem.apply_K(p.xyz, p.tets, p.tet_mat, p.materials, x)
+    for order in (np.arange(p.n_tets), perm):
+        q = ei.Problem(p.N, p.xyz, p.tets[order], p.tet_mat[order], p.node_tag, p.materials, p.V0)
+        S = E.Solver(q, precision=prec)
+        got = S.apply_K(_cuda(x)).cpu().numpy()
+        assert _relmax(got, ref) <= tol
+        S.close()
+
+
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_spmv_M(E, name):
     p = PROBLEMS[name]()
