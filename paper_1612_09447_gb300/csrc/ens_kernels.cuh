@@ -804,7 +804,7 @@ __global__ void k4_elem32(int64_t nt, const int4* __restrict__ conn, const uint8
     const float gz = d1 * c1z + d2 * c2z + d3 * c3z;
     float kap;
     if (m.is_const) {
-      kap = (float)m.klo;
+      kap = m.klo_f;
     } else {
       const float E = sqrtf(gx * gx + gy * gy + gz * gz) / D;
       kap = kappa32(m, E);
@@ -819,6 +819,76 @@ __global__ void k4_elem32(int64_t nt, const int4* __restrict__ conn, const uint8
   if (t.y < n_limit) atomicAdd(y + t.y, make_float4(r1[0], r1[1], r1[2], r1[3]));
   if (t.z < n_limit) atomicAdd(y + t.z, make_float4(r2[0], r2[1], r2[2], r2[3]));
   if (t.w < n_limit) atomicAdd(y + t.w, make_float4(r3[0], r3[1], r3[2], r3[3]));
+}
+
+// K(x)x for four columns on Kuhn cells (as k_elem32_cell): the cell's
+// corners, coordinates and four potentials loaded once, the six tets'
+// residuals summed per corner, one 16-byte atomic add per corner.
+template <int A, int B, int C, int D>
+__device__ __forceinline__ void cell_tet32x4(const float4 (&h)[8], const float4 (&l)[8], const float4 (&ya)[8],
+                                             const float4 (&yb)[8], const MaterialDev& m, float4 (&acc)[8]) {
+  float e[3][3];
+  e[0][0] = (h[B].x - h[A].x) + (l[B].x - l[A].x);
+  e[0][1] = (h[B].y - h[A].y) + (l[B].y - l[A].y);
+  e[0][2] = (h[B].z - h[A].z) + (l[B].z - l[A].z);
+  e[1][0] = (h[C].x - h[A].x) + (l[C].x - l[A].x);
+  e[1][1] = (h[C].y - h[A].y) + (l[C].y - l[A].y);
+  e[1][2] = (h[C].z - h[A].z) + (l[C].z - l[A].z);
+  e[2][0] = (h[D].x - h[A].x) + (l[D].x - l[A].x);
+  e[2][1] = (h[D].y - h[A].y) + (l[D].y - l[A].y);
+  e[2][2] = (h[D].z - h[A].z) + (l[D].z - l[A].z);
+  float r[4][4];  // [column][local vertex]
+#pragma unroll
+  for (int col = 0; col < kEnsW; ++col) {
+    // (hi, lo) of column col: columns 0, 1 in ya (x, y | z, w), 2, 3 in yb
+    const float4& pa = col < 2 ? ya[A] : yb[A];
+    const float4& pb = col < 2 ? ya[B] : yb[B];
+    const float4& pc = col < 2 ? ya[C] : yb[C];
+    const float4& pd = col < 2 ? ya[D] : yb[D];
+    const bool hi2 = (col & 1) != 0;
+    const float fa_h = hi2 ? pa.z : pa.x, fa_l = hi2 ? pa.w : pa.y;
+    const float d1 = ((hi2 ? pb.z : pb.x) - fa_h) + ((hi2 ? pb.w : pb.y) - fa_l);
+    const float d2 = ((hi2 ? pc.z : pc.x) - fa_h) + ((hi2 ? pc.w : pc.y) - fa_l);
+    const float d3 = ((hi2 ? pd.z : pd.x) - fa_h) + ((hi2 ? pd.w : pd.y) - fa_l);
+    float rr[4];
+    tet_residual<float>(e, d1, d2, d3, m, 1.0f, rr);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r[col][k] = rr[k];
+  }
+  acc[A] = acc[A] + make_float4(r[0][0], r[1][0], r[2][0], r[3][0]);
+  acc[B] = acc[B] + make_float4(r[0][1], r[1][1], r[2][1], r[3][1]);
+  acc[C] = acc[C] + make_float4(r[0][2], r[1][2], r[2][2], r[3][2]);
+  acc[D] = acc[D] + make_float4(r[0][3], r[1][3], r[2][3], r[3][3]);
+}
+
+__global__ void k4_elem32_cell(int64_t ncell, const int32_t* __restrict__ corner, const uint8_t* __restrict__ mat,
+                               const MaterialDev* __restrict__ mats, const float4* __restrict__ xh,
+                               const float4* __restrict__ xl, const float4* __restrict__ Y2, int n_limit,
+                               float4* __restrict__ y) {
+  pdl_enter();
+  const int64_t cidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cidx >= ncell) return;
+  int v[8];
+  float4 h[8], l[8], ya[8], yb[8], acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = __ldg(corner + (int64_t)k * ncell + cidx);
+    h[k] = xh[v[k]];
+    l[k] = xl[v[k]];
+    ya[k] = Y2[2 * (int64_t)v[k]];
+    yb[k] = Y2[2 * (int64_t)v[k] + 1];
+    acc[k] = zero4();
+  }
+  const uint8_t* mt = mat + 6 * cidx;
+  cell_tet32x4<0, 1, 3, 7>(h, l, ya, yb, mats[mt[0]], acc);
+  cell_tet32x4<0, 1, 7, 5>(h, l, ya, yb, mats[mt[1]], acc);
+  cell_tet32x4<0, 2, 7, 3>(h, l, ya, yb, mats[mt[2]], acc);
+  cell_tet32x4<0, 2, 6, 7>(h, l, ya, yb, mats[mt[3]], acc);
+  cell_tet32x4<0, 4, 5, 7>(h, l, ya, yb, mats[mt[4]], acc);
+  cell_tet32x4<0, 4, 7, 6>(h, l, ya, yb, mats[mt[5]], acc);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (v[k] < n_limit) atomicAdd(y + v[k], acc[k]);
 }
 
 __device__ __forceinline__ void store_split4(float4* __restrict__ Y2, int64_t i, const double4_32a& v) {

@@ -88,6 +88,7 @@ struct ReduceScratch {
 struct MaterialDev {  // one row of the material table
   double eps, klo, khi, E0, inv_w;
   int is_const, pad;
+  float klo_f, dk_f, E0_f, inv_w_f;  // FP32 copies (klo, khi - klo, E0, 1/w) for the FP32 kernels
 };
 
 struct GraphEntry {

@@ -815,9 +815,11 @@ __device__ __forceinline__ double kappa64(const MaterialDev& m, double E) {
   return m.klo + (m.khi - m.klo) * s;
 }
 
+// FP32 conductivity from the table's FP32 copies (no FP64 conversions:
+// they run on GB300's slow FP64 pipe).
 __device__ __forceinline__ float kappa32(const MaterialDev& m, float E) {
-  if (m.is_const) return (float)m.klo;
-  const float u = (E - (float)m.E0) * (float)m.inv_w;
+  if (m.is_const) return m.klo_f;
+  const float u = (E - m.E0_f) * m.inv_w_f;
   float s;
   if (u >= 0.0f) {
     s = 1.0f / (1.0f + expf(-u));
@@ -825,7 +827,7 @@ __device__ __forceinline__ float kappa32(const MaterialDev& m, float E) {
     const float e = expf(u);
     s = e / (1.0f + e);
   }
-  return (float)m.klo + (float)(m.khi - m.klo) * s;
+  return m.klo_f + m.dk_f * s;
 }
 
 __global__ void k_elem64(int64_t nt, const int4* __restrict__ conn, const uint8_t* __restrict__ mat,
@@ -901,7 +903,7 @@ __device__ __forceinline__ void elem32_tet(int64_t e, const int4* __restrict__ c
   const MaterialDev m = mats[mat[e]];
   float kap;
   if (m.is_const) {
-    kap = (float)m.klo;
+    kap = m.klo_f;
   } else {
     const float E = sqrtf(gx * gx + gy * gy + gz * gz) / D;
     kap = kappa32(m, E);
@@ -934,6 +936,12 @@ template <>
 __device__ __forceinline__ double kappa_of<double>(const MaterialDev& m, double E) { return kappa64(m, E); }
 template <>
 __device__ __forceinline__ float kappa_of<float>(const MaterialDev& m, float E) { return kappa32(m, E); }
+template <typename R>
+__device__ __forceinline__ R kappa_lo(const MaterialDev& m);
+template <>
+__device__ __forceinline__ double kappa_lo<double>(const MaterialDev& m) { return m.klo; }
+template <>
+__device__ __forceinline__ float kappa_lo<float>(const MaterialDev& m) { return m.klo_f; }
 
 // ------------------------------------------------ Kuhn-cell element kernels
 // Meshes whose tets come in groups of six forming one Kuhn-split hexahedron
@@ -959,7 +967,7 @@ __device__ __forceinline__ void tet_residual(const R (&e)[3][3], R d1, R d2, R d
   const R gz = d1 * c1z + d2 * c2z + d3 * c3z;
   R kap;
   if (m.is_const) {
-    kap = (R)m.klo;
+    kap = kappa_lo<R>(m);
   } else {
     const R E = sqrt(gx * gx + gy * gy + gz * gz) / D;
     kap = kappa_of<R>(m, E);
@@ -1112,7 +1120,7 @@ __device__ __forceinline__ void p2_residual(const R (&gl)[4][3], R D, const R (&
     for (int c = 0; c < 3; ++c) g[c] = a[0] * gl[0][c] + a[1] * gl[1][c] + a[2] * gl[2][c] + a[3] * gl[3][c];
     R kap;
     if (m.is_const) {
-      kap = (R)m.klo;
+      kap = kappa_lo<R>(m);
     } else {
       const R E = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) / D;
       kap = kappa_of<R>(m, E);

@@ -1133,9 +1133,14 @@ static eqs_status ens_enqueue_step(eqs_ctx* c, int s, double* X, const double* d
              spe ? c->d_eX : nullptr, kEnsSpe);
       if (last) break;
     }
-    launch(k4_elem32, nblk(c->n_tets), kBlock, st, c->n_tets, (const int4*)c->d_conn, (const uint8_t*)c->d_mat,
-           (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi, (const float4*)c->d_xyz_lo,
-           (const float4*)c->d_eY2, nf, c->d_ey32);
+    if (c->n_cells > 0)  // Kuhn cells: one 16-byte atomic per corner, 8 per six tets
+      launch(k4_elem32_cell, nblk(c->n_cells), kBlock, st, c->n_cells, (const int32_t*)c->d_corner,
+             (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi,
+             (const float4*)c->d_xyz_lo, (const float4*)c->d_eY2, nf, c->d_ey32);
+    else
+      launch(k4_elem32, nblk(c->n_tets), kBlock, st, c->n_tets, (const int4*)c->d_conn, (const uint8_t*)c->d_mat,
+             (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi, (const float4*)c->d_xyz_lo,
+             (const float4*)c->d_eY2, nf, c->d_ey32);
     launch(k4_rhs, nblk(nf), kBlock, st, nf, c->d_ey32, (const double*)(c->d_gp + j), (const double*)c->d_ecolv,
            (const double*)c->d_mtop, c->d_eR);
     EnsSlots sl{c->d_eiters + kEnsW * j, c->d_erelres + kEnsW * j, c->d_ezero + kEnsW * j};
@@ -1416,6 +1421,10 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     md[m].inv_w = q.kappa_hi != q.kappa_lo ? 1.0 / q.w : 0.0;
     md[m].is_const = q.kappa_hi == q.kappa_lo;
     md[m].pad = 0;
+    md[m].klo_f = (float)md[m].klo;
+    md[m].dk_f = (float)(md[m].khi - md[m].klo);
+    md[m].E0_f = (float)md[m].E0;
+    md[m].inv_w_f = (float)md[m].inv_w;
   }
   CK(upload(c, &c->d_conn, conn.data(), conn.size()));
   c->d_conn10 = nullptr;

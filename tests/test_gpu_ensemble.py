@@ -167,3 +167,14 @@ def test_ensemble_rejects_other_guess_modes(E):
         E.eqs_ens_rkc_step(S.ctx, x, SCALES, 0.0, 1e-3, 10)
     assert ex.value.status == E.EQS_ERR_STATE
     S.close()
+
+
+def test_ensemble_cell_and_tet_element_paths_agree(E):
+    """Kuhn-ordered tets take the four-column cell kernel; shuffled tets the
+    per-tet kernel: the trajectories agree."""
+    p = ei.config_problem(2, N=6)
+    perm = np.random.default_rng(2).permutation(p.n_tets)
+    q = ei.Problem(p.N, p.xyz, p.tets[perm], p.tet_mat[perm], p.node_tag, p.materials, p.V0)
+    a, _, _ = _ens_run(E, p, SCALES, 10, 2, rtol=1e-12)
+    b, _, _ = _ens_run(E, q, SCALES, 10, 2, rtol=1e-12)
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-7 * np.abs(a).max())
