@@ -798,7 +798,7 @@ def run_ensemble_headline(args, rank, world):
         "dtype": "f32/f64 mixed", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_free": p.n_free, "trajectories": 4,
                    "drive_scales": list(ENS_SCALES), "stages": S_STAGES, "rtol": RTOL,
-                   "solver": dict(SOLVER_OPTS, spe_n=4),
+                   "solver": dict(SOLVER_OPTS, spe_n=SPE_N),
                    "form": "4-member ensemble, blocked CG (SpMM over the four right-hand sides of a "
                            "stage), mixed precision, per-column SPE start vectors (Section IV)",
                    "m_solve_ms_per_rhs": ms_step / (4 * S_STAGES),

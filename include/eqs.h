@@ -123,6 +123,11 @@ typedef struct {
                           until they do; 0: lanes by row length only (for
                           contexts that run together in a batch, where each
                           instance owns a few CTAs)                         */
+  int coarse_split;    /* EQS_PREC_MIXED only: 0 (default) applies the FP32
+                          rounding of the coarsest level's dense inverse with
+                          FP32 row sums; 1 applies it as two FP32 parts with
+                          FP32-pair row sums (twice the bytes).  Ignored in
+                          FP64 mode.                                        */
 } eqs_opts;
 
 #define EQS_MAX_STAGES 64
@@ -146,7 +151,7 @@ typedef struct {
  * max_levels 10, degree 2, alpha 30, rtol 1e-8, max_iter 500, GUESS_PREV,
  * flexible 1, persistent 0, blocks_per_sm 1, spe_n 4, host_loop 0,
  * barrier_polls 0, split_m 1, pod_k 12, pod_m 6, pod_min_iters 3,
- * fill_lanes 1). */
+ * fill_lanes 1, coarse_split 0). */
 void eqs_opts_default(eqs_opts* o);
 
 /* Create a context from a tetrahedral mesh (Eq. 2 discretisation input).

@@ -286,6 +286,62 @@ __global__ void k_coarse_solve_df(int n, const float* __restrict__ ihi, const fl
     for (int c = 0; c < W; ++c) x[(int64_t)warp * W + c] = (float)((double)S[c] + (double)s[c]);
 }
 
+// Coarsest level, W interleaved columns: x = A_c^-1 b with the FP32 rounding
+// of the dense inverse and FP32 row sums (the V-cycle around it is FP32, so
+// the FP32-pair form above buys no accuracy the preconditioner keeps).  Rows
+// are padded to ld floats (a multiple of 4, zeros beyond n) so that every
+// row starts on a 16-byte boundary; one warp per row, b staged once per
+// block in shared memory, zero-padded to ld.  W = 1 reads the row as float4
+// (four columns per load, b as the matching float4); W = 4 reads one
+// column per lane and load (b rows are one float4 each: conflict-free).
+template <int W>
+__global__ void k_coarse_solve32(int n, int ld, const float* __restrict__ inv, const float* __restrict__ b,
+                                 float* __restrict__ x) {
+  static_assert(W == 1 || W == 4, "one or four interleaved columns");
+  extern __shared__ float4 sb4[];
+  float* sbf = reinterpret_cast<float*>(sb4);
+  pdl_enter();
+  for (int j = threadIdx.x; j < ld * W; j += blockDim.x) sbf[j] = j < n * W ? b[j] : 0.f;
+  __syncthreads();
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  float S[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) S[c] = 0.f;
+  if constexpr (W == 1) {
+    const float4* __restrict__ r4 = reinterpret_cast<const float4*>(inv + (int64_t)warp * ld);
+    const int n4 = ld >> 2;
+#pragma unroll 4
+    for (int q = lane; q < n4; q += 32) {
+      const float4 a = __ldg(r4 + q);
+      const float4 bq = sb4[q];
+      S[0] = fmaf(a.x, bq.x, S[0]);
+      S[0] = fmaf(a.y, bq.y, S[0]);
+      S[0] = fmaf(a.z, bq.z, S[0]);
+      S[0] = fmaf(a.w, bq.w, S[0]);
+    }
+  } else {
+    const float* __restrict__ r = inv + (int64_t)warp * ld;
+#pragma unroll 4
+    for (int j = lane; j < n; j += 32) {
+      const float a = __ldg(r + j);
+      const float4 bj = sb4[j];
+      S[0] = fmaf(a, bj.x, S[0]);
+      S[1] = fmaf(a, bj.y, S[1]);
+      S[2] = fmaf(a, bj.z, S[2]);
+      S[3] = fmaf(a, bj.w, S[3]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < W; ++c) S[c] += __shfl_xor_sync(0xffffffffu, S[c], o);
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < W; ++c) x[(int64_t)warp * W + c] = S[c];
+}
+
 // Interleave four column-major FP64 columns (column c at src + c n) into
 // rows of four, and back.
 __global__ void k4_interleave(int n, const double* __restrict__ src, double4_32a* __restrict__ dst) {

@@ -222,6 +222,8 @@ struct eqs_ctx {
   // ---- split coarse inverse (mixed precision): inv = hi + lo, FP32 parts
   float* d_cinv_hi = nullptr;
   float* d_cinv_lo = nullptr;
+  float* d_cinv32 = nullptr;  // FP32 inverse, rows padded to cinv_ld floats
+  int cinv_ld = 0;
 
   // ---- ensemble of 4 trajectories (allocated by the first ensemble call;
   // every vector row-interleaved, 4 columns per row)

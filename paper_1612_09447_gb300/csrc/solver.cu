@@ -316,6 +316,11 @@ static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStrea
   DevLevel<T>& V = L[l];
   if (l == nl - 1) {
     if constexpr (std::is_same<T, float>::value) {
+      if (c->d_cinv32) {  // FP32 inverse, FP32 row sums
+        launch_smem(k_coarse_solve32<1>, nblk((int64_t)V.n * 32), kBlock, (size_t)c->cinv_ld * sizeof(float), st,
+                    V.n, c->cinv_ld, (const float*)c->d_cinv32, (const float*)V.b, (float*)V.x);
+        return nullptr;
+      }
       if (c->d_cinv_hi) {  // FP32-pair application of the split inverse
         launch_smem(k_coarse_solve_df<1>, nblk((int64_t)V.n * 32), kBlock, (size_t)V.n * sizeof(float), st, V.n,
                     (const float*)c->d_cinv_hi, (const float*)c->d_cinv_lo, (const float*)V.b, (float*)V.x);
@@ -915,7 +920,7 @@ static eqs_status vcycle_impl(eqs_ctx* c, std::vector<DevLevel<T>>& L, const dou
 // precision with the previous-solution start vector.
 static eqs_status ens_alloc(eqs_ctx* c) {
   if (c->ens_ready) return EQS_OK;
-  if (!mixed(c) || !c->d_M_hi || !c->d_cinv_hi)
+  if (!mixed(c) || !c->d_M_hi || !(c->d_cinv_hi || c->d_cinv32))
     return fail(c, EQS_ERR_STATE, "the ensemble needs a context set up in EQS_PREC_MIXED with split_m 1");
   if (c->npe != 4) return fail(c, EQS_ERR_STATE, "the ensemble runs linear (4-node) tets");
   if (c->opts.guess != EQS_GUESS_PREV && c->opts.guess != EQS_GUESS_SPE)
@@ -959,8 +964,12 @@ static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st, bool fuse_do
   DevLevel<float>& V = L[l];
   eqs_ctx::EnsLevel& E = c->elev[l];
   if (l == nl - 1) {
-    launch_smem(k_coarse_solve_df<4>, nblk((int64_t)V.n * 32), kBlock, (size_t)V.n * sizeof(float4), st, V.n,
-                (const float*)c->d_cinv_hi, (const float*)c->d_cinv_lo, (const float*)E.b, (float*)E.x);
+    if (c->d_cinv32)
+      launch_smem(k_coarse_solve32<4>, nblk((int64_t)V.n * 32), kBlock, (size_t)c->cinv_ld * sizeof(float4), st,
+                  V.n, c->cinv_ld, (const float*)c->d_cinv32, (const float*)E.b, (float*)E.x);
+    else
+      launch_smem(k_coarse_solve_df<4>, nblk((int64_t)V.n * 32), kBlock, (size_t)V.n * sizeof(float4), st, V.n,
+                  (const float*)c->d_cinv_hi, (const float*)c->d_cinv_lo, (const float*)E.b, (float*)E.x);
     return nullptr;
   }
   const int deg = c->opts.cheb_degree;
@@ -1237,6 +1246,7 @@ void eqs_opts_default(eqs_opts* o) {
   o->pod_m = 6;
   o->pod_min_iters = 3;
   o->fill_lanes = 1;
+  o->coarse_split = 0;
 }
 
 static eqs_status mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
@@ -1318,6 +1328,7 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     eqs_opts_default(&o);
   if (o.cheb_degree < 1 || o.cheb_degree > 4 || o.blocks_per_sm < 0 || o.spe_n < 1 || o.spe_n > kSpeMax || o.max_levels < 1 || o.coarse_max < 1 ||
       o.pod_k < 1 || o.pod_k > kPodMax || o.pod_m < 1 || o.pod_m > o.pod_k || o.pod_min_iters < 0 ||
+      (o.coarse_split != 0 && o.coarse_split != 1) ||
       !(o.theta >= 0) || !(o.cheb_alpha > 1) || !(o.rtol > 0) || o.max_iter < 1 ||
       (o.precision != EQS_PREC_FP64 && o.precision != EQS_PREC_MIXED))
     return fail(c, EQS_ERR_ARG, "invalid eqs_opts");
@@ -1455,19 +1466,33 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     CK(dalloc(c, &c->d_z32, std::max<int64_t>(nf, 1)));
   }
   CK(upload(c, &c->d_coarse_inv, inv.data(), inv.size()));
-  c->d_cinv_hi = c->d_cinv_lo = nullptr;
-  if (mixed(c)) {  // the FP32-pair coarse solve of the mixed V-cycle
-    std::vector<float> ih(inv.size()), il(inv.size());
-    for (size_t k = 0; k < inv.size(); ++k) {
-      ih[k] = (float)inv[k];
-      il[k] = (float)(inv[k] - (double)ih[k]);
-    }
-    CK(upload(c, &c->d_cinv_hi, ih.data(), ih.size()));
-    CK(upload(c, &c->d_cinv_lo, il.data(), il.size()));
-    const size_t smem = (size_t)c->coarse_n * 4 * sizeof(float);
+  c->d_cinv_hi = c->d_cinv_lo = c->d_cinv32 = nullptr;
+  c->cinv_ld = 0;
+  if (mixed(c)) {  // the FP32 (or FP32-pair) coarse solve of the mixed V-cycle
+    const int nc = c->coarse_n;
+    const int ld = (nc + 3) & ~3;
+    const size_t smem = (size_t)ld * 4 * sizeof(float);
     if (smem > 227 * 1024) return fail(c, EQS_ERR_ARG, "coarsest level too large for the shared-memory coarse solve");
-    CK(cudaFuncSetAttribute(k_coarse_solve_df<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
-    CK(cudaFuncSetAttribute(k_coarse_solve_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
+    const int smem_attr = (int)std::max<size_t>(smem, 48 * 1024);
+    if (c->opts.coarse_split) {
+      std::vector<float> ih(inv.size()), il(inv.size());
+      for (size_t k = 0; k < inv.size(); ++k) {
+        ih[k] = (float)inv[k];
+        il[k] = (float)(inv[k] - (double)ih[k]);
+      }
+      CK(upload(c, &c->d_cinv_hi, ih.data(), ih.size()));
+      CK(upload(c, &c->d_cinv_lo, il.data(), il.size()));
+      CK(cudaFuncSetAttribute(k_coarse_solve_df<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_attr));
+      CK(cudaFuncSetAttribute(k_coarse_solve_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_attr));
+    } else {
+      std::vector<float> i32((size_t)nc * ld, 0.f);
+      for (int r = 0; r < nc; ++r)
+        for (int k = 0; k < nc; ++k) i32[(size_t)r * ld + k] = (float)inv[(size_t)r * nc + k];
+      CK(upload(c, &c->d_cinv32, i32.data(), i32.size()));
+      c->cinv_ld = ld;
+      CK(cudaFuncSetAttribute(k_coarse_solve32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_attr));
+      CK(cudaFuncSetAttribute(k_coarse_solve32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_attr));
+    }
   }
   c->lev64.clear();
   c->lev32.clear();

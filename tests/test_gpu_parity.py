@@ -129,6 +129,21 @@ def test_vcycle(E, name, prec, tol):
     S.close()
 
 
+@pytest.mark.parametrize("name", ["cube12", "jitter10"])
+@pytest.mark.parametrize("coarse_split", [0, 1])
+def test_vcycle_mixed_coarse_forms(E, name, coarse_split):
+    """Both mixed coarsest-level forms (FP32 inverse, FP32-pair inverse) give
+    the oracle's V-cycle to FP32 accuracy, on a three-level hierarchy."""
+    p = PROBLEMS[name]()
+    S = E.Solver(p, precision=MIXED, coarse_max=60, coarse_split=coarse_split)
+    H = amg.SAHierarchy(system.EQSSystem(p).Mff, coarse_max=60)
+    assert len(H.levels) >= 3
+    r = np.random.default_rng(14).standard_normal(p.n_free)
+    got = S.vcycle(_cuda(r)).cpu().numpy()
+    assert _relmax(got, H(r)) <= 1e-4
+    S.close()
+
+
 @pytest.mark.parametrize("name", ["cube12", "jitter10", "cube2"])
 @pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_solve_M(E, name, prec):
