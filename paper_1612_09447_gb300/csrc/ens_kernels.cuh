@@ -309,11 +309,28 @@ __global__ void k_coarse_solve32(int n, int ld, const float* __restrict__ inv, c
   float S[W];
 #pragma unroll
   for (int c = 0; c < W; ++c) S[c] = 0.f;
+  // The row's loads are issued in batches of U per lane before any of them
+  // is used, so that each warp keeps U loads in flight (the kernel is bound
+  // by load latency: a few warps per SM, one row each).
   if constexpr (W == 1) {
+    constexpr int U = 16;
     const float4* __restrict__ r4 = reinterpret_cast<const float4*>(inv + (int64_t)warp * ld);
     const int n4 = ld >> 2;
-#pragma unroll 4
-    for (int q = lane; q < n4; q += 32) {
+    int q = lane;
+    for (; q + 32 * (U - 1) < n4; q += 32 * U) {  // full batches
+      float4 a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) a[u] = __ldg(r4 + q + 32 * u);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float4 bq = sb4[q + 32 * u];
+        S[0] = fmaf(a[u].x, bq.x, S[0]);
+        S[0] = fmaf(a[u].y, bq.y, S[0]);
+        S[0] = fmaf(a[u].z, bq.z, S[0]);
+        S[0] = fmaf(a[u].w, bq.w, S[0]);
+      }
+    }
+    for (; q < n4; q += 32) {  // the rest of the row
       const float4 a = __ldg(r4 + q);
       const float4 bq = sb4[q];
       S[0] = fmaf(a.x, bq.x, S[0]);
@@ -322,9 +339,23 @@ __global__ void k_coarse_solve32(int n, int ld, const float* __restrict__ inv, c
       S[0] = fmaf(a.w, bq.w, S[0]);
     }
   } else {
+    constexpr int U = 16;
     const float* __restrict__ r = inv + (int64_t)warp * ld;
-#pragma unroll 4
-    for (int j = lane; j < n; j += 32) {
+    int j = lane;
+    for (; j + 32 * (U - 1) < n; j += 32 * U) {  // full batches
+      float a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) a[u] = __ldg(r + j + 32 * u);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float4 bj = sb4[j + 32 * u];
+        S[0] = fmaf(a[u], bj.x, S[0]);
+        S[1] = fmaf(a[u], bj.y, S[1]);
+        S[2] = fmaf(a[u], bj.z, S[2]);
+        S[3] = fmaf(a[u], bj.w, S[3]);
+      }
+    }
+    for (; j < n; j += 32) {  // the rest of the row
       const float a = __ldg(r + j);
       const float4 bj = sb4[j];
       S[0] = fmaf(a, bj.x, S[0]);
@@ -748,9 +779,16 @@ __global__ void k4_spe_gram(DevSell<double> M, int nf, const double4_32a* __rest
     }
   }
   double tot[NS];
-  if (grid_sum<NS>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0)
-    for (int c = 0; c < kEnsW; ++c)
-      spe_solve<NH>(tot + c * 2 * NH, g, m, sn, G + c * kSpeMax * kSpeMax, drop2, coef + c * (kSpeMax + 1));
+  __shared__ double stot[NS];
+  if (grid_sum<NS>(v, partials, counter, max_blocks, tot)) {  // the last block: the four small solves
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < NS; ++k) stot[k] = tot[k];
+    __syncthreads();
+    const int c = threadIdx.x;  // one thread per column, side by side
+    if (c < kEnsW)
+      spe_solve<NH>(stot + c * 2 * NH, g, m, sn, G + c * kSpeMax * kSpeMax, drop2, coef + c * (kSpeMax + 1));
+  }
 }
 
 // CG start of the four columns from their SPE vectors: x0 = X a_c,

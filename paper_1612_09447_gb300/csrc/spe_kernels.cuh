@@ -27,59 +27,77 @@ __device__ __forceinline__ int spe_slot(long long q, int NH) { return (int)(((q 
 
 // Last block of a Gram pass: store the new Gram column of slot sn (tot[0..m)),
 // solve (L L^T) y = c (c = tot[NH..NH+m)) by Cholesky with column dropping
-// (most recent first) and write y by ring slot plus the slots in use.
+// (most recent first) and write y by ring slot plus the slots in use.  One
+// thread; every loop runs over the compile-time NH (rows k >= m are zero and
+// never kept), so the small matrices stay in registers instead of local
+// memory and the serial tail is short.
 template <int NH>
 __device__ void spe_solve(const double* tot, long long g, int m, int sn, double* __restrict__ G, double drop2,
                           double* __restrict__ y_out) {
   int slot[NH];
+#pragma unroll
   for (int k = 0; k < NH; ++k) slot[k] = spe_slot(g - 1 - k, NH);
-  for (int k = 0; k < m; ++k) {  // new Gram column and row of the newest slot
-    G[slot[k] * kSpeMax + sn] = tot[k];
-    G[sn * kSpeMax + slot[k]] = tot[k];
-  }
-  double A[NH][NH], c[NH], L[NH][NH], y[NH];
+#pragma unroll
+  for (int k = 0; k < NH; ++k)
+    if (k < m) {  // new Gram column and row of the newest slot
+      G[slot[k] * kSpeMax + sn] = tot[k];
+      G[sn * kSpeMax + slot[k]] = tot[k];
+    }
+  double A[NH][NH], L[NH][NH], c[NH], z[NH], y[NH];
   bool keep[NH];
+#pragma unroll
   for (int k = 0; k < NH; ++k) {
     c[k] = tot[NH + k];
     keep[k] = false;
+    z[k] = 0.0;
     y[k] = 0.0;
+#pragma unroll
     for (int l = 0; l < NH; ++l) {
       A[k][l] = (k < m && l < m) ? G[slot[k] * kSpeMax + slot[l]] : 0.0;
       L[k][l] = 0.0;
     }
   }
-  for (int k = 0; k < m; ++k) {
+#pragma unroll
+  for (int k = 0; k < NH; ++k) {
     double d = A[k][k];
+#pragma unroll
     for (int p = 0; p < k; ++p)
       if (keep[p]) d -= L[k][p] * L[k][p];
-    if (!(A[k][k] > 0.0) || !(d > drop2 * A[k][k])) continue;
-    keep[k] = true;
+    keep[k] = A[k][k] > 0.0 && d > drop2 * A[k][k];
+    if (!keep[k]) continue;
     L[k][k] = sqrt(d);
-    for (int r = k + 1; r < m; ++r) {
+#pragma unroll
+    for (int r = k + 1; r < NH; ++r) {
       double e = A[r][k];
+#pragma unroll
       for (int p = 0; p < k; ++p)
         if (keep[p]) e -= L[r][p] * L[k][p];
       L[r][k] = e / L[k][k];
     }
   }
-  double z[NH];
-  for (int k = 0; k < m; ++k) {  // L z = c (kept rows)
-    z[k] = 0.0;
+#pragma unroll
+  for (int k = 0; k < NH; ++k) {  // L z = c (kept rows)
     if (!keep[k]) continue;
     double e = c[k];
+#pragma unroll
     for (int p = 0; p < k; ++p)
       if (keep[p]) e -= L[k][p] * z[p];
     z[k] = e / L[k][k];
   }
-  for (int k = m - 1; k >= 0; --k) {  // L^T y = z
+#pragma unroll
+  for (int k = NH - 1; k >= 0; --k) {  // L^T y = z
     if (!keep[k]) continue;
     double e = z[k];
-    for (int r = k + 1; r < m; ++r)
+#pragma unroll
+    for (int r = k + 1; r < NH; ++r)
       if (keep[r]) e -= L[r][k] * y[r];
     y[k] = e / L[k][k];
   }
+#pragma unroll
   for (int k = 0; k < NH; ++k) y_out[k] = 0.0;
-  for (int k = 0; k < m; ++k) y_out[slot[k]] = y[k];
+#pragma unroll
+  for (int k = 0; k < NH; ++k)
+    if (k < m) y_out[slot[k]] = y[k];
   reinterpret_cast<int*>(y_out + kSpeMax)[0] = m;
 }
 
