@@ -718,17 +718,24 @@ __global__ void k4_pcg_update(int n, double4_32a* __restrict__ x, double4_32a* _
     const int pass = sc->pass + 1;
     sc->pass = pass;
     int go = 0;
+    int act[kEnsW];
     for (int c = 0; c < kEnsW; ++c) {
-      if (sc->conv[c]) continue;
+      act[c] = !sc->conv[c];
+      if (!act[c]) continue;
       sc->rnorm2[c] = tot[c];
       sc->it[c] += 1;
       const int conv = tot[c] <= tol2 * sc->bnorm2[c];
       sc->conv[c] = conv;
       go |= !conv;
       if (iters_out) iters_out[c] = sc->it[c];
-      if (relres_out) relres_out[c] = sqrt(tot[c] / sc->bnorm2[c]);
     }
-    if (use_handle) cudaGraphSetConditional(h, (go && pass < maxit) ? 1u : 0u);
+    const int more = go && pass < maxit;
+    if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
+    // final relative residuals only for columns that stop now (a division
+    // and a square root are long FP64 chains in this one-thread tail)
+    if (relres_out)
+      for (int c = 0; c < kEnsW; ++c)
+        if (act[c] && (sc->conv[c] || !more)) relres_out[c] = sqrt(tot[c] / sc->bnorm2[c]);
   }
 }
 

@@ -790,7 +790,9 @@ __global__ void k_pcg_update(int n, double* __restrict__ x, double* __restrict__
     const int go = !conv && it < maxit;
     if (use_handle) cudaGraphSetConditional(h, go ? 1u : 0u);
     if (iters_out) *iters_out = it;
-    if (relres_out) *relres_out = sqrt(tot[0] / sc->bnorm2);
+    // the final relative residual only when the loop ends (a division and a
+    // square root are long FP64 chains in this one-thread tail)
+    if (relres_out && !go) *relres_out = sqrt(tot[0] / sc->bnorm2);
   }
 }
 

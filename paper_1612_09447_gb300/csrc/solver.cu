@@ -388,10 +388,15 @@ struct SpeAt {
 
 // SPE projection of solve j (templated on the history length): the newest
 // solution's product with M, the Gram column and the coefficients y.
+// Two blocks per SM where they fit: the pass is bound by FP64 latency with
+// 8 warps per SM; more blocks than are resident would run in a second wave.
 template <int NH>
 static void spe_gram_n(eqs_ctx* c, cudaStream_t st, int s, int j) {
   const int nf = (int)c->n_free;
-  launch(k_spe_gram<NH>, std::max(1, std::min(nblk(nf), c->sms)), kBlock, st, c->M64, nf,
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spe_gram<NH>, kBlock, 0) != cudaSuccess) occ = 1;
+  const int bps = std::max(1, std::min(occ, 2));
+  launch(k_spe_gram<NH>, std::max(1, std::min(nblk(nf), c->sms * bps)), kBlock, st, c->M64, nf,
          (const double*)c->d_spe_X, c->d_spe_W, (const double*)c->d_R, (const long long*)c->d_stepcount, s, j,
          c->d_spe_G, c->d_spe_partials, c->red.counter, c->red.max_blocks, 1e-12, c->d_spe_y);
 }

@@ -30,7 +30,11 @@ __device__ __forceinline__ int spe_slot(long long q, int NH) { return (int)(((q 
 // (most recent first) and write y by ring slot plus the slots in use.  One
 // thread; every loop runs over the compile-time NH (rows k >= m are zero and
 // never kept), so the small matrices stay in registers instead of local
-// memory and the serial tail is short.
+// memory.  On GB300 every FP64 instruction of this serial tail occupies the
+// slow FP64 pipe of its SM sub-partition for a whole warp's worth of lanes,
+// so the factor keeps the reciprocal of each pivot (one rsqrt per column)
+// and multiplies by it instead of dividing (an IEEE division is a chain of
+// about ten FP64 operations).
 template <int NH>
 __device__ void spe_solve(const double* tot, long long g, int m, int sn, double* __restrict__ G, double drop2,
                           double* __restrict__ y_out) {
@@ -43,12 +47,13 @@ __device__ void spe_solve(const double* tot, long long g, int m, int sn, double*
       G[slot[k] * kSpeMax + sn] = tot[k];
       G[sn * kSpeMax + slot[k]] = tot[k];
     }
-  double A[NH][NH], L[NH][NH], c[NH], z[NH], y[NH];
+  double A[NH][NH], L[NH][NH], c[NH], z[NH], y[NH], inv[NH];
   bool keep[NH];
 #pragma unroll
   for (int k = 0; k < NH; ++k) {
     c[k] = tot[NH + k];
     keep[k] = false;
+    inv[k] = 0.0;
     z[k] = 0.0;
     y[k] = 0.0;
 #pragma unroll
@@ -65,14 +70,14 @@ __device__ void spe_solve(const double* tot, long long g, int m, int sn, double*
       if (keep[p]) d -= L[k][p] * L[k][p];
     keep[k] = A[k][k] > 0.0 && d > drop2 * A[k][k];
     if (!keep[k]) continue;
-    L[k][k] = sqrt(d);
+    inv[k] = rsqrt(d);  // 1 / L[k][k]
 #pragma unroll
     for (int r = k + 1; r < NH; ++r) {
       double e = A[r][k];
 #pragma unroll
       for (int p = 0; p < k; ++p)
         if (keep[p]) e -= L[r][p] * L[k][p];
-      L[r][k] = e / L[k][k];
+      L[r][k] = e * inv[k];
     }
   }
 #pragma unroll
@@ -82,7 +87,7 @@ __device__ void spe_solve(const double* tot, long long g, int m, int sn, double*
 #pragma unroll
     for (int p = 0; p < k; ++p)
       if (keep[p]) e -= L[k][p] * z[p];
-    z[k] = e / L[k][k];
+    z[k] = e * inv[k];
   }
 #pragma unroll
   for (int k = NH - 1; k >= 0; --k) {  // L^T y = z
@@ -91,7 +96,7 @@ __device__ void spe_solve(const double* tot, long long g, int m, int sn, double*
 #pragma unroll
     for (int r = k + 1; r < NH; ++r)
       if (keep[r]) e -= L[r][k] * y[r];
-    y[k] = e / L[k][k];
+    y[k] = e * inv[k];
   }
 #pragma unroll
   for (int k = 0; k < NH; ++k) y_out[k] = 0.0;
