@@ -71,6 +71,7 @@ struct HostLevel {
 // Per-solve reduction scalars (device).
 struct PcgScalars {
   double bnorm2, rnorm2, rz, rz_old, zr_prev, pq, alpha, beta;
+  double rz_hist[2];  // deferred sums: r.z of iteration it in slot it & 1
   int it, conv, parity, use_prev;  // use_prev: the previous solution replaced the learned guess
 };
 
@@ -223,6 +224,7 @@ struct eqs_ctx {
   float* d_cinv_hi = nullptr;
   float* d_cinv_lo = nullptr;
   float* d_cinv32 = nullptr;  // FP32 inverse, rows padded to cinv_ld floats
+  double* d_dpart = nullptr;  // deferred CG sums (3 x red.max_blocks)
   int cinv_ld = 0;
 
   // ---- ensemble of 4 trajectories (allocated by the first ensemble call;

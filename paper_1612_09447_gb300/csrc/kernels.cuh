@@ -448,6 +448,37 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, unsi
   return true;
 }
 
+// Deferred sums (the CG's consumer-side reductions): a producer kernel ends
+// with its block sums in part[k * cap + block] and no grid-wide step; every
+// block of the consuming kernel adds the nb partials itself, in a fixed
+// order, so all blocks hold the same totals -- no atomic ticket, no fence
+// and no serial last block between the two kernels.
+template <int NV>
+__device__ __forceinline__ void write_partials(double (&v)[NV], double* __restrict__ part, int cap) {
+  block_sum<NV>(v);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) part[k * cap + blockIdx.x] = v[k];
+}
+
+template <int NV>
+__device__ __forceinline__ void sum_partials(const double* __restrict__ part, int nb, int cap, double (&tot)[NV]) {
+  __shared__ double bc[NV];
+  double v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += __ldcg(part + k * cap + b);
+  block_sum<NV>(v);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) bc[k] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = bc[k];
+}
+
 // ------------------------------------------------------------------ PCG
 // CG kernels run grid-stride over rows with a capped grid (fewer blocks take
 // part in the atomic ticket of each grid reduction).
@@ -598,12 +629,15 @@ __global__ void k_pcg_dots(int n, const double* __restrict__ r, const double* __
 // z = x + d (FP32 z32 for the split-M operator pass, else FP64 zd); sums
 // r_cg.z and r_prev.z; the last block forms beta (as k_pcg_dots).  Saves
 // one kernel per CG iteration: every value it needs is row-local.
-template <typename T>
+// DEFER: the two sums are left as per-block partials in dpart (the split-M
+// operator pass adds them and forms beta).
+template <typename T, bool DEFER>
 __global__ void __launch_bounds__(kBlock, 4)
 k_post_first_dots(DevSell<T> A, int n, const T* __restrict__ b, const T* __restrict__ x,
                   const T* __restrict__ dinv, T inv_theta, const double* __restrict__ rcg,
                   const double* __restrict__ rprev, double* __restrict__ zd, float* __restrict__ z32,
-                  PcgScalars* sc, double* partials, unsigned int* counter, int max_blocks, int flexible) {
+                  PcgScalars* sc, double* partials, unsigned int* counter, int max_blocks, int flexible,
+                  double* __restrict__ dpart) {
   pdl_enter();
   double v[2] = {0.0, 0.0};
   EQS_ROWS2(A, n, {
@@ -625,6 +659,10 @@ k_post_first_dots(DevSell<T> A, int n, const T* __restrict__ b, const T* __restr
       v[1] += rprev[i] * zi;
     }
   })
+  if constexpr (DEFER) {
+    write_partials<2>(v, dpart, max_blocks);
+    return;
+  }
   double tot[2];
   if (grid_sum<2>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
     const double rz = tot[0];
@@ -720,13 +758,28 @@ __device__ __forceinline__ double mat_row_split(const DevSell<double>& A, const 
 }
 
 // k_pcg_pq with the split-M product: q = M z + beta q_old, p = z + beta p,
-// p.q and alpha (z in FP32).
+// p.q and alpha (z in FP32).  DEFER: every block first adds the nb_in
+// partials of r.z and r_prev.z left by k_post_first_dots (dpart) and forms
+// beta itself (block 0 records r.z by iteration parity in sc->rz_hist), and
+// p.q is left as per-block partials (dpart + 2 cap) for k_pcg_update.
+template <bool DEFER>
 __global__ void k_pcg_pq_split(DevSell<double> M, const float* __restrict__ Mhi,
                                const float* __restrict__ Mlo, int n, const float* __restrict__ z32,
                                double* __restrict__ p, double* __restrict__ q, PcgScalars* sc,
-                               double* partials, unsigned int* counter, int max_blocks) {
+                               double* partials, unsigned int* counter, int max_blocks,
+                               double* __restrict__ dpart, int nb_in, int flexible) {
   pdl_enter();
-  const double beta = sc->beta;
+  double beta;
+  if constexpr (DEFER) {
+    double d[2];
+    sum_partials<2>(dpart, nb_in, max_blocks, d);
+    const int it = sc->it;
+    beta = 0.0;
+    if (it > 0) beta = (flexible ? d[0] - d[1] : d[0]) / sc->rz_hist[(it + 1) & 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->rz_hist[it & 1] = d[0];
+  } else {
+    beta = sc->beta;
+  }
   double v[1] = {0.0};
   const int64_t st = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i0 = gtid(); i0 < n; i0 += 2 * st) {  // two rows in flight per thread
@@ -746,6 +799,10 @@ __global__ void k_pcg_pq_split(DevSell<double> M, const float* __restrict__ Mhi,
       v[0] += pi * qi;
     }
   }
+  if constexpr (DEFER) {
+    write_partials<1>(v, dpart + 2 * (size_t)max_blocks, max_blocks);
+    return;
+  }
   double tot[1];
   if (grid_sum<1>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
     sc->pq = tot[0];
@@ -754,8 +811,10 @@ __global__ void k_pcg_pq_split(DevSell<double> M, const float* __restrict__ Mhi,
 }
 
 // x += alpha p ; r_prev = r ; r -= alpha q ; ||r||^2 ; next V-cycle input;
-// the last block updates the loop condition and the statistics.
-template <typename T>
+// the last block updates the loop condition and the statistics.  DEFER:
+// every block adds the nb_in partials of p.q (dpart + 2 cap) and forms
+// alpha = r.z / p.q itself.
+template <typename T, bool DEFER>
 __global__ void k_pcg_update(int n, double* __restrict__ x, double* __restrict__ r,
                              double* __restrict__ rprev, const double* __restrict__ p,
                              const double* __restrict__ q, const T* __restrict__ dinv0,
@@ -763,9 +822,16 @@ __global__ void k_pcg_update(int n, double* __restrict__ x, double* __restrict__
                              T* __restrict__ d0, PcgScalars* sc, double* partials,
                              unsigned int* counter, int max_blocks, double tol2, int maxit,
                              cudaGraphConditionalHandle h, int use_handle, int* iters_out,
-                             double* relres_out) {
+                             double* relres_out, const double* __restrict__ dpart, int nb_in) {
   pdl_enter();
-  const double a = sc->alpha;
+  double a;
+  if constexpr (DEFER) {
+    double pq[1];
+    sum_partials<1>(dpart + 2 * (size_t)max_blocks, nb_in, max_blocks, pq);
+    a = sc->rz_hist[sc->it & 1] / pq[0];
+  } else {
+    a = sc->alpha;
+  }
   double v[1] = {0.0};
   for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] = fma(a, p[i], x[i]);

@@ -311,7 +311,7 @@ static cudaError_t upload_levels(eqs_ctx* c, std::vector<DevLevel<T>>& L) {
 // degree-1 post-smoother's d, folded into the consumer of x), or nullptr.
 template <typename T>
 static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStream_t st,
-                       bool fuse_dots = false) {
+                       bool fuse_dots = false, bool defer = false) {
   const int nl = (int)L.size();
   DevLevel<T>& V = L[l];
   if (l == nl - 1) {
@@ -356,9 +356,16 @@ static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStrea
   launch(k_prolong<T>, mat_grid(c, V.P, V.n), kBlock, st, V.P, V.n, C.x,
          (const T*)cpend, V.x);
   if (fuse_dots && l == 0 && deg == 1) {  // the CG dot products ride on the last smoothing pass
-    launch(k_post_first_dots<T>, g, kBlock, st, V.A, V.n, (const T*)V.b, (const T*)V.x, (const T*)V.dinv,
-           (T)V.inv_theta, (const double*)c->d_r, (const double*)c->d_rprev, c->d_zd, c->d_z32, c->d_sc,
-           c->red.partials, c->red.counter, c->red.max_blocks, c->opts.flexible);
+    if (defer)
+      launch(k_post_first_dots<T, true>, g, kBlock, st, V.A, V.n, (const T*)V.b, (const T*)V.x,
+             (const T*)V.dinv, (T)V.inv_theta, (const double*)c->d_r, (const double*)c->d_rprev, c->d_zd,
+             c->d_z32, c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks, c->opts.flexible,
+             c->d_dpart);
+    else
+      launch(k_post_first_dots<T, false>, g, kBlock, st, V.A, V.n, (const T*)V.b, (const T*)V.x,
+             (const T*)V.dinv, (T)V.inv_theta, (const double*)c->d_r, (const double*)c->d_rprev, c->d_zd,
+             c->d_z32, c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks, c->opts.flexible,
+             (double*)nullptr);
     return nullptr;
   }
   launch(k_post_first<T>, g, kBlock, st, V.A, V.n, V.b, V.x, V.dinv, (T)V.inv_theta, V.r, V.dA);
@@ -508,19 +515,35 @@ static void pcg_body_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_
   const int n = (int)c->n_free;
   const int g = vec_grid(c, n);
   const bool fuse = c->opts.cheb_degree == 1 && L.size() > 1;
-  T* zpend = vcycle_level(c, L, 0, st, fuse);
+  // deferred sums: the dot products of the fused smoothing pass and of the
+  // operator pass are added by the kernel that consumes them
+  const bool defer = fuse && c->d_z32 && c->opts.defer_sums;
+  T* zpend = vcycle_level(c, L, 0, st, fuse, defer);
   if (!fuse)
     launch(k_pcg_dots<T>, g, kBlock, st, n, c->d_r, c->d_rprev, V.x, (const T*)zpend, c->d_zd, c->d_z32,
            c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks, c->opts.flexible);
+  if (defer) {
+    const int g_dots = mat_grid(c, V.A, V.n);  // the grid of k_post_first_dots
+    launch(k_pcg_pq_split<true>, g, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo, n,
+           (const float*)c->d_z32, c->d_p, c->d_q, c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks,
+           c->d_dpart, g_dots, c->opts.flexible);
+    launch(k_pcg_update<T, true>, g, kBlock, st, n, x, c->d_r, c->d_rprev, c->d_p, c->d_q, V.dinv,
+           (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials, c->red.counter,
+           c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres,
+           (const double*)c->d_dpart, g);
+    return;
+  }
   if (c->d_z32)  // mixed path: FP32 z, split-M operator pass
-    launch(k_pcg_pq_split, g, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo, n,
-           (const float*)c->d_z32, c->d_p, c->d_q, c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks);
+    launch(k_pcg_pq_split<false>, g, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo, n,
+           (const float*)c->d_z32, c->d_p, c->d_q, c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks,
+           (double*)nullptr, 0, c->opts.flexible);
   else
     launch(k_pcg_pq, g, kBlock, st, c->M64, n, c->d_zd, c->d_p, c->d_q, c->d_sc, c->red.partials,
            c->red.counter, c->red.max_blocks);
-  launch(k_pcg_update<T>, g, kBlock, st, n, x, c->d_r, c->d_rprev, c->d_p, c->d_q, V.dinv,
+  launch(k_pcg_update<T, false>, g, kBlock, st, n, x, c->d_r, c->d_rprev, c->d_p, c->d_q, V.dinv,
          (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials, c->red.counter,
-         c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres);
+         c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres,
+         (const double*)nullptr, 0);
 }
 
 // Kernel nodes at the top level of graph g (loop bodies are not entered).
@@ -1252,6 +1275,7 @@ void eqs_opts_default(eqs_opts* o) {
   o->pod_min_iters = 3;
   o->fill_lanes = 1;
   o->coarse_split = 0;
+  o->defer_sums = 1;
 }
 
 static eqs_status mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
@@ -1333,7 +1357,7 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     eqs_opts_default(&o);
   if (o.cheb_degree < 1 || o.cheb_degree > 4 || o.blocks_per_sm < 0 || o.spe_n < 1 || o.spe_n > kSpeMax || o.max_levels < 1 || o.coarse_max < 1 ||
       o.pod_k < 1 || o.pod_k > kPodMax || o.pod_m < 1 || o.pod_m > o.pod_k || o.pod_min_iters < 0 ||
-      (o.coarse_split != 0 && o.coarse_split != 1) ||
+      (o.coarse_split != 0 && o.coarse_split != 1) || (o.defer_sums != 0 && o.defer_sums != 1) ||
       !(o.theta >= 0) || !(o.cheb_alpha > 1) || !(o.rtol > 0) || o.max_iter < 1 ||
       (o.precision != EQS_PREC_FP64 && o.precision != EQS_PREC_MIXED))
     return fail(c, EQS_ERR_ARG, "invalid eqs_opts");
@@ -1520,8 +1544,11 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
   CK(dalloc(c, &c->d_zero, EQS_MAX_STAGES + 1));
   CK(dalloc(c, &c->d_g, EQS_MAX_STAGES + 1));
   CK(dalloc(c, &c->d_gp, EQS_MAX_STAGES + 1));
-  c->red.max_blocks = nblk(std::max<int64_t>(nf, 1));
+  // room for the partial sums of every reducing grid: row kernels on lane
+  // groups can launch more blocks than nblk(nf), never more than 4 per SM
+  c->red.max_blocks = std::max(nblk(std::max<int64_t>(nf, 1)), 4 * c->sms);
   CK(dalloc(c, &c->red.partials, 4 * (size_t)c->red.max_blocks));
+  CK(dalloc(c, &c->d_dpart, 3 * (size_t)c->red.max_blocks));  // deferred CG sums: r.z, r_prev.z; p.q
   CK(dalloc(c, &c->red.counter, 9));  // main + 8 group tickets
   {
     const eqs_status ps = mixed(c) ? build_plan(c, c->lev32) : build_plan(c, c->lev64);

@@ -41,7 +41,8 @@ class eqs_opts(C.Structure):
                 ("flexible", C.c_int), ("persistent", C.c_int), ("blocks_per_sm", C.c_int),
                 ("spe_n", C.c_int), ("host_loop", C.c_int), ("barrier_polls", C.c_longlong),
                 ("split_m", C.c_int), ("pod_k", C.c_int), ("pod_m", C.c_int),
-                ("pod_min_iters", C.c_int), ("fill_lanes", C.c_int), ("coarse_split", C.c_int)]
+                ("pod_min_iters", C.c_int), ("fill_lanes", C.c_int), ("coarse_split", C.c_int),
+                ("defer_sums", C.c_int)]
 
 
 class eqs_batch_stats(C.Structure):

@@ -223,3 +223,41 @@ def test_host_loop_matches_graph(E, prec):
     # FP32 atomics in the mixed element kernel sum in a different order per run
     tol = 1e-11 if prec == FP64 else 1e-7
     np.testing.assert_allclose(out[1][0], out[0][0], rtol=0, atol=tol * np.abs(out[0][0]).max())
+
+
+@pytest.mark.parametrize("name", ["cube12", "jitter10"])
+@pytest.mark.parametrize("defer", [0, 1])
+def test_mixed_degree1_trajectory_deferred_sums(E, name, defer):
+    """The mixed path in the benchmark's smoother setting (degree-1
+    Chebyshev, CG dots fused into the last smoothing pass), with the CG sums
+    formed in the producer's last block (defer_sums 0) or added by every
+    block of the consuming kernel (1): the oracle's trajectory to the mixed
+    tolerance, graph and host loop with identical iteration counts, and the
+    M-solve against a direct solve."""
+    p = PROBLEMS[name]()
+    s, steps = 10, 4
+    opts = dict(cheb_degree=1, coarse_max=60, defer_sums=defer)
+    out = []
+    for host_loop in (0, 1):
+        S = E.Solver(p, precision=MIXED, rtol=1e-13, host_loop=host_loop, **opts)
+        dt = S.dt_bound(s)
+        x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+        t, its = 0.0, []
+        for _ in range(steps):
+            st = S.step(x, t, dt, s)
+            assert st.status == 0 and st.max_relres <= 1e-13
+            its.append(list(st.iters[:s]))
+            t += dt
+        out.append((x.cpu().numpy(), its))
+        S.close()
+    assert out[0][1] == out[1][1]
+    ref = _oracle_run(p, s, steps, dt)[-1]
+    assert np.linalg.norm(out[0][0] - ref) / np.linalg.norm(ref) <= 1e-6
+    S = E.Solver(p, precision=MIXED, **opts)
+    Sy = system.EQSSystem(p)
+    R = np.random.default_rng(15).standard_normal(p.n_free)
+    zd = spla.spsolve(Sy.Mff.tocsc(), R)
+    z, iters = S.solve_M(_cuda(R), rtol=1e-12)
+    S.close()
+    assert 0 < iters[0] < 100
+    assert np.linalg.norm(z.cpu().numpy() - zd) / np.linalg.norm(zd) <= 1e-9
