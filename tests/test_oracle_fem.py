@@ -98,3 +98,23 @@ def test_kappa_law():
     assert big[1] == pytest.approx(1e-6, rel=1e-15)
     const = fem.kappa_of_E(np.array([1.0, 1e7]), ei.BACKGROUND.as_tuple())
     assert np.all(const == 1e-14)
+
+
+def test_sampled_rows_from_the_tets_around_a_node():
+    """The full-size GPU tests let the oracle compute sampled rows only, from
+    the tets that touch the sampled nodes: those rows of K(x)x and of M z
+    equal the oracle's full products exactly (every term of a row comes from
+    a tet around its node)."""
+    p = ei.config_problem(2, N=14)  # jittered, two spheres
+    rng = np.random.default_rng(5)
+    x = -5.2e5 * p.xyz[:, 2] + 2e3 * rng.standard_normal(p.n_nodes)
+    nodes = np.sort(rng.choice(p.n_nodes, 300, replace=False))
+    sub = np.isin(p.tets, nodes).any(axis=1)
+    assert 0 < sub.sum() < len(p.tets)
+    y_sub = fem.apply_K(p.xyz, p.tets[sub], p.tet_mat[sub], p.materials, x)[nodes]
+    y = fem.apply_K(p.xyz, p.tets, p.tet_mat, p.materials, x)[nodes]
+    assert np.array_equal(y_sub, y)
+    z = rng.standard_normal(p.n_nodes)
+    Mz_sub = (fem.assemble_M(p.xyz, p.tets[sub], p.tet_mat[sub], p.materials) @ z)[nodes]
+    Mz = (fem.assemble_M(p.xyz, p.tets, p.tet_mat, p.materials) @ z)[nodes]
+    np.testing.assert_allclose(Mz_sub, Mz, rtol=0, atol=1e-15 * np.abs(Mz).max())
