@@ -128,14 +128,18 @@ typedef struct {
                           FP32 row sums; 1 applies it as two FP32 parts with
                           FP32-pair row sums (twice the bytes).  Ignored in
                           FP64 mode.                                        */
-  int defer_sums;      /* EQS_PREC_MIXED, degree-1 smoother, >= 2 levels: 1
-                          (default) leaves the CG dot products of the fused
-                          smoothing pass and of the operator pass as
+  int defer_sums;      /* bit 0 (EQS_PREC_MIXED, degree-1 smoother, >= 2
+                          levels): the CG dot products of the fused smoothing
+                          pass and of the operator pass are left as
                           per-block partial sums that every block of the
                           consuming kernel adds in the same fixed order (no
-                          grid-wide ticket between the kernels); 0 forms
-                          them in the producer's last block.  Same results
-                          up to the order of the additions.                 */
+                          grid-wide ticket between the kernels); bit 1
+                          (EQS_GUESS_SPE in eqs_rkc_step): the same for the
+                          SPE Gram pass, whose sums one block then adds
+                          before the small solve.  Cleared
+                          bits form the sums in the producer's last block.
+                          0..3, default 3.  Same results up to the order of
+                          the additions.                                    */
 } eqs_opts;
 
 #define EQS_MAX_STAGES 64
@@ -159,7 +163,7 @@ typedef struct {
  * max_levels 10, degree 2, alpha 30, rtol 1e-8, max_iter 500, GUESS_PREV,
  * flexible 1, persistent 0, blocks_per_sm 1, spe_n 4, host_loop 0,
  * barrier_polls 0, split_m 1, pod_k 12, pod_m 6, pod_min_iters 3,
- * fill_lanes 1, coarse_split 0, defer_sums 1). */
+ * fill_lanes 1, coarse_split 0, defer_sums 3). */
 void eqs_opts_default(eqs_opts* o);
 
 /* Create a context from a tetrahedral mesh (Eq. 2 discretisation input).

@@ -398,24 +398,39 @@ struct SpeAt {
 // Two blocks per SM where they fit: the pass is bound by FP64 latency with
 // 8 warps per SM; more blocks than are resident would run in a second wave.
 template <int NH>
-static void spe_gram_n(eqs_ctx* c, cudaStream_t st, int s, int j) {
-  const int nf = (int)c->n_free;
+static int spe_gram_grid(eqs_ctx* c, int nf) {
   int occ = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spe_gram<NH>, kBlock, 0) != cudaSuccess) occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spe_gram<NH, false>, kBlock, 0) != cudaSuccess) occ = 1;
   const int bps = std::max(1, std::min(occ, 2));
-  launch(k_spe_gram<NH>, std::max(1, std::min(nblk(nf), c->sms * bps)), kBlock, st, c->M64, nf,
-         (const double*)c->d_spe_X, c->d_spe_W, (const double*)c->d_R, (const long long*)c->d_stepcount, s, j,
-         c->d_spe_G, c->d_spe_partials, c->red.counter, c->red.max_blocks, 1e-12, c->d_spe_y);
+  return std::max(1, std::min(nblk(nf), c->sms * bps));
 }
 
-static void spe_gram(eqs_ctx* c, cudaStream_t st, int s, int j) {
+// defer: leave the sums as per-block partials, added by one block of
+// k_spe_solve.
+template <int NH>
+static void spe_gram_n(eqs_ctx* c, cudaStream_t st, int s, int j, bool defer) {
+  const int nf = (int)c->n_free;
+  const int grid = spe_gram_grid<NH>(c, nf);
+  if (defer) {
+    launch(k_spe_gram<NH, true>, grid, kBlock, st, c->M64, nf, (const double*)c->d_spe_X, c->d_spe_W,
+           (const double*)c->d_R, (const long long*)c->d_stepcount, s, j, c->d_spe_G, c->d_spe_partials,
+           c->red.counter, c->red.max_blocks, 1e-12, c->d_spe_y);
+    launch(k_spe_solve<NH>, 1, kBlock, st, (const long long*)c->d_stepcount, j, c->d_spe_G, 1e-12,
+           (const double*)c->d_spe_partials, grid, c->red.max_blocks, c->d_spe_y);
+  } else
+    launch(k_spe_gram<NH, false>, grid, kBlock, st, c->M64, nf, (const double*)c->d_spe_X, c->d_spe_W,
+           (const double*)c->d_R, (const long long*)c->d_stepcount, s, j, c->d_spe_G, c->d_spe_partials,
+           c->red.counter, c->red.max_blocks, 1e-12, c->d_spe_y);
+}
+
+static void spe_gram(eqs_ctx* c, cudaStream_t st, int s, int j, bool defer) {
   switch (c->opts.spe_n) {
-    case 1: spe_gram_n<1>(c, st, s, j); break;
-    case 2: spe_gram_n<2>(c, st, s, j); break;
-    case 3: spe_gram_n<3>(c, st, s, j); break;
-    case 4: spe_gram_n<4>(c, st, s, j); break;
-    case 5: spe_gram_n<5>(c, st, s, j); break;
-    default: spe_gram_n<6>(c, st, s, j); break;
+    case 1: spe_gram_n<1>(c, st, s, j, defer); break;
+    case 2: spe_gram_n<2>(c, st, s, j, defer); break;
+    case 3: spe_gram_n<3>(c, st, s, j, defer); break;
+    case 4: spe_gram_n<4>(c, st, s, j, defer); break;
+    case 5: spe_gram_n<5>(c, st, s, j, defer); break;
+    default: spe_gram_n<6>(c, st, s, j, defer); break;
   }
 }
 
@@ -517,7 +532,7 @@ static void pcg_body_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_
   const bool fuse = c->opts.cheb_degree == 1 && L.size() > 1;
   // deferred sums: the dot products of the fused smoothing pass and of the
   // operator pass are added by the kernel that consumes them
-  const bool defer = fuse && c->d_z32 && c->opts.defer_sums;
+  const bool defer = fuse && c->d_z32 && (c->opts.defer_sums & 1);
   T* zpend = vcycle_level(c, L, 0, st, fuse, defer);
   if (!fuse)
     launch(k_pcg_dots<T>, g, kBlock, st, n, c->d_r, c->d_rprev, V.x, (const T*)zpend, c->d_zd, c->d_z32,
@@ -797,7 +812,7 @@ static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
              (const __nv_bfloat16*)c->d_theta_bf16, (const double*)c->d_sh, Fbuf(c, j));
       stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, h1, c->d_mlp_used + j);
     } else if (c->opts.guess == EQS_GUESS_SPE) {
-      spe_gram(c, st, s, j);
+      spe_gram(c, st, s, j, (c->opts.defer_sums & 2) != 0);
       const SpeAt at{s, j, false};
       stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, nullptr, nullptr, &at);
     } else if (c->opts.guess == EQS_GUESS_POD || c->opts.guess == EQS_GUESS_POD2) {
@@ -1275,7 +1290,7 @@ void eqs_opts_default(eqs_opts* o) {
   o->pod_min_iters = 3;
   o->fill_lanes = 1;
   o->coarse_split = 0;
-  o->defer_sums = 1;
+  o->defer_sums = 3;
 }
 
 static eqs_status mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
@@ -1357,7 +1372,7 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     eqs_opts_default(&o);
   if (o.cheb_degree < 1 || o.cheb_degree > 4 || o.blocks_per_sm < 0 || o.spe_n < 1 || o.spe_n > kSpeMax || o.max_levels < 1 || o.coarse_max < 1 ||
       o.pod_k < 1 || o.pod_k > kPodMax || o.pod_m < 1 || o.pod_m > o.pod_k || o.pod_min_iters < 0 ||
-      (o.coarse_split != 0 && o.coarse_split != 1) || (o.defer_sums != 0 && o.defer_sums != 1) ||
+      (o.coarse_split != 0 && o.coarse_split != 1) || o.defer_sums < 0 || o.defer_sums > 3 ||
       !(o.theta >= 0) || !(o.cheb_alpha > 1) || !(o.rtol > 0) || o.max_iter < 1 ||
       (o.precision != EQS_PREC_FP64 && o.precision != EQS_PREC_MIXED))
     return fail(c, EQS_ERR_ARG, "invalid eqs_opts");
@@ -2234,7 +2249,7 @@ eqs_status eqs_spe_eval(eqs_ctx* c, const double* X, const double* b, int n, dou
     const double* col = X + (size_t)(n - 1 - q) * nf;
     CK(cudaMemcpyAsync(c->d_spe_X + (size_t)(q % n) * nf, col, nf * sizeof(double), cudaMemcpyDeviceToDevice,
                        st));
-    spe_gram(c, st, 1, q + 1);
+    spe_gram(c, st, 1, q + 1, false);
   }
   SolveSlots sl{nullptr, nullptr, nullptr};
   if (mixed(c))

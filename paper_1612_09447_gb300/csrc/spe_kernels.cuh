@@ -25,28 +25,26 @@ constexpr int kSpeSums = 2 * kSpeMax;  // Gram column + projections of b
 
 __device__ __forceinline__ int spe_slot(long long q, int NH) { return (int)(((q % NH) + NH) % NH); }
 
-// Last block of a Gram pass: store the new Gram column of slot sn (tot[0..m)),
-// solve (L L^T) y = c (c = tot[NH..NH+m)) by Cholesky with column dropping
-// (most recent first) and write y by ring slot plus the slots in use.  One
+// The SPE coefficients of solve g: with m = min(g, NH) slots in use and the
+// newest solution in slot sn = slot(g - 1), solve (L L^T) y = c for the Gram
+// matrix A (row and column of the newest slot from tot[0..m), every other
+// entry from the stored G, which is not read at the newest slot) and
+// c = tot[NH..NH+m), by Cholesky with column dropping (most recent first);
+// y_out[k] is the coefficient of solution g - 1 - k (ring slot
+// slot(g - 1 - k)).  One
 // thread; every loop runs over the compile-time NH (rows k >= m are zero and
 // never kept), so the small matrices stay in registers instead of local
-// memory.  On GB300 every FP64 instruction of this serial tail occupies the
+// memory.  On GB300 every FP64 instruction of this serial code occupies the
 // slow FP64 pipe of its SM sub-partition for a whole warp's worth of lanes,
 // so the factor keeps the reciprocal of each pivot (one rsqrt per column)
 // and multiplies by it instead of dividing (an IEEE division is a chain of
 // about ten FP64 operations).
 template <int NH>
-__device__ void spe_solve(const double* tot, long long g, int m, int sn, double* __restrict__ G, double drop2,
-                          double* __restrict__ y_out) {
+__device__ void spe_coeffs(const double* tot, long long g, int m, const double* G, double drop2,
+                           double (&y_out)[NH]) {
   int slot[NH];
 #pragma unroll
   for (int k = 0; k < NH; ++k) slot[k] = spe_slot(g - 1 - k, NH);
-#pragma unroll
-  for (int k = 0; k < NH; ++k)
-    if (k < m) {  // new Gram column and row of the newest slot
-      G[slot[k] * kSpeMax + sn] = tot[k];
-      G[sn * kSpeMax + slot[k]] = tot[k];
-    }
   double A[NH][NH], L[NH][NH], c[NH], z[NH], y[NH], inv[NH];
   bool keep[NH];
 #pragma unroll
@@ -58,7 +56,9 @@ __device__ void spe_solve(const double* tot, long long g, int m, int sn, double*
     y[k] = 0.0;
 #pragma unroll
     for (int l = 0; l < NH; ++l) {
-      A[k][l] = (k < m && l < m) ? G[slot[k] * kSpeMax + slot[l]] : 0.0;
+      double a = 0.0;
+      if (k < m && l < m) a = k == 0 ? tot[l] : (l == 0 ? tot[k] : G[slot[k] * kSpeMax + slot[l]]);
+      A[k][l] = a;
       L[k][l] = 0.0;
     }
   }
@@ -99,10 +99,35 @@ __device__ void spe_solve(const double* tot, long long g, int m, int sn, double*
     y[k] = e * inv[k];
   }
 #pragma unroll
+  for (int k = 0; k < NH; ++k) y_out[k] = k < m ? y[k] : 0.0;
+}
+
+// Store the new Gram column and row of the newest slot sn (tot[0..m)).
+template <int NH>
+__device__ __forceinline__ void spe_store_column(const double* tot, long long g, int m, int sn,
+                                                 double* __restrict__ G) {
+#pragma unroll
+  for (int k = 0; k < NH; ++k)
+    if (k < m) {
+      const int sk = spe_slot(g - 1 - k, NH);
+      G[sk * kSpeMax + sn] = tot[k];
+      G[sn * kSpeMax + sk] = tot[k];
+    }
+}
+
+// Last block of a Gram pass: store the new Gram column, solve for the
+// coefficients and write them by ring slot plus the slots in use.
+template <int NH>
+__device__ void spe_solve(const double* tot, long long g, int m, int sn, double* __restrict__ G, double drop2,
+                          double* __restrict__ y_out) {
+  double y[NH];
+  spe_coeffs<NH>(tot, g, m, G, drop2, y);
+  spe_store_column<NH>(tot, g, m, sn, G);
+#pragma unroll
   for (int k = 0; k < NH; ++k) y_out[k] = 0.0;
 #pragma unroll
   for (int k = 0; k < NH; ++k)
-    if (k < m) y_out[slot[k]] = y[k];
+    if (k < m) y_out[spe_slot(g - 1 - k, NH)] = y[k];
   reinterpret_cast<int*>(y_out + kSpeMax)[0] = m;
 }
 
@@ -111,8 +136,10 @@ __device__ void spe_solve(const double* tot, long long g, int m, int sn, double*
 // the Gram column G[k][g-1] over the stored solutions k and c_k = x_k . b.
 // The last block updates G and solves (L L^T) y = c with column dropping;
 // y_out[slot] is the coefficient of the solution in that ring slot and
-// y_out[kSpeMax] (as int) the number of slots in use.
-template <int NH>
+// y_out[kSpeMax] (as int) the number of slots in use.  DEFER: the 2 NH sums
+// are left as per-block partials (partials[k * max_blocks + block]) for
+// k_spe_solve.
+template <int NH, bool DEFER>
 __global__ void k_spe_gram(DevSell<double> M, int nf, const double* __restrict__ X, double* __restrict__ W,
                            const double* __restrict__ b, const long long* __restrict__ stepcount, int s,
                            int j, double* __restrict__ G, double* partials, unsigned int* counter,
@@ -120,7 +147,7 @@ __global__ void k_spe_gram(DevSell<double> M, int nf, const double* __restrict__
   pdl_enter();
   const long long g = stepcount[0] + j;
   if (g == 0) {  // uniform over the grid: no history, no reduction
-    if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<int*>(y_out + kSpeMax)[0] = 0;
+    if (!DEFER && blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<int*>(y_out + kSpeMax)[0] = 0;
     return;
   }
   const int m = (int)(g < NH ? g : NH);
@@ -145,9 +172,32 @@ __global__ void k_spe_gram(DevSell<double> M, int nf, const double* __restrict__
       v[NH + k] = fma(xk, bi, v[NH + k]);
     }
   }
+  if constexpr (DEFER) {
+    write_partials<NS>(v, partials, max_blocks);
+    return;
+  }
   double tot[NS];
   if (grid_sum<NS>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0)
     spe_solve<NH>(tot, g, m, sn, G, drop2, y_out);
+}
+
+// The deferred form's small solve: one block adds the Gram pass's nb
+// per-block partials (in a fixed order), then thread 0 updates G and writes
+// the coefficients as the last block of the undeferred pass does -- without
+// the pass's atomic ticket, fences and serial last block.
+template <int NH>
+__global__ void k_spe_solve(const long long* __restrict__ stepcount, int j, double* __restrict__ G, double drop2,
+                            const double* __restrict__ part, int nb, int cap, double* __restrict__ y_out) {
+  pdl_enter();
+  const long long g = stepcount[0] + j;
+  if (g == 0) {
+    if (threadIdx.x == 0) reinterpret_cast<int*>(y_out + kSpeMax)[0] = 0;
+    return;
+  }
+  const int m = (int)(g < NH ? g : NH);
+  double tot[2 * NH];
+  sum_partials<2 * NH>(part, nb, cap, tot);
+  if (threadIdx.x == 0) spe_solve<NH>(tot, g, m, spe_slot(g - 1, NH), G, drop2, y_out);
 }
 
 // Start of the CG solve from a projection start vector (SPE or POD): with

@@ -123,7 +123,7 @@ def test_p2_mesh_validation(E):
 @pytest.mark.parametrize("field,value", [("pod_k", 0), ("pod_k", 17), ("pod_m", 0), ("pod_m", 13),
                                          ("pod_min_iters", -1), ("spe_n", 7), ("cheb_degree", 5),
                                          ("rtol", 0.0), ("precision", 2), ("coarse_split", 2),
-                                         ("defer_sums", 2)])
+                                         ("defer_sums", 4), ("defer_sums", -1)])
 def test_invalid_options_are_rejected_before_any_device_work(E, field, value):
     p = ei.make_problem(2)
     ctx = E.eqs_mesh_create(p.xyz, p.tets, p.node_tag)

@@ -46,14 +46,17 @@ def test_spe_projection_matches_oracle(E, n, prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6)])
-def test_spe_trajectory_and_iterations(E, prec, tol):
+@pytest.mark.parametrize("defer", [0, 3])
+def test_spe_trajectory_and_iterations(E, prec, tol, defer):
     """The start vector changes iteration counts, never the converged
-    trajectory; SPE needs far fewer CG iterations than the previous solution."""
+    trajectory; SPE needs far fewer CG iterations than the previous solution.
+    defer 3: the Gram pass leaves its sums as per-block partials for the
+    one-block small solve (and the CG sums are deferred where they apply)."""
     p = ei.config_problem(0)
     s, steps = 10, 8
     res = {}
     for mode in (E.EQS_GUESS_PREV, E.EQS_GUESS_SPE):
-        S = E.Solver(p, precision=prec, rtol=1e-13)
+        S = E.Solver(p, precision=prec, rtol=1e-13, defer_sums=defer)
         E.eqs_set_guess(S.ctx, mode)
         x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
         dt, t, its, traj = S.dt_bound(s), 0.0, 0, []
