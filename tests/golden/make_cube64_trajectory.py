@@ -13,7 +13,7 @@ iteration count).  phi is stored at 8192 seeded sample nodes after steps 50
 and 100, next to the step size and the sample seed.
 
 This script calls only oracle/ and the seeded input generator.  It runs for
-about two and a half hours:
+about two hours:
 
     python tests/golden/make_cube64_trajectory.py [--steps 100]
 """
