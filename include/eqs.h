@@ -138,8 +138,9 @@ typedef struct {
                           SPE Gram pass, whose sums one block then adds
                           before the small solve.  Cleared
                           bits form the sums in the producer's last block.
-                          0..3, default 3.  Same results up to the order of
-                          the additions.                                    */
+                          0..3, default 2 (bit 1 only: measured faster; the
+                          CG hand-over was not).  Same results up to the
+                          order of the additions.                           */
 } eqs_opts;
 
 #define EQS_MAX_STAGES 64
@@ -163,7 +164,7 @@ typedef struct {
  * max_levels 10, degree 2, alpha 30, rtol 1e-8, max_iter 500, GUESS_PREV,
  * flexible 1, persistent 0, blocks_per_sm 1, spe_n 4, host_loop 0,
  * barrier_polls 0, split_m 1, pod_k 12, pod_m 6, pod_min_iters 3,
- * fill_lanes 1, coarse_split 0, defer_sums 3). */
+ * fill_lanes 1, coarse_split 0, defer_sums 2). */
 void eqs_opts_default(eqs_opts* o);
 
 /* Create a context from a tetrahedral mesh (Eq. 2 discretisation input).

@@ -1290,7 +1290,7 @@ void eqs_opts_default(eqs_opts* o) {
   o->pod_min_iters = 3;
   o->fill_lanes = 1;
   o->coarse_split = 0;
-  o->defer_sums = 3;
+  o->defer_sums = 2;
 }
 
 static eqs_status mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
