@@ -144,3 +144,17 @@ def test_call_order_errors(E):
             call()
         assert ex.value.status == E.EQS_ERR_STATE
     E.eqs_destroy(ctx)
+
+
+def test_option_defaults_match_the_header(E):
+    """eqs_opts_default fills the values include/eqs.h documents."""
+    o = E.eqs_opts_default()
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "eqs.h")).read()
+    doc = hdr[hdr.index("/* Fill *o with the defaults"):]
+    doc = " ".join(doc[:doc.index("*/")].replace("*", " ").split())
+    for field in ("split_m", "pod_k", "pod_m", "pod_min_iters", "fill_lanes", "coarse_split", "defer_sums",
+                  "spe_n", "max_iter", "persistent", "host_loop"):
+        m = re.search(rf"\b{field} (\d+)", doc)
+        assert m, field
+        assert getattr(o, field) == int(m.group(1)), field
+    assert o.precision == E.EQS_PREC_FP64 and o.rtol == 1e-8 and o.flexible == 1
