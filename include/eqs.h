@@ -60,9 +60,10 @@ typedef struct {
 
 typedef enum {
   EQS_PREC_FP64 = 0,  /* every kernel in FP64                                */
-  EQS_PREC_MIXED = 1  /* FP32 element kernel and AMG V-cycle; FP64 CG
-                         residual, dot products, RKC recurrence, coarsest
-                         solve                                              */
+  EQS_PREC_MIXED = 1  /* FP32 element kernel and AMG V-cycle (coarsest
+                         level: FP32 dense inverse, or FP32 pairs with
+                         eqs_opts.coarse_split 1); FP64 CG residual, dot
+                         products and RKC recurrence                        */
 } eqs_precision;
 
 typedef enum {
