@@ -48,9 +48,12 @@ S_STAGES = 20
 CONFIG_INDEX = 1
 WORKLOAD = WORKLOADS[CONFIG_INDEX]
 # AMG/solver options of the timed runs (both precisions): degree-1 Chebyshev
-# smoothing and a 2066-row coarsest level (dense FP64 inverse) gave the
-# lowest step time on GB300 among degree 1-3 and coarse sizes 88/2066.
-SOLVER_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0)
+# smoothing and a 2066-row coarsest level (dense inverse: FP64 on the FP64
+# path, its FP32 rounding on the mixed path) gave the lowest step time on
+# GB300 among degree 1-3 and coarse sizes 88/2066; the SPE Gram pass hands
+# its sums to a one-block solve (defer_sums 2; the CG hand-over measured
+# slower and stays off).
+SOLVER_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0, coarse_split=0, defer_sums=2)
 SPE_N = 6  # solutions spanning the SPE subspace
 # DRAM bytes (read + write) of one k_spmv64 launch per workload from an ncu
 # capture (profiles/k_spmv_split_cube64.md); None where not captured.

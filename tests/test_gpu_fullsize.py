@@ -29,7 +29,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP64, MIXED = 0, 1
-BENCH_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0)  # bench.py's solver options
+# bench.py's solver options
+BENCH_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0, coarse_split=0, defer_sums=2)
 CASES = {"cube64": 1, "jitter128": 2}
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cube64_block_trajectory.txt")
 _PROBLEMS = {}
