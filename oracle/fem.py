@@ -86,13 +86,15 @@ def local_matrices(G, V, coef):
     return (coef * V)[:, None, None] * np.einsum("tkd,tld->tkl", G, G)
 
 
-def apply_K(xyz, tets, tet_mat, materials, x):
+def apply_K(xyz, tets, tet_mat, materials, x, geometry=None):
     """y = K(x) x, formed tet by tet and scattered into y (Section III).
-    10-node tets go to the P2 element (oracle.fem_p2)."""
+    10-node tets go to the P2 element (oracle.fem_p2).  ``geometry`` is an
+    optional (G, V) pair from tet_geometry of the same mesh (the geometry
+    does not depend on x; passing it only saves recomputing it)."""
     if tets.shape[1] == 10:
         from . import fem_p2
         return fem_p2.apply_K(xyz, tets, tet_mat, materials, x)
-    G, V = tet_geometry(xyz, tets)
+    G, V = tet_geometry(xyz, tets) if geometry is None else geometry
     kap, _ = tet_kappa(xyz, tets, tet_mat, materials, x, G)
     Ke = local_matrices(G, V, kap)
     re = np.einsum("tkl,tl->tk", Ke, x[tets])

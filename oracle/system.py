@@ -38,6 +38,13 @@ class EQSSystem:
         self.Mfd = self.M[self.free][:, self.dir].tocsr()
         self.m_top = self.Mfd @ self.top  # M_fd 1_top
         self._lu = None
+        self._geom = None
+
+    def geometry(self):
+        """(G, V) of every P1 tet, computed once (None for P2 meshes)."""
+        if self._geom is None and self.p.tets.shape[1] == 4:
+            self._geom = fem.tet_geometry(self.p.xyz, self.p.tets)
+        return self._geom
 
     # Dirichlet data g(t) and g'(t) on the d nodes
     def g(self, t):
@@ -59,7 +66,7 @@ class EQSSystem:
         """R(t, x_f) = -[K(x~)x~]_f - M_fd g'(t)."""
         p = self.p
         x = self.full(t, xf)
-        y = fem.apply_K(p.xyz, p.tets, p.tet_mat, p.materials, x)
+        y = fem.apply_K(p.xyz, p.tets, p.tet_mat, p.materials, x, geometry=self.geometry())
         return -y[self.free] - self.Mfd @ self.gdot(t)
 
     def solve_direct(self, R):
