@@ -215,7 +215,8 @@ eqs_status eqs_amg_setup(eqs_ctx* ctx, const eqs_opts* opts);
  * mesh order; y is overwritten.  Uses the precision chosen at setup. */
 eqs_status eqs_apply_K(eqs_ctx* ctx, const double* x, double* y);
 
-/* y = K(x) x exactly as eqs_apply_K, for callers that must not allocate
+/* y = K(x) x as eqs_apply_K computes it (the same element kernel; results
+ * differ only by the order of the atomic additions), for callers that must not allocate
  * device memory during the call: code running where cudaMalloc is not
  * allowed or not wanted, e.g. under a fixed device-memory budget that was
  * claimed up front, or on a real-time or callback path where an allocation
@@ -224,8 +225,10 @@ eqs_status eqs_apply_K(eqs_ctx* ctx, const double* x, double* y);
  * the result staged in the library's internal node order) is a static
  * 12 MiB device array inside the library, which every GPU that loads the
  * library holds until the process exits.  Limit: n_nodes <= 524288, else
- * EQS_ERR_ARG.  The first call on a device looks up the array's address;
- * make that first call before any stream capture.  All calls share the one
+ * EQS_ERR_ARG.  The first call on a device looks up the array's address
+ * and keeps it for the rest of the process; make that first call before
+ * any stream capture.  A device reset (cudaDeviceReset) may move the array,
+ * so after one this entry point must not be used again in that process.  All calls share the one
  * array, so calls whose work overlaps on the GPU (other streams, other
  * threads, several contexts on one device) race; serialise them.  x, y:
  * device, n_nodes doubles, mesh order; the context's device must be
@@ -396,6 +399,30 @@ eqs_status eqs_ens_get_step_stats(eqs_ctx* ctx, eqs_ens_stats* stats);
  * the solutions on exit.  iters_out: host, EQS_ENS_W ints or NULL.
  * Synchronises; EQS_ERR_NOCONV if a column hit max_iter. */
 eqs_status eqs_ens_solve_M(eqs_ctx* ctx, const double* rhs, double* z, int* iters_out);
+
+/* ---- One kernel of the step, launched alone (measurement).
+ * Enqueues ONE launch of the named kernel of the last step
+ * (eqs_rkc_step, or eqs_ens_rkc_step for the EQS_KERNEL_ENS_* ids) on the
+ * context stream, with the arguments that step's last stage solve used, so
+ * that a caller can time the kernel with events on that stream:
+ *   SPE_GRAM: the SPE Gram pass of Sec. IV, Eq. 4-5 (the product W = M x
+ *             of the newest solution, the new Gram column and the
+ *             projections of the right-hand side; the small solve that
+ *             follows it in a step is not launched);
+ *   ELEM:     the element kernel of Sec. III on the last stage state, its
+ *             K(x)x scattered into a private buffer of the context
+ *             (allocated on the first such call);
+ *   PCG_PQ:   the CG operator pass q = M z + beta q of Sec. IV.
+ * The Gram pass recomputes the last solve's column (same values); the CG
+ * pass overwrites CG vectors that the next solve re-initialises.  So a
+ * later step is unaffected, but the call must not overlap a step.
+ * EQS_ERR_STATE when no such step has run (or SPE is not in use for the
+ * Gram ids), EQS_ERR_ARG for an unknown id.  Asynchronous. */
+enum {
+  EQS_KERNEL_SPE_GRAM = 0, EQS_KERNEL_ELEM = 1, EQS_KERNEL_PCG_PQ = 2,
+  EQS_KERNEL_ENS_SPE_GRAM = 16, EQS_KERNEL_ENS_ELEM = 17, EQS_KERNEL_ENS_PCG_PQ = 18
+};
+eqs_status eqs_launch_kernel(eqs_ctx* ctx, int kernel);
 
 /* ---- Batched serving: many independent instances advance together.
  * Every RKC stage of all instances is one cooperative launch in which each

@@ -999,9 +999,9 @@ __device__ __forceinline__ void store_split4(float4* __restrict__ Y2, int64_t i,
 }
 
 // Y0 (interleaved, internal order) from the caller's column-major mesh-order
-// X (column c at X + c n), Dirichlet rows = g(t) times the column's drive
-// scale; the start vector of the first solve (previous solution).
-__global__ void k4_gather_state(int n, int nf, const double* __restrict__ X, const int32_t* __restrict__ noi,
+// X = prm->x (column c at X + c n), Dirichlet rows = g(t) times the column's
+// drive scale; the start vector of the first solve (previous solution).
+__global__ void k4_gather_state(int n, int nf, const StepParams* prm, const int32_t* __restrict__ noi,
                                 const double* __restrict__ dir_scale, const double* __restrict__ g,
                                 const double* __restrict__ colv, double4_32a* __restrict__ Y0,
                                 float4* __restrict__ Y2, const double4_32a* __restrict__ Fsrc,
@@ -1011,6 +1011,7 @@ __global__ void k4_gather_state(int n, int nf, const double* __restrict__ X, con
   if (i >= n) return;
   double4_32a v;
   if (i < nf) {
+    const double* __restrict__ X = prm->x;
     const int64_t m = noi[i];
     v.x = X[m];
     v.y = X[(int64_t)n + m];
@@ -1030,7 +1031,8 @@ __global__ void k4_gather_state(int n, int nf, const double* __restrict__ X, con
 
 // Stage recurrence for the four columns (same coefficients; a column whose
 // right-hand side was zero contributes F = 0), the next start vector and,
-// after the last stage, x(t + dt) back to the caller's column-major layout.
+// after the last stage (write_x), x(t + dt) back to the caller's column-major
+// layout at prm->x.
 __global__ void k4_recurrence(int n, int nf, double c0, double mu, double nu, double mut, double gt,
                               const StepParams* prm, const double4_32a* __restrict__ Y0,
                               const double4_32a* __restrict__ Yjm1, const double4_32a* __restrict__ Yjm2,
@@ -1038,7 +1040,7 @@ __global__ void k4_recurrence(int n, int nf, double c0, double mu, double nu, do
                               const int* __restrict__ zero_flags, int jm1, const double* __restrict__ dir_scale,
                               const double* __restrict__ gj, const double* __restrict__ colv,
                               double4_32a* __restrict__ Yj, float4* __restrict__ Y2,
-                              double4_32a* __restrict__ Fguess, double* __restrict__ X,
+                              double4_32a* __restrict__ Fguess, int write_x,
                               const int32_t* __restrict__ noi, const long long* __restrict__ stepcount, int s,
                               double4_32a* __restrict__ ring, int nh) {
   pdl_enter();
@@ -1065,7 +1067,8 @@ __global__ void k4_recurrence(int n, int nf, double c0, double mu, double nu, do
   }
   Yj[i] = v;
   if (Y2) store_split4(Y2, i, v);
-  if (X) {
+  if (write_x) {
+    double* __restrict__ X = prm->x;
     const int64_t m = noi[i];
     X[m] = v.x;
     X[(int64_t)n + m] = v.y;

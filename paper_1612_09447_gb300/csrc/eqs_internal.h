@@ -77,6 +77,7 @@ struct PcgScalars {
 
 struct StepParams {  // device-resident per-call parameters
   double t, dt;
+  double* x;  // the caller's node vector(s) of this call (step graphs do not depend on it)
 };
 
 // All scratch used by the reduction kernels of one solve.
@@ -255,20 +256,21 @@ struct eqs_ctx {
   double* d_espart = nullptr;        // reduction slots of the ensemble Gram pass
   long long* d_estepcount = nullptr; // ensemble step counter (history index)
   int64_t ens_body_kernels = 0;
-  std::map<std::pair<int, uintptr_t>, eqs::GraphEntry> ens_graphs;   // key: (s, x)
+  std::map<int, eqs::GraphEntry> ens_graphs;   // key: s (graph), -s (host-loop entry)
   const eqs::GraphEntry* ens_last = nullptr;
+  float4* d_ktime = nullptr;  // private K(x)x target of eqs_launch_kernel (n_nodes float4)
   eqs::GraphEntry ens_solve_graph;   // eqs_ens_solve_M (rtol of the setup)
   double ens_solve_tol = -1.0;
 
   // ---- adaptive stepping: F(t, x) evaluation graphs (key: x) and scratch
-  std::map<uintptr_t, eqs::GraphEntry> eval_graphs;
+  eqs::GraphEntry eval_graph;  // F(t, x) of the adaptive step (x through d_params)
   double* d_xsave = nullptr;         // x(t_n) of the step being tried (n_nodes, mesh order)
   double* d_Fnew = nullptr;          // F(t_n+1, x_n+1) (n_free, internal order)
   double* d_err = nullptr;           // error norm of the last try
   long long* d_evalcount = nullptr;  // dummy history counter of the evaluations
   double* d_cj0 = nullptr;           // {0}: stage abscissa of an evaluation
 
-  std::map<std::pair<int, uintptr_t>, eqs::GraphEntry> step_graphs;  // key: (s, x)
+  std::map<int, eqs::GraphEntry> step_graphs;  // key: s (graph), -s (host-loop entry)
   const eqs::GraphEntry* last_step = nullptr;                       // graph of the last step
   int64_t body_kernels = 0;  // kernel nodes of the last captured CG loop body
   std::map<double, eqs::GraphEntry> solve_graphs;                   // key: rtol

@@ -1320,10 +1320,11 @@ __global__ void k_stage_scalars(int s1, const double* __restrict__ cj, const Ste
   gp[j] = V0 * w * cos(a);
 }
 
-// Y0 (internal order) from the caller's mesh-order x, Dirichlet rows = g(t);
-// the start vector of the first solve (previous solution) and, in FP64 mode,
-// R = -g'(t) M_fd 1_top (the element kernel then subtracts K(Y0)Y0).
-__global__ void k_gather_state(int n, int nf, const double* __restrict__ xmesh,
+// Y0 (internal order) from the caller's mesh-order x (prm->x), Dirichlet
+// rows = g(t); the start vector of the first solve (previous solution) and,
+// in FP64 mode, R = -g'(t) M_fd 1_top (the element kernel then subtracts
+// K(Y0)Y0).
+__global__ void k_gather_state(int n, int nf, const StepParams* prm,
                                const int32_t* __restrict__ node_of_internal,
                                const double* __restrict__ dir_scale, const double* __restrict__ g,
                                const double* __restrict__ gp, const double* __restrict__ mtop,
@@ -1335,7 +1336,7 @@ __global__ void k_gather_state(int n, int nf, const double* __restrict__ xmesh,
   if (i >= n) return;
   double v;
   if (i < nf) {
-    v = xmesh[node_of_internal[i]];
+    v = prm->x[node_of_internal[i]];
     if (Fdst) Fdst[i] = Fsrc[i];
     if (R) R[i] = -gp[0] * mtop[i];
   } else {
@@ -1349,7 +1350,7 @@ __global__ void k_gather_state(int n, int nf, const double* __restrict__ xmesh,
 //   Y_j = c0 Y0 + mu Y_{j-1} + nu Y_{j-2} + mut dt F_{j-1} + gt dt F_0
 // on free rows, g(t_j) on Dirichlet rows.  Also the next solve's start vector
 // (F_j <- F_{j-1}), the FP64 right-hand side start R = -g'(t_j) M_fd 1_top,
-// and, after the last stage, x(t + dt) in mesh order.
+// and, after the last stage (write_x), x(t + dt) in mesh order into prm->x.
 __global__ void k_recurrence(int n, int nf, double c0, double mu, double nu, double mut, double gt,
                              const StepParams* prm, const double* __restrict__ Y0,
                              const double* __restrict__ Yjm1, const double* __restrict__ Yjm2,
@@ -1359,7 +1360,7 @@ __global__ void k_recurrence(int n, int nf, double c0, double mu, double nu, dou
                              const double* __restrict__ gpj, const double* __restrict__ mtop,
                              double* __restrict__ Yj, float2* __restrict__ Y32,
                              double* __restrict__ Fguess, double* __restrict__ R,
-                             double* __restrict__ xmesh, const int32_t* __restrict__ node_of_internal,
+                             int write_x, const int32_t* __restrict__ node_of_internal,
                              float* __restrict__ ring, const long long* __restrict__ stepcount, int s,
                              float* __restrict__ store, long long store_cap, double* __restrict__ spe_ring,
                              int spe_n) {
@@ -1385,7 +1386,7 @@ __global__ void k_recurrence(int n, int nf, double c0, double mu, double nu, dou
   }
   Yj[i] = v;
   if (Y32) Y32[i] = split2(v);
-  if (xmesh) xmesh[node_of_internal[i]] = v;
+  if (write_x) prm->x[node_of_internal[i]] = v;
 }
 
 // Mixed precision: R = -y32 - g'(t_j) M_fd 1_top in FP64, and clear y32.

@@ -406,16 +406,17 @@ static int spe_gram_grid(eqs_ctx* c, int nf) {
 }
 
 // defer: leave the sums as per-block partials, added by one block of
-// k_spe_solve.
+// k_spe_solve (not launched when solve is false).
 template <int NH>
-static void spe_gram_n(eqs_ctx* c, cudaStream_t st, int s, int j, bool defer) {
+static void spe_gram_n(eqs_ctx* c, cudaStream_t st, int s, int j, bool defer, bool solve = true) {
   const int nf = (int)c->n_free;
   const int grid = spe_gram_grid<NH>(c, nf);
   if (defer) {
     launch(k_spe_gram<NH, true>, grid, kBlock, st, c->M64, nf, (const double*)c->d_spe_X, c->d_spe_W,
            (const double*)c->d_R, (const long long*)c->d_stepcount, s, j, c->d_spe_G, c->d_spe_partials,
            c->red.counter, c->red.max_blocks, 1e-12, c->d_spe_y);
-    launch(k_spe_solve<NH>, 1, kBlock, st, (const long long*)c->d_stepcount, j, c->d_spe_G, 1e-12,
+    if (solve)
+      launch(k_spe_solve<NH>, 1, kBlock, st, (const long long*)c->d_stepcount, j, c->d_spe_G, 1e-12,
            (const double*)c->d_spe_partials, grid, c->red.max_blocks, c->d_spe_y);
   } else
     launch(k_spe_gram<NH, false>, grid, kBlock, st, c->M64, nf, (const double*)c->d_spe_X, c->d_spe_W,
@@ -423,14 +424,14 @@ static void spe_gram_n(eqs_ctx* c, cudaStream_t st, int s, int j, bool defer) {
            c->red.counter, c->red.max_blocks, 1e-12, c->d_spe_y);
 }
 
-static void spe_gram(eqs_ctx* c, cudaStream_t st, int s, int j, bool defer) {
+static void spe_gram(eqs_ctx* c, cudaStream_t st, int s, int j, bool defer, bool solve = true) {
   switch (c->opts.spe_n) {
-    case 1: spe_gram_n<1>(c, st, s, j, defer); break;
-    case 2: spe_gram_n<2>(c, st, s, j, defer); break;
-    case 3: spe_gram_n<3>(c, st, s, j, defer); break;
-    case 4: spe_gram_n<4>(c, st, s, j, defer); break;
-    case 5: spe_gram_n<5>(c, st, s, j, defer); break;
-    default: spe_gram_n<6>(c, st, s, j, defer); break;
+    case 1: spe_gram_n<1>(c, st, s, j, defer, solve); break;
+    case 2: spe_gram_n<2>(c, st, s, j, defer, solve); break;
+    case 3: spe_gram_n<3>(c, st, s, j, defer, solve); break;
+    case 4: spe_gram_n<4>(c, st, s, j, defer, solve); break;
+    case 5: spe_gram_n<5>(c, st, s, j, defer, solve); break;
+    default: spe_gram_n<6>(c, st, s, j, defer, solve); break;
   }
 }
 
@@ -726,13 +727,15 @@ static eqs_status solve_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, const do
 static bool mixed(const eqs_ctx* c) { return c->opts.precision == EQS_PREC_MIXED; }
 
 // ------------------------------------------------------------ element
+// Mixed precision reads the two-float potential Y2 (default: c->d_Y32).
 static void elem_launch(eqs_ctx* c, cudaStream_t st, const double* Y, int n_limit, double* y64,
-                        float* y32) {
+                        float* y32, const float2* Y2 = nullptr) {
+  const float2* y2in = Y2 ? Y2 : c->d_Y32;
   if (c->npe == 10) {  // quadratic tets
     if (mixed(c))
       launch(k_elem32_p2, nblk(c->n_tets), kBlock, st, c->n_tets, (const int32_t*)c->d_conn10,
              (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi,
-             (const float4*)c->d_xyz_lo, (const float2*)c->d_Y32, n_limit, y32);
+             (const float4*)c->d_xyz_lo, y2in, n_limit, y32);
     else
       launch(k_elem64_p2, nblk(c->n_tets), kBlock, st, c->n_tets, (const int32_t*)c->d_conn10,
              (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats, (const double4*)c->d_xyz, Y, n_limit,
@@ -743,7 +746,7 @@ static void elem_launch(eqs_ctx* c, cudaStream_t st, const double* Y, int n_limi
     if (mixed(c))
       launch(k_elem32_cell, nblk(c->n_cells), kBlock, st, c->n_cells, (const int32_t*)c->d_corner,
              (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi,
-             (const float4*)c->d_xyz_lo, (const float2*)c->d_Y32, n_limit, y32);
+             (const float4*)c->d_xyz_lo, y2in, n_limit, y32);
     else
       launch(k_elem64_cell, nblk(c->n_cells), kBlock, st, c->n_cells, (const int32_t*)c->d_corner,
              (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats, (const double4*)c->d_xyz, Y, n_limit,
@@ -752,7 +755,7 @@ static void elem_launch(eqs_ctx* c, cudaStream_t st, const double* Y, int n_limi
   }
   if (mixed(c))
     launch(k_elem32, nblk(c->n_tets), kBlock, st, c->n_tets, c->d_conn, c->d_mat, c->d_mats,
-                                                 c->d_xyz_hi, c->d_xyz_lo, c->d_Y32, n_limit, y32);
+                                                 c->d_xyz_hi, c->d_xyz_lo, y2in, n_limit, y32);
   else
     launch(k_elem64, nblk(c->n_tets), kBlock, st, c->n_tets, c->d_conn, c->d_mat, c->d_mats, c->d_xyz,
                                                  Y, n_limit, y64 == c->d_R ? -1.0 : 1.0, y64);
@@ -763,10 +766,12 @@ static double* Ybuf(eqs_ctx* c, int j) { return j == 0 ? c->d_Y[0] : c->d_Y[1 + 
 static double* Fbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_F[0] : c->d_F[1 + (j - 1) % 2]; }
 
 // Enqueue one RKC step on st: captured into a graph (c->direct false) or
-// launched directly with a host-driven CG loop (c->direct true).
+// launched directly with a host-driven CG loop (c->direct true).  The
+// caller's x is read and written through the parameter block
+// (c->d_params->x), so a captured step does not depend on it.
 template <typename T>
-static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, double* xdev,
-                               const double* d_cj, cudaStream_t st) {
+static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, const double* d_cj,
+                               cudaStream_t st) {
   std::vector<double> mu, nu, mut, gt, cj;
   double beta;
   rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
@@ -776,7 +781,8 @@ static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
   launch(k_stage_scalars, 1, 64, st, s + 1, d_cj, c->d_params, c->V0, w, c->phase, c->d_g, c->d_gp,
          c->d_stepcount);
   const bool mx = mixed(c);
-  launch(k_gather_state, nblk(n), kBlock, st, n, nf, xdev, c->d_node_of_internal, c->d_dir_scale, c->d_g,
+  launch(k_gather_state, nblk(n), kBlock, st, n, nf, (const StepParams*)c->d_params, c->d_node_of_internal,
+         c->d_dir_scale, c->d_g,
                                              c->d_gp, c->d_mtop, Ybuf(c, 0), mx ? c->d_Y32 : nullptr,
                                              Fbuf(c, s - 1), Fbuf(c, 0), mx ? nullptr : c->d_R);
   eqs_status stt = EQS_OK;
@@ -790,7 +796,7 @@ static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
           Ybuf(c, 0), Ybuf(c, j - 1), Ybuf(c, j >= 2 ? j - 2 : 0), Fbuf(c, j - 1), Fbuf(c, 0), c->d_zero,
           j - 1, c->d_dir_scale, c->d_g + j, c->d_gp + j, c->d_mtop, Ybuf(c, j),
           (mx && !last) ? c->d_Y32 : nullptr, last ? nullptr : Fbuf(c, j),
-          (mx || last) ? nullptr : c->d_R, last ? xdev : nullptr, c->d_node_of_internal, c->d_ring,
+          (mx || last) ? nullptr : c->d_R, last ? 1 : 0, c->d_node_of_internal, c->d_ring,
           (const long long*)c->d_stepcount, s, c->recording ? c->d_store : nullptr, (long long)c->store_cap,
           c->d_spe_X, c->opts.spe_n);
       if (last) break;
@@ -830,8 +836,7 @@ static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
 }
 
 template <typename T>
-static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, double* xdev,
-                               GraphEntry& ge) {
+static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, GraphEntry& ge) {
   std::vector<double> mu, nu, mut, gt, cj;
   double beta;
   rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
@@ -839,7 +844,7 @@ static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
   cudaStream_t st = c->cap_stream;
   c->direct = false;
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-  eqs_status stt = enqueue_step<T>(c, L, s, xdev, ge.d_cj, st);
+  eqs_status stt = enqueue_step<T>(c, L, s, ge.d_cj, st);
   cudaError_t le = cudaGetLastError();
   cudaGraph_t graph = nullptr;
   cudaError_t ee = cudaStreamEndCapture(st, &graph);
@@ -861,14 +866,14 @@ static eqs_status capture_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, d
 // order; its content is the CG start vector): the stage evaluation of a step
 // as a graph of its own (time from the device parameters).
 template <typename T>
-static eqs_status enqueue_eval_F(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* xmesh, double* Fout,
-                                 cudaStream_t st) {
+static eqs_status enqueue_eval_F(eqs_ctx* c, std::vector<DevLevel<T>>& L, double* Fout, cudaStream_t st) {
   const int n = (int)c->n_nodes, nf = (int)c->n_free;
   const bool mx = mixed(c);
   const double w = 2.0 * M_PI * c->freq;
   launch(k_stage_scalars, 1, 64, st, 1, (const double*)c->d_cj0, (const StepParams*)c->d_params, c->V0, w,
          c->phase, c->d_g, c->d_gp, c->d_evalcount);
-  launch(k_gather_state, nblk(n), kBlock, st, n, nf, xmesh, (const int32_t*)c->d_node_of_internal,
+  launch(k_gather_state, nblk(n), kBlock, st, n, nf, (const StepParams*)c->d_params,
+         (const int32_t*)c->d_node_of_internal,
          (const double*)c->d_dir_scale, (const double*)c->d_g, (const double*)c->d_gp, (const double*)c->d_mtop,
          c->d_tmpn, mx ? c->d_Y32 : nullptr, (const double*)nullptr, (double*)nullptr, mx ? nullptr : c->d_R);
   if (mx) {
@@ -884,12 +889,11 @@ static eqs_status enqueue_eval_F(eqs_ctx* c, std::vector<DevLevel<T>>& L, const 
 }
 
 template <typename T>
-static eqs_status capture_eval_F(eqs_ctx* c, std::vector<DevLevel<T>>& L, const double* xmesh, double* Fout,
-                                 GraphEntry& ge) {
+static eqs_status capture_eval_F(eqs_ctx* c, std::vector<DevLevel<T>>& L, double* Fout, GraphEntry& ge) {
   cudaStream_t st = c->cap_stream;
   c->direct = false;
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-  const eqs_status stt = enqueue_eval_F<T>(c, L, xmesh, Fout, st);
+  const eqs_status stt = enqueue_eval_F<T>(c, L, Fout, st);
   cudaError_t le = cudaGetLastError();
   cudaGraph_t graph = nullptr;
   cudaError_t ee = cudaStreamEndCapture(st, &graph);
@@ -935,8 +939,7 @@ static void destroy_graphs(eqs_ctx* c) {
   c->step_graphs.clear();
   for (auto& kv : c->solve_graphs) destroy_graph(kv.second);
   c->solve_graphs.clear();
-  for (auto& kv : c->eval_graphs) destroy_graph(kv.second);
-  c->eval_graphs.clear();
+  destroy_graph(c->eval_graph);
   c->ens_last = nullptr;
   for (auto& kv : c->ens_graphs) destroy_graph(kv.second);
   c->ens_graphs.clear();
@@ -1156,7 +1159,9 @@ static eqs_status ens_pcg_direct(eqs_ctx* c, const double4_32a* R, double4_32a* 
 static double4_32a* eYbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_eY[0] : c->d_eY[1 + (j - 1) % 3]; }
 static double4_32a* eFbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_eF[0] : c->d_eF[1 + (j - 1) % 2]; }
 
-static eqs_status ens_enqueue_step(eqs_ctx* c, int s, double* X, const double* d_cj, cudaStream_t st) {
+// The caller's X is read and written through the parameter block
+// (c->d_params->x), so the captured graph does not depend on it.
+static eqs_status ens_enqueue_step(eqs_ctx* c, int s, const double* d_cj, cudaStream_t st) {
   std::vector<double> mu, nu, mut, gt, cj;
   double beta;
   rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
@@ -1166,7 +1171,8 @@ static eqs_status ens_enqueue_step(eqs_ctx* c, int s, double* X, const double* d
   const bool spe = c->opts.guess == EQS_GUESS_SPE;
   launch(k_stage_scalars, 1, 64, st, s + 1, d_cj, c->d_params, c->V0, w, c->phase, c->d_g, c->d_gp,
          c->d_estepcount);
-  launch(k4_gather_state, nblk(n), kBlock, st, n, nf, (const double*)X, (const int32_t*)c->d_node_of_internal,
+  launch(k4_gather_state, nblk(n), kBlock, st, n, nf, (const StepParams*)c->d_params,
+         (const int32_t*)c->d_node_of_internal,
          (const double*)c->d_dir_scale, (const double*)c->d_g, (const double*)c->d_ecolv, eYbuf(c, 0), c->d_eY2,
          (const double4_32a*)eFbuf(c, s - 1), eFbuf(c, 0));
   eqs_status stt = EQS_OK;
@@ -1180,7 +1186,7 @@ static eqs_status ens_enqueue_step(eqs_ctx* c, int s, double* X, const double* d
              (const double4_32a*)eYbuf(c, j - 1), (const double4_32a*)eYbuf(c, j >= 2 ? j - 2 : 0),
              (const double4_32a*)eFbuf(c, j - 1), (const double4_32a*)eFbuf(c, 0), (const int*)c->d_ezero, j - 1,
              (const double*)c->d_dir_scale, (const double*)(c->d_g + j), (const double*)c->d_ecolv, eYbuf(c, j),
-             last ? nullptr : c->d_eY2, last ? nullptr : eFbuf(c, j), last ? X : nullptr,
+             last ? nullptr : c->d_eY2, last ? nullptr : eFbuf(c, j), last ? 1 : 0,
              (const int32_t*)c->d_node_of_internal, (const long long*)c->d_estepcount, s,
              spe ? c->d_eX : nullptr, kEnsSpe);
       if (last) break;
@@ -1208,7 +1214,7 @@ static eqs_status ens_enqueue_step(eqs_ctx* c, int s, double* X, const double* d
   return stt;
 }
 
-static eqs_status ens_capture_step(eqs_ctx* c, int s, double* X, GraphEntry& ge) {
+static eqs_status ens_capture_step(eqs_ctx* c, int s, GraphEntry& ge) {
   std::vector<double> mu, nu, mut, gt, cj;
   double beta;
   rkc_coefficients(s, mu, nu, mut, gt, cj, beta);
@@ -1216,7 +1222,7 @@ static eqs_status ens_capture_step(eqs_ctx* c, int s, double* X, GraphEntry& ge)
   cudaStream_t st = c->cap_stream;
   c->direct = false;
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-  eqs_status stt = ens_enqueue_step(c, s, X, ge.d_cj, st);
+  eqs_status stt = ens_enqueue_step(c, s, ge.d_cj, st);
   cudaError_t le = cudaGetLastError();
   cudaGraph_t graph = nullptr;
   cudaError_t ee = cudaStreamEndCapture(st, &graph);
@@ -1679,21 +1685,12 @@ eqs_status eqs_apply_K_static(eqs_ctx* c, const double* x, double* y) {
   k_gather_perm<<<nblk(n), kBlock, 0, st>>>(n, x, c->d_node_of_internal, xg, mx ? x2 : nullptr);
   // the accumulator keeps the previous call's contents: clear it
   CK(cudaMemsetAsync(yacc, 0, (size_t)n * (mx ? sizeof(float) : sizeof(double)), st));
-  if (mx && c->npe == 10) {
-    k_elem32_p2<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn10, c->d_mat, c->d_mats, c->d_xyz_hi,
-                                                    c->d_xyz_lo, x2, n, (float*)yacc);
-    k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, nullptr, (const float*)yacc, c->d_node_of_internal, y);
-  } else if (c->npe == 10) {
-    k_elem64_p2<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn10, c->d_mat, c->d_mats, c->d_xyz, xg, n,
-                                                    1.0, (double*)yacc);
-    k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, (const double*)yacc, nullptr, c->d_node_of_internal, y);
-  } else if (mx) {
-    k_elem32<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn, c->d_mat, c->d_mats, c->d_xyz_hi,
-                                                 c->d_xyz_lo, x2, n, (float*)yacc);
+  // the element kernel eqs_apply_K takes (cell, tet or P2), on the static regions
+  if (mx) {
+    elem_launch(c, st, nullptr, n, nullptr, (float*)yacc, x2);
     k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, nullptr, (const float*)yacc, c->d_node_of_internal, y);
   } else {
-    k_elem64<<<nblk(c->n_tets), kBlock, 0, st>>>(c->n_tets, c->d_conn, c->d_mat, c->d_mats, c->d_xyz, xg, n,
-                                                 1.0, (double*)yacc);
+    elem_launch(c, st, xg, n, (double*)yacc, nullptr);
     k_scatter_perm<<<nblk(n), kBlock, 0, st>>>(n, (const double*)yacc, nullptr, c->d_node_of_internal, y);
   }
   CK(cudaGetLastError());
@@ -1770,8 +1767,9 @@ eqs_status eqs_rkc_step(eqs_ctx* c, double* x, double t, double dt, int s, eqs_s
   if (!x) return fail(c, EQS_ERR_ARG, "x is NULL");
   if (s < 2 || s > EQS_MAX_STAGES) return fail(c, EQS_ERR_ARG, "s out of range [2, 64]");
   if (!std::isfinite(t) || !(dt > 0) || !std::isfinite(dt)) return fail(c, EQS_ERR_ARG, "bad t or dt");
+  const StepParams prm{t, dt, x};
   if (c->opts.host_loop) {  // same kernels, CG loops driven from the host
-    const std::pair<int, uintptr_t> dkey(-s, 0);
+    const int dkey = -s;
     auto dit = c->step_graphs.find(dkey);
     if (dit == c->step_graphs.end()) {
       GraphEntry ge;
@@ -1782,12 +1780,11 @@ eqs_status eqs_rkc_step(eqs_ctx* c, double* x, double t, double dt, int s, eqs_s
       ge.s = s;
       dit = c->step_graphs.emplace(dkey, ge).first;
     }
-    StepParams prm{t, dt};
     CK(cudaMemcpyAsync(c->d_params, &prm, sizeof(prm), cudaMemcpyHostToDevice, c->stream));
     c->direct = true;
     g_launches = 0;
-    eqs_status st = mixed(c) ? enqueue_step(c, c->lev32, s, x, dit->second.d_cj, c->stream)
-                             : enqueue_step(c, c->lev64, s, x, dit->second.d_cj, c->stream);
+    eqs_status st = mixed(c) ? enqueue_step(c, c->lev32, s, dit->second.d_cj, c->stream)
+                             : enqueue_step(c, c->lev64, s, dit->second.d_cj, c->stream);
     c->direct = false;
     if (st != EQS_OK) return st;
     dit->second.fixed_kernels = g_launches;
@@ -1796,15 +1793,13 @@ eqs_status eqs_rkc_step(eqs_ctx* c, double* x, double t, double dt, int s, eqs_s
     if (c->recording) c->recorded = std::min<int64_t>(c->recorded + s, c->store_cap);
     return stats ? eqs_get_step_stats(c, stats) : EQS_OK;
   }
-  const std::pair<int, uintptr_t> key(s, (uintptr_t)x);
-  auto it = c->step_graphs.find(key);
+  auto it = c->step_graphs.find(s);
   if (it == c->step_graphs.end()) {
     GraphEntry ge;
-    eqs_status st = mixed(c) ? capture_step(c, c->lev32, s, x, ge) : capture_step(c, c->lev64, s, x, ge);
+    eqs_status st = mixed(c) ? capture_step(c, c->lev32, s, ge) : capture_step(c, c->lev64, s, ge);
     if (st != EQS_OK) return st;
-    it = c->step_graphs.emplace(key, ge).first;
+    it = c->step_graphs.emplace(s, ge).first;
   }
-  StepParams prm{t, dt};
   CK(cudaMemcpyAsync(c->d_params, &prm, sizeof(prm), cudaMemcpyHostToDevice, c->stream));
   CK(cudaGraphLaunch(it->second.exec, c->stream));
   c->last_step = &it->second;
@@ -1884,17 +1879,14 @@ eqs_status eqs_rkc_adaptive_step(eqs_ctx* c, double* x, double t, double h_try, 
     out->total_iters += st.total_iters;
     // F(t + h, x_new), started from F(t, x_old) (the step's first stage)
     CK(cudaMemcpyAsync(c->d_Fnew, c->d_F[0], nf * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    auto it = c->eval_graphs.find((uintptr_t)x);
-    if (it == c->eval_graphs.end()) {
-      GraphEntry ge;
-      const eqs_status es = mixed(c) ? capture_eval_F(c, c->lev32, x, c->d_Fnew, ge)
-                                     : capture_eval_F(c, c->lev64, x, c->d_Fnew, ge);
+    if (!c->eval_graph.exec) {
+      const eqs_status es = mixed(c) ? capture_eval_F(c, c->lev32, c->d_Fnew, c->eval_graph)
+                                     : capture_eval_F(c, c->lev64, c->d_Fnew, c->eval_graph);
       if (es != EQS_OK) return es;
-      it = c->eval_graphs.emplace((uintptr_t)x, ge).first;
     }
-    StepParams prm{t + h, h};
+    const StepParams prm{t + h, h, x};
     CK(cudaMemcpyAsync(c->d_params, &prm, sizeof(prm), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaGraphLaunch(it->second.exec, c->stream));
+    CK(cudaGraphLaunch(c->eval_graph.exec, c->stream));
     k_rkc_errnorm<<<vec_grid(c, nf), kBlock, 0, c->stream>>>(
         nf, c->d_xsave, x, c->d_node_of_internal, c->d_F[0], c->d_Fnew, h, atol, rtol, c->red.partials,
         c->red.counter, c->red.max_blocks, c->d_err);
@@ -1936,11 +1928,11 @@ eqs_status eqs_ens_rkc_step(eqs_ctx* c, double* x, const double* v0_scale, doubl
     return fail(c, EQS_ERR_STATE, "the ensemble starts from EQS_GUESS_PREV or EQS_GUESS_SPE");
   const eqs_status as = ens_alloc(c);
   if (as != EQS_OK) return as;
-  StepParams prm{t, dt};
+  StepParams prm{t, dt, x};
   CK(cudaMemcpyAsync(c->d_params, &prm, sizeof(prm), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_ecolv, v0_scale, EQS_ENS_W * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   if (c->opts.host_loop) {
-    const std::pair<int, uintptr_t> dkey(-s, 0);
+    const int dkey = -s;
     auto dit = c->ens_graphs.find(dkey);
     if (dit == c->ens_graphs.end()) {
       GraphEntry ge;
@@ -1953,18 +1945,18 @@ eqs_status eqs_ens_rkc_step(eqs_ctx* c, double* x, const double* v0_scale, doubl
     }
     c->direct = true;
     g_launches = 0;
-    const eqs_status st = ens_enqueue_step(c, s, x, dit->second.d_cj, c->stream);
+    const eqs_status st = ens_enqueue_step(c, s, dit->second.d_cj, c->stream);
     c->direct = false;
     if (st != EQS_OK) return st;
     dit->second.fixed_kernels = g_launches;
     dit->second.per_iter_kernels = 0;
     c->ens_last = &dit->second;
   } else {
-    const std::pair<int, uintptr_t> key(s, (uintptr_t)x);
+    const int key = s;
     auto it = c->ens_graphs.find(key);
     if (it == c->ens_graphs.end()) {
       GraphEntry ge;
-      const eqs_status st = ens_capture_step(c, s, x, ge);
+      const eqs_status st = ens_capture_step(c, s, ge);
       if (st != EQS_OK) return st;
       it = c->ens_graphs.emplace(key, ge).first;
     }
@@ -1972,6 +1964,68 @@ eqs_status eqs_ens_rkc_step(eqs_ctx* c, double* x, const double* v0_scale, doubl
     c->ens_last = &it->second;
   }
   return stats ? eqs_ens_get_step_stats(c, stats) : EQS_OK;
+}
+
+eqs_status eqs_launch_kernel(eqs_ctx* c, int kernel) {
+  REQUIRE_SETUP(c);
+  if (!((kernel >= EQS_KERNEL_SPE_GRAM && kernel <= EQS_KERNEL_PCG_PQ) ||
+        (kernel >= EQS_KERNEL_ENS_SPE_GRAM && kernel <= EQS_KERNEL_ENS_PCG_PQ)))
+    return fail(c, EQS_ERR_ARG, "unknown kernel id");
+  const bool ens = kernel >= EQS_KERNEL_ENS_SPE_GRAM;
+  const GraphEntry* last = ens ? c->ens_last : c->last_step;
+  if (!last) return fail(c, EQS_ERR_STATE, ens ? "run an ensemble step first" : "run a step first");
+  const int s = last->s, j = s - 1;  // the last solve of that step
+  const int nf = (int)c->n_free;
+  cudaStream_t st = c->stream;
+  if ((kernel == EQS_KERNEL_ELEM || kernel == EQS_KERNEL_ENS_ELEM) && !c->d_ktime)
+    CK(dalloc(c, &c->d_ktime, (size_t)c->n_nodes));
+  const int g = vec_grid(c, nf);
+  switch (kernel) {
+    case EQS_KERNEL_SPE_GRAM:
+      if (c->opts.guess != EQS_GUESS_SPE) return fail(c, EQS_ERR_STATE, "SPE start vectors are not in use");
+      spe_gram(c, st, s, j, (c->opts.defer_sums & 2) != 0, false);  // the Gram pass alone
+      break;
+    case EQS_KERNEL_ELEM:
+      if (mixed(c))
+        elem_launch(c, st, nullptr, nf, nullptr, (float*)c->d_ktime);
+      else
+        elem_launch(c, st, Ybuf(c, 0), nf, (double*)c->d_ktime, nullptr);
+      break;
+    case EQS_KERNEL_PCG_PQ:
+      if (c->d_z32)
+        launch(k_pcg_pq_split<false>, g, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo,
+               nf, (const float*)c->d_z32, c->d_p, c->d_q, c->d_sc, c->red.partials, c->red.counter,
+               c->red.max_blocks, (double*)nullptr, 0, c->opts.flexible);
+      else
+        launch(k_pcg_pq, g, kBlock, st, c->M64, nf, c->d_zd, c->d_p, c->d_q, c->d_sc, c->red.partials,
+               c->red.counter, c->red.max_blocks);
+      break;
+    case EQS_KERNEL_ENS_SPE_GRAM:
+      if (c->opts.guess != EQS_GUESS_SPE) return fail(c, EQS_ERR_STATE, "SPE start vectors are not in use");
+      launch(k4_spe_gram<kEnsSpe>, std::max(1, std::min(nblk(nf), c->sms)), kBlock, st, c->M64, nf,
+             (const double4_32a*)c->d_eX, c->d_eW, (const double4_32a*)c->d_eR, (const long long*)c->d_estepcount,
+             s, j, c->d_eG, c->d_espart, c->red.counter, c->red.max_blocks, 1e-12, c->d_ecoef);
+      break;
+    case EQS_KERNEL_ENS_ELEM:
+      if (c->n_cells > 0)
+        launch(k4_elem32_cell, nblk(c->n_cells), kBlock, st, c->n_cells, (const int32_t*)c->d_corner,
+               (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi,
+               (const float4*)c->d_xyz_lo, (const float4*)c->d_eY2, nf, c->d_ktime);
+      else
+        launch(k4_elem32, nblk(c->n_tets), kBlock, st, c->n_tets, (const int4*)c->d_conn, (const uint8_t*)c->d_mat,
+               (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi, (const float4*)c->d_xyz_lo,
+               (const float4*)c->d_eY2, nf, c->d_ktime);
+      break;
+    case EQS_KERNEL_ENS_PCG_PQ:
+      launch(k4_pcg_pq, g, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo, nf,
+             (const float4*)c->d_ez32, c->d_ep, c->d_eq, (EnsScalars*)c->d_esc, c->d_epart, c->red.counter,
+             c->red.max_blocks);
+      break;
+    default:
+      return fail(c, EQS_ERR_ARG, "unknown kernel id");
+  }
+  CK(cudaGetLastError());
+  return EQS_OK;
 }
 
 eqs_status eqs_ens_get_step_stats(eqs_ctx* c, eqs_ens_stats* stats) {

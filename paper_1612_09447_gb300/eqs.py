@@ -21,6 +21,8 @@ EQS_PREC_FP64, EQS_PREC_MIXED = 0, 1
 EQS_GUESS_PREV, EQS_GUESS_MLP, EQS_GUESS_ZERO, EQS_GUESS_SPE = 0, 1, 2, 3
 EQS_GUESS_POD, EQS_GUESS_POD2 = 4, 5
 EQS_MAX_STAGES = 64
+EQS_KERNEL_SPE_GRAM, EQS_KERNEL_ELEM, EQS_KERNEL_PCG_PQ = 0, 1, 2
+EQS_KERNEL_ENS_SPE_GRAM, EQS_KERNEL_ENS_ELEM, EQS_KERNEL_ENS_PCG_PQ = 16, 17, 18
 
 
 class EqsError(RuntimeError):
@@ -125,6 +127,7 @@ def _declare(L):
         "eqs_ens_get_step_stats": (I, [P, C.POINTER(eqs_ens_stats)]),
         "eqs_ens_solve_M": (I, [P, P, P, P]),
         "eqs_pod_eval": (I, [P, P, I, P, P]),
+        "eqs_launch_kernel": (I, [P, I]),
         "eqs_pod_info": (I, [P, P, P, P, P, P]),
         "eqs_rkc_adaptive_step": (I, [P, P, D, D, D, D, I, C.POINTER(eqs_adapt_stats)]),
         "eqs_destroy": (I, [P]),
@@ -378,6 +381,10 @@ def eqs_ens_solve_M(ctx, rhs, z):
     it = (C.c_int * EQS_ENS_W)()
     _check(lib().eqs_ens_solve_M(ctx, _dev(rhs), _dev(z), it), ctx)
     return list(it)
+
+
+def eqs_launch_kernel(ctx, kernel):
+    _check(lib().eqs_launch_kernel(ctx, kernel), ctx)
 
 
 def eqs_destroy(ctx):

@@ -4,7 +4,8 @@ Some callers cannot allocate device memory at call time (a fixed device
 memory budget claimed up front, a real-time or callback path where an
 allocation may block or fail); this entry point serves them from a static
 device array inside the library.  Checked here through the C ABI against
-eqs_apply_K on two calls in a row.  This file is collected last so that a
+eqs_apply_K on two calls in a row, for linear tets (the Kuhn-cell and the
+jittered mesh) and quadratic (10-node) tets.  This file is collected last so that a
 run stopping at the first failure has already run every other test.
 """
 import os
@@ -35,9 +36,10 @@ def _state(p, seed):
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
-@pytest.mark.parametrize("problem", ["cube12", "jitter10"])
+@pytest.mark.parametrize("problem", ["cube12", "jitter10", "p2_cube8"])
 def test_static_matches_apply_K_twice(E, prec, tol, problem):
-    p = ei.config_problem(0) if problem == "cube12" else ei.config_problem(2, N=10)
+    p = {"cube12": lambda: ei.config_problem(0), "jitter10": lambda: ei.config_problem(2, N=10),
+         "p2_cube8": lambda: ei.make_problem_p2(8)}[problem]()
     S = E.Solver(p, precision=prec)
     for seed in (11, 12):  # two calls in a row: the shared scratch is reused
         x = _state(p, seed)
