@@ -2,10 +2,15 @@
 """Benchmark of the explicit RKC EQS solver on GB300.
 
 Metric: RKC DOF-stages/s (free unknowns x stages x steps / second) with
-every stage M-solve at ||R - M z|| / ||R|| <= 1e-8, on the 64^3-cell
-Kuhn cube (274,625 nodes, 266,175 free, 1.57 M tets, block varistor,
-s = 20 stages, dt at the RKC stability bound).  The timed form is the
-mixed-precision path; the plain FP64 AMG-PCG form is measured beside it.
+every stage M-solve at ||R - M z|| / ||R|| <= 1e-8.  Default workload: the
+128^3-cell jittered Kuhn cube with two varistor spheres (2,146,689 nodes,
+2,113,407 free, 12.6 M P1 tets, s = 20 stages, dt at the RKC stability
+bound), the paper's P1 problem size, as a 4-member ensemble (drive
+V0 x 0.5/1/1.5/2) whose stage right-hand sides are solved 4 at a time, in
+mixed precision with SPE start vectors.  The metric's comparison, plain FP64
+AMG-PCG with the previous-solution start, and the other single-trajectory
+forms are measured beside it on the same mesh (--config 1, 3, 4: the 64^3
+cube, the learned start vector, batched serving).
 
 A "step" is one RKC step (20 stages: element kernel, right-hand side, AMG-PCG
 solve, recurrence) through the C ABI.  L2 is flushed (256 MiB write) between
@@ -13,7 +18,8 @@ timed steps, outside the timed intervals.  Multi-GPU runs are independent
 replicas (one instance per GPU, no collective on the data path).
 
 --impl reference times the CPU oracle on a bounded sample of the same
-workload (first stages of an RKC step) with the same metric.
+workload (steady-state CG iterations and the element operator of a warm
+stage, stage time extrapolated) with the same metric.
 """
 from __future__ import annotations
 
@@ -45,7 +51,7 @@ WORKLOADS = {
 }
 RTOL = 1e-8
 S_STAGES = 20
-CONFIG_INDEX = 1
+CONFIG_INDEX = 2
 WORKLOAD = WORKLOADS[CONFIG_INDEX]
 # AMG/solver options of the timed runs (both precisions): degree-1 Chebyshev
 # smoothing and a 2066-row coarsest level (dense inverse: FP64 on the FP64
@@ -55,12 +61,10 @@ WORKLOAD = WORKLOADS[CONFIG_INDEX]
 # slower and stays off).
 SOLVER_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0, coarse_split=0, defer_sums=2)
 SPE_N = 6  # solutions spanning the SPE subspace
-# DRAM bytes (read + write) of one k_spmv64 launch per workload from an ncu
-# capture (profiles/k_spmv_split_cube64.md); None where not captured.
-TRAFFIC_SPMV64 = {1: 33821696, 2: None}
-# DRAM bytes (read + write) of one k_spmv_split launch per workload from an
-# ncu capture (profiles/k_spmv_split_cube64.md); None where not captured.
-TRAFFIC_SPLIT = {1: 32744704, 2: None}
+# DRAM bytes (read + write) of one launch, per (kernel, workload), from a
+# one-kernel ncu capture of the current build (dram__bytes_read.sum +
+# dram__bytes_write.sum); a kernel without an entry reports null.
+TRAFFIC = {}
 
 
 def parse():
@@ -73,8 +77,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--N", type=int, default=None, help="override mesh size (testing)")
-    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3, 4],
-                    help="workload: 1 = 64^3 block cube (default), 2 = 128^3 jittered spheres, "
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
+                    help="workload: 1 = 64^3 block cube, 2 = 128^3 jittered spheres (default), "
                          "3 = learned guess on the 128^3 mesh, 4 = batched serving of 64 instances")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the CG loops from the host (same kernels; for ncu launch lists)")
@@ -107,44 +111,68 @@ sys.path.insert(0, {root!r})
 import eqs_inputs as ei
 from oracle import run
 p = ei.config_problem({cfg}, N={N})
-r = run.time_stage_sample(p, {s}, {n_stages}, rtol={rtol})
-print(json.dumps(r))
+run.steady_stage_sample(p, {s}, {warm}, {samples}, rtol={rtol}, with_K={with_K},
+                        report=lambda k, r: print(json.dumps(r), flush=True))
 """
 
 
-def oracle_sample(n_stages, N=None):
-    """Run the oracle in a fresh single-threaded process (spawned, no CUDA)."""
+def oracle_start(samples, N=None, warm=2, with_K=True):
+    """Start the oracle's steady-state sampler in a fresh single-threaded
+    process (no CUDA); it prints one JSON line per sample."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = ORACLE_SNIPPET.format(root=ROOT, cfg=CONFIG_INDEX, N=N, s=S_STAGES, n_stages=n_stages,
-                                 rtol=RTOL)
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                         timeout=1800)
-    if out.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    code = ORACLE_SNIPPET.format(root=ROOT, cfg=1 if CONFIG_INDEX == 1 else 2, N=N, s=S_STAGES, warm=warm,
+                                 samples=samples, rtol=RTOL, with_K=with_K)
+    return subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                            stderr=subprocess.PIPE, text=True)
+
+
+def oracle_collect(proc, timeout=1800):
+    out, err = proc.communicate(timeout=timeout)
+    if proc.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + err[-2000:])
+    return [json.loads(line) for line in out.strip().splitlines() if line.startswith("{")]
+
+
+def host_cores():
+    return os.cpu_count() or 0
+
+
+def cpu_baseline_entry(rs):
+    """cpu_baseline object from the oracle's steady-state samples."""
+    stage = sum(r["stage_s"] for r in rs) / len(rs)
+    r = rs[-1]
+    return {"value": r["n_free"] / stage, "unit": "DOF-stages/s", "cores": 1, "host_cores": host_cores(),
+            "kind": "oracle",
+            "sample": f"numpy/scipy FP64 oracle, single thread: {len(rs)} timed samples at a warm stage of "
+                      f"the first RKC step (after {len(r['warm_iters'])} stages with full M-solves to 1e-8, "
+                      f"previous-solution start; CG iterations {r['warm_iters']}): element operator + "
+                      f"right-hand side t_K = {r['t_K']:.2f} s, a one-iteration PCG t_1 = {r['t_pcg1']:.2f} s; "
+                      f"stage time extrapolated as t_K + (it_ss/2) t_1 with it_ss = {r['cg_iters_ss']}"}
 
 
 def run_reference(args, rank):
+    """The oracle (CPU, single thread) as the reference arm: setup and warm
+    stages once, then per step one sample (a one-iteration PCG at the warm
+    stage; the element operator time of the warm stages) extrapolated to a
+    stage; value = DOF-stages/s over the timed steps."""
     if rank != 0:
         return
-    n_stages = 2
-    t_total, dof = 0.0, 0
-    for k in range(args.warmup + args.steps):
-        r = oracle_sample(n_stages, args.N)
-        if k >= args.warmup:
-            t_total += r["seconds"]
-            dof += r["n_free"] * r["stages"]
+    proc = oracle_start(args.warmup + args.steps, args.N, warm=2, with_K=False)
+    rs = oracle_collect(proc)[args.warmup:]
+    t_total = sum(r["stage_s"] for r in rs) * S_STAGES
+    dof = sum(r["n_free"] for r in rs) * S_STAGES
     value = dof / t_total
+    cpu = cpu_baseline_entry(rs)
+    cpu["sample"] += "; per step one one-iteration PCG sample, t_K from the warm stages"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-stages/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"first {n_stages} stages of an RKC step per step"},
-        "cpu_baseline": {"value": value, "unit": "DOF-stages/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{n_stages} stage evaluations per step, oracle numpy/scipy "
-                                   f"FP64 AMG-PCG, single thread"},
+        "config": {"workload": WORKLOAD + " (single trajectory, previous-solution start)",
+                   "sample": "per step: one RKC step's 20 stages extrapolated from one steady-state sample"},
+        "cpu_baseline": dict(cpu, value=value),
         "e2e": {"value": value, "unit": "DOF-stages/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -294,7 +322,10 @@ def run_ours(args, rank, world):
         t += dt
     e2e_ms = max_over_ranks(e2e_ms, dist)
     e2e_value = units / (e2e_ms / 1e3)
-    roof = dominant_kernel_roofline(torch, eqs, solver, p, flush)
+    roof = kernel_roofline(torch, eqs, solver, p, flush,
+                           {eqs.EQS_KERNEL_SPE_GRAM: S_STAGES, eqs.EQS_KERNEL_ELEM: S_STAGES,
+                            eqs.EQS_KERNEL_PCG_PQ: float(np.mean(iters)) * S_STAGES},
+                           total_ms / args.steps, CONFIG_INDEX)
     solver.close()
 
     variants = {}
@@ -348,11 +379,7 @@ def run_ours(args, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rr = oracle_sample(4, args.N)
-        cpu = {"value": rr["dof_stages_per_s"], "unit": "DOF-stages/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {rr['stages']} stage evaluations of one RKC step "
-                         f"({rr['seconds']:.1f} s, numpy/scipy FP64 AMG-PCG with previous-solution "
-                         f"start, single thread)"}
+        cpu = cpu_baseline_entry(oracle_collect(oracle_start(2, args.N)))
     if rank != 0:
         return
     ms_step = total_ms / args.steps
@@ -508,33 +535,58 @@ def _time_launches(torch, fn, flush, reps=20):
     return statistics.median(ts[3:])
 
 
-def dominant_kernel_roofline(torch, eqs, solver, p, flush):
-    """The CG operator product M z of the timed mixed path (k_spmv_split:
-    M as two FP32 parts, FP32 z, FP32-pair row sums; the same row product
-    as k_pcg_pq_split) timed alone with CUDA events on the launch stream,
-    L2 flushed before each launch.  Algorithmic bytes per launch: 8 B per
-    non-zero (hi + lo) + 4 B of z and 8 B of y per row.  The FP64 product
-    (k_spmv64, the FP64 path's operator) is reported beside it."""
-    nf = p.n_free
-    rows, nnz = solver.amg_info()
-    z = torch.randn(nf, dtype=torch.float32, device="cuda")
-    x = z.double()
-    y = torch.empty(nf, dtype=torch.float64, device="cuda")
+def kernel_bytes(eqs, kid, p, nnz0, nf):
+    """Algorithmic bytes of one launch (what the kernel must move once):
+    matrix values and per-row vectors read or written once, connectivity and
+    materials once per cell (Kuhn cells: 8 corner indices + 6 material
+    bytes) or per tet, node data once per node."""
+    n = p.n_nodes
+    cells = p.N ** 3 if p.tets.shape[1] == 4 else 0
+    if kid == eqs.EQS_KERNEL_ENS_SPE_GRAM:  # M (FP64) + newest x, W, b and 5 older columns, 4 doubles each
+        return 8 * nnz0 + 8 * 32 * nf
+    if kid == eqs.EQS_KERNEL_ENS_ELEM:  # cells + coords (hi, lo) + potentials (4 hi/lo pairs) + y (float4 RMW)
+        return 38 * cells + (32 + 32 + 32) * n
+    if kid == eqs.EQS_KERNEL_ENS_PCG_PQ:  # M (hi, lo FP32) + z (float4) + p, q (double4, read + write)
+        return 8 * nnz0 + (16 + 64 + 64) * nf
+    if kid == eqs.EQS_KERNEL_SPE_GRAM:  # M (FP64) + newest x, W, b and 5 older columns
+        return 8 * nnz0 + 8 * 8 * nf
+    if kid == eqs.EQS_KERNEL_ELEM:  # cells + coords (hi, lo) + potential (hi, lo) + y (float RMW)
+        return 38 * cells + (32 + 8 + 8) * n
+    if kid == eqs.EQS_KERNEL_PCG_PQ:  # M (hi, lo FP32) + z (float) + p, q (read + write)
+        return 8 * nnz0 + (4 + 16 + 16) * nf
+    raise ValueError(kid)
+
+
+KERNEL_NAMES = {16: "k4_spe_gram<6> (ensemble SPE Gram pass)", 17: "k4_elem32_cell (ensemble element kernel)",
+                18: "k4_pcg_pq (ensemble CG operator pass, split M)", 0: "k_spe_gram<6> (SPE Gram pass)",
+                1: "k_elem32_cell (element kernel)", 2: "k_pcg_pq_split (CG operator pass, split M)"}
+
+
+def kernel_roofline(torch, eqs, S, p, flush, kernels, step_ms, workload_key):
+    """Each kernel of the last step timed alone (eqs_launch_kernel on the
+    context stream, CUDA events, L2 flushed before every launch) with its
+    algorithmic bytes; kernels: {id: launches per step}.  The roofline entry
+    is the kernel with the largest (time per launch x launches per step);
+    the element kernel is reported beside it."""
+    rows, nnz = S.amg_info()
     peak, kind = _peaks()
-    ms32 = _time_launches(torch, lambda: eqs.eqs_spmv_M32(solver.ctx, z, y), flush)
-    b32 = nnz[0] * 8 + nf * (4 + 8)
-    ms64 = _time_launches(torch, lambda: eqs.eqs_spmv_M(solver.ctx, x, y), flush)
-    b64 = nnz[0] * 8 + nf * 8 * 2
-    ach = b32 / (ms32 / 1e3) / 1e9
-    a64 = b64 / (ms64 / 1e3) / 1e9
-    return {"kernel": "k_spmv_split (mixed-path CG operator product M z, as in k_pcg_pq_split)",
-            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": TRAFFIC_SPLIT.get(CONFIG_INDEX), "bytes_per_launch": b32, "ms_per_launch": ms32,
-            "peak_kind": f"{kind} hbm_gbs (burst: kernel timed alone, L2 flushed before each launch)",
-            "fp64_operator": {"kernel": "k_spmv64 (FP64 DIA SpMV of M_ff)", "achieved": a64, "frac": a64 / peak,
-                              "bytes_per_launch": b64, "ms_per_launch": ms64,
-                              "fp64_tflops": 2.0 * nnz[0] / (ms64 / 1e3) / 1e12,
-                              "traffic": TRAFFIC_SPMV64.get(CONFIG_INDEX)}}
+    table = {}
+    for kid, per_step in kernels.items():
+        ms = _time_launches(torch, lambda: eqs.eqs_launch_kernel(S.ctx, kid), flush)
+        b = kernel_bytes(eqs, kid, p, nnz[0], S.nf)
+        ach = b / (ms / 1e3) / 1e9
+        name = KERNEL_NAMES[kid]
+        table[name] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                       "traffic": TRAFFIC.get((name.split()[0], workload_key)), "bytes_per_launch": b,
+                       "ms_per_launch": ms, "launches_per_step": per_step,
+                       "est_share_of_step": ms * per_step / step_ms}
+    top = max(table, key=lambda k: table[k]["ms_per_launch"] * table[k]["launches_per_step"])
+    elem = [k for k in table if "elem" in k][0]
+    roof = dict(kernel=top, **table[top])
+    roof["peak_kind"] = f"{kind} hbm_gbs (burst: kernel timed alone, L2 flushed before each launch)"
+    roof["element"] = dict(kernel=elem, **table[elem])
+    roof["kernels"] = table
+    return roof
 
 
 def run_batch(args, rank, world):
@@ -686,10 +738,46 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def time_single(torch, eqs, p, make, flush, prec, guess, steps, warmup=2, theta=None):
+    """Single-trajectory steps on the workload's mesh: ms/step, CG
+    iterations per solve, DOF-stages/s."""
+    import numpy as np
+
+    T = make(prec, guess, theta)
+    dt = T.dt_bound(S_STAGES)
+    xs = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+    ts = 0.0
+    for _ in range(warmup):
+        T.step(xs, ts, dt, S_STAGES)
+        ts += dt
+    tm, it, kept = [], [], 0
+    for _ in range(steps):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        T.step(xs, ts, dt, S_STAGES, stats=False)
+        e1.record()
+        stt = T.last_stats()
+        tm.append(e0.elapsed_time(e1))
+        it.append(stt.total_iters / S_STAGES)
+        kept += stt.guess_kept
+        ts += dt
+    T.close()
+    out = {"value": p.n_free * S_STAGES * len(tm) / (sum(tm) / 1e3), "ms_per_step": sum(tm) / len(tm),
+           "m_solve_ms_per_rhs": sum(tm) / len(tm) / S_STAGES, "cg_iters_per_solve": float(np.mean(it)),
+           "steps": steps}
+    if guess == eqs.EQS_GUESS_MLP:
+        out["learned_guess_kept"] = kept / (steps * S_STAGES)
+    return out
+
+
 def run_ensemble_headline(args, rank, world):
     """Config 2: the 4-member ensemble (drive V0 x {0.5, 1, 1.5, 2}) on the
     128^3 jittered mesh, every stage's four right-hand sides solved together
-    (blocked CG, SpMM), mixed precision, per-column SPE start vectors."""
+    (blocked CG, SpMM), mixed precision, per-column SPE start vectors.  The
+    metric's comparison (plain FP64 AMG-PCG, previous-solution start) and the
+    other single-trajectory forms run on the same mesh beside it."""
     import numpy as np
     import torch
 
@@ -697,6 +785,9 @@ def run_ensemble_headline(args, rank, world):
     from paper_1612_09447_gb300 import eqs
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_proc = oracle_start(2, args.N)  # runs on a host core while the GPU forms run
     torch.cuda.set_device(local)
     eqs.lib()
     p = ei.config_problem(CONFIG_INDEX, N=args.N)
@@ -709,9 +800,11 @@ def run_ensemble_headline(args, rank, world):
     def flush():
         flushbuf.zero_()
 
-    def make(precision, guess):
+    def make(precision, guess, theta=None):
         S = eqs.Solver(p, precision=precision, rtol=RTOL, host_loop=int(args.host_loop), spe_n=SPE_N,
                        **SOLVER_OPTS)
+        if theta is not None:
+            eqs.eqs_guess_set_params(S.ctx, theta)
         eqs.eqs_set_guess(S.ctx, guess)
         return S
 
@@ -725,8 +818,9 @@ def run_ensemble_headline(args, rank, world):
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
+    torch.cuda.synchronize()
     clk = ClockSampler(local)
-    times, iters, launches = [], [], 0
+    times, iters, launches, passes = [], [], 0, 0
     for _ in range(args.steps):
         flush()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -738,9 +832,12 @@ def run_ensemble_headline(args, rank, world):
         times.append(e0.elapsed_time(e1))
         iters.append([v / S_STAGES for v in st.total_iters])
         launches += st.launches
+        passes += st.passes
         t += dt
     torch.cuda.synchronize()
     clocks = clk.stop()
+    if dist is not None:
+        dist.barrier()
     total_ms = max_over_ranks(sum(times), dist)
     units = world * 4 * p.n_free * S_STAGES * args.steps
     value = job_throughput(4 * p.n_free * S_STAGES * args.steps, world, total_ms)
@@ -763,37 +860,31 @@ def run_ensemble_headline(args, rank, world):
         e2e_ms += max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_host))
         t += dt
     e2e_ms = max_over_ranks(e2e_ms, dist)
-    roof = dominant_kernel_roofline(torch, eqs, S, p, flush)
+    ms_step = total_ms / args.steps
+    roof = kernel_roofline(torch, eqs, S, p, flush,
+                           {eqs.EQS_KERNEL_ENS_SPE_GRAM: S_STAGES, eqs.EQS_KERNEL_ENS_ELEM: S_STAGES,
+                            eqs.EQS_KERNEL_ENS_PCG_PQ: passes / args.steps},
+                           ms_step, CONFIG_INDEX)
     S.close()
     forms = {}
     if not args.no_fp64:
         short = max(3, args.steps // 4)
         forms["ensemble4_mixed_prev"] = measure_ensemble(torch, eqs, p, make, flush, short, 2)
-        for name, guess in (("single_mixed_spe", eqs.EQS_GUESS_SPE), ("single_mixed_prev", eqs.EQS_GUESS_PREV)):
-            T = make(eqs.EQS_PREC_MIXED, guess)
-            xs = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
-            ts = 0.0
-            for _ in range(2):
-                T.step(xs, ts, dt, S_STAGES)
-                ts += dt
-            tm, it = [], []
-            for _ in range(short):
-                flush()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                T.step(xs, ts, dt, S_STAGES, stats=False)
-                e1.record()
-                stt = T.last_stats()
-                tm.append(e0.elapsed_time(e1))
-                it.append(stt.total_iters / S_STAGES)
-                ts += dt
-            T.close()
-            forms[name] = {"value": p.n_free * S_STAGES * len(tm) / (sum(tm) / 1e3),
-                           "ms_per_step": sum(tm) / len(tm), "cg_iters_per_solve": float(np.mean(it))}
+        # the metric's baseline: plain FP64 AMG-PCG with the previous-solution start
+        for name, prec, guess in (("fp64_plain", eqs.EQS_PREC_FP64, eqs.EQS_GUESS_PREV),
+                                  ("single_mixed_prev", eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_PREV),
+                                  ("single_fp64_spe", eqs.EQS_PREC_FP64, eqs.EQS_GUESS_SPE),
+                                  ("single_mixed_spe", eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_SPE)):
+            forms[name] = time_single(torch, eqs, p, make, flush, prec, guess, short)
+        forms["ensemble_vs_fp64_plain_per_trajectory_step"] = (
+            forms["fp64_plain"]["ms_per_step"] / (ms_step / 4))
+    cpu = None
+    if cpu_proc is not None:
+        cpu = cpu_baseline_entry(oracle_collect(cpu_proc))
     if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
         return
-    ms_step = total_ms / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": "DOF-stages/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -806,12 +897,13 @@ def run_ensemble_headline(args, rank, world):
                            "stage), mixed precision, per-column SPE start vectors (Section IV)",
                    "m_solve_ms_per_rhs": ms_step / (4 * S_STAGES),
                    "cg_iters_per_solve_by_column": [float(v) for v in np.mean(iters, axis=0)],
-                   "l2": "flushed between timed steps (256 MiB write)",
+                   "cg_passes_per_stage": passes / (args.steps * S_STAGES),
+                   "l2": "flushed between timed steps (256 MiB write); working set > L2",
                    "parallelism": f"replicas x{world}"},
         "forms": forms,
         "e2e": {"value": units / (e2e_ms / 1e3), "unit": "DOF-stages/s",
                 "h2d_bytes_per_step": 4 * p.n_nodes * 8, "d2h_bytes_per_step": 4 * p.n_nodes * 8},
-        "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": None, "clocks": clocks,
+        "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
