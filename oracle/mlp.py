@@ -15,11 +15,17 @@ counterpart in the paper) is a per-node network:
   update  Adam (Kingma & Ba 2015) on FP32 master weights; forward and backward
           use the weights rounded to BF16 (round to nearest even).
 
+A second mode corrects the SPE start vector from solution increments
+(spe_features / spe_guess below).
+
 Everything here is FP64 numpy.  Pins (tests/test_oracle_mlp.py): central
 finite differences of the loss against the analytic gradient; GELU against
 its erf definition and derivative; the zero output layer returns h1 exactly;
-Adam's first step equals -lr * sign(g); 1-ring means against a dense
-adjacency count.
+Adam's first step equals -lr * sign(g) and its hand-computed second and
+third steps; 1-ring means against a dense adjacency count; the SPE-correction
+inputs are increments (a common offset of all vectors changes nothing), the
+zero output layer returns x0, the line search never increases the M-norm
+error and lands on the solution when the direction is the error itself.
 """
 from __future__ import annotations
 
@@ -146,3 +152,61 @@ def guess(theta, A, H):
         return np.array(H[0], dtype=np.float64, copy=True)
     o, _ = forward(to_bf16(theta), X)
     return H[0] + s_h * o
+
+
+# ------------------------------------------------ correction of the SPE start
+# The second mode of the learned estimator proposes a correction direction
+# for the SPE start vector x0 (Eq. 4-5) and takes the step along it that
+# minimises the M-norm error (an exact line search; M is SPD):
+#
+#   inputs  x = [d0, d1, d2, d3, m(d0), m(d1), m(d2), m(d3)] / s   at free node i
+#           d0 = x0 - h1 (the SPE step from the previous solution),
+#           d_k = h_k - h_{k+1} (k = 1..3; h1 the most recent solution),
+#           m(d) = mean of d over the free graph neighbours of i (self
+#           excluded), s = RMS of d0 over the free nodes
+#   direction  d = s o  (0 when s = 0)
+#   start      z0 = x0 + alpha d,  alpha = d.(R - M x0) / d.(M d)  (0 when d.Md = 0)
+#   target     (z - x0) / RMS(z - x0)   (the scale of d is immaterial to z0)
+#
+# with the same 8-32-32-1 network, loss and optimizer as above.  The inputs
+# are increments: the information is in how the solutions change, which is
+# small against the solutions themselves; fed raw, those inputs would ask
+# BF16 weights to cancel them to better than their 8-bit precision.  The
+# line search keeps a poor direction harmless: ||z0 - z||_M <= ||x0 - z||_M.
+def spe_increments(x0, H):
+    """[d0, d1, d2, d3] of the SPE-correction mode (H = [h1, h2, h3, h4])."""
+    return [x0 - H[0], H[0] - H[1], H[1] - H[2], H[2] - H[3]]
+
+
+def spe_features(A, x0, H):
+    """(n, 8) normalised inputs and s of the SPE-correction mode."""
+    D = spe_increments(x0, H)
+    s = float(np.sqrt(np.mean(D[0] * D[0])))
+    M = ring_means(A, D)
+    X = np.stack(D + M, axis=1)
+    return (X / s if s > 0 else X), s
+
+
+def spe_direction(theta, A, x0, H):
+    """d = s * MLP(x) (0 when s = 0)."""
+    X, s = spe_features(A, x0, H)
+    if s == 0.0:
+        return np.zeros_like(x0)
+    o, _ = forward(to_bf16(theta), X)
+    return s * o
+
+
+def spe_corrected_start(Mff, theta, A, x0, H, R):
+    """z0 = x0 + alpha d with the M-norm optimal alpha along the direction d."""
+    d = spe_direction(theta, A, x0, H)
+    Md = Mff @ d
+    den = float(d @ Md)
+    alpha = float(d @ (R - Mff @ x0)) / den if den > 0 else 0.0
+    return x0 + alpha * d, alpha
+
+
+def spe_target(z, x0):
+    """Normalised training target (z - x0) / RMS(z - x0) of one solve (0 when z = x0)."""
+    e = z - x0
+    r = float(np.sqrt(np.mean(e * e)))
+    return e / r if r > 0 else np.zeros_like(e)

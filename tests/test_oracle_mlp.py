@@ -91,3 +91,72 @@ def test_adam_first_step_is_signed_lr():
     g = rng.standard_normal(10)
     th1, m, v = mlp.adam_step(th, g, np.zeros(10), np.zeros(10), 1, lr=1e-3)
     np.testing.assert_allclose(th1, th - 1e-3 * np.sign(g), rtol=0, atol=1e-8)
+
+
+def test_adam_second_step_bias_correction():
+    """Hand-computed second Adam step (Kingma & Ba, Algorithm 1) of a scalar
+    with gradients g1 = 1, g2 = -1: m2 = 0.9*0.1 - 0.1 = -0.01, so the
+    bias-corrected m2 / (1 - 0.9^2) = -1/19; v2 = 0.999*0.001 + 0.001 =
+    0.001999 = 1 - 0.999^2, so the corrected v2 is 1.  The step is
+    +lr/19/(1 + eps).  With g2 = +1 both corrected moments are 1."""
+    lr, eps = 1e-3, 1e-8
+    th1, m, v = mlp.adam_step(np.array([0.5]), np.array([1.0]), np.zeros(1), np.zeros(1), 1, lr=lr, eps=eps)
+    th2, m2, v2 = mlp.adam_step(th1, np.array([-1.0]), m, v, 2, lr=lr, eps=eps)
+    assert m2[0] == pytest.approx(-0.01, rel=1e-14)
+    assert v2[0] == pytest.approx(0.001999, rel=1e-13)
+    assert th2[0] - th1[0] == pytest.approx(lr / 19.0 / (1.0 + eps), rel=1e-10)
+    th2b, _, _ = mlp.adam_step(th1, np.array([1.0]), m, v, 2, lr=lr, eps=eps)
+    assert th2b[0] - th1[0] == pytest.approx(-lr / (1.0 + eps), rel=1e-10)
+    # third step, g3 = 0: m3 = 0.9 m2, v3 = 0.999 v2; corrected with 1 - b^3
+    th3, _, _ = mlp.adam_step(th2, np.array([0.0]), m2, v2, 3, lr=lr, eps=eps)
+    mh = 0.9 * -0.01 / (1 - 0.9 ** 3)
+    vh = 0.999 * 0.001999 / (1 - 0.999 ** 3)
+    assert th3[0] - th2[0] == pytest.approx(-lr * mh / (math.sqrt(vh) + eps), rel=1e-10)
+
+
+def test_spe_correction_inputs_and_line_search():
+    """SPE-correction mode: inputs are increments (adding one vector to x0
+    and every h changes neither inputs nor scale), the 1-ring columns are
+    the means of the increment columns; the zero output layer gives no
+    direction and returns x0; the line search never increases the M-norm
+    error (any direction) and returns the solution exactly when the
+    direction is the error itself (alpha = 1 for d = z - x0, alpha = 1/2
+    for d = 2(z - x0))."""
+    p = ei.make_problem(4)
+    S = system.EQSSystem(p)
+    A = mlp.free_adjacency(p.tets, S.free, p.n_nodes)
+    rng = np.random.default_rng(6)
+    n = p.n_free
+    H = [np.sin(np.arange(n) * 0.1 + k) + 0.01 * rng.standard_normal(n) for k in range(4)]
+    x0 = H[0] + 0.02 * rng.standard_normal(n)
+    X, s = mlp.spe_features(A, x0, H)
+    assert s == pytest.approx(np.sqrt(np.mean((x0 - H[0]) ** 2)))
+    np.testing.assert_allclose(X[:, 0] * s, x0 - H[0], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(X[:, 3] * s, H[2] - H[3], rtol=0, atol=1e-15)
+    D = A.toarray()
+    i = 7
+    nb = np.nonzero(D[i])[0]
+    assert X[i, 5] * s == pytest.approx(np.mean(H[0][nb] - H[1][nb]))
+    off = 3.7 * np.cos(np.arange(n))
+    X2, s2 = mlp.spe_features(A, x0 + off, [h + off for h in H])
+    assert s2 == pytest.approx(s, rel=1e-12)
+    np.testing.assert_allclose(X2, X, rtol=0, atol=1e-9)
+    R = rng.standard_normal(n)
+    z = S.solve_direct(R)
+    z0, alpha = mlp.spe_corrected_start(S.Mff, ei.mlp_init(), A, x0, H, R)
+    assert alpha == 0.0 and np.array_equal(z0, x0)
+
+    def err_M(v):
+        e = v - z
+        return float(e @ (S.Mff @ e))
+
+    th = _theta(3)
+    z1, _ = mlp.spe_corrected_start(S.Mff, th, A, x0, H, R)
+    assert err_M(z1) <= err_M(x0) * (1 + 1e-12)
+    for scale, want in ((1.0, 1.0), (2.0, 0.5)):
+        d = scale * (z - x0)
+        alpha = float(d @ (R - S.Mff @ x0)) / float(d @ (S.Mff @ d))
+        assert alpha == pytest.approx(want, rel=1e-9)
+    T = mlp.spe_target(z, x0)
+    assert np.sqrt(np.mean(T * T)) == pytest.approx(1.0)
+    np.testing.assert_allclose(T * np.sqrt(np.mean((z - x0) ** 2)), z - x0, rtol=1e-12, atol=0)
