@@ -542,8 +542,8 @@ def kernel_bytes(eqs, kid, p, nnz0, nf):
     bytes) or per tet, node data once per node."""
     n = p.n_nodes
     cells = p.N ** 3 if p.tets.shape[1] == 4 else 0
-    if kid == eqs.EQS_KERNEL_ENS_SPE_GRAM:  # M (FP64) + newest x, W, b and 5 older columns, 4 doubles each
-        return 8 * nnz0 + 8 * 32 * nf
+    if kid == eqs.EQS_KERNEL_ENS_SPE_GRAM:  # M (hi, lo FP32), row sums (pair) + newest x, W, b and
+        return 8 * nnz0 + (8 + 8 * 32) * nf  # 5 older columns, 4 values of 8 B each
     if kid == eqs.EQS_KERNEL_ENS_ELEM:  # cells + coords (hi, lo) + potentials (4 hi/lo pairs) + y (float4 RMW)
         return 38 * cells + (32 + 32 + 32) * n
     if kid == eqs.EQS_KERNEL_ENS_PCG_PQ:  # M (hi, lo FP32) + z (float4) + p, q (double4, read + write)
@@ -557,7 +557,7 @@ def kernel_bytes(eqs, kid, p, nnz0, nf):
     raise ValueError(kid)
 
 
-KERNEL_NAMES = {16: "k4_spe_gram<6> (ensemble SPE Gram pass)", 17: "k4_elem32_cell (ensemble element kernel)",
+KERNEL_NAMES = {16: "k4_spe_gram_df<6> (ensemble SPE Gram pass, double-float)", 17: "k4_elem32_cell (ensemble element kernel)",
                 18: "k4_pcg_pq (ensemble CG operator pass, split M)", 0: "k_spe_gram<6> (SPE Gram pass)",
                 1: "k_elem32_cell (element kernel)", 2: "k_pcg_pq_split (CG operator pass, split M)"}
 
@@ -589,10 +589,18 @@ def kernel_roofline(torch, eqs, S, p, flush, kernels, step_ms, workload_key):
     return roof
 
 
+BATCH_SOLVER_CANDIDATES = (dict(cheb_degree=1, coarse_max=300), dict(cheb_degree=1, coarse_max=2500),
+                           dict(cheb_degree=2, coarse_max=300), dict(cheb_degree=2, coarse_max=2500))
+BATCH_ROWS_CANDIDATES = (256, 512, 1024, 2048)
+
+
 def run_batch(args, rank, world):
     """Batched serving: all instances advance together, one cooperative launch
-    per stage (rows per CTA autotuned); the same instances stepped one after
-    another with the single-instance graphs are measured beside it."""
+    per stage.  Solver options (smoother degree, coarsest-level size) are
+    tuned per size class, rows per CTA for the batched launch; the timed
+    batch starts every solve from the instance's SPE vector, the
+    previous-solution batch and the same instances stepped one after another
+    are measured beside it."""
     import torch
 
     import eqs_inputs as ei
@@ -607,41 +615,59 @@ def run_batch(args, rank, world):
         dist.init_process_group("nccl")
     s = 10
     probs = [ei.config_problem(4, instance=i) for i in range(64)]
+    base = dict(SOLVER_OPTS)
+    base.pop("cheb_degree")
+    base.pop("coarse_max")
+    classes, per_inst = autotune.tune_solver_by_class(
+        eqs, probs, [dict(base, fill_lanes=0, spe_n=6, **c) for c in BATCH_SOLVER_CANDIDATES], s=s,
+        guess=eqs.EQS_GUESS_SPE)
     # instances own a few CTAs each in the batched launch: lanes by row length only
-    solvers = [eqs.Solver(p, precision=eqs.EQS_PREC_MIXED, rtol=RTOL, fill_lanes=0, **SOLVER_OPTS)
-               for p in probs]
+    solvers = [eqs.Solver(p, precision=eqs.EQS_PREC_MIXED, rtol=RTOL, **o) for p, o in zip(probs, per_inst)]
+    for S in solvers:
+        eqs.eqs_set_guess(S.ctx, eqs.EQS_GUESS_SPE)
     nfree = sum(S.nf for S in solvers)
-    best, tuning = autotune.tune_batch(eqs, solvers, candidates=(256, 512, 1024, 2048), s=s, steps=2)
-    b = eqs.eqs_batch_create([S.ctx for S in solvers], best)
-    ctas, rows_used = eqs.eqs_batch_info(b)
-    dt = solvers[0].dt_bound(s)
-    xs = [torch.zeros(S.n, dtype=torch.float64, device="cuda") for S in solvers]
-    t = 0.0
-    for _ in range(args.warmup):
-        eqs.eqs_batch_rkc_step(b, xs, t, dt, s)
-        t += dt
+    best, tuning, separated = autotune.tune_batch(eqs, solvers, candidates=BATCH_ROWS_CANDIDATES, s=s, steps=2)
     flushbuf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    times, iters = [], 0
-    for _ in range(args.steps):
-        flushbuf.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        eqs.eqs_batch_rkc_step(b, xs, t, dt, s, want_stats=False)
-        e1.record()
-        st, _ = eqs.eqs_batch_get_stats(b, len(solvers))
-        times.append(e0.elapsed_time(e1))
-        iters += st.total_iters
-        t += dt
-    clocks = clk.stop()
-    launches = st.launches * args.steps
+    dt = solvers[0].dt_bound(s)
+
+    def timed_batch(steps, warmup, clk=None):
+        b = eqs.eqs_batch_create([S.ctx for S in solvers], best)
+        ctas, rows_used = eqs.eqs_batch_info(b)
+        xs = [torch.zeros(S.n, dtype=torch.float64, device="cuda") for S in solvers]
+        t = 0.0
+        for _ in range(warmup):
+            eqs.eqs_batch_rkc_step(b, xs, t, dt, s)
+            t += dt
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if clk else None
+        times, iters = [], 0
+        for _ in range(steps):
+            flushbuf.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            eqs.eqs_batch_rkc_step(b, xs, t, dt, s, want_stats=False)
+            e1.record()
+            st, _ = eqs.eqs_batch_get_stats(b, len(solvers))
+            times.append(e0.elapsed_time(e1))
+            iters += st.total_iters
+            t += dt
+        clocks = sampler.stop() if sampler else None
+        eqs.eqs_batch_destroy(b)
+        return times, iters, st.launches * steps, ctas, rows_used, clocks
+
+    times, iters, launches, ctas, rows_used, clocks = timed_batch(args.steps, args.warmup, clk=True)
     total_ms = max_over_ranks(sum(times), dist)
     value = job_throughput(nfree * s * args.steps, world, total_ms)
-    # the same instances one after another (single-instance step graphs)
+    # the previous-solution batch (same contexts, same tuned options)
+    for S in solvers:
+        eqs.eqs_set_guess(S.ctx, eqs.EQS_GUESS_PREV)
+    short = max(3, args.steps // 4)
+    ptimes, piters, _, _, _, _ = timed_batch(short, 2)
+    # the same instances one after another (single-instance step graphs, SPE)
+    for S in solvers:
+        eqs.eqs_set_guess(S.ctx, eqs.EQS_GUESS_SPE)
     xsolo = [torch.zeros(S.n, dtype=torch.float64, device="cuda") for S in solvers]
-    ts = 0.0
     for S, x in zip(solvers, xsolo):
         S.step(x, 0.0, dt, s)
     torch.cuda.synchronize()
@@ -661,15 +687,23 @@ def run_batch(args, rank, world):
         "dtype": "f32/f64 mixed", "data": "synthetic",
         "config": {"workload": WORKLOAD, "instances": len(solvers), "n_free_total": nfree,
                    "stages": s, "rtol": RTOL, "rows_per_block": rows_used, "ctas": ctas,
-                   "autotune_ms_per_step": {str(k): v[0] for k, v in tuning.items()},
+                   "start_vector": "SPE (six solutions per instance, Gram pass inside the instance's CTA group)",
+                   "autotune_rows_per_block": {str(k): {"ms_median": v[0], "ms_spread": v[1], "ctas": v[2]}
+                                               for k, v in tuning.items()},
+                   "autotune_rows_separated": separated,
+                   "autotune_solver_by_class": [
+                       {"instances": len(c), "N": [probs[i].N for i in c][:3] + ["..."], "best": o,
+                        "ms_median": m, "ms_spread": sp} for c, o, m, sp in classes],
                    "cg_iters_per_solve": iters / (args.steps * s * len(solvers)),
                    "l2": "flushed between timed steps (256 MiB write)"},
+        "forms": {"batched_previous_solution": {
+            "value": nfree * s * len(ptimes) / (sum(ptimes) / 1e3), "ms_per_step": sum(ptimes) / len(ptimes),
+            "cg_iters_per_solve": piters / (len(ptimes) * s * len(solvers))}},
         "sequential_single_instance": {"value": seq_value, "unit": "DOF-stages/s"},
         "gpu_launches": int(launches), "clocks": clocks,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    eqs.eqs_batch_destroy(b)
     for S in solvers:
         S.close()
     if dist is not None:
@@ -769,6 +803,32 @@ def time_single(torch, eqs, p, make, flush, prec, guess, steps, warmup=2, theta=
            "steps": steps}
     if guess == eqs.EQS_GUESS_MLP:
         out["learned_guess_kept"] = kept / (steps * S_STAGES)
+    return out
+
+
+def measure_spe_mlp(torch, eqs, p, make, flush, steps, n_rec=6, iters=1000):
+    """The learned correction of the SPE start (EQS_GUESS_SPE_MLP): record
+    n_rec mixed-precision SPE steps, train the network on the GPU, then time
+    single-trajectory steps with the corrected start (network direction,
+    M-norm line search) from the recorded state."""
+    import eqs_inputs as ei
+
+    R = make(eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_SPE, ei.mlp_init())
+    eqs.eqs_guess_record(R.ctx, n_rec * S_STAGES)
+    dt = R.dt_bound(S_STAGES)
+    x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+    for k in range(n_rec):
+        R.step(x, k * dt, dt, S_STAGES)
+    eqs.eqs_set_guess(R.ctx, eqs.EQS_GUESS_SPE_MLP)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lf, ll = eqs.eqs_guess_train(R.ctx, iters, 8192, 2e-3, 1612094470)
+    train_s = time.perf_counter() - t0
+    theta = eqs.eqs_guess_get_params(R.ctx)
+    R.close()
+    out = time_single(torch, eqs, p, make, flush, eqs.EQS_PREC_MIXED, eqs.EQS_GUESS_SPE_MLP, steps, theta=theta)
+    out.update(train_s=train_s, loss_first=lf, loss_last=ll, recorded_steps=n_rec,
+               note="starts from phi = 0 after training (the other forms likewise start from 0)")
     return out
 
 
@@ -878,6 +938,7 @@ def run_ensemble_headline(args, rank, world):
             forms[name] = time_single(torch, eqs, p, make, flush, prec, guess, short)
         forms["ensemble_vs_fp64_plain_per_trajectory_step"] = (
             forms["fp64_plain"]["ms_per_step"] / (ms_step / 4))
+        forms["single_mixed_spe_mlp"] = measure_spe_mlp(torch, eqs, p, make, flush, short)
     cpu = None
     if cpu_proc is not None:
         cpu = cpu_baseline_entry(oracle_collect(cpu_proc))

@@ -76,10 +76,13 @@ typedef enum {
                          solutions are the snapshots, their leading pod_m
                          POD modes span the projection of Eq. 5, computed
                          once; earlier solves start from the previous one  */
-  EQS_GUESS_POD2 = 5  /* rolling POD-MOR (Sec. IV, "MOR2"): a solution whose
+  EQS_GUESS_POD2 = 5, /* rolling POD-MOR (Sec. IV, "MOR2"): a solution whose
                          solve took more than pod_min_iters iterations
                          replaces the oldest of pod_k snapshots and the
                          basis is recomputed                                */
+  EQS_GUESS_SPE_MLP = 6 /* the SPE start x0 corrected along the learned
+                         network's direction by an M-norm line search (its
+                         second mode, inputs: solution increments)          */
 } eqs_guess_mode;
 
 /* Options of eqs_amg_setup (fill with eqs_opts_default). */
@@ -158,7 +161,7 @@ typedef struct {
                                    nodes outside loops + loop-body kernel
                                    nodes x CG iterations)                    */
   int guess_kept;               /* solves that started from the learned guess
-                                   (EQS_GUESS_MLP; else 0)                   */
+                                   (EQS_GUESS_MLP, EQS_GUESS_SPE_MLP; else 0) */
 } eqs_step_stats;
 
 /* Fill *o with the defaults (precision FP64, theta 0.08, coarse_max 500,
@@ -322,7 +325,9 @@ eqs_status eqs_amg_aggregates(const eqs_ctx* ctx, int level, int32_t* agg_out);
  * and their means over the free mesh neighbours, divided by the RMS s_h of
  * h1; network 8 -> 32 -> 32 -> 1 with exact-erf GELU, BF16 weights, FP32
  * accumulation; start vector z0 = h1 + s_h * output.  In EQS_GUESS_MLP mode
- * each solve starts from z0 unless ||R - M h1|| < ||R - M z0||. */
+ * each solve starts from z0 unless ||R - M h1|| < ||R - M z0||.  Its second
+ * mode (EQS_GUESS_SPE_MLP, eqs_guess_eval_spe) corrects the SPE start x0
+ * along the network's direction instead. */
 
 /* Select the start vector of the stage solves (an eqs_guess_mode value). */
 eqs_status eqs_set_guess(eqs_ctx* ctx, int mode);
@@ -334,8 +339,9 @@ eqs_status eqs_guess_set_params(eqs_ctx* ctx, const float* theta, int n);
 eqs_status eqs_guess_get_params(eqs_ctx* ctx, float* theta, int n);
 
 /* Record the next `capacity` stage solutions of eqs_rkc_step (device, FP32)
- * as training data; 0 stops recording and frees the record.  Restarts the
- * solution history. */
+ * as training data, with steps in an SPE mode also each solution's distance
+ * z - x0 from its SPE start; 0 stops recording and frees the record.
+ * Restarts the solution history. */
 eqs_status eqs_guess_record(eqs_ctx* ctx, int64_t capacity);
 
 /* Train on the recorded solutions: `iters` Adam steps (learning rate lr) on
@@ -350,6 +356,30 @@ eqs_status eqs_guess_train(eqs_ctx* ctx, int iters, int batch, float lr, uint64_
  * 1377), loss (host, nullable).  For checking the training kernel. */
 eqs_status eqs_guess_grad(eqs_ctx* ctx, const float* X, const float* T, int B, float* grad,
                           float* loss);
+
+/* n_batches Adam steps (Kingma & Ba; FP32 master weights, BF16 copies for
+ * the forward and backward passes) on given mini-batches: X (host,
+ * n_batches x B x 8 normalised inputs), T (host, n_batches x B targets),
+ * with the training and update kernels of eqs_guess_train.  The Adam step
+ * counter continues from earlier training (eqs_guess_set_params resets it).
+ * losses (host, n_batches floats, nullable): the loss of each mini-batch
+ * before its update.  For checking the training loop against a reference. */
+eqs_status eqs_guess_train_batches(eqs_ctx* ctx, const float* X, const float* T, int B, int n_batches,
+                                   float lr, float* losses);
+
+/* The start of the network's SPE-correction mode (EQS_GUESS_SPE_MLP): the
+ * network, fed the increments x0 - h1, h1 - h2, h2 - h3, h3 - h4 at the node
+ * and their 1-ring means divided by s = RMS(x0 - h1), gives a direction
+ * d = s * output; the start is z0 = x0 + alpha d with the step that
+ * minimises the M-norm error along d, alpha = d.(R - M x0) / d.(M d)
+ * (0 when d.Md = 0), so z0 is never further from the solution in the
+ * M-norm than x0.  x0 (device, n_free doubles: the SPE start), H (device,
+ * 4 x n_free doubles: h1 first), R (device, n_free: the right-hand side),
+ * z0 (device, n_free doubles).  In EQS_GUESS_SPE_MLP mode eqs_guess_train
+ * trains this mode on steps recorded with EQS_GUESS_SPE or
+ * EQS_GUESS_SPE_MLP (target (z - x0)/RMS(z - x0); EQS_ERR_STATE
+ * otherwise).  Synchronises. */
+eqs_status eqs_guess_eval_spe(eqs_ctx* ctx, const double* x0, const double* H, const double* R, double* z0);
 
 /* z0 of the network for the history H (device, 4 x n_free doubles: h1 first)
  * into z0 (device, n_free doubles); synchronises. */
@@ -400,6 +430,15 @@ eqs_status eqs_ens_get_step_stats(eqs_ctx* ctx, eqs_ens_stats* stats);
  * Synchronises; EQS_ERR_NOCONV if a column hit max_iter. */
 eqs_status eqs_ens_solve_M(eqs_ctx* ctx, const double* rhs, double* z, int* iters_out);
 
+/* SPE start vectors of the four columns (Sec. IV, Eq. 4-5) from a given
+ * history, as the ensemble step forms them: X (device, 6 x 4 x n_free
+ * doubles; solution k of column c at X + (4 k + c) n_free, k = 0 the most
+ * recent), b (device, 4 x n_free: the right-hand sides).  x0 (device,
+ * 4 x n_free) receives the start vectors, r0 (device, 4 x n_free) the start
+ * residuals b - W y as the CG starts from them (W = M X from the Gram pass,
+ * no further product with M).  Synchronises.  For checking the pass. */
+eqs_status eqs_ens_spe_eval(eqs_ctx* ctx, const double* X, const double* b, double* x0, double* r0);
+
 /* ---- One kernel of the step, launched alone (measurement).
  * Enqueues ONE launch of the named kernel of the last step
  * (eqs_rkc_step, or eqs_ens_rkc_step for the EQS_KERNEL_ENS_* ids) on the
@@ -412,7 +451,9 @@ eqs_status eqs_ens_solve_M(eqs_ctx* ctx, const double* rhs, double* z, int* iter
  *   ELEM:     the element kernel of Sec. III on the last stage state, its
  *             K(x)x scattered into a private buffer of the context
  *             (allocated on the first such call);
- *   PCG_PQ:   the CG operator pass q = M z + beta q of Sec. IV.
+ *   PCG_PQ:   the CG operator pass q = M z + beta q of Sec. IV (for the
+ *             ensemble with all four columns active: their convergence
+ *             flags are cleared first, one small memset on the stream).
  * The Gram pass recomputes the last solve's column (same values); the CG
  * pass overwrites CG vectors that the next solve re-initialises.  So a
  * later step is unaffected, but the call must not overlap a step.
@@ -446,6 +487,19 @@ typedef struct {
 } eqs_batch_stats;
 
 eqs_status eqs_batch_create(eqs_ctx* const* ctxs, int n, int rows_per_block, eqs_batch** out);
+
+/* When every context selects EQS_GUESS_SPE, each batched solve starts from
+ * the SPE vector of its instance (Sec. IV, Eq. 4-5, six solutions; the
+ * Gram pass and the small solve run inside the instance's CTA group, on
+ * the context's solution ring, so a context must not step on its own
+ * between batched steps); otherwise from the previous solution.
+ *
+ * Wait budget of every group barrier of the batched launches, in polls
+ * (0: the default, 2^22); a wait that runs out sets the instance's error
+ * flag, every CTA of the group returns, and the step reports
+ * EQS_ERR_TIMEOUT (x of that step is then undefined).  Takes effect from
+ * the next step. */
+eqs_status eqs_batch_set_barrier_polls(eqs_batch* b, long long polls);
 
 /* One RKC step of s stages for every instance: x is a host array of n
  * device pointers (instance k: n_nodes of ctx k doubles, mesh order, in x(t),

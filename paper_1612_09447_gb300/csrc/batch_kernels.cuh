@@ -8,8 +8,11 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "spe_kernels.cuh"
 
 namespace eqs {
+
+constexpr int kBatchSpe = 6;  // SPE history of a batched instance (2 x 6 sums in the group's 16 slots)
 
 struct BatchInst {
   const PPlan<float>* plan;
@@ -34,6 +37,11 @@ struct BatchInst {
   double* relres;
   int* zero;
   double V0, w, phase;
+  // SPE start vectors (Sec. IV, Eq. 4-5; null X: previous solution): the
+  // instance context's solution ring, Gram matrix and coefficients
+  double* X;
+  double* G;
+  double* coef;
 };
 
 __device__ __forceinline__ double* bY(const BatchInst& I, int j) { return j == 0 ? I.Y[0] : I.Y[1 + (j - 1) % 3]; }
@@ -44,11 +52,16 @@ __device__ __forceinline__ float2 split2d(double v) {
   return make_float2(h, (float)(v - (double)h));
 }
 
-// g(t_j), g'(t_j) of every instance at the stage times t + c_j dt.
+// g(t_j), g'(t_j) of every instance at the stage times t + c_j dt; the
+// solve counter (count[0]: solves before this step, count[1]: after it).
 __global__ void k_batch_drive(int ninst, int s1, const BatchInst* __restrict__ insts,
                               const double* __restrict__ cj, const StepParams* prm, double* gtab,
-                              double* gptab) {
+                              double* gptab, long long* count) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) {
+    count[0] = count[1];
+    count[1] += s1 - 1;
+  }
   if (k >= ninst * s1) return;
   const int b = k / s1, j = k % s1;
   const BatchInst& I = insts[b];
@@ -58,7 +71,7 @@ __global__ void k_batch_drive(int ninst, int s1, const BatchInst* __restrict__ i
 }
 
 __device__ __forceinline__ GridCtx batch_group(const BatchInst* insts, const int* blk2inst,
-                                               const int* first, const int* nblk, int& b) {
+                                               const int* first, const int* nblk, long long max_spins, int& b) {
   b = blk2inst[blockIdx.x];
   GridCtx g;
   g.rank = blockIdx.x - first[b];
@@ -67,8 +80,63 @@ __device__ __forceinline__ GridCtx batch_group(const BatchInst* insts, const int
   g.stride = (int64_t)g.nblocks * blockDim.x;
   g.bar = insts[b].bar;
   g.partials = insts[b].partials;
-  g.max_spins = kMaxSpins;
+  g.max_spins = max_spins;
   return g;
+}
+
+// SPE start of solve g of instance I inside its CTA group: the newest
+// solution (in x, the solve's start buffer) enters ring slot g - 1, then
+// w = M x_new, the Gram column x_k . w and the projections x_k . R are
+// reduced over the group, one thread updates G and solves for the
+// coefficients (spe_solve, as the single-instance pass), and every row gets
+// x0 = X y.  False when a group barrier gave up.
+__device__ bool batch_spe_start(const BatchInst& I, const GridCtx& g, long long gi, double* __restrict__ x) {
+  constexpr int NH = kBatchSpe;
+  const int nf = I.nf;
+  const DevSell<double>& M = I.plan->M;
+  if (gi == 0) return true;  // no history: the previous solution stays the start
+  const int m = (int)(gi < NH ? gi : NH);
+  const int sn = spe_slot(gi - 1, NH);
+  double* __restrict__ xn = I.X + (size_t)sn * nf;
+  for (int64_t i = g.tid; i < nf; i += g.stride) xn[i] = x[i];
+  double v[2 * NH];
+#pragma unroll
+  for (int k = 0; k < 2 * NH; ++k) v[k] = 0.0;
+  for (int64_t i = g.tid; i < nf; i += g.stride) {
+    const double w = mat_row<double>(M, i, nf, x);
+    const double bi = I.R[i];
+#pragma unroll
+    for (int k = 0; k < NH; ++k) {
+      const double xk = k < m ? I.X[(size_t)spe_slot(gi - 1 - k, NH) * nf + i] : 0.0;
+      v[k] = fma(xk, w, v[k]);
+      v[NH + k] = fma(xk, bi, v[NH + k]);
+    }
+  }
+  put_partials<2 * NH>(v, g.partials, 0, g.nblocks, g.rank);
+  if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return false;
+  __shared__ double stot[2 * NH];
+  if (g.rank == 0) {
+#pragma unroll
+    for (int k = 0; k < 2 * NH; ++k) {
+      const double t = get_total(g.partials, k, g.nblocks);
+      if (threadIdx.x == 0) stot[k] = t;
+    }
+    if (threadIdx.x == 0) spe_solve<NH>(stot, gi, m, sn, I.G, 1e-12, I.coef);
+  }
+  if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return false;
+  const int mu = reinterpret_cast<const int*>(I.coef + kSpeMax)[0];
+  double y[NH];
+#pragma unroll
+  for (int k = 0; k < NH; ++k) y[k] = k < mu ? __ldcg(I.coef + spe_slot(gi - 1 - k, NH)) : 0.0;
+  if (mu > 0)
+    for (int64_t i = g.tid; i < nf; i += g.stride) {
+      double xi = 0.0;
+#pragma unroll
+      for (int k = 0; k < NH; ++k)
+        if (k < mu) xi = fma(y[k], I.X[(size_t)spe_slot(gi - 1 - k, NH) * nf + i], xi);
+      x[i] = xi;
+    }
+  return grid_barrier(g.bar, g.nblocks, g.max_spins);
 }
 
 // Stage vector Y_j of instance I: gather (j = 0) or recurrence (j >= 1), the
@@ -106,9 +174,9 @@ __global__ void __launch_bounds__(kPBlock) k_batch_stage(
     const BatchInst* __restrict__ insts, const int* __restrict__ blk2inst, const int* __restrict__ first,
     const int* __restrict__ nblk, int j, int s, double c0, double mu, double nu, double mut, double gt,
     const StepParams* prm, const double* __restrict__ gtab, const double* __restrict__ gptab,
-    double* const* __restrict__ xmesh, double tol2) {
+    double* const* __restrict__ xmesh, double tol2, const long long* __restrict__ count, long long max_spins) {
   int b;
-  const GridCtx g = batch_group(insts, blk2inst, first, nblk, b);
+  const GridCtx g = batch_group(insts, blk2inst, first, nblk, max_spins, b);
   const BatchInst& I = insts[b];
   const double gj = gtab[b * (s + 1) + j], gpj = gptab[b * (s + 1) + j];
   batch_stage_vector(I, g, j, s, c0, mu, nu, mut, gt, prm->dt, gj, xmesh[b], nullptr);
@@ -121,6 +189,7 @@ __global__ void __launch_bounds__(kPBlock) k_batch_stage(
     I.y32[i] = 0.0f;
   }
   if (!grid_barrier(g.bar, g.nblocks, g.max_spins)) return;
+  if (I.X && !batch_spe_start(I, g, count[0] + j, bF(I, j))) return;
   pcg_group_solve(*I.plan, g, I.R, bF(I, j), tol2, I.iters + j, I.relres + j, I.zero + j);
 }
 
@@ -130,7 +199,7 @@ __global__ void k_batch_final(const BatchInst* __restrict__ insts, const int* __
                               double mu, double nu, double mut, double gt, const StepParams* prm,
                               const double* __restrict__ gtab, double* const* __restrict__ xmesh) {
   int b;
-  const GridCtx g = batch_group(insts, blk2inst, first, nblk, b);
+  const GridCtx g = batch_group(insts, blk2inst, first, nblk, kMaxSpins, b);
   const BatchInst& I = insts[b];
   batch_stage_vector(I, g, s, s, c0, mu, nu, mut, gt, prm->dt, gtab[b * (s + 1) + s], xmesh[b], xmesh[b]);
 }

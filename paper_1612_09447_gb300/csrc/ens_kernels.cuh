@@ -744,14 +744,76 @@ __global__ void k4_pcg_update(int n, double4_32a* __restrict__ x, double4_32a* _
 // all four columns (row-interleaved) and W = M X; column c has its own Gram
 // matrix G[c] and coefficients.  One pass: w = M x_newest (four columns per
 // matrix entry), the Gram column and c_k = x_k . b of every column; the last
-// block solves the four small systems.  coef: per column kSpeMax + 1 doubles
-// (coefficients by slot, then the slots in use).
+// block solves the four small systems (k4_spe_gram_df below).  coef: per
+// column kSpeMax + 1 doubles (coefficients by slot, then the slots in use).
+// Double-float (FP32 pair) arithmetic on the FP32 pipe (Dekker's exact
+// product by FMA and Knuth's two-sum): S + s += (ah + al)(zh + zl), the
+// al zl term (below 2^-48 of the product) dropped; the pair keeps about 44
+// bits of the running sum.
+__device__ __forceinline__ void df_acc2(float& S, float& s, float ah, float al, float zh, float zl) {
+  const float p = __fmul_rn(ah, zh);
+  float t = __fmaf_rn(ah, zh, -p);  // ah zh = p + t exactly
+  t = __fmaf_rn(al, zh, t);
+  t = __fmaf_rn(ah, zl, t);
+  const float S1 = __fadd_rn(S, p);
+  const float bv = __fsub_rn(S1, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(S1, bv)), __fsub_rn(p, bv));  // S + p = S1 + err
+  S = S1;
+  s = __fadd_rn(s, __fadd_rn(err, t));
+}
+
+// a - b = d + err exactly (two-sum of a and -b).
+__device__ __forceinline__ float two_diff(float a, float b, float& err) {
+  const float d = __fsub_rn(a, b);
+  const float bb = __fsub_rn(d, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(d, bb)), __fsub_rn(-b, bb));
+  return d;
+}
+
+// S + s += (ah + al)((zh + zl) - (xh + xl)): a matrix entry times the
+// difference of two pair values, the difference formed without rounding
+// of its leading part.
+__device__ __forceinline__ void df_acc_diff(float& S, float& s, float ah, float al, float zh, float zl, float xh,
+                                            float xl) {
+  float err;
+  const float dh = two_diff(zh, xh, err);
+  const float dl = __fadd_rn(__fsub_rn(zl, xl), err);
+  df_acc2(S, s, ah, al, dh, dl);
+}
+
+// Renormalised pair (hi, lo) of S + s.
+__device__ __forceinline__ float2 df_norm(float S, float s) {
+  const float h = __fadd_rn(S, s);
+  return make_float2(h, __fsub_rn(s, __fsub_rn(h, S)));
+}
+
+// The SPE Gram pass of the four columns in double-float on the FP32 pipe
+// (GB300 runs FP64 at about 1/64 of the FP32 rate, which bound an FP64 pass
+// at 0.15 of HBM bandwidth).  Two threads per row, thread h taking columns
+// 2h and 2h+1, whose (hi, lo) pairs are float4 h of the row in the pair
+// layout (store_split4):
+//   W_new = M x_new with M as two FP32 parts (Mhi + Mlo) and x_new from the
+//           pair ring X2, in difference form
+//             (M x)_i = sum_j m_ij (x_j - x_i) + r_i x_i,
+//           r_i the row sum of the split M (rs, formed in FP64 at setup):
+//           M is Laplace-type, so sum_j m_ij x_j cancels to a small part of
+//           sum_j |m_ij x_j| for a smooth x, while the differences carry no
+//           such cancellation -- the pair arithmetic (about 2^-45 of the sum
+//           of magnitudes) then gives W to FP64-class accuracy; stored in
+//           FP64 into the ring W;
+//   c_k = x_k . W_new and d_k = x_k . b with x_k from X2, b from the pair
+//           copy b2 of the right-hand side;
+// the sums are widened to FP64, added over the lanes of one parity within a
+// warp, then over warps and blocks; the last block runs the four small
+// solves.  (Four threads per row, one column each, measured slower: the
+// matrix and index work repeats per thread.)
 template <int NH>
-__global__ void k4_spe_gram(DevSell<double> M, int nf, const double4_32a* __restrict__ X,
-                            double4_32a* __restrict__ W, const double4_32a* __restrict__ b,
-                            const long long* __restrict__ stepcount, int s, int j, double* __restrict__ G,
-                            double* partials, unsigned int* counter, int max_blocks, double drop2,
-                            double* __restrict__ coef) {
+__global__ void __launch_bounds__(kBlock, 2)
+k4_spe_gram_df(DevSell<double> M, const float* __restrict__ Mhi, const float* __restrict__ Mlo,
+               const float2* __restrict__ rs, int nf, const float4* __restrict__ X2, double4_32a* __restrict__ W,
+               const float4* __restrict__ b2, const long long* __restrict__ stepcount, int s, int j,
+               double* __restrict__ G, double* partials, unsigned int* counter, int max_blocks, double drop2,
+               double* __restrict__ coef) {
   pdl_enter();
   const long long g = stepcount[0] + j;
   if (g == 0) {
@@ -761,41 +823,125 @@ __global__ void k4_spe_gram(DevSell<double> M, int nf, const double4_32a* __rest
   }
   const int m = (int)(g < NH ? g : NH);
   const int sn = spe_slot(g - 1, NH);
-  constexpr int NS = 2 * NH * kEnsW;  // per column: Gram column (NH), projections (NH)
-  double v[NS];
+  const int h = threadIdx.x & 1;  // column pair of this thread
+  constexpr int NP = 2 * NH * 2;  // per column of the pair: Gram column (NH), projections (NH)
+  float S[NP], e[NP];
 #pragma unroll
-  for (int k = 0; k < NS; ++k) v[k] = 0.0;
-  const double4_32a* xs[NH];
+  for (int k = 0; k < NP; ++k) S[k] = e[k] = 0.f;
+  const float4* xs[NH];
 #pragma unroll
-  for (int k = 0; k < NH; ++k) xs[k] = X + (size_t)spe_slot(g - 1 - k, NH) * nf;
-  const double4_32a* __restrict__ xn = X + (size_t)sn * nf;
-  double4_32a* __restrict__ wn = W + (size_t)sn * nf;
-  for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x) {
-    const double4_32a w = mat_row_d4(M, i, nf, xn);
-    wn[i] = w;
-    const double4_32a bi = b[i];
+  for (int k = 0; k < NH; ++k) xs[k] = X2 + (size_t)spe_slot(g - 1 - k, NH) * 2 * nf;
+  const float4* __restrict__ xn = X2 + (size_t)sn * 2 * nf;
+  double* __restrict__ wn = reinterpret_cast<double*>(W + (size_t)sn * nf);
+  const int64_t n2 = 2 * (int64_t)nf;
+  for (int64_t u = gtid(); u < n2; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = u >> 1;
+    const float4 xi = __ldg(xn + u);
+    const float2 ri = __ldg(rs + i);
+    float A0 = 0.f, a0 = 0.f, A1 = 0.f, a1 = 0.f;  // (M x_new) of the two columns, as pairs
+    df_acc2(A0, a0, ri.x, ri.y, xi.x, xi.y);
+    df_acc2(A1, a1, ri.x, ri.y, xi.z, xi.w);
+    if (M.G == 0) {
+      constexpr int C = kDiaChunk / 2;
+      for (int d0 = 0; d0 < M.ndiag; d0 += C) {
+        float mh[C], ml[C];
+        float4 xx[C];
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+          const int d = d0 + q;
+          const int jj = (int)i + M.off[d < kMaxDiag ? d : 0];
+          const bool ok = d < M.ndiag && (unsigned)jj < (unsigned)M.n_cols;
+          const int64_t k = (int64_t)d * nf + i;
+          mh[q] = ok ? __ldg(Mhi + k) : 0.f;
+          ml[q] = ok ? __ldg(Mlo + k) : 0.f;
+          xx[q] = ok ? __ldg(xn + 2 * (int64_t)jj + h) : xi;  // outside: a zero difference
+        }
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+          df_acc_diff(A0, a0, mh[q], ml[q], xx[q].x, xx[q].y, xi.x, xi.y);
+          df_acc_diff(A1, a1, mh[q], ml[q], xx[q].z, xx[q].w, xi.z, xi.w);
+        }
+      }
+    } else {
+      const int64_t sl = i >> 5, lane = i & 31;
+      const int64_t end = M.slice_ptr[sl + 1];
+      for (int64_t k = M.slice_ptr[sl] + lane; k < end; k += 32) {
+        const float mh = __ldg(Mhi + k), ml = __ldg(Mlo + k);
+        const float4 xj = __ldg(xn + 2 * (int64_t)__ldg(M.col + k) + h);
+        df_acc_diff(A0, a0, mh, ml, xj.x, xj.y, xi.x, xi.y);
+        df_acc_diff(A1, a1, mh, ml, xj.z, xj.w, xi.z, xi.w);
+      }
+    }
+    const float2 w0 = df_norm(A0, a0), w1 = df_norm(A1, a1);
+    *reinterpret_cast<double2*>(wn + 4 * i + 2 * h) =
+        make_double2((double)w0.x + (double)w0.y, (double)w1.x + (double)w1.y);
+    const float4 bi = __ldg(b2 + u);
 #pragma unroll
     for (int k = 0; k < NH; ++k) {
       if (k >= m) break;
-      const double4_32a xk = xs[k][i];
-#pragma unroll
-      for (int c = 0; c < kEnsW; ++c) {
-        v[c * 2 * NH + k] = fma(dc4(xk, c), dc4(w, c), v[c * 2 * NH + k]);
-        v[c * 2 * NH + NH + k] = fma(dc4(xk, c), dc4(bi, c), v[c * 2 * NH + NH + k]);
-      }
+      const float4 xk = __ldg(xs[k] + u);
+      df_acc2(S[k], e[k], xk.x, xk.y, w0.x, w0.y);
+      df_acc2(S[NH + k], e[NH + k], xk.x, xk.y, bi.x, bi.y);
+      df_acc2(S[2 * NH + k], e[2 * NH + k], xk.z, xk.w, w1.x, w1.y);
+      df_acc2(S[3 * NH + k], e[3 * NH + k], xk.z, xk.w, bi.z, bi.w);
     }
   }
-  double tot[NS];
+  // Sums widened to FP64, slot h NP + k (column c at c 2 NH: NH Gram entries,
+  // then NH projections): lanes of one parity add over the warp, then the
+  // warps of the block in shared memory, one partial per slot and block.
+  constexpr int NS = 2 * NH * kEnsW;
+  __shared__ double wsum[kBlock / 32][NS];
   __shared__ double stot[NS];
-  if (grid_sum<NS>(v, partials, counter, max_blocks, tot)) {  // the last block: the four small solves
-    if (threadIdx.x == 0)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-      for (int k = 0; k < NS; ++k) stot[k] = tot[k];
-    __syncthreads();
-    const int c = threadIdx.x;  // one thread per column, side by side
-    if (c < kEnsW)
-      spe_solve<NH>(stot + c * 2 * NH, g, m, sn, G + c * kSpeMax * kSpeMax, drop2, coef + c * (kSpeMax + 1));
+  for (int k = 0; k < NP; ++k) {
+    double t = (double)S[k] + (double)e[k];
+#pragma unroll
+    for (int o = 16; o >= 2; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane < 2) wsum[warp][lane * NP + k] = t;
   }
+  __syncthreads();
+  if (threadIdx.x < NS) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w][threadIdx.x];
+    partials[threadIdx.x * max_blocks + blockIdx.x] = t;
+    __threadfence();  // every writer publishes its partial before the ticket
+  }
+  __syncthreads();
+  if (!grid_ticket(counter)) return;
+  __threadfence();
+  if (threadIdx.x < NS) {  // the last block: totals per slot, then the four small solves
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(partials + threadIdx.x * max_blocks + b);
+    stot[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0u;
+  if (threadIdx.x < kEnsW)
+    spe_solve<NH>(stot + threadIdx.x * 2 * NH, g, m, sn, G + threadIdx.x * kSpeMax * kSpeMax, drop2,
+                  coef + threadIdx.x * (kSpeMax + 1));
+}
+
+// Row sums of the split M (hi + lo) in FP64, kept as FP32 pairs: the r_i of
+// the difference-form products (one thread per row; setup).
+__global__ void k_rowsum_split(DevSell<double> M, const float* __restrict__ Mhi, const float* __restrict__ Mlo,
+                               int n, float2* __restrict__ rs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double t = 0.0;
+  if (M.G == 0) {
+    for (int d = 0; d < M.ndiag; ++d) {
+      const int j = (int)i + M.off[d];
+      if ((unsigned)j >= (unsigned)M.n_cols) continue;
+      const int64_t k = (int64_t)d * n + i;
+      t += (double)Mhi[k] + (double)Mlo[k];
+    }
+  } else {
+    const int64_t sl = i >> 5, lane = i & 31;
+    for (int64_t k = M.slice_ptr[sl] + lane; k < M.slice_ptr[sl + 1]; k += 32) t += (double)Mhi[k] + (double)Mlo[k];
+  }
+  const float h = (float)t;
+  rs[i] = make_float2(h, (float)(t - (double)h));
 }
 
 // CG start of the four columns from their SPE vectors: x0 = X a_c,
@@ -925,68 +1071,61 @@ __global__ void k4_elem32(int64_t nt, const int4* __restrict__ conn, const uint8
 // K(x)x for four columns on Kuhn cells (as k_elem32_cell): the cell's
 // corners, coordinates and four potentials loaded once, the six tets'
 // residuals summed per corner, one 16-byte atomic add per corner.
-template <int A, int B, int C, int D>
-__device__ __forceinline__ void cell_tet32x4(const float4 (&h)[8], const float4 (&l)[8], const float4 (&ya)[8],
-                                             const float4 (&yb)[8], const MaterialDev& m, float4 (&acc)[8]) {
-  float e[3][3];
-  e[0][0] = (h[B].x - h[A].x) + (l[B].x - l[A].x);
-  e[0][1] = (h[B].y - h[A].y) + (l[B].y - l[A].y);
-  e[0][2] = (h[B].z - h[A].z) + (l[B].z - l[A].z);
-  e[1][0] = (h[C].x - h[A].x) + (l[C].x - l[A].x);
-  e[1][1] = (h[C].y - h[A].y) + (l[C].y - l[A].y);
-  e[1][2] = (h[C].z - h[A].z) + (l[C].z - l[A].z);
-  e[2][0] = (h[D].x - h[A].x) + (l[D].x - l[A].x);
-  e[2][1] = (h[D].y - h[A].y) + (l[D].y - l[A].y);
-  e[2][2] = (h[D].z - h[A].z) + (l[D].z - l[A].z);
+template <int B, int C, int D>
+__device__ __forceinline__ void cell_tet32x4(const float (&dx)[8][3], const float4 (&dp)[8], const MaterialDev& m,
+                                             float4 (&acc)[8]) {
+  const float e[3][3] = {{dx[B][0], dx[B][1], dx[B][2]}, {dx[C][0], dx[C][1], dx[C][2]},
+                         {dx[D][0], dx[D][1], dx[D][2]}};
   float r[4][4];  // [column][local vertex]
 #pragma unroll
   for (int col = 0; col < kEnsW; ++col) {
-    // (hi, lo) of column col: columns 0, 1 in ya (x, y | z, w), 2, 3 in yb
-    const float4& pa = col < 2 ? ya[A] : yb[A];
-    const float4& pb = col < 2 ? ya[B] : yb[B];
-    const float4& pc = col < 2 ? ya[C] : yb[C];
-    const float4& pd = col < 2 ? ya[D] : yb[D];
-    const bool hi2 = (col & 1) != 0;
-    const float fa_h = hi2 ? pa.z : pa.x, fa_l = hi2 ? pa.w : pa.y;
-    const float d1 = ((hi2 ? pb.z : pb.x) - fa_h) + ((hi2 ? pb.w : pb.y) - fa_l);
-    const float d2 = ((hi2 ? pc.z : pc.x) - fa_h) + ((hi2 ? pc.w : pc.y) - fa_l);
-    const float d3 = ((hi2 ? pd.z : pd.x) - fa_h) + ((hi2 ? pd.w : pd.y) - fa_l);
     float rr[4];
-    tet_residual<float>(e, d1, d2, d3, m, 1.0f, rr);
+    tet_residual<float>(e, comp(dp[B], col), comp(dp[C], col), comp(dp[D], col), m, 1.0f, rr);
 #pragma unroll
     for (int k = 0; k < 4; ++k) r[col][k] = rr[k];
   }
-  acc[A] = acc[A] + make_float4(r[0][0], r[1][0], r[2][0], r[3][0]);
+  acc[0] = acc[0] + make_float4(r[0][0], r[1][0], r[2][0], r[3][0]);
   acc[B] = acc[B] + make_float4(r[0][1], r[1][1], r[2][1], r[3][1]);
   acc[C] = acc[C] + make_float4(r[0][2], r[1][2], r[2][2], r[3][2]);
   acc[D] = acc[D] + make_float4(r[0][3], r[1][3], r[2][3], r[3][3]);
 }
 
-__global__ void k4_elem32_cell(int64_t ncell, const int32_t* __restrict__ corner, const uint8_t* __restrict__ mat,
-                               const MaterialDev* __restrict__ mats, const float4* __restrict__ xh,
-                               const float4* __restrict__ xl, const float4* __restrict__ Y2, int n_limit,
-                               float4* __restrict__ y) {
+// Only the corners' offsets to corner 0 stay live across the six tets (all
+// share the diagonal 0-7): positions dx[k] and the four potentials dp[k],
+// each formed from the (hi, lo) FP32 pairs as (hi_k - hi_0) + (lo_k - lo_0).
+__global__ void __launch_bounds__(kBlock, 2)
+k4_elem32_cell(int64_t ncell, const int32_t* __restrict__ corner, const uint8_t* __restrict__ mat,
+               const MaterialDev* __restrict__ mats, const float4* __restrict__ xh, const float4* __restrict__ xl,
+               const float4* __restrict__ Y2, int n_limit, float4* __restrict__ y) {
   pdl_enter();
   const int64_t cidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (cidx >= ncell) return;
   int v[8];
-  float4 h[8], l[8], ya[8], yb[8], acc[8];
+  float dx[8][3];
+  float4 dp[8], acc[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    v[k] = __ldg(corner + (int64_t)k * ncell + cidx);
-    h[k] = xh[v[k]];
-    l[k] = xl[v[k]];
-    ya[k] = Y2[2 * (int64_t)v[k]];
-    yb[k] = Y2[2 * (int64_t)v[k] + 1];
-    acc[k] = zero4();
+  for (int k = 0; k < 8; ++k) v[k] = __ldg(corner + (int64_t)k * ncell + cidx);
+  const float4 h0 = xh[v[0]], l0 = xl[v[0]], a0 = Y2[2 * (int64_t)v[0]], b0 = Y2[2 * (int64_t)v[0] + 1];
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    const float4 h = xh[v[k]], l = xl[v[k]];
+    const float4 a = Y2[2 * (int64_t)v[k]], b = Y2[2 * (int64_t)v[k] + 1];
+    dx[k][0] = (h.x - h0.x) + (l.x - l0.x);
+    dx[k][1] = (h.y - h0.y) + (l.y - l0.y);
+    dx[k][2] = (h.z - h0.z) + (l.z - l0.z);
+    // columns 0, 1 in a as (hi, lo, hi, lo), columns 2, 3 in b
+    dp[k] = make_float4((a.x - a0.x) + (a.y - a0.y), (a.z - a0.z) + (a.w - a0.w), (b.x - b0.x) + (b.y - b0.y),
+                        (b.z - b0.z) + (b.w - b0.w));
   }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = zero4();
   const uint8_t* mt = mat + 6 * cidx;
-  cell_tet32x4<0, 1, 3, 7>(h, l, ya, yb, mats[mt[0]], acc);
-  cell_tet32x4<0, 1, 7, 5>(h, l, ya, yb, mats[mt[1]], acc);
-  cell_tet32x4<0, 2, 7, 3>(h, l, ya, yb, mats[mt[2]], acc);
-  cell_tet32x4<0, 2, 6, 7>(h, l, ya, yb, mats[mt[3]], acc);
-  cell_tet32x4<0, 4, 5, 7>(h, l, ya, yb, mats[mt[4]], acc);
-  cell_tet32x4<0, 4, 7, 6>(h, l, ya, yb, mats[mt[5]], acc);
+  cell_tet32x4<1, 3, 7>(dx, dp, mats[mt[0]], acc);
+  cell_tet32x4<1, 7, 5>(dx, dp, mats[mt[1]], acc);
+  cell_tet32x4<2, 7, 3>(dx, dp, mats[mt[2]], acc);
+  cell_tet32x4<2, 6, 7>(dx, dp, mats[mt[3]], acc);
+  cell_tet32x4<4, 5, 7>(dx, dp, mats[mt[4]], acc);
+  cell_tet32x4<4, 7, 6>(dx, dp, mats[mt[5]], acc);
 #pragma unroll
   for (int k = 0; k < 8; ++k)
     if (v[k] < n_limit) atomicAdd(y + v[k], acc[k]);
@@ -996,6 +1135,21 @@ __device__ __forceinline__ void store_split4(float4* __restrict__ Y2, int64_t i,
   const float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z, hw = (float)v.w;
   Y2[2 * i] = make_float4(hx, (float)(v.x - (double)hx), hy, (float)(v.y - (double)hy));
   Y2[2 * i + 1] = make_float4(hz, (float)(v.z - (double)hz), hw, (float)(v.w - (double)hw));
+}
+
+// Four column-major columns (src + c n) into the interleaved FP64 layout and
+// the FP32-pair layout.
+__global__ void k4_interleave_pair(int n, const double* __restrict__ src, double4_32a* __restrict__ dst,
+                                   float4* __restrict__ dst2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double4_32a v;
+  v.x = src[i];
+  v.y = src[(int64_t)n + i];
+  v.z = src[2 * (int64_t)n + i];
+  v.w = src[3 * (int64_t)n + i];
+  dst[i] = v;
+  store_split4(dst2, i, v);
 }
 
 // Y0 (interleaved, internal order) from the caller's column-major mesh-order
@@ -1042,7 +1196,7 @@ __global__ void k4_recurrence(int n, int nf, double c0, double mu, double nu, do
                               double4_32a* __restrict__ Yj, float4* __restrict__ Y2,
                               double4_32a* __restrict__ Fguess, int write_x,
                               const int32_t* __restrict__ noi, const long long* __restrict__ stepcount, int s,
-                              double4_32a* __restrict__ ring, int nh) {
+                              double4_32a* __restrict__ ring, float4* __restrict__ ring2, int nh) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -1050,7 +1204,11 @@ __global__ void k4_recurrence(int n, int nf, double c0, double mu, double nu, do
   if (i < nf) {
     const double dt = prm->dt;
     const double4_32a y0 = Y0[i], y1 = Yjm1[i], y2 = Yjm2[i], f1 = Fjm1[i], f0 = F0[i];
-    if (ring) ring[(size_t)((stepcount[0] + jm1) % nh) * nf + i] = f1;  // SPE history
+    if (ring) {  // SPE history, in FP64 and as FP32 pairs
+      const size_t slot = (size_t)((stepcount[0] + jm1) % nh);
+      ring[slot * nf + i] = f1;
+      store_split4(ring2 + slot * 2 * nf, i, f1);
+    }
 #pragma unroll
     for (int c = 0; c < kEnsW; ++c) {
       const double fj = zero_flags[jm1 * kEnsW + c] ? 0.0 : dc4(f1, c);
@@ -1077,10 +1235,11 @@ __global__ void k4_recurrence(int n, int nf, double c0, double mu, double nu, do
   }
 }
 
-// R = -y - g'(t_j) v_c M_fd 1_top per column in FP64, and clear y.
+// R = -y - g'(t_j) v_c M_fd 1_top per column in FP64 (and as FP32 pairs
+// into R2 when given), and clear y.
 __global__ void k4_rhs(int nf, float4* __restrict__ y32, const double* __restrict__ gpj,
                        const double* __restrict__ colv, const double* __restrict__ mtop,
-                       double4_32a* __restrict__ R) {
+                       double4_32a* __restrict__ R, float4* __restrict__ R2) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nf) return;
@@ -1092,6 +1251,7 @@ __global__ void k4_rhs(int nf, float4* __restrict__ y32, const double* __restric
   r.z = -(double)y.z - gm * colv[2];
   r.w = -(double)y.w - gm * colv[3];
   R[i] = r;
+  if (R2) store_split4(R2, i, r);
   y32[i] = zero4();
 }
 

@@ -202,6 +202,11 @@ struct eqs_ctx {
   double* d_sh = nullptr;            // RMS of h1 (scale of the features)
   int* d_mlp_used = nullptr;         // per stage: 1 if the network's guess was kept
   float* d_store = nullptr;          // recorded solutions (capacity x n_free)
+  float* d_store_e = nullptr;        // recorded distances z - x0 from the SPE starts (capacity x n_free)
+  bool store_e_valid = false;        // every recorded step ran with SPE start vectors
+  double* d_x0 = nullptr;            // SPE start of the current solve (learned correction, recording)
+  double* d_alpha = nullptr;         // step along the learned direction
+  float* d_store_rms_e = nullptr;    // per recorded solve: RMS(z - x0) (training target scale)
   float* d_store_rms = nullptr;
   int64_t store_cap = 0, recorded = 0;
   bool recording = false;
@@ -251,6 +256,9 @@ struct eqs_ctx {
   double* d_ecolv = nullptr;         // drive scale of each column
   double4_32a* d_eX = nullptr;       // SPE history of the four columns (row-interleaved rings)
   double4_32a* d_eW = nullptr;       // W = M X
+  float4* d_eX2 = nullptr;           // the rings X as FP32 pairs (two float4 per row; Gram pass)
+  float4* d_eR2 = nullptr;           // the stage right-hand side as FP32 pairs (Gram pass)
+  float2* d_M_rs = nullptr;          // row sums of the split M (FP32 pairs; difference-form products)
   double* d_eG = nullptr;            // per-column Gram matrices (4 x 6 x 6)
   double* d_ecoef = nullptr;         // per-column coefficients (+ slots in use)
   double* d_espart = nullptr;        // reduction slots of the ensemble Gram pass

@@ -412,14 +412,11 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
 // Grid-wide deterministic sum: every block stores its partials; the last
 // block to finish (atomic ticket) sums them in block order and returns true
 // in all of its threads with the totals in `tot` (thread 0).
-template <int NV>
-__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* counter,
-                                         int max_blocks, double (&tot)[NV]) {
+// Arrival of this block after its partials are written (thread 0 has
+// written them): true in every thread of the last block to arrive.
+__device__ __forceinline__ bool grid_ticket(unsigned int* counter) {
   __shared__ bool am_last;
-  block_sum<NV>(v);
   if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) partials[k * max_blocks + blockIdx.x] = v[k];
     __threadfence();
     // two-level ticket: blocks arrive on one of 8 group counters (counter[1..8]);
     // the last block of each group arrives on counter[0]
@@ -435,7 +432,18 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, unsi
     am_last = last;
   }
   __syncthreads();
-  if (!am_last) return false;
+  return am_last;
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* counter,
+                                         int max_blocks, double (&tot)[NV]) {
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[k * max_blocks + blockIdx.x] = v[k];
+  }
+  if (!grid_ticket(counter)) return false;
   __threadfence();
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
@@ -1067,25 +1075,18 @@ __device__ __forceinline__ void cell_tet64(const double (&px)[8][3], const doubl
   acc[D] += r[3];
 }
 
-template <int A, int B, int C, int D>
-__device__ __forceinline__ void cell_tet32(const float4 (&h)[8], const float4 (&l)[8], const float2 (&f)[8],
-                                           const MaterialDev& m, float (&acc)[8]) {
-  float e[3][3];
-  e[0][0] = (h[B].x - h[A].x) + (l[B].x - l[A].x);
-  e[0][1] = (h[B].y - h[A].y) + (l[B].y - l[A].y);
-  e[0][2] = (h[B].z - h[A].z) + (l[B].z - l[A].z);
-  e[1][0] = (h[C].x - h[A].x) + (l[C].x - l[A].x);
-  e[1][1] = (h[C].y - h[A].y) + (l[C].y - l[A].y);
-  e[1][2] = (h[C].z - h[A].z) + (l[C].z - l[A].z);
-  e[2][0] = (h[D].x - h[A].x) + (l[D].x - l[A].x);
-  e[2][1] = (h[D].y - h[A].y) + (l[D].y - l[A].y);
-  e[2][2] = (h[D].z - h[A].z) + (l[D].z - l[A].z);
-  const float d1 = (f[B].x - f[A].x) + (f[B].y - f[A].y);
-  const float d2 = (f[C].x - f[A].x) + (f[C].y - f[A].y);
-  const float d3 = (f[D].x - f[A].x) + (f[D].y - f[A].y);
+// One tet (0, B, C, D) of a Kuhn cell (all six share the diagonal 0-7) from
+// the corners' offsets to corner 0: dx[k] = position, df[k] = potential,
+// each formed from the (hi, lo) FP32 pairs as (hi_k - hi_0) + (lo_k - lo_0),
+// so only these 4 floats per corner stay live across the six tets.
+template <int B, int C, int D>
+__device__ __forceinline__ void cell_tet32(const float (&dx)[8][3], const float (&df)[8], const MaterialDev& m,
+                                           float (&acc)[8]) {
+  const float e[3][3] = {{dx[B][0], dx[B][1], dx[B][2]}, {dx[C][0], dx[C][1], dx[C][2]},
+                         {dx[D][0], dx[D][1], dx[D][2]}};
   float r[4];
-  tet_residual<float>(e, d1, d2, d3, m, 1.0f, r);
-  acc[A] += r[0];
+  tet_residual<float>(e, df[B], df[C], df[D], m, 1.0f, r);
+  acc[0] += r[0];
   acc[B] += r[1];
   acc[C] += r[2];
   acc[D] += r[3];
@@ -1121,32 +1122,37 @@ __global__ void k_elem64_cell(int64_t ncell, const int32_t* __restrict__ corner,
     if (v[k] < n_limit) atomicAdd(y + v[k], acc[k]);
 }
 
-__global__ void k_elem32_cell(int64_t ncell, const int32_t* __restrict__ corner, const uint8_t* __restrict__ mat,
-                              const MaterialDev* __restrict__ mats, const float4* __restrict__ xh,
-                              const float4* __restrict__ xl, const float2* __restrict__ x, int n_limit,
-                              float* __restrict__ y) {
+__global__ void __launch_bounds__(kBlock, 3)
+k_elem32_cell(int64_t ncell, const int32_t* __restrict__ corner, const uint8_t* __restrict__ mat,
+              const MaterialDev* __restrict__ mats, const float4* __restrict__ xh, const float4* __restrict__ xl,
+              const float2* __restrict__ x, int n_limit, float* __restrict__ y) {
   pdl_enter();
   const int64_t cidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (cidx >= ncell) return;
   int v[8];
-  float4 h[8], l[8];
-  float2 f[8];
-  float acc[8];
+  float dx[8][3], df[8], acc[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    v[k] = __ldg(corner + (int64_t)k * ncell + cidx);
-    h[k] = xh[v[k]];
-    l[k] = xl[v[k]];
-    f[k] = x[v[k]];
-    acc[k] = 0.f;
+  for (int k = 0; k < 8; ++k) v[k] = __ldg(corner + (int64_t)k * ncell + cidx);
+  const float4 h0 = xh[v[0]], l0 = xl[v[0]];
+  const float2 f0 = x[v[0]];
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    const float4 h = xh[v[k]], l = xl[v[k]];
+    const float2 f = x[v[k]];
+    dx[k][0] = (h.x - h0.x) + (l.x - l0.x);
+    dx[k][1] = (h.y - h0.y) + (l.y - l0.y);
+    dx[k][2] = (h.z - h0.z) + (l.z - l0.z);
+    df[k] = (f.x - f0.x) + (f.y - f0.y);
   }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = 0.f;
   const uint8_t* mt = mat + 6 * cidx;
-  cell_tet32<0, 1, 3, 7>(h, l, f, mats[mt[0]], acc);
-  cell_tet32<0, 1, 7, 5>(h, l, f, mats[mt[1]], acc);
-  cell_tet32<0, 2, 7, 3>(h, l, f, mats[mt[2]], acc);
-  cell_tet32<0, 2, 6, 7>(h, l, f, mats[mt[3]], acc);
-  cell_tet32<0, 4, 5, 7>(h, l, f, mats[mt[4]], acc);
-  cell_tet32<0, 4, 7, 6>(h, l, f, mats[mt[5]], acc);
+  cell_tet32<1, 3, 7>(dx, df, mats[mt[0]], acc);
+  cell_tet32<1, 7, 5>(dx, df, mats[mt[1]], acc);
+  cell_tet32<2, 7, 3>(dx, df, mats[mt[2]], acc);
+  cell_tet32<2, 6, 7>(dx, df, mats[mt[3]], acc);
+  cell_tet32<4, 5, 7>(dx, df, mats[mt[4]], acc);
+  cell_tet32<4, 7, 6>(dx, df, mats[mt[5]], acc);
 #pragma unroll
   for (int k = 0; k < 8; ++k)
     if (v[k] < n_limit) atomicAdd(y + v[k], acc[k]);
@@ -1363,7 +1369,7 @@ __global__ void k_recurrence(int n, int nf, double c0, double mu, double nu, dou
                              int write_x, const int32_t* __restrict__ node_of_internal,
                              float* __restrict__ ring, const long long* __restrict__ stepcount, int s,
                              float* __restrict__ store, long long store_cap, double* __restrict__ spe_ring,
-                             int spe_n) {
+                             int spe_n, float* __restrict__ store_e, const double* __restrict__ x0save) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -1373,7 +1379,11 @@ __global__ void k_recurrence(int n, int nf, double c0, double mu, double nu, dou
     const long long gidx = stepcount[0] + jm1;
     const float f32 = (float)Fjm1[i];
     ring[(size_t)(gidx & 3) * nf + i] = f32;
-    if (store && gidx < store_cap) store[(size_t)gidx * nf + i] = f32;
+    if (store && gidx < store_cap) {
+      store[(size_t)gidx * nf + i] = f32;
+      // the solve's distance from its SPE start, z - x0 (FP64 difference)
+      if (store_e) store_e[(size_t)gidx * nf + i] = (float)(Fjm1[i] - x0save[i]);
+    }
     if (spe_ring) spe_ring[(size_t)(gidx % spe_n) * nf + i] = Fjm1[i];
     const double dt = prm->dt;
     const double fj = zero_flags[jm1] ? 0.0 : Fjm1[i];
@@ -1517,7 +1527,7 @@ struct PPlan {
   const double* coarse_inv;
   DevSell<double> M;
   double *r, *rprev, *pA, *pB, *q, *zd;
-  double* partials;  // 8 slots x gridDim
+  double* partials;  // 16 slots x gridDim
   GridBarrier* bar;
   PLevel<T> lev[kMaxLevels];
 };
@@ -1529,7 +1539,7 @@ struct GridCtx {
   unsigned int nblocks;     // CTAs in the group
   unsigned int rank;        // this CTA's index in the group
   GridBarrier* bar;         // the group's barrier
-  double* partials;         // the group's reduction slots (8 x nblocks)
+  double* partials;         // the group's reduction slots (16 x nblocks)
   long long max_spins;      // wait budget of one barrier (polls)
 };
 

@@ -127,6 +127,182 @@ __global__ void k_mlp_guess(int nf, const double* __restrict__ h1d, const float*
   }
 }
 
+// ---- correction of the SPE start (the second mode of the network).
+// Inputs at free node i: the increments d0 = x0 - h1 (the SPE step from the
+// previous solution), d1 = h1 - h2, d2 = h2 - h3, d3 = h3 - h4 and their
+// means over the free graph neighbours, divided by s = RMS(d0); output o;
+// direction d = s o; start z0 = x0 + alpha d with the step alpha that
+// minimises the M-norm error along d (so a poor direction costs nothing).
+// Increments, not the solutions themselves: the information is in how the
+// solutions change, small against their size, and BF16 weights could not
+// cancel raw inputs to that precision.
+
+// s = sqrt(mean((x0 - h1)^2)) over the free nodes; 0 without SPE history
+// (*nuse == 0, when x0 is h1).
+__global__ void k_rms_diff(int n, const double* __restrict__ a, const double* __restrict__ b,
+                           const int* __restrict__ nuse, double* s, double* partials, unsigned int* counter,
+                           int max_blocks) {
+  pdl_enter();
+  const bool has = *nuse > 0;
+  double v[1] = {0.0};
+  if (has)
+    for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      const double d = a[i] - b[i];
+      v[0] = fma(d, d, v[0]);
+    }
+  double tot[1];
+  if (grid_sum<1>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) *s = sqrt(tot[0] / n);
+}
+
+__device__ __forceinline__ void spe_node_features(int i, const double* __restrict__ x0, const double* __restrict__ h1d,
+                                                  const float* __restrict__ r0, const float* __restrict__ r1,
+                                                  const float* __restrict__ r2, const float* __restrict__ r3,
+                                                  const int32_t* __restrict__ adj_ptr,
+                                                  const int32_t* __restrict__ adj_col,
+                                                  const float* __restrict__ inv_deg, float inv_s, float x[8]) {
+  x[0] = (float)(x0[i] - h1d[i]) * inv_s;
+  x[1] = (r0[i] - r1[i]) * inv_s;
+  x[2] = (r1[i] - r2[i]) * inv_s;
+  x[3] = (r2[i] - r3[i]) * inv_s;
+  float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+  const int e = adj_ptr[i + 1];
+  for (int k = adj_ptr[i]; k < e; ++k) {
+    const int j = adj_col[k];
+    m0 += (float)(x0[j] - h1d[j]);
+    m1 += r0[j] - r1[j];
+    m2 += r1[j] - r2[j];
+    m3 += r2[j] - r3[j];
+  }
+  const float w = inv_deg[i] * inv_s;
+  x[4] = m0 * w;
+  x[5] = m1 * w;
+  x[6] = m2 * w;
+  x[7] = m3 * w;
+}
+
+// Direction d = s MLP(features) for the solve g = stepcount[0] + j from its
+// SPE start x0; d = 0 without SPE history (*nuse == 0), with fewer than four
+// earlier solutions, or when s = 0.
+__global__ void k_mlp_dir_spe(int nf, const double* __restrict__ x0, const double* __restrict__ h1d,
+                              const float* __restrict__ ring, const long long* __restrict__ stepcount, int j,
+                              const int* __restrict__ nuse, const int32_t* __restrict__ adj_ptr,
+                              const int32_t* __restrict__ adj_col, const float* __restrict__ inv_deg,
+                              const __nv_bfloat16* __restrict__ wb, const double* __restrict__ sd,
+                              double* __restrict__ d) {
+  pdl_enter();
+  __shared__ float sw[kNP + 3];
+  load_weights(wb, sw);
+  const long long g = stepcount[0] + j;
+  const double s = *nuse > 0 ? *sd : 0.0;
+  const bool use = g >= 4 && s > 0.0;
+  const float* hr[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) hr[l] = ring + (size_t)(((g - 1 - l) % 4 + 4) % 4) * nf;
+  const float inv_s = use ? (float)(1.0 / s) : 0.f;
+  for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!use) {
+      d[i] = 0.0;
+      continue;
+    }
+    float x[8];
+    spe_node_features((int)i, x0, h1d, hr[0], hr[1], hr[2], hr[3], adj_ptr, adj_col, inv_deg, inv_s, x);
+    d[i] = s * (double)mlp_forward(sw, x);
+  }
+}
+
+// Line search along d from x0: q = M d and alpha = d.r0 / d.q (0 when
+// d.q <= 0), r0 = R - M x0 given as r, or formed here from R and x0 when r
+// is null.  The last block writes alpha.
+__global__ void k_dir_alpha(DevSell<double> M, int nf, const double* __restrict__ d, const double* __restrict__ r,
+                            const double* __restrict__ R, const double* __restrict__ x0, double* __restrict__ q,
+                            double* __restrict__ alpha, double* partials, unsigned int* counter, int max_blocks) {
+  pdl_enter();
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+    const double qi = mat_row<double>(M, i, nf, d);
+    q[i] = qi;
+    const double ri = r ? r[i] : R[i] - mat_row<double>(M, i, nf, x0);
+    v[0] = fma(d[i], ri, v[0]);
+    v[1] = fma(d[i], qi, v[1]);
+  }
+  double tot[2];
+  if (grid_sum<2>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0)
+    *alpha = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
+}
+
+// The corrected CG start: x += alpha d, r -= alpha q, the first V-cycle input
+// and ||r||^2; the last block redoes the stopping test of the start
+// (||R||^2 already in sc->bnorm2) and counts the solve as started from the
+// learned direction when alpha != 0.
+template <typename T>
+__global__ void k_dir_apply(int nf, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ d,
+                            const double* __restrict__ q, const double* __restrict__ alpha,
+                            const T* __restrict__ dinv0, T inv_theta0, T* __restrict__ b0, T* __restrict__ x0v,
+                            T* __restrict__ d0v, PcgScalars* sc, double* partials, unsigned int* counter,
+                            int max_blocks, double tol2, int maxit, cudaGraphConditionalHandle h, int use_handle,
+                            double* relres_out, int* kept_out) {
+  pdl_enter();
+  const double a = *alpha;
+  double v[1] = {0.0};
+  for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+    const double xi = fma(a, d[i], x[i]);
+    const double ri = fma(-a, q[i], r[i]);
+    x[i] = xi;
+    r[i] = ri;
+    const T bi = (T)ri;
+    b0[i] = bi;
+    const T dd = dinv0[i] * bi * inv_theta0;
+    x0v[i] = dd;
+    d0v[i] = dd;
+    v[0] = fma(ri, ri, v[0]);
+  }
+  double tot[1];
+  if (grid_sum<1>(v, partials, counter, max_blocks, tot) && threadIdx.x == 0) {
+    const double b2 = sc->bnorm2;
+    sc->rnorm2 = tot[0];
+    const int zero = b2 == 0.0;
+    const int go = !zero && tot[0] > tol2 * b2 && maxit > 0;
+    sc->conv = !go;
+    if (use_handle) cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (relres_out) *relres_out = zero ? 0.0 : sqrt(tot[0] / b2);
+    if (kept_out) *kept_out = a != 0.0;
+  }
+}
+
+// z0 = x0 + alpha d (the corrected start alone).
+__global__ void k_axpy_alpha(int nf, const double* __restrict__ x0, const double* __restrict__ d,
+                             const double* __restrict__ alpha, double* __restrict__ z0) {
+  const int64_t i = gtid();
+  if (i < nf) z0[i] = fma(*alpha, d[i], x0[i]);
+}
+
+// Per recorded solve k >= 1 of the SPE-correction mode: the input scale
+// s_k = RMS(d0) with d0 = x0_k - z_{k-1} = (z_k - z_{k-1}) - e_k, and the
+// target scale RMS(e_k), from the stored solutions z and distances
+// e = z - x0 (block k; 0 for k = 0).
+__global__ void k_store_rms_spe(int nf, const float* __restrict__ store, const float* __restrict__ store_e,
+                                float* __restrict__ rms, float* __restrict__ rms_e) {
+  const int k = blockIdx.x;
+  if (k == 0) {
+    if (threadIdx.x == 0) rms[0] = rms_e[0] = 0.f;
+    return;
+  }
+  const float* z = store + (size_t)k * nf;
+  const float* zp = store + (size_t)(k - 1) * nf;
+  const float* e = store_e + (size_t)k * nf;
+  double acc[2] = {0.0, 0.0};
+  for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+    const double d = ((double)z[i] - (double)zp[i]) - (double)e[i];
+    acc[0] += d * d;
+    acc[1] += (double)e[i] * (double)e[i];
+  }
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) {
+    rms[k] = (float)sqrt(acc[0] / nf);
+    rms_e[k] = (float)sqrt(acc[1] / nf);
+  }
+}
+
 // Per-block RMS of each recorded solution: rms[k] = sqrt(mean(store[k]^2)).
 __global__ void k_store_rms(int nf, const float* __restrict__ store, float* __restrict__ rms) {
   const float* v = store + (size_t)blockIdx.x * nf;
@@ -140,12 +316,17 @@ __global__ void k_store_rms(int nf, const float* __restrict__ store, float* __re
 // the parameter gradients are added to grad.  Samples are either drawn
 // (solve k in [4, count), node i) from splitmix64 stream `seed`, values
 // 2 (step B + b) and 2 (step B + b) + 1, or given as X (B x 8) / T (B).
+// With store_e (the SPE-correction mode) a drawn sample has the increment
+// inputs of k_mlp_dir_spe (scale s_k = rms[k]), x0_k = z_k - e_k, and target
+// e_k / RMS(e_k) (rms_e[k]); otherwise the previous-solution mode's inputs
+// and target.
 __global__ void __launch_bounds__(kTrainBlock) k_mlp_train(
     int nf, const float* __restrict__ store, const float* __restrict__ rms, int count,
     const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj_col,
     const float* __restrict__ inv_deg, const __nv_bfloat16* __restrict__ wb, float* __restrict__ grad,
     float* __restrict__ loss, unsigned long long seed, long long step, int B,
-    const float* __restrict__ Xin, const float* __restrict__ Tin) {
+    const float* __restrict__ Xin, const float* __restrict__ Tin, const float* __restrict__ store_e,
+    const float* __restrict__ rms_e) {
   extern __shared__ float sm[];
   float* sw = sm;
   const int S = kTrainBlock + 1;  // padded stride of the per-sample arrays
@@ -169,8 +350,33 @@ __global__ void __launch_bounds__(kTrainBlock) k_mlp_train(
       const uint64_t ctr = 2ull * ((uint64_t)step * (uint64_t)B + (uint64_t)b);
       const int k = 4 + (int)(smix64(seed, ctr) % (uint64_t)(count - 4));
       const int i = (int)(smix64(seed, ctr + 1) % (uint64_t)nf);
-      const float s_h = rms[k - 1];
-      if (s_h > 0.f) {
+      const float s_h = store_e ? rms[k] : rms[k - 1];
+      if (store_e && s_h > 0.f && rms_e[k] > 0.f) {
+        // z_k, z_{k-1} .. z_{k-4}: d0 = (z_k - z_{k-1}) - e_k, d_l = z_{k-l} - z_{k-l-1}
+        const float* z[5];  // z_k, z_{k-1}, ..., z_{k-4}
+#pragma unroll
+        for (int l = 0; l < 5; ++l) z[l] = store + (size_t)(k - l) * nf;
+        const float* ek = store_e + (size_t)k * nf;
+        const float inv_s = 1.0f / s_h;
+        float dd[4], mm[4] = {0.f, 0.f, 0.f, 0.f};
+        dd[0] = (z[0][i] - z[1][i]) - ek[i];
+#pragma unroll
+        for (int l = 1; l < 4; ++l) dd[l] = z[l][i] - z[l + 1][i];
+        const int e = adj_ptr[i + 1];
+        for (int q = adj_ptr[i]; q < e; ++q) {
+          const int jn = adj_col[q];
+          mm[0] += (z[0][jn] - z[1][jn]) - ek[jn];
+#pragma unroll
+          for (int l = 1; l < 4; ++l) mm[l] += z[l][jn] - z[l + 1][jn];
+        }
+        const float w = inv_deg[i] * inv_s;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          x[l] = dd[l] * inv_s;
+          x[4 + l] = mm[l] * w;
+        }
+        t = ek[i] / rms_e[k];
+      } else if (!store_e && s_h > 0.f) {
         const float* h0 = store + (size_t)(k - 1) * nf;
         node_features(i, h0, h0 - nf, h0 - 2 * (size_t)nf, h0 - 3 * (size_t)nf, adj_ptr, adj_col, inv_deg,
                       1.0f / s_h, x);

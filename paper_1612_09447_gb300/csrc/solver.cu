@@ -391,7 +391,14 @@ struct SolveSlots {
 struct SpeAt {
   int s, j;
   bool pod;
+  bool learned;  // SPE start corrected along the network's direction
 };
+
+// Steps record each solution's distance from its SPE start (z - x0).
+static bool recording_e(const eqs_ctx* c) {
+  return c->recording && c->d_store_e &&
+         (c->opts.guess == EQS_GUESS_SPE || c->opts.guess == EQS_GUESS_SPE_MLP);
+}
 
 // SPE projection of solve j (templated on the history length): the newest
 // solution's product with M, the Gram column and the coefficients y.
@@ -440,27 +447,29 @@ static void spe_gram(eqs_ctx* c, cudaStream_t st, int s, int j, bool defer, bool
 template <typename T, int NH>
 static void spe_start_n(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st, int s, int j,
                         const double* R, double* x, double tol2, cudaGraphConditionalHandle h,
-                        int use_handle, SolveSlots sl) {
+                        int use_handle, SolveSlots sl, double* x_copy) {
   DevLevel<T>& V = L[0];
   const int nf = (int)c->n_free;
   launch(k_proj_start<T, NH>, vec_grid(c, nf), kBlock, st, c->M64, nf, (const double*)c->d_spe_X,
          (const double*)c->d_spe_W, (const double*)c->d_spe_y, (const int*)(c->d_spe_y + kSpeMax), R, x,
          R ? c->d_r : nullptr, V.dinv, (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials,
          c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres,
-         sl.zero);
+         sl.zero, x_copy);
 }
 
+// x_copy (nullable) also receives x0 (recording the distance of the
+// solution from its SPE start).
 template <typename T>
 static void spe_start(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st, int s, int j,
                       const double* R, double* x, double tol2, cudaGraphConditionalHandle h,
-                      int use_handle, SolveSlots sl) {
+                      int use_handle, SolveSlots sl, double* x_copy = nullptr) {
   switch (c->opts.spe_n) {
-    case 1: spe_start_n<T, 1>(c, L, st, s, j, R, x, tol2, h, use_handle, sl); break;
-    case 2: spe_start_n<T, 2>(c, L, st, s, j, R, x, tol2, h, use_handle, sl); break;
-    case 3: spe_start_n<T, 3>(c, L, st, s, j, R, x, tol2, h, use_handle, sl); break;
-    case 4: spe_start_n<T, 4>(c, L, st, s, j, R, x, tol2, h, use_handle, sl); break;
-    case 5: spe_start_n<T, 5>(c, L, st, s, j, R, x, tol2, h, use_handle, sl); break;
-    default: spe_start_n<T, 6>(c, L, st, s, j, R, x, tol2, h, use_handle, sl); break;
+    case 1: spe_start_n<T, 1>(c, L, st, s, j, R, x, tol2, h, use_handle, sl, x_copy); break;
+    case 2: spe_start_n<T, 2>(c, L, st, s, j, R, x, tol2, h, use_handle, sl, x_copy); break;
+    case 3: spe_start_n<T, 3>(c, L, st, s, j, R, x, tol2, h, use_handle, sl, x_copy); break;
+    case 4: spe_start_n<T, 4>(c, L, st, s, j, R, x, tol2, h, use_handle, sl, x_copy); break;
+    case 5: spe_start_n<T, 5>(c, L, st, s, j, R, x, tol2, h, use_handle, sl, x_copy); break;
+    default: spe_start_n<T, 6>(c, L, st, s, j, R, x, tol2, h, use_handle, sl, x_copy); break;
   }
 }
 
@@ -493,7 +502,39 @@ static void pod_start(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st, 
          (const double*)c->d_pod_W, (const double*)c->d_pod_a, (const int*)&ps->nuse, R, x,
          R ? c->d_r : nullptr, V.dinv, (T)V.inv_theta, V.b, V.x, V.dA, c->d_sc, c->red.partials,
          c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres,
-         sl.zero);
+         sl.zero, (double*)nullptr);
+}
+
+// Stage vectors of a step: Y_j and the stage solutions F_j (rotating buffers).
+static double* Ybuf(eqs_ctx* c, int j) { return j == 0 ? c->d_Y[0] : c->d_Y[1 + (j - 1) % 3]; }
+static double* Fbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_F[0] : c->d_F[1 + (j - 1) % 2]; }
+
+// The learned correction of an SPE start (EQS_GUESS_SPE_MLP): the network's
+// direction d from the increments around x0 (kept in d_x0), q = M d, the
+// M-norm optimal step alpha, then x = x0 + alpha d and r = r0 - alpha q with
+// the CG start redone on them.  d goes to d_rtmp, q to the CG vector q
+// (its first pass does not read it).
+template <typename T>
+static void learned_correction(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_t st, int s, int j, double* x,
+                               double tol2, cudaGraphConditionalHandle h, int use_handle, SolveSlots sl,
+                               int* kept) {
+  DevLevel<T>& V = L[0];
+  const int nf = (int)c->n_free;
+  const double* h1 = Fbuf(c, j == 0 ? s - 1 : j - 1);
+  const int* nuse = (const int*)(c->d_spe_y + kSpeMax);
+  launch(k_rms_diff, vec_grid(c, nf), kBlock, st, nf, (const double*)c->d_x0, h1, nuse, c->d_sh,
+         c->red.partials, c->red.counter, c->red.max_blocks);
+  launch(k_mlp_dir_spe, std::max(1, std::min(nblk(nf), 4 * c->sms)), kBlock, st, nf, (const double*)c->d_x0, h1,
+         (const float*)c->d_ring, (const long long*)c->d_stepcount, j, nuse, (const int32_t*)c->d_adj_ptr,
+         (const int32_t*)c->d_adj_col, (const float*)c->d_inv_deg, (const __nv_bfloat16*)c->d_theta_bf16,
+         (const double*)c->d_sh, c->d_rtmp);
+  launch(k_dir_alpha, vec_grid(c, nf), kBlock, st, c->M64, nf, (const double*)c->d_rtmp, (const double*)c->d_r,
+         (const double*)nullptr, (const double*)nullptr, c->d_q, c->d_alpha, c->red.partials, c->red.counter,
+         c->red.max_blocks);
+  launch(k_dir_apply<T>, vec_grid(c, nf), kBlock, st, nf, x, c->d_r, (const double*)c->d_rtmp,
+         (const double*)c->d_q, (const double*)c->d_alpha, (const T*)V.dinv, (T)V.inv_theta, V.b, V.x, V.dA,
+         c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle,
+         sl.relres, kept);
 }
 
 template <typename T>
@@ -507,7 +548,9 @@ static void pcg_init_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_
     if (spe->pod)
       pod_start<T>(c, L, st, R, x, tol2, h, use_handle, sl);
     else
-      spe_start<T>(c, L, st, spe->s, spe->j, R, x, tol2, h, use_handle, sl);
+      spe_start<T>(c, L, st, spe->s, spe->j, R, x, tol2, h, use_handle, sl,
+                   (recording_e(c) || spe->learned) ? c->d_x0 : nullptr);
+    if (spe->learned) learned_correction<T>(c, L, st, spe->s, spe->j, x, tol2, h, use_handle, sl, kept);
     return;
   }
   if (h1) {  // learned start vector with the previous solution as fallback
@@ -640,7 +683,7 @@ static eqs_status build_plan(eqs_ctx* c, std::vector<DevLevel<T>>& L) {
   if (occ < 1) return fail(c, EQS_ERR_CUDA, "persistent solve kernel cannot be resident");
   const int bps = std::min(occ, std::max(1, c->opts.blocks_per_sm));
   c->pblocks = sms * bps;
-  CK(dalloc(c, &c->d_ppartials, 8 * (size_t)c->pblocks));
+  CK(dalloc(c, &c->d_ppartials, 16 * (size_t)c->pblocks));
   GridBarrier* bar = nullptr;
   CK(dalloc(c, &bar, 1));
   c->d_bar = bar;
@@ -715,7 +758,7 @@ static eqs_status solve_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, const do
                                double tol2, SolveSlots sl, const double* h1 = nullptr, int* kept = nullptr,
                                const SpeAt* spe = nullptr) {
   if (c->direct) return pcg_direct<T>(c, L, R, x, tol2, sl, h1, kept, spe);
-  if (c->opts.persistent && !h1) {
+  if (c->opts.persistent && !h1 && !(spe && spe->learned)) {
     // the persistent kernel forms its own initial residual: only x0 here
     if (spe && spe->pod) pod_start<T>(c, L, c->cap_stream, nullptr, x, tol2, 0, 0, sl);
     else if (spe) spe_start<T>(c, L, c->cap_stream, spe->s, spe->j, nullptr, x, tol2, 0, 0, sl);
@@ -762,8 +805,7 @@ static void elem_launch(eqs_ctx* c, cudaStream_t st, const double* Y, int n_limi
 }
 
 // -------------------------------------------------------- step graph
-static double* Ybuf(eqs_ctx* c, int j) { return j == 0 ? c->d_Y[0] : c->d_Y[1 + (j - 1) % 3]; }
-static double* Fbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_F[0] : c->d_F[1 + (j - 1) % 2]; }
+
 
 // Enqueue one RKC step on st: captured into a graph (c->direct false) or
 // launched directly with a host-driven CG loop (c->direct true).  The
@@ -798,7 +840,7 @@ static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, c
           (mx && !last) ? c->d_Y32 : nullptr, last ? nullptr : Fbuf(c, j),
           (mx || last) ? nullptr : c->d_R, last ? 1 : 0, c->d_node_of_internal, c->d_ring,
           (const long long*)c->d_stepcount, s, c->recording ? c->d_store : nullptr, (long long)c->store_cap,
-          c->d_spe_X, c->opts.spe_n);
+          c->d_spe_X, c->opts.spe_n, recording_e(c) ? c->d_store_e : nullptr, (const double*)c->d_x0);
       if (last) break;
     }
     if (mx) {
@@ -819,12 +861,17 @@ static eqs_status enqueue_step(eqs_ctx* c, std::vector<DevLevel<T>>& L, int s, c
       stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, h1, c->d_mlp_used + j);
     } else if (c->opts.guess == EQS_GUESS_SPE) {
       spe_gram(c, st, s, j, (c->opts.defer_sums & 2) != 0);
-      const SpeAt at{s, j, false};
+      const SpeAt at{s, j, false, false};
       stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, nullptr, nullptr, &at);
+    } else if (c->opts.guess == EQS_GUESS_SPE_MLP) {
+      // the SPE start, corrected along the network's direction (line search in the M-norm)
+      spe_gram(c, st, s, j, (c->opts.defer_sums & 2) != 0);
+      const SpeAt at{s, j, false, true};
+      stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, nullptr, c->d_mlp_used + j, &at);
     } else if (c->opts.guess == EQS_GUESS_POD || c->opts.guess == EQS_GUESS_POD2) {
       const int jp = j == 0 ? s - 1 : j - 1;  // the solve that produced the newest solution
       pod_prepare(c, st, s, j, Fbuf(c, jp), c->d_iters + jp, c->d_zero + jp, (const long long*)c->d_stepcount);
-      const SpeAt at{s, j, true};
+      const SpeAt at{s, j, true, false};
       stt = solve_launch<T>(c, L, c->d_R, Fbuf(c, j), tol2, sl, nullptr, nullptr, &at);
     } else {
       if (c->opts.guess == EQS_GUESS_ZERO && cudaMemsetAsync(Fbuf(c, j), 0, nf * sizeof(double), st) != cudaSuccess)
@@ -994,6 +1041,8 @@ static eqs_status ens_alloc(eqs_ctx* c) {
   CK(dalloc(c, &c->d_ecolv, kEnsW));
   CK(dalloc(c, &c->d_eX, (size_t)kEnsSpe * nf));
   CK(dalloc(c, &c->d_eW, (size_t)kEnsSpe * nf));
+  CK(dalloc(c, &c->d_eX2, (size_t)kEnsSpe * 2 * nf));
+  CK(dalloc(c, &c->d_eR2, (size_t)2 * nf));
   CK(dalloc(c, &c->d_eG, (size_t)kEnsW * kSpeMax * kSpeMax));
   CK(dalloc(c, &c->d_ecoef, (size_t)kEnsW * (kSpeMax + 1)));
   CK(dalloc(c, &c->d_espart, 2 * (size_t)kEnsSpe * kEnsW * c->red.max_blocks));
@@ -1156,6 +1205,21 @@ static eqs_status ens_pcg_direct(eqs_ctx* c, const double4_32a* R, double4_32a* 
   return EQS_OK;
 }
 
+// SPE Gram pass of the four columns (double-float on the FP32 pipe), two
+// threads per row, as many CTAs as are resident at once.
+static void ens_spe_gram(eqs_ctx* c, cudaStream_t st, int s, int j) {
+  const int nf = (int)c->n_free;
+  static int occ = 0;
+  if (occ == 0 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_spe_gram_df<kEnsSpe>, kBlock, 0) != cudaSuccess)
+    occ = 1;
+  const int grid = std::max(1, std::min(std::min(nblk(2 * (int64_t)nf), c->sms * std::max(1, occ)), c->red.max_blocks));
+  launch(k4_spe_gram_df<kEnsSpe>, grid, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo,
+         (const float2*)c->d_M_rs, nf,
+         (const float4*)c->d_eX2, c->d_eW, (const float4*)c->d_eR2, (const long long*)c->d_estepcount, s, j,
+         c->d_eG, c->d_espart, c->red.counter, c->red.max_blocks, 1e-12, c->d_ecoef);
+}
+
 static double4_32a* eYbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_eY[0] : c->d_eY[1 + (j - 1) % 3]; }
 static double4_32a* eFbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_eF[0] : c->d_eF[1 + (j - 1) % 2]; }
 
@@ -1188,7 +1252,7 @@ static eqs_status ens_enqueue_step(eqs_ctx* c, int s, const double* d_cj, cudaSt
              (const double*)c->d_dir_scale, (const double*)(c->d_g + j), (const double*)c->d_ecolv, eYbuf(c, j),
              last ? nullptr : c->d_eY2, last ? nullptr : eFbuf(c, j), last ? 1 : 0,
              (const int32_t*)c->d_node_of_internal, (const long long*)c->d_estepcount, s,
-             spe ? c->d_eX : nullptr, kEnsSpe);
+             spe ? c->d_eX : nullptr, c->d_eX2, kEnsSpe);
       if (last) break;
     }
     if (c->n_cells > 0)  // Kuhn cells: one 16-byte atomic per corner, 8 per six tets
@@ -1200,12 +1264,9 @@ static eqs_status ens_enqueue_step(eqs_ctx* c, int s, const double* d_cj, cudaSt
              (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi, (const float4*)c->d_xyz_lo,
              (const float4*)c->d_eY2, nf, c->d_ey32);
     launch(k4_rhs, nblk(nf), kBlock, st, nf, c->d_ey32, (const double*)(c->d_gp + j), (const double*)c->d_ecolv,
-           (const double*)c->d_mtop, c->d_eR);
+           (const double*)c->d_mtop, c->d_eR, spe ? c->d_eR2 : nullptr);
     EnsSlots sl{c->d_eiters + kEnsW * j, c->d_erelres + kEnsW * j, c->d_ezero + kEnsW * j};
-    if (spe)
-      launch(k4_spe_gram<kEnsSpe>, std::max(1, std::min(nblk(nf), c->sms)), kBlock, st, c->M64, nf,
-             (const double4_32a*)c->d_eX, c->d_eW, (const double4_32a*)c->d_eR, (const long long*)c->d_estepcount,
-             s, j, c->d_eG, c->d_espart, c->red.counter, c->red.max_blocks, 1e-12, c->d_ecoef);
+    if (spe) ens_spe_gram(c, st, s, j);
     if (c->direct)
       stt = ens_pcg_direct(c, c->d_eR, eFbuf(c, j), tol2, sl, spe);
     else
@@ -1502,6 +1563,7 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
   CK(upload(c, &c->d_mtop, mtop.data(), mtop.size()));
   CK(upload_sell(c, Mff, c->M64, false));  // CG kernels use one thread per row (DIA or SELL)
   c->d_M_hi = c->d_M_lo = nullptr;
+  c->d_M_rs = nullptr;
   c->d_z32 = nullptr;
   if (mixed(c) && c->opts.split_m) {  // M_ff = hi + lo in FP32 parts, same layout
     std::vector<double> mv((size_t)c->M64.stored);
@@ -1514,6 +1576,11 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     CK(upload(c, &c->d_M_hi, mh.data(), mh.size()));
     CK(upload(c, &c->d_M_lo, ml.data(), ml.size()));
     CK(dalloc(c, &c->d_z32, std::max<int64_t>(nf, 1)));
+    CK(dalloc(c, &c->d_M_rs, std::max<int64_t>(nf, 1)));
+    if (nf > 0) {
+      k_rowsum_split<<<nblk(nf), kBlock>>>(c->M64, c->d_M_hi, c->d_M_lo, (int)nf, c->d_M_rs);
+      CK(cudaGetLastError());
+    }
   }
   CK(upload(c, &c->d_coarse_inv, inv.data(), inv.size()));
   c->d_cinv_hi = c->d_cinv_lo = c->d_cinv32 = nullptr;
@@ -1603,6 +1670,8 @@ eqs_status eqs_amg_setup(eqs_ctx* c, const eqs_opts* opts) {
     CK(dalloc(c, &c->d_stepcount, 2));
     CK(dalloc(c, &c->d_sh, 1));
     CK(dalloc(c, &c->d_mlp_used, EQS_MAX_STAGES + 1));
+    CK(dalloc(c, &c->d_x0, nf));
+    CK(dalloc(c, &c->d_alpha, 1));
     CK(dalloc(c, &c->d_rtmp, nf));
     CK(dalloc(c, &c->d_xsave, n));
     CK(dalloc(c, &c->d_Fnew, nf));
@@ -1767,6 +1836,7 @@ eqs_status eqs_rkc_step(eqs_ctx* c, double* x, double t, double dt, int s, eqs_s
   if (!x) return fail(c, EQS_ERR_ARG, "x is NULL");
   if (s < 2 || s > EQS_MAX_STAGES) return fail(c, EQS_ERR_ARG, "s out of range [2, 64]");
   if (!std::isfinite(t) || !(dt > 0) || !std::isfinite(dt)) return fail(c, EQS_ERR_ARG, "bad t or dt");
+  if (c->recording && !recording_e(c)) c->store_e_valid = false;  // no SPE start to measure from
   const StepParams prm{t, dt, x};
   if (c->opts.host_loop) {  // same kernels, CG loops driven from the host
     const int dkey = -s;
@@ -1830,7 +1900,7 @@ eqs_status eqs_get_step_stats(eqs_ctx* c, eqs_step_stats* stats) {
     else if (rr[j] > c->opts.rtol && res == EQS_OK) res = EQS_ERR_NOCONV;
   }
   stats->launches = c->last_step->fixed_kernels + c->last_step->per_iter_kernels * stats->total_iters;
-  if (c->opts.guess == EQS_GUESS_MLP) {
+  if (c->opts.guess == EQS_GUESS_MLP || c->opts.guess == EQS_GUESS_SPE_MLP) {
     int kept[EQS_MAX_STAGES];
     CK(cudaMemcpy(kept, c->d_mlp_used, s * sizeof(int), cudaMemcpyDeviceToHost));
     for (int j = 0; j < s; ++j) stats->guess_kept += kept[j];
@@ -2002,9 +2072,7 @@ eqs_status eqs_launch_kernel(eqs_ctx* c, int kernel) {
       break;
     case EQS_KERNEL_ENS_SPE_GRAM:
       if (c->opts.guess != EQS_GUESS_SPE) return fail(c, EQS_ERR_STATE, "SPE start vectors are not in use");
-      launch(k4_spe_gram<kEnsSpe>, std::max(1, std::min(nblk(nf), c->sms)), kBlock, st, c->M64, nf,
-             (const double4_32a*)c->d_eX, c->d_eW, (const double4_32a*)c->d_eR, (const long long*)c->d_estepcount,
-             s, j, c->d_eG, c->d_espart, c->red.counter, c->red.max_blocks, 1e-12, c->d_ecoef);
+      ens_spe_gram(c, st, s, j);
       break;
     case EQS_KERNEL_ENS_ELEM:
       if (c->n_cells > 0)
@@ -2016,7 +2084,8 @@ eqs_status eqs_launch_kernel(eqs_ctx* c, int kernel) {
                (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi, (const float4*)c->d_xyz_lo,
                (const float4*)c->d_eY2, nf, c->d_ktime);
       break;
-    case EQS_KERNEL_ENS_PCG_PQ:
+    case EQS_KERNEL_ENS_PCG_PQ:  // as in a pass with all four columns active
+      CK(cudaMemsetAsync(((EnsScalars*)c->d_esc)->conv, 0, sizeof(int) * kEnsW, st));
       launch(k4_pcg_pq, g, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo, nf,
              (const float4*)c->d_ez32, c->d_ep, c->d_eq, (EnsScalars*)c->d_esc, c->d_epart, c->red.counter,
              c->red.max_blocks);
@@ -2104,6 +2173,37 @@ eqs_status eqs_ens_solve_M(eqs_ctx* c, const double* rhs, double* z, int* iters_
   return res;
 }
 
+eqs_status eqs_ens_spe_eval(eqs_ctx* c, const double* X, const double* b, double* x0, double* r0) {
+  REQUIRE_SETUP(c);
+  if (!X || !b || !x0 || !r0) return fail(c, EQS_ERR_ARG, "null vector");
+  const eqs_status as = ens_alloc(c);
+  if (as != EQS_OK) return as;
+  const int nf = (int)c->n_free;
+  cudaStream_t st = c->stream;
+  TmpBuf<long long> tcnt;
+  CK(tcnt.alloc(2));
+  const long long zero2[2] = {0, 1};  // stepcount 0: solve index g = j
+  CK(cudaMemcpyAsync(tcnt.p, zero2, sizeof(zero2), cudaMemcpyHostToDevice, st));
+  PtrRestore<long long> restore{&c->d_estepcount, c->d_estepcount};
+  c->d_estepcount = tcnt.p;
+  k4_interleave_pair<<<nblk(nf), kBlock, 0, st>>>(nf, b, c->d_eR, c->d_eR2);
+  // push the history oldest first (solution q into slot q), updating the
+  // Gram matrices as the step does, then form the start of the solve g = NH
+  for (int q = 0; q < kEnsSpe; ++q) {
+    const double* col = X + (size_t)(kEnsSpe - 1 - q) * kEnsW * nf;
+    k4_interleave_pair<<<nblk(nf), kBlock, 0, st>>>(nf, col, c->d_eX + (size_t)q * nf,
+                                                    c->d_eX2 + (size_t)q * 2 * nf);
+    ens_spe_gram(c, st, 1, q + 1);
+  }
+  EnsSlots sl{c->d_eiters, c->d_erelres, c->d_ezero};
+  ens_init_launch(c, st, c->d_eR, c->d_esol, 0.0, 0, 0, sl, true);
+  k4_deinterleave<<<nblk(nf), kBlock, 0, st>>>(nf, c->d_esol, x0);
+  k4_deinterleave<<<nblk(nf), kBlock, 0, st>>>(nf, c->d_er, r0);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
+  return EQS_OK;
+}
+
 double eqs_rkc_dt_bound(const eqs_ctx* c, int s) {
   if (!c || !c->have_materials || s < 2 || s > EQS_MAX_STAGES) return -1.0;
   std::vector<double> mu, nu, mut, gt, cj;
@@ -2151,11 +2251,14 @@ eqs_status eqs_amg_aggregates(const eqs_ctx* c, int level, int32_t* agg_out) {
 eqs_status eqs_set_guess(eqs_ctx* c, int mode) {
   REQUIRE_SETUP(c);
   if (mode != EQS_GUESS_PREV && mode != EQS_GUESS_MLP && mode != EQS_GUESS_ZERO && mode != EQS_GUESS_SPE &&
-      mode != EQS_GUESS_POD && mode != EQS_GUESS_POD2)
+      mode != EQS_GUESS_POD && mode != EQS_GUESS_POD2 && mode != EQS_GUESS_SPE_MLP)
     return fail(c, EQS_ERR_ARG, "unknown guess mode");
   if (mode != c->opts.guess) {
     destroy_graphs(c);
-    if (mode == EQS_GUESS_SPE || mode == EQS_GUESS_POD || mode == EQS_GUESS_POD2) {
+    // SPE and its learned correction share the rings: between them the history carries over
+    const bool spe_new = mode == EQS_GUESS_SPE || mode == EQS_GUESS_SPE_MLP;
+    const bool spe_old = c->opts.guess == EQS_GUESS_SPE || c->opts.guess == EQS_GUESS_SPE_MLP;
+    if ((spe_new && !spe_old) || mode == EQS_GUESS_POD || mode == EQS_GUESS_POD2) {
       // the solution rings / snapshot set start empty: restart the history
       CK(cudaStreamSynchronize(c->stream));
       CK(cudaMemset(c->d_stepcount, 0, 2 * sizeof(long long)));
@@ -2197,7 +2300,7 @@ eqs_status eqs_guess_record(eqs_ctx* c, int64_t capacity) {
   CK(cudaStreamSynchronize(c->stream));
   if (c->d_store) {
     for (auto it = c->allocs.begin(); it != c->allocs.end();)
-      if (*it == c->d_store || *it == c->d_store_rms) {
+      if (*it == c->d_store || *it == c->d_store_rms || *it == c->d_store_e || *it == c->d_store_rms_e) {
         cudaFree(*it);
         it = c->allocs.erase(it);
       } else {
@@ -2205,13 +2308,18 @@ eqs_status eqs_guess_record(eqs_ctx* c, int64_t capacity) {
       }
     c->d_store = nullptr;
     c->d_store_rms = nullptr;
+    c->d_store_e = nullptr;
+    c->d_store_rms_e = nullptr;
   }
   c->store_cap = 0;
   c->recording = false;
   c->recorded = 0;
   if (capacity == 0) return EQS_OK;
   CK(dalloc(c, &c->d_store, (size_t)capacity * (size_t)c->n_free, false));
+  CK(dalloc(c, &c->d_store_e, (size_t)capacity * (size_t)c->n_free, false));
   CK(dalloc(c, &c->d_store_rms, (size_t)capacity));
+  CK(dalloc(c, &c->d_store_rms_e, (size_t)capacity));
+  c->store_e_valid = true;
   CK(cudaMemset(c->d_stepcount, 0, 2 * sizeof(long long)));  // history index restarts at 0
   c->store_cap = capacity;
   c->recording = true;
@@ -2219,13 +2327,14 @@ eqs_status eqs_guess_record(eqs_ctx* c, int64_t capacity) {
 }
 
 static eqs_status train_batch(eqs_ctx* c, int count, int B, unsigned long long seed, long long step,
-                              const float* X, const float* T) {
+                              const float* X, const float* T, const float* store_e = nullptr) {
   const int S = kTrainBlock + 1;
   const size_t smem = sizeof(float) * (kNP + 3 + (size_t)S * (8 + 32 * 4 + 1));
   CK(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_mlp_train<<<nblk(B, kTrainBlock), kTrainBlock, smem, c->stream>>>(
       (int)c->n_free, c->d_store, c->d_store_rms, count, c->d_adj_ptr, c->d_adj_col, c->d_inv_deg,
-      (const __nv_bfloat16*)c->d_theta_bf16, c->d_grad, c->d_loss, seed, step, B, X, T);
+      (const __nv_bfloat16*)c->d_theta_bf16, c->d_grad, c->d_loss, seed, step, B, X, T, store_e,
+      (const float*)c->d_store_rms_e);
   CK(cudaGetLastError());
   return EQS_OK;
 }
@@ -2235,13 +2344,20 @@ eqs_status eqs_guess_train(eqs_ctx* c, int iters, int batch, float lr, uint64_t 
   REQUIRE_SETUP(c);
   if (iters < 1 || batch < 1 || !(lr > 0)) return fail(c, EQS_ERR_ARG, "bad training arguments");
   if (c->recorded < 5) return fail(c, EQS_ERR_STATE, "record at least 5 solutions first");
+  const bool spe = c->opts.guess == EQS_GUESS_SPE_MLP;  // train the correction of the SPE start
+  if (spe && !c->store_e_valid)
+    return fail(c, EQS_ERR_STATE, "the SPE correction trains on steps recorded with SPE start vectors");
   CK(cudaStreamSynchronize(c->stream));
   const int count = (int)c->recorded;
-  k_store_rms<<<count, kBlock, 0, c->stream>>>((int)c->n_free, c->d_store, c->d_store_rms);
+  if (spe)
+    k_store_rms_spe<<<count, kBlock, 0, c->stream>>>((int)c->n_free, c->d_store, c->d_store_e, c->d_store_rms,
+                                                      c->d_store_rms_e);
+  else
+    k_store_rms<<<count, kBlock, 0, c->stream>>>((int)c->n_free, c->d_store, c->d_store_rms);
   float lf = 0.f, ll = 0.f;
   for (int it = 0; it < iters; ++it) {
     CK(cudaMemsetAsync(c->d_loss, 0, sizeof(float), c->stream));
-    const eqs_status st = train_batch(c, count, batch, seed, it, nullptr, nullptr);
+    const eqs_status st = train_batch(c, count, batch, seed, it, nullptr, nullptr, spe ? c->d_store_e : nullptr);
     if (st != EQS_OK) return st;
     c->adam_t += 1;
     const float bc1 = 1.0f - std::pow(0.9f, (float)c->adam_t);
@@ -2281,6 +2397,34 @@ eqs_status eqs_guess_grad(eqs_ctx* c, const float* X, const float* T, int B, flo
     if (e != cudaSuccess) st = fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
   }
   return st;
+}
+
+eqs_status eqs_guess_train_batches(eqs_ctx* c, const float* X, const float* T, int B, int n_batches, float lr,
+                                   float* losses) {
+  REQUIRE_SETUP(c);
+  if (!X || !T || B < 1 || n_batches < 1 || !(lr > 0)) return fail(c, EQS_ERR_ARG, "bad training arguments");
+  TmpBuf<float> tX, tT;
+  CK(tX.alloc((size_t)B * 8 * n_batches));
+  CK(tT.alloc((size_t)B * n_batches));
+  CK(cudaMemcpy(tX.p, X, (size_t)B * 8 * n_batches * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(tT.p, T, (size_t)B * n_batches * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemset(c->d_grad, 0, kNP * sizeof(float)));
+  for (int k = 0; k < n_batches; ++k) {
+    CK(cudaMemsetAsync(c->d_loss, 0, sizeof(float), c->stream));
+    const eqs_status st = train_batch(c, 5, B, 0ull, 0, tX.p + (size_t)k * B * 8, tT.p + (size_t)k * B);
+    if (st != EQS_OK) return st;
+    c->adam_t += 1;  // the same update as eqs_guess_train
+    const float bc1 = 1.0f - std::pow(0.9f, (float)c->adam_t);
+    const float bc2 = 1.0f - std::pow(0.999f, (float)c->adam_t);
+    k_adam<<<nblk(kNP), kBlock, 0, c->stream>>>(c->d_theta, c->d_adam_m, c->d_adam_v, c->d_grad,
+                                                (__nv_bfloat16*)c->d_theta_bf16, lr, bc1, bc2);
+    if (losses) {
+      CK(cudaMemcpyAsync(losses + k, c->d_loss, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return EQS_OK;
 }
 
 eqs_status eqs_spe_eval(eqs_ctx* c, const double* X, const double* b, int n, double* x0) {
@@ -2394,6 +2538,38 @@ eqs_status eqs_guess_eval(eqs_ctx* c, const double* H, double* z0) {
   return EQS_OK;
 }
 
+eqs_status eqs_guess_eval_spe(eqs_ctx* c, const double* x0, const double* H, const double* R, double* z0) {
+  REQUIRE_SETUP(c);
+  if (!x0 || !H || !R || !z0) return fail(c, EQS_ERR_ARG, "null vector");
+  const int nf = (int)c->n_free;
+  cudaStream_t st = c->stream;
+  TmpBuf<float> tring;
+  TmpBuf<long long> tcnt;
+  TmpBuf<double> td, tq;
+  TmpBuf<int> tuse;
+  CK(tring.alloc(4 * (size_t)nf));
+  CK(tcnt.alloc(2));
+  CK(td.alloc(nf));
+  CK(tq.alloc(nf));
+  CK(tuse.alloc(1));
+  for (int l = 0; l < 4; ++l)  // solve index g = 4: h_l (l = 1..4) goes to slot (4 - l) % 4
+    k_push_solution<<<nblk(nf), kBlock, 0, st>>>(nf, H + (size_t)l * nf, tring.p + (size_t)((3 - l) & 3) * nf);
+  const long long four[2] = {4, 5};
+  const int one = 1;
+  CK(cudaMemcpyAsync(tcnt.p, four, sizeof(four), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(tuse.p, &one, sizeof(one), cudaMemcpyHostToDevice, st));
+  k_rms_diff<<<vec_grid(c, nf), kBlock, 0, st>>>(nf, x0, H, tuse.p, c->d_sh, c->red.partials, c->red.counter,
+                                                 c->red.max_blocks);
+  k_mlp_dir_spe<<<nblk(nf), kBlock, 0, st>>>(nf, x0, H, tring.p, tcnt.p, 0, tuse.p, c->d_adj_ptr, c->d_adj_col,
+                                             c->d_inv_deg, (const __nv_bfloat16*)c->d_theta_bf16, c->d_sh, td.p);
+  k_dir_alpha<<<vec_grid(c, nf), kBlock, 0, st>>>(c->M64, nf, td.p, nullptr, R, x0, tq.p, c->d_alpha,
+                                                  c->red.partials, c->red.counter, c->red.max_blocks);
+  k_axpy_alpha<<<nblk(nf), kBlock, 0, st>>>(nf, x0, td.p, c->d_alpha, z0);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(c, EQS_ERR_CUDA, cudaGetErrorString(e));
+  return EQS_OK;
+}
+
 // ------------------------------------------------------------- batches
 }  // extern "C"
 
@@ -2407,6 +2583,8 @@ struct eqs_batch {
   double *d_gtab = nullptr, *d_gptab = nullptr;
   double** d_x = nullptr;
   StepParams* d_params = nullptr;
+  long long* d_count = nullptr;       // solves before / after the current step (SPE history index)
+  long long max_spins = kMaxSpins;    // wait budget of one group barrier (polls)
   cudaStream_t stream = nullptr, cap = nullptr;
   std::map<int, GraphEntry> graphs;
   std::vector<void*> allocs;
@@ -2460,7 +2638,7 @@ static eqs_status batch_capture(eqs_batch* b, int s, GraphEntry& ge) {
   BCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
   cudaMemsetAsync(b->d_bars, 0, ninst * sizeof(GridBarrier), st);
   k_batch_drive<<<nblk((int64_t)ninst * (s + 1)), kBlock, 0, st>>>(ninst, s + 1, b->d_insts, d_cj, b->d_params,
-                                                                    b->d_gtab, b->d_gptab);
+                                                                    b->d_gtab, b->d_gptab, b->d_count);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
@@ -2477,7 +2655,7 @@ static eqs_status batch_capture(eqs_batch* b, int s, GraphEntry& ge) {
                        (const int*)b->d_first, (const int*)b->d_nblk, j, s, c0, first ? 0.0 : mu[j],
                        first ? 0.0 : nu[j], j == 0 ? 0.0 : mut[j], first ? 0.0 : gt[j],
                        (const StepParams*)b->d_params, (const double*)b->d_gtab, (const double*)b->d_gptab,
-                       (double* const*)b->d_x, tol2);
+                       (double* const*)b->d_x, tol2, (const long long*)b->d_count, b->max_spins);
   }
   k_batch_final<<<b->total_blocks, kPBlock, 0, st>>>(b->d_insts, b->d_blk2inst, b->d_first, b->d_nblk, s,
                                                     1.0 - mu[s] - nu[s], mu[s], nu[s], mut[s], gt[s],
@@ -2542,6 +2720,9 @@ eqs_status eqs_batch_create(eqs_ctx* const* ctxs, int n, int rows_per_block, eqs
     r += r / 4 + 1;
   }
   b->rows_per_block = r;
+  // SPE start vectors when every instance's context selects them
+  bool spe = true;
+  for (int k = 0; k < n; ++k) spe = spe && ctxs[k]->opts.guess == EQS_GUESS_SPE;
   b->blk2inst.resize(b->total_blocks);
   for (int k = 0; k < n; ++k)
     for (int q = 0; q < b->nblk[k]; ++q) b->blk2inst[b->first[k] + q] = k;
@@ -2573,6 +2754,9 @@ eqs_status eqs_batch_create(eqs_ctx* const* ctxs, int n, int rows_per_block, eqs
     I.V0 = c->V0;
     I.w = 2.0 * M_PI * c->freq;
     I.phase = c->phase;
+    I.X = spe ? c->d_spe_X : nullptr;
+    I.G = spe ? c->d_spe_G : nullptr;
+    I.coef = spe ? c->d_spe_y : nullptr;
   }
   cudaError_t e = cudaSetDevice(b->device);
   if (e == cudaSuccess) e = balloc(b, &b->d_bars, n);
@@ -2590,6 +2774,8 @@ eqs_status eqs_batch_create(eqs_ctx* const* ctxs, int n, int rows_per_block, eqs
   if (e == cudaSuccess) e = balloc(b, &b->d_gptab, (size_t)n * (EQS_MAX_STAGES + 1));
   if (e == cudaSuccess) e = balloc(b, &b->d_x, n);
   if (e == cudaSuccess) e = balloc(b, &b->d_params, 1);
+  if (e == cudaSuccess) e = balloc(b, &b->d_count, 2);
+  if (e == cudaSuccess) e = cudaMemset(b->d_count, 0, 2 * sizeof(long long));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     g_create_err = std::string("batch setup: ") + cudaGetErrorString(e);
@@ -2668,6 +2854,19 @@ eqs_status eqs_batch_info(const eqs_batch* b, int* total_blocks, int* rows_per_b
   if (!b) return bfail(nullptr, EQS_ERR_ARG, "batch is NULL");
   if (total_blocks) *total_blocks = b->total_blocks;
   if (rows_per_block) *rows_per_block = b->rows_per_block;
+  return EQS_OK;
+}
+
+eqs_status eqs_batch_set_barrier_polls(eqs_batch* b, long long polls) {
+  if (!b) return bfail(nullptr, EQS_ERR_ARG, "batch is NULL");
+  if (polls < 0) return bfail(b, EQS_ERR_ARG, "polls must be >= 0");
+  const long long v = polls == 0 ? kMaxSpins : polls;
+  if (v != b->max_spins) {  // the budget is an argument of the captured launches
+    BCK(cudaStreamSynchronize(b->stream));
+    for (auto& kv : b->graphs) destroy_graph(kv.second);
+    b->graphs.clear();
+    b->max_spins = v;
+  }
   return EQS_OK;
 }
 

@@ -215,7 +215,7 @@ __global__ void k_proj_start(DevSell<double> M, int nf, const double* __restrict
                              T inv_theta0, T* __restrict__ b0, T* __restrict__ x0, T* __restrict__ d0,
                              PcgScalars* sc, double* partials, unsigned int* counter, int max_blocks,
                              double tol2, int maxit, cudaGraphConditionalHandle h, int use_handle,
-                             int* iters_out, double* relres_out, int* zero_out) {
+                             int* iters_out, double* relres_out, int* zero_out, double* __restrict__ x_copy) {
   pdl_enter();
   const int m = *nuse;
   double y[NH];
@@ -234,8 +234,10 @@ __global__ void k_proj_start(DevSell<double> M, int nf, const double* __restrict
           mx = fma(y[k], W[(size_t)k * nf + i], mx);
         }
       x[i] = xi;
+      if (x_copy) x_copy[i] = xi;
     } else {
       mx = r ? mat_row<double>(M, i, nf, x) : 0.0;
+      if (x_copy) x_copy[i] = x[i];
     }
     if (!r) continue;
     const double Ri = R[i];

@@ -19,7 +19,7 @@ EQS_OK, EQS_ERR_ARG, EQS_ERR_MESH, EQS_ERR_CUDA = 0, -1, -2, -3
 EQS_ERR_NOCONV, EQS_ERR_TIMEOUT, EQS_ERR_NAN, EQS_ERR_STATE = -4, -5, -6, -7
 EQS_PREC_FP64, EQS_PREC_MIXED = 0, 1
 EQS_GUESS_PREV, EQS_GUESS_MLP, EQS_GUESS_ZERO, EQS_GUESS_SPE = 0, 1, 2, 3
-EQS_GUESS_POD, EQS_GUESS_POD2 = 4, 5
+EQS_GUESS_POD, EQS_GUESS_POD2, EQS_GUESS_SPE_MLP = 4, 5, 6
 EQS_MAX_STAGES = 64
 EQS_KERNEL_SPE_GRAM, EQS_KERNEL_ELEM, EQS_KERNEL_PCG_PQ = 0, 1, 2
 EQS_KERNEL_ENS_SPE_GRAM, EQS_KERNEL_ENS_ELEM, EQS_KERNEL_ENS_PCG_PQ = 16, 17, 18
@@ -116,11 +116,14 @@ def _declare(L):
         "eqs_guess_train": (I, [P, I, I, C.c_float, C.c_uint64, P, P]),
         "eqs_guess_grad": (I, [P, P, P, I, P, P]),
         "eqs_guess_eval": (I, [P, P, P]),
+        "eqs_guess_eval_spe": (I, [P, P, P, P, P]),
+        "eqs_guess_train_batches": (I, [P, P, P, I, I, C.c_float, P]),
         "eqs_spe_eval": (I, [P, P, P, I, P]),
         "eqs_batch_create": (I, [P, I, I, C.POINTER(C.c_void_p)]),
         "eqs_batch_rkc_step": (I, [P, P, D, D, I, C.POINTER(eqs_batch_stats)]),
         "eqs_batch_get_stats": (I, [P, C.POINTER(eqs_batch_stats), P]),
         "eqs_batch_info": (I, [P, P, P]),
+        "eqs_batch_set_barrier_polls": (I, [P, C.c_longlong]),
         "eqs_batch_destroy": (I, [P]),
         "eqs_batch_last_error": (C.c_char_p, [P]),
         "eqs_ens_rkc_step": (I, [P, P, P, D, D, I, C.POINTER(eqs_ens_stats)]),
@@ -128,6 +131,7 @@ def _declare(L):
         "eqs_ens_solve_M": (I, [P, P, P, P]),
         "eqs_pod_eval": (I, [P, P, I, P, P]),
         "eqs_launch_kernel": (I, [P, I]),
+        "eqs_ens_spe_eval": (I, [P, P, P, P, P]),
         "eqs_pod_info": (I, [P, P, P, P, P, P]),
         "eqs_rkc_adaptive_step": (I, [P, P, D, D, D, D, I, C.POINTER(eqs_adapt_stats)]),
         "eqs_destroy": (I, [P]),
@@ -301,6 +305,22 @@ def eqs_guess_grad(ctx, X, T):
     return g, loss.value
 
 
+def eqs_guess_train_batches(ctx, X, T, lr):
+    """X: (n_batches, B, 8), T: (n_batches, B) host arrays; returns the losses."""
+    X, pX = _host(X, np.float32)
+    T, pT = _host(T, np.float32)
+    nb, B = T.shape
+    if X.shape != (nb, B, 8):
+        raise ValueError("X must be (n_batches, B, 8)")
+    losses = np.empty(nb, dtype=np.float32)
+    _check(lib().eqs_guess_train_batches(ctx, pX, pT, B, nb, lr, losses.ctypes.data_as(C.c_void_p)), ctx)
+    return losses
+
+
+def eqs_guess_eval_spe(ctx, x0, H, R, z0):
+    _check(lib().eqs_guess_eval_spe(ctx, _dev(x0), _dev(H), _dev(R), _dev(z0)), ctx)
+
+
 def eqs_guess_eval(ctx, H, z0):
     _check(lib().eqs_guess_eval(ctx, _dev(H), _dev(z0)), ctx)
 
@@ -335,6 +355,10 @@ def eqs_batch_info(b):
     tb, rpb = C.c_int(), C.c_int()
     _bcheck(lib().eqs_batch_info(b, C.byref(tb), C.byref(rpb)), b)
     return tb.value, rpb.value
+
+
+def eqs_batch_set_barrier_polls(b, polls):
+    _bcheck(lib().eqs_batch_set_barrier_polls(b, polls), b)
 
 
 def eqs_batch_destroy(b):
@@ -381,6 +405,11 @@ def eqs_ens_solve_M(ctx, rhs, z):
     it = (C.c_int * EQS_ENS_W)()
     _check(lib().eqs_ens_solve_M(ctx, _dev(rhs), _dev(z), it), ctx)
     return list(it)
+
+
+def eqs_ens_spe_eval(ctx, X, b, x0, r0):
+    """X: CUDA float64 (6, 4, n_free) history (newest first); b, x0, r0: (4, n_free)."""
+    _check(lib().eqs_ens_spe_eval(ctx, _dev(X), _dev(b), _dev(x0), _dev(r0)), ctx)
 
 
 def eqs_launch_kernel(ctx, kernel):

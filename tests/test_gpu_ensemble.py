@@ -178,3 +178,42 @@ def test_ensemble_cell_and_tet_element_paths_agree(E):
     a, _, _ = _ens_run(E, p, SCALES, 10, 2, rtol=1e-12)
     b, _, _ = _ens_run(E, q, SCALES, 10, 2, rtol=1e-12)
     np.testing.assert_allclose(b, a, rtol=0, atol=1e-7 * np.abs(a).max())
+
+
+def test_ensemble_spe_start_matches_oracle_and_true_residual(E):
+    """The ensemble's SPE start (Eq. 4-5) from a given six-solution history:
+    x0 of every column against the oracle's projection, and the start
+    residual b - W y that the CG begins from against the true b - M x0
+    (W = M X comes from the Gram pass's FP32-pair products).  The history
+    carries a large constant offset: M is Laplace-type, so M x cancels to a
+    tiny fraction of sum |m_ij x_j|; the start residual must still agree
+    with the FP64 product to about FP64 rounding."""
+    from oracle import spe
+
+    p = ei.config_problem(2, N=12)
+    S = E.Solver(p, precision=MIXED, rtol=1e-10)
+    Sy = system.EQSSystem(p)
+    xyz = p.xyz[Sy.free]
+    nf = p.n_free
+    hist = np.empty((6, 4, nf))
+    for k in range(6):
+        for c in range(4):
+            w = 2 * np.pi / 0.1 * (1 + 0.3 * c)
+            hist[k, c] = (1e3 * (1 + c) + 40 * np.sin(w * xyz[:, 0] + 0.2 * k) * np.cos(w * xyz[:, 1])
+                          + 25 * (1 + 0.1 * k) * np.sin(w * xyz[:, 2] * 0.5 + c))
+    coef = np.array([1.9, -1.2, 0.5, -0.2, 0.05, -0.01])
+    rng = np.random.default_rng(4)
+    b = np.stack([Sy.Mff @ (np.tensordot(coef, hist[:, c], 1) + 5 * np.sin(9 * xyz[:, 0] / 0.1)
+                            + 0.5 * rng.standard_normal(nf)) for c in range(4)])
+    X = torch.tensor(hist, dtype=torch.float64, device="cuda")
+    bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+    x0 = torch.empty((4, nf), dtype=torch.float64, device="cuda")
+    r0 = torch.empty_like(x0)
+    E.eqs_ens_spe_eval(S.ctx, X, bd, x0, r0)
+    x0, r0 = x0.cpu().numpy(), r0.cpu().numpy()
+    for c in range(4):
+        ref = spe.spe_start(Sy.Mff, [hist[k, c] for k in range(6)], b[c])
+        assert np.linalg.norm(x0[c] - ref) <= 1e-7 * np.linalg.norm(ref), c
+        true_r = b[c] - Sy.Mff @ x0[c]
+        assert np.linalg.norm(r0[c] - true_r) <= 1e-11 * np.linalg.norm(b[c]), c
+    S.close()
