@@ -61,10 +61,11 @@ WORKLOAD = WORKLOADS[CONFIG_INDEX]
 # slower and stays off).
 SOLVER_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0, coarse_split=0, defer_sums=2)
 SPE_N = 6  # solutions spanning the SPE subspace
-# DRAM bytes (read + write) of one launch, per (kernel, workload), from a
-# one-kernel ncu capture of the current build (dram__bytes_read.sum +
-# dram__bytes_write.sum); a kernel without an entry reports null.
-TRAFFIC = {}
+# DRAM bytes (read + write) of one launch, per (kernel, workload), from an
+# ncu capture of the lone launches of the current build on the full 128^3
+# workload (dram__bytes_read.sum + dram__bytes_write.sum, mean of 20
+# launches); a kernel without an entry reports null.
+TRAFFIC = {("k4_spe_gram_df<6>", 2): 802385036, ("k4_elem32_cell", 2): 272317145, ("k4_pcg_pq", 2): 525365081}
 
 
 def parse():
