@@ -14,14 +14,6 @@ namespace eqs {
 constexpr int kBlock = 256;
 // DIA diagonals whose loads are issued together (8: a batch of 16 loads per
 // row; 16 measured no faster on GB300).
-template <typename T>
-struct DiaChunk {
-  static constexpr int v = 8;
-};
-template <>
-struct DiaChunk<float> {
-  static constexpr int v = 8;
-};
 constexpr int kDiaChunk = 8;
 
 // Programmatic dependent launch: wait until the preceding kernel of the
@@ -55,7 +47,7 @@ __device__ __forceinline__ T mat_row_impl(const DevSell<T>& A, int64_t tid, int 
     if (row >= n) return acc;
     const T* __restrict__ v = A.val + row;
     T acc1 = T(0);
-    constexpr int CH = DiaChunk<T>::v;
+    constexpr int CH = kDiaChunk;
     for (int d0 = 0; d0 < A.ndiag; d0 += CH) {
       T a[CH], xs[CH];
 #pragma unroll
@@ -740,7 +732,7 @@ __device__ __forceinline__ double mat_row_split(const DevSell<double>& A, const 
   float S = 0.0f, s = 0.0f;
   if (row >= n) return 0.0;
   if (A.G == 0) {  // chunks of diagonals: all loads before the sums
-    constexpr int CH = DiaChunk<float>::v;
+    constexpr int CH = kDiaChunk;
     for (int d0 = 0; d0 < A.ndiag; d0 += CH) {
       float ah[CH], al[CH], zz[CH];
 #pragma unroll
