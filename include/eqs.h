@@ -439,6 +439,14 @@ eqs_status eqs_ens_solve_M(eqs_ctx* ctx, const double* rhs, double* z, int* iter
  * no further product with M).  Synchronises.  For checking the pass. */
 eqs_status eqs_ens_spe_eval(eqs_ctx* ctx, const double* X, const double* b, double* x0, double* r0);
 
+/* The CG kernels of the mixed path widen FP32 values to FP64 with integer
+ * operations (GB300 executes the hardware conversion on its slow FP64 pipe).
+ * This call applies that widening to n values on the current device (f
+ * device float input, f_wide device double output) so it can be checked
+ * against the exact conversion.  Synchronises the device.  No counterpart
+ * in the paper. */
+eqs_status eqs_convert_check(const float* f, int n, double* f_wide);
+
 /* ---- One kernel of the step, launched alone (measurement).
  * Enqueues ONE launch of the named kernel of the last step
  * (eqs_rkc_step, or eqs_ens_rkc_step for the EQS_KERNEL_ENS_* ids) on the

@@ -552,7 +552,7 @@ __global__ void k4_pcg_dots(int n, const double4_32a* __restrict__ r, const doub
     const double4_32a ri = r[i], pi = rprev[i];
 #pragma unroll
     for (int c = 0; c < kEnsW; ++c) {
-      const double zc = (double)comp(zt, c);
+      const double zc = f2d(comp(zt, c));
       v[c] = fma(dc4(ri, c), zc, v[c]);
       v[kEnsW + c] = fma(dc4(pi, c), zc, v[kEnsW + c]);
     }
@@ -588,7 +588,7 @@ k4_post_first_dots(DevSell<float> A, int n, const float4* __restrict__ b, const 
       const double4_32a pi = rprev[i];
 #pragma unroll
       for (int c = 0; c < kEnsW; ++c) {
-        const double zc = (double)comp(zt, c);
+        const double zc = f2d(comp(zt, c));
         v[c] = fma(dc4(ri, c), zc, v[c]);
         v[kEnsW + c] = fma(dc4(pi, c), zc, v[kEnsW + c]);
       }
@@ -657,8 +657,8 @@ __global__ void k4_pcg_pq(DevSell<double> M, const float* __restrict__ Mhi, cons
 #pragma unroll
     for (int c = 0; c < kEnsW; ++c) {
       if (!act[c]) continue;
-      const double w = (double)S[c] + (double)s[c];
-      const double zc = (double)comp(zi, c);
+      const double w = f2d(S[c]) + f2d(s[c]);
+      const double zc = f2d(comp(zi, c));
       const double qn = fma(beta[c], dc4(qi, c), w);
       const double pn = fma(beta[c], dc4(pi, c), zc);
       set4(qi, c, qn);

@@ -24,6 +24,31 @@ __device__ __forceinline__ void pdl_enter() {
   cudaTriggerProgrammaticLaunchCompletion();
 }
 
+// FP32 -> FP64 widening by integer operations, exact (the same value as
+// (double)f, subnormal inputs normalised, infinities and NaN kept): GB300
+// executes the hardware conversion on its FP64 pipe (about 1/64 of the FP32
+// rate), which bounds the FP64-accumulating CG kernels; this runs on the
+// integer pipe with no hardware-conversion path to predicate in.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  const unsigned sh = m ? __clz(m) - 8u : 0u;  // subnormal: bring the leading one to bit 23
+  const unsigned ed = e == 0u ? (m ? 897u - sh : 0u) : (e == 0xFFu ? 0x7FFu : e + 896u);
+  const unsigned md = e == 0u ? ((m << sh) & 0x7FFFFFu) : m;
+  const unsigned hi = (u & 0x80000000u) | (ed << 20) | (md >> 3);
+  return __hiloint2double((int)hi, (int)(md << 29));
+}
+
+// Widening for the precision T of a V-cycle (float: f2d; double: as is).
+__device__ __forceinline__ double widen(float f) { return f2d(f); }
+__device__ __forceinline__ double widen(double d) { return d; }
+
+// Both conversions over arrays (for checking f2d against (double)f).
+__global__ void k_convert_check(int n, const float* __restrict__ f, double* __restrict__ f_wide) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f_wide[i] = f2d(f[i]);
+}
+
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
 
@@ -605,7 +630,7 @@ __global__ void k_pcg_dots(int n, const double* __restrict__ r, const double* __
   double v[2] = {0.0, 0.0};
   for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T zt = zpend ? z[i] + zpend[i] : z[i];
-    const double zi = (double)zt;
+    const double zi = widen(zt);
     if (z32)
       z32[i] = (float)zt;
     else
@@ -650,7 +675,7 @@ k_post_first_dots(DevSell<T> A, int n, const T* __restrict__ b, const T* __restr
       const int i = (int)(t >> A.logG);
       const T r = b[i] - (h ? a1 : a0);
       const T zt = x[i] + dinv[i] * r * inv_theta;
-      const double zi = (double)zt;
+      const double zi = widen(zt);
       if (z32)
         z32[i] = (float)zt;
       else
@@ -754,7 +779,7 @@ __device__ __forceinline__ double mat_row_split(const DevSell<double>& A, const 
     for (int64_t k = A.slice_ptr[sl] + lane; k < end; k += 32)
       df_acc(S, s, __ldg(hi + k), __ldg(lo + k), __ldg(z + __ldg(A.col + k)));
   }
-  return (double)S + (double)s;
+  return f2d(S) + f2d(s);
 }
 
 // k_pcg_pq with the split-M product: q = M z + beta q_old, p = z + beta p,
@@ -791,7 +816,7 @@ __global__ void k_pcg_pq_split(DevSell<double> M, const float* __restrict__ Mhi,
       const int64_t i = h ? i1 : i0;
       if (i >= n) continue;
       const double w = h ? w1 : w0;
-      const double zi = (double)z32[i];
+      const double zi = f2d(z32[i]);
       const double qi = beta == 0.0 ? w : fma(beta, q[i], w);
       const double pi = beta == 0.0 ? zi : fma(beta, p[i], zi);
       p[i] = pi;

@@ -2857,6 +2857,15 @@ eqs_status eqs_batch_info(const eqs_batch* b, int* total_blocks, int* rows_per_b
   return EQS_OK;
 }
 
+eqs_status eqs_convert_check(const float* f, int n, double* f_wide) {
+  if (!f || !f_wide || n < 0) return fail(nullptr, EQS_ERR_ARG, "bad conversion check arguments");
+  if (n == 0) return EQS_OK;
+  k_convert_check<<<nblk(n), kBlock>>>(n, f, f_wide);
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(nullptr, EQS_ERR_CUDA, cudaGetErrorString(e));
+  return EQS_OK;
+}
+
 eqs_status eqs_batch_set_barrier_polls(eqs_batch* b, long long polls) {
   if (!b) return bfail(nullptr, EQS_ERR_ARG, "batch is NULL");
   if (polls < 0) return bfail(b, EQS_ERR_ARG, "polls must be >= 0");

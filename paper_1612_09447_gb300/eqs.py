@@ -131,6 +131,7 @@ def _declare(L):
         "eqs_ens_solve_M": (I, [P, P, P, P]),
         "eqs_pod_eval": (I, [P, P, I, P, P]),
         "eqs_launch_kernel": (I, [P, I]),
+        "eqs_convert_check": (I, [P, I, P]),
         "eqs_ens_spe_eval": (I, [P, P, P, P, P]),
         "eqs_pod_info": (I, [P, P, P, P, P, P]),
         "eqs_rkc_adaptive_step": (I, [P, P, D, D, D, D, I, C.POINTER(eqs_adapt_stats)]),
@@ -410,6 +411,11 @@ def eqs_ens_solve_M(ctx, rhs, z):
 def eqs_ens_spe_eval(ctx, X, b, x0, r0):
     """X: CUDA float64 (6, 4, n_free) history (newest first); b, x0, r0: (4, n_free)."""
     _check(lib().eqs_ens_spe_eval(ctx, _dev(X), _dev(b), _dev(x0), _dev(r0)), ctx)
+
+
+def eqs_convert_check(f, f_wide):
+    """f (CUDA float32) -> f_wide (CUDA float64) with the kernels' widening."""
+    _check(lib().eqs_convert_check(_dev(f), f.numel(), _dev(f_wide)))
 
 
 def eqs_launch_kernel(ctx, kernel):

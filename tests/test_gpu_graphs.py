@@ -107,3 +107,23 @@ def test_launch_kernel(E):
     torch.cuda.synchronize()
     S.close()
     ref.close()
+
+
+def test_integer_widening_is_exact(E):
+    """The CG kernels' FP32 -> FP64 widening by integer operations equals the
+    exact conversion bit for bit: random values over the whole exponent
+    range, zeros of both signs, the smallest and largest normals,
+    subnormals, infinities and NaN."""
+    rng = np.random.default_rng(21)
+    n = 1 << 20
+    bits = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    f = bits.view(np.float32).copy()
+    edges = np.array([0.0, -0.0, 1.0, -1.5, np.finfo(np.float32).max, np.finfo(np.float32).tiny,
+                      np.float32(1e-40), -np.float32(1e-45), np.inf, -np.inf, np.nan], dtype=np.float32)
+    f[: len(edges)] = edges
+    want = f.astype(np.float64)
+    fw = torch.empty(n, dtype=torch.float64, device="cuda")
+    E.eqs_convert_check(torch.tensor(f, device="cuda"), fw)
+    got = fw.cpu().numpy()
+    ok = (got.view(np.uint64) == want.view(np.uint64)) | (np.isnan(got) & np.isnan(want))
+    assert ok.all(), f[~ok][:5]
