@@ -447,10 +447,14 @@ __device__ __forceinline__ double4_32a mat_row_d4(const DevSell<double>& A, int6
 }
 
 // The V-cycle input of a row from its four FP64 residuals.
+__device__ __forceinline__ float4 vc_f4(const double4_32a& v) {
+  return make_float4(vc_narrow(v.x), vc_narrow(v.y), vc_narrow(v.z), vc_narrow(v.w));
+}
+
 __device__ __forceinline__ void vc_input4(int64_t i, const double4_32a& r, const float* __restrict__ dinv0,
                                           float inv_theta0, float4* __restrict__ b0, float4* __restrict__ x0,
                                           float4* __restrict__ d0) {
-  const float4 bi = to_f4(r);
+  const float4 bi = vc_f4(r);
   b0[i] = bi;
   const float4 d = (dinv0[i] * inv_theta0) * bi;
   x0[i] = d;

@@ -39,6 +39,26 @@ __device__ __forceinline__ double f2d(float f) {
   return __hiloint2double((int)hi, (int)(md << 29));
 }
 
+// FP64 -> FP32 for a V-cycle input by integer operations: the mantissa is
+// truncated (not rounded), magnitudes below the FP32 normal range become
+// zero and those above it the largest FP32 value.  Only the preconditioner
+// sees these values (the flexible CG keeps r, x and the dot products in
+// FP64), so the truncation costs nothing in accuracy, and it keeps the
+// conversion off GB300's FP64 pipe.
+__device__ __forceinline__ float vc_narrow(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned mag = e <= 896u ? 0u : (e >= 1151u ? 0x7F7FFFFFu : ((e - 896u) << 23) | m);
+  return __uint_as_float((hi & 0x80000000u) | mag);
+}
+template <typename T>
+__device__ __forceinline__ T vc_in(double d);
+template <>
+__device__ __forceinline__ float vc_in<float>(double d) { return vc_narrow(d); }
+template <>
+__device__ __forceinline__ double vc_in<double>(double d) { return d; }
+
 // Widening for the precision T of a V-cycle (float: f2d; double: as is).
 __device__ __forceinline__ double widen(float f) { return f2d(f); }
 __device__ __forceinline__ double widen(double d) { return d; }
@@ -525,7 +545,7 @@ __global__ void k_pcg_init(DevSell<double> M, int n, const double* __restrict__ 
     const double Ri = R[i];
     const double ri = Ri - mat_row<double>(M, i, n, x);
     r[i] = ri;
-    const T bi = (T)ri;
+    const T bi = vc_in<T>(ri);
     b0[i] = bi;
     const T d = dinv0[i] * bi * inv_theta0;
     x0[i] = d;
@@ -569,7 +589,7 @@ __global__ void k_pcg_init_dual(DevSell<double> M, int n, const double* __restri
     const double r2 = Ri - mat_row<double>(M, i, n, h1);
     r[i] = r1;
     rtmp[i] = r2;
-    const T bi = (T)r1;
+    const T bi = vc_in<T>(r1);
     b0[i] = bi;
     const T d = dinv0[i] * bi * inv_theta0;
     x0[i] = d;
@@ -610,7 +630,7 @@ __global__ void k_pcg_select(int n, double* __restrict__ x, const double* __rest
     x[i] = h1[i];
     const double ri = rtmp[i];
     r[i] = ri;
-    const T bi = (T)ri;
+    const T bi = vc_in<T>(ri);
     b0[i] = bi;
     const T d = dinv0[i] * bi * inv_theta0;
     x0[i] = d;
@@ -865,7 +885,7 @@ __global__ void k_pcg_update(int n, double* __restrict__ x, double* __restrict__
     const double rn = fma(-a, q[i], ro);
     r[i] = rn;
     v[0] += rn * rn;
-    const T bi = (T)rn;
+    const T bi = vc_in<T>(rn);
     b0[i] = bi;
     const T d = dinv0[i] * bi * inv_theta0;
     x0[i] = d;
@@ -1806,7 +1826,7 @@ __device__ bool pcg_group_solve(const PPlan<T>& P, const GridCtx& g, const doubl
       const double Ri = R[i];
       const double ri = Ri - mat_row<double>(P.M, i, n, x);
       P.r[i] = ri;
-      const T bi = (T)ri;
+      const T bi = vc_in<T>(ri);
       L0.b[i] = bi;
       if (!single) {
         const T d = L0.dinv[i] * bi * L0.inv_theta;
@@ -1874,7 +1894,7 @@ __device__ bool pcg_group_solve(const PPlan<T>& P, const GridCtx& g, const doubl
         const double rn = fma(-alpha, P.q[i], ro);
         P.r[i] = rn;
         v[0] += rn * rn;
-        const T bi = (T)rn;
+        const T bi = vc_in<T>(rn);
         L0.b[i] = bi;
         if (!single) {
           const T d = L0.dinv[i] * bi * L0.inv_theta;

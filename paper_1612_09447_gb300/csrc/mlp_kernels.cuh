@@ -249,7 +249,7 @@ __global__ void k_dir_apply(int nf, double* __restrict__ x, double* __restrict__
     const double ri = fma(-a, q[i], r[i]);
     x[i] = xi;
     r[i] = ri;
-    const T bi = (T)ri;
+    const T bi = vc_in<T>(ri);
     b0[i] = bi;
     const T dd = dinv0[i] * bi * inv_theta0;
     x0v[i] = dd;

@@ -243,7 +243,7 @@ __global__ void k_proj_start(DevSell<double> M, int nf, const double* __restrict
     const double Ri = R[i];
     const double ri = Ri - mx;
     r[i] = ri;
-    const T bi = (T)ri;
+    const T bi = vc_in<T>(ri);
     b0[i] = bi;
     const T d = dinv0[i] * bi * inv_theta0;
     x0[i] = d;
