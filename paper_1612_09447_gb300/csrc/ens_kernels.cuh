@@ -878,7 +878,7 @@ k4_spe_gram_df(DevSell<double> M, const float* __restrict__ Mhi, const float* __
     }
     const float2 w0 = df_norm(A0, a0), w1 = df_norm(A1, a1);
     *reinterpret_cast<double2*>(wn + 4 * i + 2 * h) =
-        make_double2((double)w0.x + (double)w0.y, (double)w1.x + (double)w1.y);
+        make_double2(f2d(w0.x) + f2d(w0.y), f2d(w1.x) + f2d(w1.y));
     const float4 bi = __ldg(b2 + u);
 #pragma unroll
     for (int k = 0; k < NH; ++k) {
@@ -899,7 +899,7 @@ k4_spe_gram_df(DevSell<double> M, const float* __restrict__ Mhi, const float* __
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
-    double t = (double)S[k] + (double)e[k];
+    double t = f2d(S[k]) + f2d(e[k]);
 #pragma unroll
     for (int o = 16; o >= 2; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane < 2) wsum[warp][lane * NP + k] = t;
@@ -1135,10 +1135,20 @@ k4_elem32_cell(int64_t ncell, const int32_t* __restrict__ corner, const uint8_t*
     if (v[k] < n_limit) atomicAdd(y + v[k], acc[k]);
 }
 
+// The (hi, lo) FP32 pair of an FP64 value: hi truncated to FP32 by integer
+// operations, lo the truncated remainder (one FP64 subtraction; the pair
+// carries about 47 bits: the truncated tail of lo is below 2^-47 of the
+// value).  Magnitudes below the FP32 normal range pair to 0 (there below
+// 1e-38 in absolute terms).
+__device__ __forceinline__ float2 split_pair(double v) {
+  const float h = vc_narrow(v);
+  return make_float2(h, vc_narrow(v - f2d(h)));
+}
+
 __device__ __forceinline__ void store_split4(float4* __restrict__ Y2, int64_t i, const double4_32a& v) {
-  const float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z, hw = (float)v.w;
-  Y2[2 * i] = make_float4(hx, (float)(v.x - (double)hx), hy, (float)(v.y - (double)hy));
-  Y2[2 * i + 1] = make_float4(hz, (float)(v.z - (double)hz), hw, (float)(v.w - (double)hw));
+  const float2 x = split_pair(v.x), y = split_pair(v.y), z = split_pair(v.z), w = split_pair(v.w);
+  Y2[2 * i] = make_float4(x.x, x.y, y.x, y.y);
+  Y2[2 * i + 1] = make_float4(z.x, z.y, w.x, w.y);
 }
 
 // Four column-major columns (src + c n) into the interleaved FP64 layout and
@@ -1250,10 +1260,10 @@ __global__ void k4_rhs(int nf, float4* __restrict__ y32, const double* __restric
   const float4 y = y32[i];
   const double gm = (*gpj) * mtop[i];
   double4_32a r;
-  r.x = -(double)y.x - gm * colv[0];
-  r.y = -(double)y.y - gm * colv[1];
-  r.z = -(double)y.z - gm * colv[2];
-  r.w = -(double)y.w - gm * colv[3];
+  r.x = -f2d(y.x) - gm * colv[0];
+  r.y = -f2d(y.y) - gm * colv[1];
+  r.z = -f2d(y.z) - gm * colv[2];
+  r.w = -f2d(y.w) - gm * colv[3];
   R[i] = r;
   if (R2) store_split4(R2, i, r);
   y32[i] = zero4();
