@@ -105,17 +105,22 @@ __device__ __forceinline__ float4 mat_row4_impl(const DevSell<float>& A, int64_t
     k = A.slice_ptr[row] + g;
     end = A.slice_ptr[row + 1];
   }
-  for (; k < end; k += (int64_t)A.G * 2) {
-    int c[2];
-    float a[2];
+  // four entries per lane and round: the float4 gathers of long rows (AMG
+  // coarse operators, restriction) are latency bound
+  for (; k < end; k += (int64_t)A.G * 4) {
+    int c[4];
+    float a[4];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < 4; ++u) {
       const int64_t kk = k + (int64_t)A.G * u;
       c[u] = kk < end ? __ldg(A.col + kk) : 0;
       a[u] = kk < end ? __ldg(A.val + kk) : 0.f;
     }
+    float4 xs[4];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) acc = fma4(a[u], xv4<ADD>(x, xadd, c[u]), acc);
+    for (int u = 0; u < 4; ++u) xs[u] = xv4<ADD>(x, xadd, c[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc = fma4(a[u], xs[u], acc);
   }
   for (int o = A.G >> 1; o > 0; o >>= 1) acc = acc + shfl_xor4(acc, o);
   return acc;
