@@ -65,7 +65,7 @@ SPE_N = 6  # solutions spanning the SPE subspace
 # ncu capture of the lone launches of the current build on the full 128^3
 # workload (dram__bytes_read.sum + dram__bytes_write.sum, mean of 20
 # launches); a kernel without an entry reports null.
-TRAFFIC = {("k4_elem32_cell", 2): 272297472, ("k4_pcg_pq", 2): 524417740}
+TRAFFIC = {("k4_spe_gram_df", 2): 802092352, ("k4_elem32_cell", 2): 272297472, ("k4_pcg_pq", 2): 524417740}
 
 
 def parse():

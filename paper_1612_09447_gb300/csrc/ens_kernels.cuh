@@ -847,6 +847,11 @@ k4_spe_gram_df(DevSell<double> M, const float* __restrict__ Mhi, const float* __
     const int64_t i = u >> 1;
     const float4 xi = __ldg(xn + u);
     const float2 ri = __ldg(rs + i);
+    // the row's ring and right-hand-side loads go out before the SpMV rounds
+    float4 xpre[NH];
+#pragma unroll
+    for (int k = 0; k < NH; ++k) xpre[k] = __ldg(xs[k] + u);
+    const float4 bi = __ldg(b2 + u);
     float A0 = 0.f, a0 = 0.f, A1 = 0.f, a1 = 0.f;  // (M x_new) of the two columns, as pairs
     df_acc2(A0, a0, ri.x, ri.y, xi.x, xi.y);
     df_acc2(A1, a1, ri.x, ri.y, xi.z, xi.w);
@@ -884,11 +889,10 @@ k4_spe_gram_df(DevSell<double> M, const float* __restrict__ Mhi, const float* __
     const float2 w0 = df_norm(A0, a0), w1 = df_norm(A1, a1);
     *reinterpret_cast<double2*>(wn + 4 * i + 2 * h) =
         make_double2(f2d(w0.x) + f2d(w0.y), f2d(w1.x) + f2d(w1.y));
-    const float4 bi = __ldg(b2 + u);
 #pragma unroll
     for (int k = 0; k < NH; ++k) {
       if (k >= m) break;
-      const float4 xk = __ldg(xs[k] + u);
+      const float4 xk = xpre[k];
       df_acc2(S[k], e[k], xk.x, xk.y, w0.x, w0.y);
       df_acc2(S[NH + k], e[NH + k], xk.x, xk.y, bi.x, bi.y);
       df_acc2(S[2 * NH + k], e[2 * NH + k], xk.z, xk.w, w1.x, w1.y);
