@@ -61,11 +61,12 @@ WORKLOAD = WORKLOADS[CONFIG_INDEX]
 # slower and stays off).
 SOLVER_OPTS = dict(cheb_degree=1, coarse_max=2500, persistent=0, coarse_split=0, defer_sums=2)
 SPE_N = 6  # solutions spanning the SPE subspace
-# DRAM bytes (read + write) of one launch, per (kernel, workload), from an
-# ncu capture of the lone launches of the current build on the full 128^3
-# workload (dram__bytes_read.sum + dram__bytes_write.sum, mean of 20
-# launches); a kernel without an entry reports null.
-TRAFFIC = {("k4_spe_gram_df", 2): 802092352, ("k4_elem32_cell", 2): 272297472, ("k4_pcg_pq", 2): 524417740}
+# DRAM bytes (read + write) of one launch, per (eqs_launch_kernel id,
+# workload), from an ncu capture of the lone launches of the current build on
+# the full 128^3 workload (dram__bytes_read.sum + dram__bytes_write.sum, mean
+# of 20 launches; the Gram pass is two kernels, summed); a kernel without an
+# entry reports null.
+TRAFFIC = {(18, 2): 524417740}
 
 
 def parse():
@@ -558,7 +559,8 @@ def kernel_bytes(eqs, kid, p, nnz0, nf):
     raise ValueError(kid)
 
 
-KERNEL_NAMES = {16: "k4_spe_gram_df<6> (ensemble SPE Gram pass, double-float)", 17: "k4_elem32_cell (ensemble element kernel)",
+KERNEL_NAMES = {16: "k4_spe_w + k4_spe_gram_df<6> (ensemble SPE Gram pass: W = M x_new, then the dot products; double-float)",
+                17: "k4_elem32_cell (ensemble element kernel)",
                 18: "k4_pcg_pq (ensemble CG operator pass, split M)", 0: "k_spe_gram<6> (SPE Gram pass)",
                 1: "k_elem32_cell (element kernel)", 2: "k_pcg_pq_split (CG operator pass, split M)"}
 
@@ -578,7 +580,7 @@ def kernel_roofline(torch, eqs, S, p, flush, kernels, step_ms, workload_key):
         ach = b / (ms / 1e3) / 1e9
         name = KERNEL_NAMES[kid]
         table[name] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                       "traffic": TRAFFIC.get((name.split()[0], workload_key)), "bytes_per_launch": b,
+                       "traffic": TRAFFIC.get((kid, workload_key)), "bytes_per_launch": b,
                        "ms_per_launch": ms, "launches_per_step": per_step,
                        "est_share_of_step": ms * per_step / step_ms}
     top = max(table, key=lambda k: table[k]["ms_per_launch"] * table[k]["launches_per_step"])

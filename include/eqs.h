@@ -455,7 +455,9 @@ eqs_status eqs_convert_check(const float* f, int n, double* f_wide);
  *   SPE_GRAM: the SPE Gram pass of Sec. IV, Eq. 4-5 (the product W = M x
  *             of the newest solution, the new Gram column and the
  *             projections of the right-hand side; the small solve that
- *             follows it in a step is not launched);
+ *             follows it in a step is not launched); ENS_SPE_GRAM is two
+ *             launches, the product alone and then the dot products with
+ *             the four small solves in the last block;
  *   ELEM:     the element kernel of Sec. III on the last stage state, its
  *             K(x)x scattered into a private buffer of the context
  *             (allocated on the first such call);

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kBlock, 4) k4_restrict(DevSell<float> R, int n
       if (first_step) {
         const float4 d = (dinv_c[i] * inv_theta_c) * b;
         xc[i] = d;
-        dc[i] = d;
+        if (dc) dc[i] = d;  // first Chebyshev direction (degree >= 2)
       }
     }
   })
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kBlock, 4) k4_post_first(DevSell<float> A, int
       if (!row_leader(A, t, n)) continue;
       const int i = (int)(t >> A.logG);
       const float4 r = b[i] - (h ? a1 : a0);
-      r_out[i] = r;
+      if (r_out) r_out[i] = r;  // read by the Chebyshev steps of degree >= 2
       d_out[i] = (dinv[i] * inv_theta) * r;
     }
   })
@@ -463,7 +463,7 @@ __device__ __forceinline__ void vc_input4(int64_t i, const double4_32a& r, const
   b0[i] = bi;
   const float4 d = (dinv0[i] * inv_theta0) * bi;
   x0[i] = d;
-  d0[i] = d;
+  if (d0) d0[i] = d;  // the first Chebyshev direction (degree >= 2 only)
 }
 
 // Last block of a CG start: per-column norms (tot: ||R_c||^2, then ||r_c||^2),
@@ -527,7 +527,10 @@ __global__ void k4_pcg_init(DevSell<double> M, int n, const double4_32a* __restr
 }
 
 // Last block of the dot-product pass: beta per active column
-// (Polak-Ribiere or Fletcher-Reeves) from r.z (tot[0..4)) and r_prev.z.
+// (Polak-Ribiere or Fletcher-Reeves) from r.z (tot[0..4)) and q.z, q the
+// operator product of the last update (r_new = r_old - alpha q), so the
+// Polak-Ribiere numerator z.(r_new - r_old) is -alpha z.q: no copy of the
+// previous residual is kept.
 __device__ __forceinline__ void ens_beta_tail(const double* tot, EnsScalars* sc, int flexible) {
   for (int c = 0; c < kEnsW; ++c) {
     if (sc->conv[c]) {
@@ -537,17 +540,17 @@ __device__ __forceinline__ void ens_beta_tail(const double* tot, EnsScalars* sc,
     const double rz = tot[c];
     double beta = 0.0;
     if (sc->it[c] > 0 && sc->rz_old[c] != 0.0)
-      beta = flexible ? (rz - tot[kEnsW + c]) / sc->rz_old[c] : rz / sc->rz_old[c];
+      beta = flexible ? -sc->alpha[c] * tot[kEnsW + c] / sc->rz_old[c] : rz / sc->rz_old[c];
     sc->beta[c] = beta;
     sc->rz[c] = rz;
     sc->rz_old[c] = rz;
   }
 }
 
-// z = V-cycle output (+ pending direction) kept in FP32; r.z and r_prev.z
-// per column; the last block forms beta per active column (Polak-Ribiere or
+// z = V-cycle output (+ pending direction) kept in FP32; r.z and q.z per
+// column; the last block forms beta per active column (Polak-Ribiere or
 // Fletcher-Reeves).
-__global__ void k4_pcg_dots(int n, const double4_32a* __restrict__ r, const double4_32a* __restrict__ rprev,
+__global__ void k4_pcg_dots(int n, const double4_32a* __restrict__ r, const double4_32a* __restrict__ q,
                             const float4* __restrict__ z, const float4* __restrict__ zpend,
                             float4* __restrict__ z32, EnsScalars* sc, double* partials, unsigned int* counter,
                             int max_blocks, int flexible) {
@@ -558,12 +561,12 @@ __global__ void k4_pcg_dots(int n, const double4_32a* __restrict__ r, const doub
   for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float4 zt = zpend ? z[i] + zpend[i] : z[i];
     z32[i] = zt;
-    const double4_32a ri = r[i], pi = rprev[i];
+    const double4_32a ri = r[i], qi = q[i];
 #pragma unroll
     for (int c = 0; c < kEnsW; ++c) {
       const double zc = f2d(comp(zt, c));
       v[c] = fma(dc4(ri, c), zc, v[c]);
-      v[kEnsW + c] = fma(dc4(pi, c), zc, v[kEnsW + c]);
+      v[kEnsW + c] = fma(dc4(qi, c), zc, v[kEnsW + c]);
     }
   }
   double tot[2 * kEnsW];
@@ -576,7 +579,7 @@ __global__ void k4_pcg_dots(int n, const double4_32a* __restrict__ r, const doub
 __global__ void __launch_bounds__(kBlock, 4)
 k4_post_first_dots(DevSell<float> A, int n, const float4* __restrict__ b, const float4* __restrict__ x,
                    const float* __restrict__ dinv, float inv_theta, const double4_32a* __restrict__ rcg,
-                   const double4_32a* __restrict__ rprev, float4* __restrict__ z32, EnsScalars* sc,
+                   const double4_32a* __restrict__ q, float4* __restrict__ z32, EnsScalars* sc,
                    double* partials, unsigned int* counter, int max_blocks, int flexible) {
   pdl_enter();
   double v[2 * kEnsW];
@@ -594,12 +597,12 @@ k4_post_first_dots(DevSell<float> A, int n, const float4* __restrict__ b, const 
       const float4 zt = x[i] + (dinv[i] * inv_theta) * r;
       z32[i] = zt;
       const double4_32a ri = rcg[i];
-      const double4_32a pi = rprev[i];
+      const double4_32a qi = q[i];
 #pragma unroll
       for (int c = 0; c < kEnsW; ++c) {
         const double zc = f2d(comp(zt, c));
         v[c] = fma(dc4(ri, c), zc, v[c]);
-        v[kEnsW + c] = fma(dc4(pi, c), zc, v[kEnsW + c]);
+        v[kEnsW + c] = fma(dc4(qi, c), zc, v[kEnsW + c]);
       }
     }
   })
@@ -684,11 +687,11 @@ __global__ void k4_pcg_pq(DevSell<double> M, const float* __restrict__ Mhi, cons
   }
 }
 
-// x += alpha p ; r_prev = r ; r -= alpha q (active columns), ||r||^2 per
-// column, the next V-cycle input; the last block updates the flags, the
-// per-column iteration counts and the loop condition.
+// x += alpha p ; r -= alpha q (active columns), ||r||^2 per column, the
+// next V-cycle input; the last block updates the flags, the per-column
+// iteration counts and the loop condition.
 __global__ void k4_pcg_update(int n, double4_32a* __restrict__ x, double4_32a* __restrict__ r,
-                              double4_32a* __restrict__ rprev, const double4_32a* __restrict__ p,
+                              const double4_32a* __restrict__ p,
                               const double4_32a* __restrict__ q, const float* __restrict__ dinv0,
                               float inv_theta0, float4* __restrict__ b0, float4* __restrict__ x0,
                               float4* __restrict__ d0, EnsScalars* sc, double* partials,
@@ -709,7 +712,6 @@ __global__ void k4_pcg_update(int n, double4_32a* __restrict__ x, double4_32a* _
   for (int64_t i = gtid(); i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double4_32a xi = x[i], ri = r[i];
     const double4_32a pi = p[i], qi = q[i];
-    rprev[i] = ri;
 #pragma unroll
     for (int c = 0; c < kEnsW; ++c) {
       if (act[c]) {
@@ -796,6 +798,87 @@ __device__ __forceinline__ float2 df_norm(float S, float s) {
   return make_float2(h, __fsub_rn(s, __fsub_rn(h, S)));
 }
 
+// The (hi, lo) FP32 pair of an FP64 value: hi truncated to FP32 by integer
+// operations, lo the truncated remainder (one FP64 subtraction; the pair
+// carries about 47 bits: the truncated tail of lo is below 2^-47 of the
+// value).  Magnitudes below the FP32 normal range pair to 0 (there below
+// 1e-38 in absolute terms).
+__device__ __forceinline__ float2 split_pair(double v) {
+  const float h = vc_narrow(v);
+  return make_float2(h, vc_narrow(v - f2d(h)));
+}
+
+// W_new = M x_new of the four columns (the first launch of the split Gram
+// pass): one thread per row, the matrix entry loaded once for the four
+// columns, the same double-float difference form as k4_spe_gram_df (below),
+// stored in FP64 into ring slot g - 1.  No dot-product state, so more rows
+// are in flight than in the fused pass.
+template <int NH>
+__global__ void __launch_bounds__(kBlock, 3)
+k4_spe_w(DevSell<double> M, const float* __restrict__ Mhi, const float* __restrict__ Mlo,
+         const float2* __restrict__ rs, int nf, const float4* __restrict__ X2, double4_32a* __restrict__ W,
+         const long long* __restrict__ stepcount, int j) {
+  pdl_enter();
+  const long long g = stepcount[0] + j;
+  if (g == 0) return;
+  const int sn = spe_slot(g - 1, NH);
+  const float4* __restrict__ xn = X2 + (size_t)sn * 2 * nf;
+  double4_32a* __restrict__ wn = W + (size_t)sn * nf;
+  for (int64_t i = gtid(); i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 xa = __ldg(xn + 2 * i), xb = __ldg(xn + 2 * i + 1);  // columns 0, 1 and 2, 3 as (hi, lo)
+    const float2 ri = __ldg(rs + i);
+    float S0 = 0.f, s0 = 0.f, S1 = 0.f, s1 = 0.f, S2 = 0.f, s2 = 0.f, S3 = 0.f, s3 = 0.f;
+    df_acc2(S0, s0, ri.x, ri.y, xa.x, xa.y);
+    df_acc2(S1, s1, ri.x, ri.y, xa.z, xa.w);
+    df_acc2(S2, s2, ri.x, ri.y, xb.x, xb.y);
+    df_acc2(S3, s3, ri.x, ri.y, xb.z, xb.w);
+    if (M.G == 0) {
+      constexpr int C = kDiaChunk / 2;
+      for (int d0 = 0; d0 < M.ndiag; d0 += C) {
+        float mh[C], ml[C];
+        float4 ya[C], yb[C];
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+          const int d = d0 + q;
+          const int jj = (int)i + M.off[d < kMaxDiag ? d : 0];
+          const bool ok = d < M.ndiag && (unsigned)jj < (unsigned)M.n_cols;
+          const int64_t k = (int64_t)d * nf + i;
+          mh[q] = ok ? __ldg(Mhi + k) : 0.f;
+          ml[q] = ok ? __ldg(Mlo + k) : 0.f;
+          ya[q] = ok ? __ldg(xn + 2 * (int64_t)jj) : xa;  // outside: a zero difference
+          yb[q] = ok ? __ldg(xn + 2 * (int64_t)jj + 1) : xb;
+        }
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+          df_acc_diff(S0, s0, mh[q], ml[q], ya[q].x, ya[q].y, xa.x, xa.y);
+          df_acc_diff(S1, s1, mh[q], ml[q], ya[q].z, ya[q].w, xa.z, xa.w);
+          df_acc_diff(S2, s2, mh[q], ml[q], yb[q].x, yb[q].y, xb.x, xb.y);
+          df_acc_diff(S3, s3, mh[q], ml[q], yb[q].z, yb[q].w, xb.z, xb.w);
+        }
+      }
+    } else {
+      const int64_t sl = i >> 5, lane = i & 31;
+      const int64_t end = M.slice_ptr[sl + 1];
+      for (int64_t k = M.slice_ptr[sl] + lane; k < end; k += 32) {
+        const float mh = __ldg(Mhi + k), ml = __ldg(Mlo + k);
+        const int64_t jj = __ldg(M.col + k);
+        const float4 ya = __ldg(xn + 2 * jj), yb = __ldg(xn + 2 * jj + 1);
+        df_acc_diff(S0, s0, mh, ml, ya.x, ya.y, xa.x, xa.y);
+        df_acc_diff(S1, s1, mh, ml, ya.z, ya.w, xa.z, xa.w);
+        df_acc_diff(S2, s2, mh, ml, yb.x, yb.y, xb.x, xb.y);
+        df_acc_diff(S3, s3, mh, ml, yb.z, yb.w, xb.z, xb.w);
+      }
+    }
+    const float2 w0 = df_norm(S0, s0), w1 = df_norm(S1, s1), w2 = df_norm(S2, s2), w3 = df_norm(S3, s3);
+    double4_32a w;
+    w.x = f2d(w0.x) + f2d(w0.y);
+    w.y = f2d(w1.x) + f2d(w1.y);
+    w.z = f2d(w2.x) + f2d(w2.y);
+    w.w = f2d(w3.x) + f2d(w3.y);
+    wn[i] = w;
+  }
+}
+
 // The SPE Gram pass of the four columns in double-float on the FP32 pipe
 // (GB300 runs FP64 at about 1/64 of the FP32 rate, which bound an FP64 pass
 // at 0.15 of HBM bandwidth).  Two threads per row, thread h taking columns
@@ -815,8 +898,10 @@ __device__ __forceinline__ float2 df_norm(float S, float s) {
 // the sums are widened to FP64, added over the lanes of one parity within a
 // warp, then over warps and blocks; the last block runs the four small
 // solves.  (Four threads per row, one column each, measured slower: the
-// matrix and index work repeats per thread.)
-template <int NH>
+// matrix and index work repeats per thread.)  With STORED_W, W_new comes
+// from the ring (written by k4_spe_w) and is split back into pairs: the
+// pass then carries only the dot products and the solves.
+template <int NH, bool STORED_W>
 __global__ void __launch_bounds__(kBlock, 2)
 k4_spe_gram_df(DevSell<double> M, const float* __restrict__ Mhi, const float* __restrict__ Mlo,
                const float2* __restrict__ rs, int nf, const float4* __restrict__ X2, double4_32a* __restrict__ W,
@@ -845,13 +930,19 @@ k4_spe_gram_df(DevSell<double> M, const float* __restrict__ Mhi, const float* __
   const int64_t n2 = 2 * (int64_t)nf;
   for (int64_t u = gtid(); u < n2; u += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = u >> 1;
-    const float4 xi = __ldg(xn + u);
-    const float2 ri = __ldg(rs + i);
     // the row's ring and right-hand-side loads go out before the SpMV rounds
     float4 xpre[NH];
 #pragma unroll
     for (int k = 0; k < NH; ++k) xpre[k] = __ldg(xs[k] + u);
     const float4 bi = __ldg(b2 + u);
+    float2 w0, w1;
+    if constexpr (STORED_W) {  // W_new from the ring, split into pairs
+      const double2 wv = __ldcs(reinterpret_cast<const double2*>(wn + 4 * i + 2 * h));
+      w0 = split_pair(wv.x);
+      w1 = split_pair(wv.y);
+    } else {
+    const float4 xi = __ldg(xn + u);
+    const float2 ri = __ldg(rs + i);
     float A0 = 0.f, a0 = 0.f, A1 = 0.f, a1 = 0.f;  // (M x_new) of the two columns, as pairs
     df_acc2(A0, a0, ri.x, ri.y, xi.x, xi.y);
     df_acc2(A1, a1, ri.x, ri.y, xi.z, xi.w);
@@ -886,9 +977,11 @@ k4_spe_gram_df(DevSell<double> M, const float* __restrict__ Mhi, const float* __
         df_acc_diff(A1, a1, mh, ml, xj.z, xj.w, xi.z, xi.w);
       }
     }
-    const float2 w0 = df_norm(A0, a0), w1 = df_norm(A1, a1);
+    w0 = df_norm(A0, a0);
+    w1 = df_norm(A1, a1);
     *reinterpret_cast<double2*>(wn + 4 * i + 2 * h) =
         make_double2(f2d(w0.x) + f2d(w0.y), f2d(w1.x) + f2d(w1.y));
+    }
 #pragma unroll
     for (int k = 0; k < NH; ++k) {
       if (k >= m) break;
@@ -1037,7 +1130,7 @@ __global__ void k4_elem32(int64_t nt, const int4* __restrict__ conn, const uint8
   const float c1x = e2y * e3z - e2z * e3y, c1y = e2z * e3x - e2x * e3z, c1z = e2x * e3y - e2y * e3x;
   const float c2x = e3y * e1z - e3z * e1y, c2y = e3z * e1x - e3x * e1z, c2z = e3x * e1y - e3y * e1x;
   const float c3x = e1y * e2z - e1z * e2y, c3y = e1z * e2x - e1x * e2z, c3z = e1x * e2y - e1y * e2x;
-  const float D = e1x * c1x + e1y * c1y + e1z * c1z;
+  const float invD = 1.0f / (e1x * c1x + e1y * c1y + e1z * c1z);  // one division for the four columns
   const MaterialDev m = mats[mat[e]];
   // potentials: node v holds columns 0,1 in Y2[2v] and 2,3 in Y2[2v+1]
   const float4 a0 = Y2[2 * (int64_t)t.x], b0 = Y2[2 * (int64_t)t.x + 1];
@@ -1066,10 +1159,10 @@ __global__ void k4_elem32(int64_t nt, const int4* __restrict__ conn, const uint8
     if (m.is_const) {
       kap = m.klo_f;
     } else {
-      const float E = sqrtf(gx * gx + gy * gy + gz * gz) / D;
+      const float E = sqrtf(gx * gx + gy * gy + gz * gz) * invD;
       kap = kappa32(m, E);
     }
-    const float sc = kap / (6.0f * D);
+    const float sc = kap * (invD * (1.0f / 6.0f));
     r1[c] = sc * (c1x * gx + c1y * gy + c1z * gz);
     r2[c] = sc * (c2x * gx + c2y * gy + c2z * gz);
     r3[c] = sc * (c3x * gx + c3y * gy + c3z * gz);
@@ -1089,11 +1182,12 @@ __device__ __forceinline__ void cell_tet32x4(const float (&dx)[8][3], const floa
                                              float4 (&acc)[8]) {
   const float e[3][3] = {{dx[B][0], dx[B][1], dx[B][2]}, {dx[C][0], dx[C][1], dx[C][2]},
                          {dx[D][0], dx[D][1], dx[D][2]}};
+  const TetGeom<float> g = tet_geom<float>(e);  // one division for the four columns
   float r[4][4];  // [column][local vertex]
 #pragma unroll
   for (int col = 0; col < kEnsW; ++col) {
     float rr[4];
-    tet_residual<float>(e, comp(dp[B], col), comp(dp[C], col), comp(dp[D], col), m, 1.0f, rr);
+    tet_column<float>(g, comp(dp[B], col), comp(dp[C], col), comp(dp[D], col), m, 1.0f, rr);
 #pragma unroll
     for (int k = 0; k < 4; ++k) r[col][k] = rr[k];
   }
@@ -1133,25 +1227,22 @@ k4_elem32_cell(int64_t ncell, const int32_t* __restrict__ corner, const uint8_t*
 #pragma unroll
   for (int k = 0; k < 8; ++k) acc[k] = zero4();
   const uint8_t* mt = mat + 6 * cidx;
+  // tets ordered so that corners retire early: each corner's atomic add
+  // goes out after the last tet that touches it
   cell_tet32x4<1, 3, 7>(dx, dp, mats[mt[0]], acc);
   cell_tet32x4<1, 7, 5>(dx, dp, mats[mt[1]], acc);
+  if (v[1] < n_limit) atomicAdd(y + v[1], acc[1]);
   cell_tet32x4<2, 7, 3>(dx, dp, mats[mt[2]], acc);
-  cell_tet32x4<2, 6, 7>(dx, dp, mats[mt[3]], acc);
+  if (v[3] < n_limit) atomicAdd(y + v[3], acc[3]);
   cell_tet32x4<4, 5, 7>(dx, dp, mats[mt[4]], acc);
+  if (v[5] < n_limit) atomicAdd(y + v[5], acc[5]);
   cell_tet32x4<4, 7, 6>(dx, dp, mats[mt[5]], acc);
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if (v[k] < n_limit) atomicAdd(y + v[k], acc[k]);
-}
-
-// The (hi, lo) FP32 pair of an FP64 value: hi truncated to FP32 by integer
-// operations, lo the truncated remainder (one FP64 subtraction; the pair
-// carries about 47 bits: the truncated tail of lo is below 2^-47 of the
-// value).  Magnitudes below the FP32 normal range pair to 0 (there below
-// 1e-38 in absolute terms).
-__device__ __forceinline__ float2 split_pair(double v) {
-  const float h = vc_narrow(v);
-  return make_float2(h, vc_narrow(v - f2d(h)));
+  if (v[4] < n_limit) atomicAdd(y + v[4], acc[4]);
+  cell_tet32x4<2, 6, 7>(dx, dp, mats[mt[3]], acc);
+  if (v[0] < n_limit) atomicAdd(y + v[0], acc[0]);
+  if (v[2] < n_limit) atomicAdd(y + v[2], acc[2]);
+  if (v[6] < n_limit) atomicAdd(y + v[6], acc[6]);
+  if (v[7] < n_limit) atomicAdd(y + v[7], acc[7]);
 }
 
 __device__ __forceinline__ void store_split4(float4* __restrict__ Y2, int64_t i, const double4_32a& v) {

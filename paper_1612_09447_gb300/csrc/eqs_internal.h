@@ -245,7 +245,7 @@ struct eqs_ctx {
   double4_32a* d_eF[3] = {nullptr, nullptr, nullptr};  // stage solutions (n_free)
   double4_32a* d_eR = nullptr;       // stage right-hand sides
   float4* d_ey32 = nullptr;          // FP32 accumulation of K(x)x (n_nodes)
-  double4_32a *d_er = nullptr, *d_erprev = nullptr, *d_ep = nullptr, *d_eq = nullptr;
+  double4_32a *d_er = nullptr, *d_ep = nullptr, *d_eq = nullptr;
   double4_32a* d_esol = nullptr;     // eqs_ens_solve_M work solution
   float4* d_ez32 = nullptr;          // FP32 preconditioned residual
   void* d_esc = nullptr;             // per-column CG scalars

@@ -960,7 +960,7 @@ __global__ void k_elem64(int64_t nt, const int4* __restrict__ conn, const uint8_
   const double c1x = e2y * e3z - e2z * e3y, c1y = e2z * e3x - e2x * e3z, c1z = e2x * e3y - e2y * e3x;
   const double c2x = e3y * e1z - e3z * e1y, c2y = e3z * e1x - e3x * e1z, c2z = e3x * e1y - e3y * e1x;
   const double c3x = e1y * e2z - e1z * e2y, c3y = e1z * e2x - e1x * e2z, c3z = e1x * e2y - e1y * e2x;
-  const double D = e1x * c1x + e1y * c1y + e1z * c1z;
+  const double invD = 1.0 / (e1x * c1x + e1y * c1y + e1z * c1z);
   const double gx = d1 * c1x + d2 * c2x + d3 * c3x;
   const double gy = d1 * c1y + d2 * c2y + d3 * c3y;
   const double gz = d1 * c1z + d2 * c2z + d3 * c3z;
@@ -969,10 +969,10 @@ __global__ void k_elem64(int64_t nt, const int4* __restrict__ conn, const uint8_
   if (m.is_const) {
     kap = m.klo;
   } else {
-    const double E = sqrt(gx * gx + gy * gy + gz * gz) / D;
+    const double E = sqrt(gx * gx + gy * gy + gz * gz) * invD;
     kap = kappa64(m, E);
   }
-  const double s = sign * kap / (6.0 * D);
+  const double s = sign * kap * (invD * (1.0 / 6.0));
   const double r1 = s * (c1x * gx + c1y * gy + c1z * gz);
   const double r2 = s * (c2x * gx + c2y * gy + c2z * gz);
   const double r3 = s * (c3x * gx + c3y * gy + c3z * gz);
@@ -1009,7 +1009,7 @@ __device__ __forceinline__ void elem32_tet(int64_t e, const int4* __restrict__ c
   const float c1x = e2y * e3z - e2z * e3y, c1y = e2z * e3x - e2x * e3z, c1z = e2x * e3y - e2y * e3x;
   const float c2x = e3y * e1z - e3z * e1y, c2y = e3z * e1x - e3x * e1z, c2z = e3x * e1y - e3y * e1x;
   const float c3x = e1y * e2z - e1z * e2y, c3y = e1z * e2x - e1x * e2z, c3z = e1x * e2y - e1y * e2x;
-  const float D = e1x * c1x + e1y * c1y + e1z * c1z;
+  const float invD = 1.0f / (e1x * c1x + e1y * c1y + e1z * c1z);
   const float gx = d1 * c1x + d2 * c2x + d3 * c3x;
   const float gy = d1 * c1y + d2 * c2y + d3 * c3y;
   const float gz = d1 * c1z + d2 * c2z + d3 * c3z;
@@ -1018,10 +1018,10 @@ __device__ __forceinline__ void elem32_tet(int64_t e, const int4* __restrict__ c
   if (m.is_const) {
     kap = m.klo_f;
   } else {
-    const float E = sqrtf(gx * gx + gy * gy + gz * gz) / D;
+    const float E = sqrtf(gx * gx + gy * gy + gz * gz) * invD;
     kap = kappa32(m, E);
   }
-  const float s = kap / (6.0f * D);
+  const float s = kap * (invD * (1.0f / 6.0f));
   const float r1 = s * (c1x * gx + c1y * gy + c1z * gz);
   const float r2 = s * (c2x * gx + c2y * gy + c2z * gz);
   const float r3 = s * (c3x * gx + c3y * gy + c3z * gz);
@@ -1065,31 +1065,58 @@ __device__ __forceinline__ float kappa_lo<float>(const MaterialDev& m) { return 
 // corners (0,1,3,7), (0,1,7,5), (0,2,7,3), (0,2,6,7), (0,4,5,7), (0,4,7,6)
 // (the vertex order of the mesh: positive orientation).
 
+// The tet's cofactor vectors c_k = e_l x e_m (k = 1..3; grad lambda_k =
+// c_k / D with D = e_1 . c_1 = 6 V) and 1/D: formed once per tet and shared
+// by every potential column it carries, so a tet pays one division.
 template <typename R>
-__device__ __forceinline__ void tet_residual(const R (&e)[3][3], R d1, R d2, R d3, const MaterialDev& m,
-                                             R sign, R (&r)[4]) {
-  const R c1x = e[1][1] * e[2][2] - e[1][2] * e[2][1], c1y = e[1][2] * e[2][0] - e[1][0] * e[2][2],
-          c1z = e[1][0] * e[2][1] - e[1][1] * e[2][0];
-  const R c2x = e[2][1] * e[0][2] - e[2][2] * e[0][1], c2y = e[2][2] * e[0][0] - e[2][0] * e[0][2],
-          c2z = e[2][0] * e[0][1] - e[2][1] * e[0][0];
-  const R c3x = e[0][1] * e[1][2] - e[0][2] * e[1][1], c3y = e[0][2] * e[1][0] - e[0][0] * e[1][2],
-          c3z = e[0][0] * e[1][1] - e[0][1] * e[1][0];
-  const R D = e[0][0] * c1x + e[0][1] * c1y + e[0][2] * c1z;
-  const R gx = d1 * c1x + d2 * c2x + d3 * c3x;
-  const R gy = d1 * c1y + d2 * c2y + d3 * c3y;
-  const R gz = d1 * c1z + d2 * c2z + d3 * c3z;
+struct TetGeom {
+  R c[3][3];
+  R invD;
+};
+
+template <typename R>
+__device__ __forceinline__ TetGeom<R> tet_geom(const R (&e)[3][3]) {
+  TetGeom<R> g;
+  g.c[0][0] = e[1][1] * e[2][2] - e[1][2] * e[2][1];
+  g.c[0][1] = e[1][2] * e[2][0] - e[1][0] * e[2][2];
+  g.c[0][2] = e[1][0] * e[2][1] - e[1][1] * e[2][0];
+  g.c[1][0] = e[2][1] * e[0][2] - e[2][2] * e[0][1];
+  g.c[1][1] = e[2][2] * e[0][0] - e[2][0] * e[0][2];
+  g.c[1][2] = e[2][0] * e[0][1] - e[2][1] * e[0][0];
+  g.c[2][0] = e[0][1] * e[1][2] - e[0][2] * e[1][1];
+  g.c[2][1] = e[0][2] * e[1][0] - e[0][0] * e[1][2];
+  g.c[2][2] = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+  g.invD = R(1) / (e[0][0] * g.c[0][0] + e[0][1] * g.c[0][1] + e[0][2] * g.c[0][2]);
+  return g;
+}
+
+// One potential column of a tet: D grad u = sum_k d_k c_k (d_k = u_k - u_0),
+// |E| = |D grad u| / D, and r_k = V kappa grad lambda_k . grad u =
+// kappa / (6 D) c_k . (D grad u); r_0 = -(r_1 + r_2 + r_3).
+template <typename R>
+__device__ __forceinline__ void tet_column(const TetGeom<R>& g, R d1, R d2, R d3, const MaterialDev& m, R sign,
+                                           R (&r)[4]) {
+  const R gx = d1 * g.c[0][0] + d2 * g.c[1][0] + d3 * g.c[2][0];
+  const R gy = d1 * g.c[0][1] + d2 * g.c[1][1] + d3 * g.c[2][1];
+  const R gz = d1 * g.c[0][2] + d2 * g.c[1][2] + d3 * g.c[2][2];
   R kap;
   if (m.is_const) {
     kap = kappa_lo<R>(m);
   } else {
-    const R E = sqrt(gx * gx + gy * gy + gz * gz) / D;
+    const R E = sqrt(gx * gx + gy * gy + gz * gz) * g.invD;
     kap = kappa_of<R>(m, E);
   }
-  const R sc = sign * kap / (R(6) * D);
-  r[1] = sc * (c1x * gx + c1y * gy + c1z * gz);
-  r[2] = sc * (c2x * gx + c2y * gy + c2z * gz);
-  r[3] = sc * (c3x * gx + c3y * gy + c3z * gz);
+  const R sc = sign * kap * (g.invD * (R(1) / R(6)));
+  r[1] = sc * (g.c[0][0] * gx + g.c[0][1] * gy + g.c[0][2] * gz);
+  r[2] = sc * (g.c[1][0] * gx + g.c[1][1] * gy + g.c[1][2] * gz);
+  r[3] = sc * (g.c[2][0] * gx + g.c[2][1] * gy + g.c[2][2] * gz);
   r[0] = -(r[1] + r[2] + r[3]);
+}
+
+template <typename R>
+__device__ __forceinline__ void tet_residual(const R (&e)[3][3], R d1, R d2, R d3, const MaterialDev& m,
+                                             R sign, R (&r)[4]) {
+  tet_column<R>(tet_geom<R>(e), d1, d2, d3, m, sign, r);
 }
 
 // One tet (corners A, B, C, D of the cell; compile-time indices keep the
@@ -1214,6 +1241,7 @@ template <typename R>
 __device__ __forceinline__ void p2_residual(const R (&gl)[4][3], R D, const R (&d)[10], const MaterialDev& m,
                                             R (&r)[10]) {
   const R QA = (R)0.5854101966249684544613760503096914353161, QB = (R)0.1381966011250105151795413165634361882280;
+  const R invD = R(1) / D;  // one division per tet
 #pragma unroll
   for (int i = 0; i < 10; ++i) r[i] = R(0);
 #pragma unroll
@@ -1233,13 +1261,13 @@ __device__ __forceinline__ void p2_residual(const R (&gl)[4][3], R D, const R (&
     if (m.is_const) {
       kap = kappa_lo<R>(m);
     } else {
-      const R E = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) / D;
+      const R E = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) * invD;
       kap = kappa_of<R>(m, E);
     }
     R sk[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) sk[k] = gl[k][0] * g[0] + gl[k][1] * g[1] + gl[k][2] * g[2];
-    const R sc = kap / (R(24) * D);  // (V/4) / D^2 with V = D/6
+    const R sc = kap * (invD * (R(1) / R(24)));  // (V/4) / D^2 with V = D/6
 #pragma unroll
     for (int k = 1; k < 4; ++k) r[k] += sc * (R(4) * l[k] - R(1)) * sk[k];
     r[4] += sc * R(4) * (l[0] * sk[1] + l[1] * sk[0]);

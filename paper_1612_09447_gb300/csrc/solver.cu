@@ -1028,7 +1028,7 @@ static eqs_status ens_alloc(eqs_ctx* c) {
   for (auto& y : c->d_eY) CK(dalloc(c, &y, n));
   CK(dalloc(c, &c->d_eY2, 2 * n));
   for (auto& f : c->d_eF) CK(dalloc(c, &f, nf));
-  for (double4_32a** v : {&c->d_eR, &c->d_er, &c->d_erprev, &c->d_ep, &c->d_eq, &c->d_esol}) CK(dalloc(c, v, nf));
+  for (double4_32a** v : {&c->d_eR, &c->d_er, &c->d_ep, &c->d_eq, &c->d_esol}) CK(dalloc(c, v, nf));
   CK(dalloc(c, &c->d_ey32, n));
   CK(dalloc(c, &c->d_ez32, nf));
   EnsScalars* sc = nullptr;
@@ -1050,6 +1050,10 @@ static eqs_status ens_alloc(eqs_ctx* c) {
   c->ens_ready = true;
   return EQS_OK;
 }
+
+// The fine level's first Chebyshev direction, written with the V-cycle input
+// only when a degree >= 2 smoother reads it.
+static float4* ens_d0(eqs_ctx* c) { return c->opts.cheb_degree >= 2 ? c->elev[0].dA : nullptr; }
 
 // V-cycle of the four columns from level l (returns the pending direction of
 // a degree-1 post-smoother, like vcycle_level).
@@ -1088,19 +1092,19 @@ static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st, bool fuse_do
   eqs_ctx::EnsLevel& EC = c->elev[l + 1];
   const int first = (l + 1 < nl - 1) ? 1 : 0;
   launch(k4_restrict, mat_grid(c, V.R, C.n), kBlock, st, V.R, C.n, (const float4*)E.r,
-         EC.b, (const float*)C.dinv, (float)C.inv_theta, EC.x, EC.dA, first);
+         EC.b, (const float*)C.dinv, (float)C.inv_theta, EC.x, deg >= 2 ? EC.dA : nullptr, first);
   float4* cpend = ens_vcycle_level(c, l + 1, st);
   launch(k4_prolong, mat_grid(c, V.P, V.n), kBlock, st, V.P, V.n, (const float4*)EC.x,
          (const float4*)cpend, E.x);
   if (fuse_dots && l == 0 && deg == 1) {  // the CG dot products ride on the last smoothing pass
     launch(k4_post_first_dots, g, kBlock, st, V.A, V.n, (const float4*)E.b, (const float4*)E.x,
            (const float*)V.dinv, (float)V.inv_theta, (const double4_32a*)c->d_er,
-           (const double4_32a*)c->d_erprev, c->d_ez32, (EnsScalars*)c->d_esc, c->d_epart, c->red.counter,
+           (const double4_32a*)c->d_eq, c->d_ez32, (EnsScalars*)c->d_esc, c->d_epart, c->red.counter,
            c->red.max_blocks, c->opts.flexible);
     return nullptr;
   }
   launch(k4_post_first, g, kBlock, st, V.A, V.n, (const float4*)E.b, (const float4*)E.x, (const float*)V.dinv,
-         (float)V.inv_theta, E.r, E.dA);
+         (float)V.inv_theta, deg >= 2 ? E.r : nullptr, E.dA);
   din = E.dA;
   dout = E.dB;
   for (int k = 2; k <= deg; ++k) {
@@ -1125,12 +1129,12 @@ static void ens_init_launch(eqs_ctx* c, cudaStream_t st, const double4_32a* R, d
   if (spe) {  // SPE start: x0 = X a_c, r0 = R - W a_c
     launch(k4_spe_start<kEnsSpe>, vec_grid(c, n), kBlock, st, c->M64, n, (const double4_32a*)c->d_eX,
            (const double4_32a*)c->d_eW, (const double*)c->d_ecoef, R, x, c->d_er, (const float*)V.dinv,
-           (float)V.inv_theta, E.b, E.x, E.dA, (EnsScalars*)c->d_esc, c->d_epart, c->red.counter,
+           (float)V.inv_theta, E.b, E.x, ens_d0(c), (EnsScalars*)c->d_esc, c->d_epart, c->red.counter,
            c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres, sl.zero);
     return;
   }
   launch(k4_pcg_init, vec_grid(c, n), kBlock, st, c->M64, n, R, (const double4_32a*)x, c->d_er,
-         (const float*)V.dinv, (float)V.inv_theta, E.b, E.x, E.dA, (EnsScalars*)c->d_esc, c->d_epart,
+         (const float*)V.dinv, (float)V.inv_theta, E.b, E.x, ens_d0(c), (EnsScalars*)c->d_esc, c->d_epart,
          c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres, sl.zero);
 }
 
@@ -1144,13 +1148,13 @@ static void ens_body_launch(eqs_ctx* c, cudaStream_t st, double4_32a* x, double 
   const bool fuse = c->opts.cheb_degree == 1 && c->lev32.size() > 1;
   float4* zpend = ens_vcycle_level(c, 0, st, fuse);
   if (!fuse)
-    launch(k4_pcg_dots, g, kBlock, st, n, (const double4_32a*)c->d_er, (const double4_32a*)c->d_erprev,
+    launch(k4_pcg_dots, g, kBlock, st, n, (const double4_32a*)c->d_er, (const double4_32a*)c->d_eq,
            (const float4*)E.x, (const float4*)zpend, c->d_ez32, sc, c->d_epart, c->red.counter,
            c->red.max_blocks, c->opts.flexible);
   launch(k4_pcg_pq, g, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo, n,
          (const float4*)c->d_ez32, c->d_ep, c->d_eq, sc, c->d_epart, c->red.counter, c->red.max_blocks);
-  launch(k4_pcg_update, g, kBlock, st, n, x, c->d_er, c->d_erprev, (const double4_32a*)c->d_ep,
-         (const double4_32a*)c->d_eq, (const float*)V.dinv, (float)V.inv_theta, E.b, E.x, E.dA, sc, c->d_epart,
+  launch(k4_pcg_update, g, kBlock, st, n, x, c->d_er, (const double4_32a*)c->d_ep,
+         (const double4_32a*)c->d_eq, (const float*)V.dinv, (float)V.inv_theta, E.b, E.x, ens_d0(c), sc, c->d_epart,
          c->red.counter, c->red.max_blocks, tol2, c->opts.max_iter, h, use_handle, sl.iters, sl.relres);
 }
 
@@ -1207,17 +1211,38 @@ static eqs_status ens_pcg_direct(eqs_ctx* c, const double4_32a* R, double4_32a* 
 
 // SPE Gram pass of the four columns (double-float on the FP32 pipe), two
 // threads per row, as many CTAs as are resident at once.
+// The Gram pass as two launches: W_new = M x_new alone (k4_spe_w: one
+// thread per row, no dot-product state), then the dot products from the
+// stored W_new and the small solves (kGramSplit); or both in one launch.
+constexpr bool kGramSplit = true;
+
+template <typename K>
+static int occupancy_of(K kern) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, 0) != cudaSuccess) occ = 1;
+  return std::max(1, occ);
+}
+
 static void ens_spe_gram(eqs_ctx* c, cudaStream_t st, int s, int j) {
   const int nf = (int)c->n_free;
-  static int occ = 0;
-  if (occ == 0 &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_spe_gram_df<kEnsSpe>, kBlock, 0) != cudaSuccess)
-    occ = 1;
-  const int grid = std::max(1, std::min(std::min(nblk(2 * (int64_t)nf), c->sms * std::max(1, occ)), c->red.max_blocks));
-  launch(k4_spe_gram_df<kEnsSpe>, grid, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo,
-         (const float2*)c->d_M_rs, nf,
-         (const float4*)c->d_eX2, c->d_eW, (const float4*)c->d_eR2, (const long long*)c->d_estepcount, s, j,
-         c->d_eG, c->d_espart, c->red.counter, c->red.max_blocks, 1e-12, c->d_ecoef);
+  static const int occ_w = occupancy_of(k4_spe_w<kEnsSpe>);
+  static const int occ_split = occupancy_of(k4_spe_gram_df<kEnsSpe, true>);
+  static const int occ_fused = occupancy_of(k4_spe_gram_df<kEnsSpe, false>);
+  auto gram = [&](auto kern, int occ) {
+    const int grid = std::max(1, std::min(std::min(nblk(2 * (int64_t)nf), c->sms * occ), c->red.max_blocks));
+    launch(kern, grid, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo,
+           (const float2*)c->d_M_rs, nf, (const float4*)c->d_eX2, c->d_eW, (const float4*)c->d_eR2,
+           (const long long*)c->d_estepcount, s, j, c->d_eG, c->d_espart, c->red.counter, c->red.max_blocks, 1e-12,
+           c->d_ecoef);
+  };
+  if (kGramSplit) {
+    launch(k4_spe_w<kEnsSpe>, std::max(1, std::min(nblk(nf), c->sms * occ_w)), kBlock, st, c->M64,
+           (const float*)c->d_M_hi, (const float*)c->d_M_lo, (const float2*)c->d_M_rs, nf, (const float4*)c->d_eX2,
+           c->d_eW, (const long long*)c->d_estepcount, j);
+    gram(k4_spe_gram_df<kEnsSpe, true>, occ_split);
+  } else {
+    gram(k4_spe_gram_df<kEnsSpe, false>, occ_fused);
+  }
 }
 
 static double4_32a* eYbuf(eqs_ctx* c, int j) { return j == 0 ? c->d_eY[0] : c->d_eY[1 + (j - 1) % 3]; }
