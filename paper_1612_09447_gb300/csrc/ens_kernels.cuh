@@ -211,10 +211,13 @@ __global__ void __launch_bounds__(kBlock, 4) k4_prolong(DevSell<float> P, int nf
   })
 }
 
+// First post-smoothing step: d = D^-1 (b - A x) / theta into d_out, or with
+// write_iterate (degree-1 smoothing, nothing follows) the smoothed iterate
+// x + d, so the prolongation above gathers one vector instead of two.
 __global__ void __launch_bounds__(kBlock, 4) k4_post_first(DevSell<float> A, int n, const float4* __restrict__ b,
                                                            const float4* __restrict__ x, const float* __restrict__ dinv,
                                                            float inv_theta, float4* __restrict__ r_out,
-                                                           float4* __restrict__ d_out) {
+                                                           float4* __restrict__ d_out, int write_iterate) {
   pdl_enter();
   EQS_ROWS2(A, n, {
     const float4 a0 = mat_row4(A, t0, n, x);
@@ -226,7 +229,8 @@ __global__ void __launch_bounds__(kBlock, 4) k4_post_first(DevSell<float> A, int
       const int i = (int)(t >> A.logG);
       const float4 r = b[i] - (h ? a1 : a0);
       if (r_out) r_out[i] = r;  // read by the Chebyshev steps of degree >= 2
-      d_out[i] = (dinv[i] * inv_theta) * r;
+      const float4 d = (dinv[i] * inv_theta) * r;
+      d_out[i] = write_iterate ? x[i] + d : d;
     }
   })
 }

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_prolong(DevSell<T> P, int nf, con
 template <typename T>
 __global__ void __launch_bounds__(kBlock, 4) k_post_first(DevSell<T> A, int n, const T* __restrict__ b,
                              const T* __restrict__ x, const T* __restrict__ dinv, T inv_theta,
-                             T* __restrict__ r_out, T* __restrict__ d_out) {
+                             T* __restrict__ r_out, T* __restrict__ d_out, int write_iterate) {
   pdl_enter();
   EQS_ROWS2(A, n, {
     const T a0 = mat_row(A, t0, n, x);
@@ -319,8 +319,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_post_first(DevSell<T> A, int n, c
       if (!row_leader(A, t, n)) continue;
       const int i = (int)(t >> A.logG);
       const T r = b[i] - (h ? a1 : a0);
-      r_out[i] = r;
-      d_out[i] = dinv[i] * r * inv_theta;
+      if (r_out) r_out[i] = r;  // read by the Chebyshev steps of degree >= 2
+      const T d = dinv[i] * r * inv_theta;
+      d_out[i] = write_iterate ? x[i] + d : d;  // degree 1: the smoothed iterate
     }
   })
 }

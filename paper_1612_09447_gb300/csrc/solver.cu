@@ -307,8 +307,10 @@ static cudaError_t upload_levels(eqs_ctx* c, std::vector<DevLevel<T>>& L) {
 }
 
 // ------------------------------------------------------------ V-cycle
-// Returns the Chebyshev direction still to be added to the level's x (the
-// degree-1 post-smoother's d, folded into the consumer of x), or nullptr.
+// Returns where the level's result lives: V.x, or V.dA after degree-1
+// post-smoothing (the smoother writes the smoothed iterate there instead of
+// updating x in place, so the prolongation above gathers one vector);
+// nullptr when the fine level's last pass went into the CG dot products.
 template <typename T>
 static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStream_t st,
                        bool fuse_dots = false, bool defer = false) {
@@ -319,17 +321,17 @@ static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStrea
       if (c->d_cinv32) {  // FP32 inverse, FP32 row sums
         launch_smem(k_coarse_solve32<1>, nblk((int64_t)V.n * 32), kBlock, (size_t)c->cinv_ld * sizeof(float), st,
                     V.n, c->cinv_ld, (const float*)c->d_cinv32, (const float*)V.b, (float*)V.x);
-        return nullptr;
+        return V.x;
       }
       if (c->d_cinv_hi) {  // FP32-pair application of the split inverse
         launch_smem(k_coarse_solve_df<1>, nblk((int64_t)V.n * 32), kBlock, (size_t)V.n * sizeof(float), st, V.n,
                     (const float*)c->d_cinv_hi, (const float*)c->d_cinv_lo, (const float*)V.b, (float*)V.x);
-        return nullptr;
+        return V.x;
       }
     }
     launch_smem(k_coarse_solve<T>, nblk((int64_t)V.n * 32), kBlock, (size_t)V.n * sizeof(double), st, V.n,
                 c->d_coarse_inv, (const T*)V.b, V.x);
-    return nullptr;
+    return V.x;
   }
   const int deg = c->opts.cheb_degree;
   std::vector<double> c1, c2;
@@ -352,9 +354,8 @@ static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStrea
   const int first = (l + 1 < nl - 1) ? 1 : 0;
   launch(k_restrict<T>, mat_grid(c, V.R, C.n), kBlock, st, V.R, C.n, V.r, C.b,
          C.dinv, (T)C.inv_theta, C.x, C.dA, first);
-  T* cpend = vcycle_level(c, L, l + 1, st);
-  launch(k_prolong<T>, mat_grid(c, V.P, V.n), kBlock, st, V.P, V.n, C.x,
-         (const T*)cpend, V.x);
+  const T* xc = vcycle_level(c, L, l + 1, st);
+  launch(k_prolong<T>, mat_grid(c, V.P, V.n), kBlock, st, V.P, V.n, xc, (const T*)nullptr, V.x);
   if (fuse_dots && l == 0 && deg == 1) {  // the CG dot products ride on the last smoothing pass
     if (defer)
       launch(k_post_first_dots<T, true>, g, kBlock, st, V.A, V.n, (const T*)V.b, (const T*)V.x,
@@ -368,7 +369,8 @@ static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStrea
              (double*)nullptr);
     return nullptr;
   }
-  launch(k_post_first<T>, g, kBlock, st, V.A, V.n, V.b, V.x, V.dinv, (T)V.inv_theta, V.r, V.dA);
+  launch(k_post_first<T>, g, kBlock, st, V.A, V.n, V.b, V.x, V.dinv, (T)V.inv_theta, deg >= 2 ? V.r : nullptr,
+         V.dA, deg == 1 ? 1 : 0);
   din = V.dA;
   dout = V.dB;
   for (int k = 2; k <= deg; ++k) {
@@ -376,7 +378,7 @@ static T* vcycle_level(eqs_ctx* c, std::vector<DevLevel<T>>& L, int l, cudaStrea
            k == 2 ? 1 : 0);
     std::swap(din, dout);
   }
-  return deg == 1 ? V.dA : nullptr;
+  return deg == 1 ? V.dA : V.x;
 }
 
 // ------------------------------------------------------------- PCG
@@ -577,9 +579,9 @@ static void pcg_body_launch(eqs_ctx* c, std::vector<DevLevel<T>>& L, cudaStream_
   // deferred sums: the dot products of the fused smoothing pass and of the
   // operator pass are added by the kernel that consumes them
   const bool defer = fuse && c->d_z32 && (c->opts.defer_sums & 1);
-  T* zpend = vcycle_level(c, L, 0, st, fuse, defer);
+  const T* z = vcycle_level(c, L, 0, st, fuse, defer);
   if (!fuse)
-    launch(k_pcg_dots<T>, g, kBlock, st, n, c->d_r, c->d_rprev, V.x, (const T*)zpend, c->d_zd, c->d_z32,
+    launch(k_pcg_dots<T>, g, kBlock, st, n, c->d_r, c->d_rprev, z, (const T*)nullptr, c->d_zd, c->d_z32,
            c->d_sc, c->red.partials, c->red.counter, c->red.max_blocks, c->opts.flexible);
   if (defer) {
     const int g_dots = mat_grid(c, V.A, V.n);  // the grid of k_post_first_dots
@@ -1001,9 +1003,8 @@ static eqs_status vcycle_impl(eqs_ctx* c, std::vector<DevLevel<T>>& L, const dou
   DevLevel<T>& V = L[0];
   launch(k_to_T<T>, nblk(nf), kBlock, st, nf, r, V.b);
   if (L.size() > 1) launch(k_first_step<T>, nblk(nf), kBlock, st, nf, V.b, V.dinv, (T)V.inv_theta, V.x, V.dA);
-  T* zpend = vcycle_level(c, L, 0, st);
-  if (zpend) launch(k_axpy1<T>, nblk(nf), kBlock, st, nf, V.x, (const T*)zpend);
-  launch(k_from_T<T>, nblk(nf), kBlock, st, nf, V.x, z);
+  const T* res = vcycle_level(c, L, 0, st);
+  launch(k_from_T<T>, nblk(nf), kBlock, st, nf, res, z);
   CK(cudaGetLastError());
   return EQS_OK;
 }
@@ -1055,9 +1056,11 @@ static eqs_status ens_alloc(eqs_ctx* c) {
 // only when a degree >= 2 smoother reads it.
 static float4* ens_d0(eqs_ctx* c) { return c->opts.cheb_degree >= 2 ? c->elev[0].dA : nullptr; }
 
-// V-cycle of the four columns from level l (returns the pending direction of
-// a degree-1 post-smoother, like vcycle_level).
-static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st, bool fuse_dots = false) {
+// V-cycle of the four columns from level l; returns where the level's
+// result lives (E.x, or E.dA after degree-1 post-smoothing, which writes the
+// smoothed iterate there instead of updating E.x in place), nullptr when the
+// fine level's last pass went into the CG dot products.
+static const float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st, bool fuse_dots = false) {
   std::vector<DevLevel<float>>& L = c->lev32;
   const int nl = (int)L.size();
   DevLevel<float>& V = L[l];
@@ -1069,7 +1072,7 @@ static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st, bool fuse_do
     else
       launch_smem(k_coarse_solve_df<4>, nblk((int64_t)V.n * 32), kBlock, (size_t)V.n * sizeof(float4), st, V.n,
                   (const float*)c->d_cinv_hi, (const float*)c->d_cinv_lo, (const float*)E.b, (float*)E.x);
-    return nullptr;
+    return E.x;
   }
   const int deg = c->opts.cheb_degree;
   std::vector<double> c1, c2;
@@ -1093,9 +1096,8 @@ static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st, bool fuse_do
   const int first = (l + 1 < nl - 1) ? 1 : 0;
   launch(k4_restrict, mat_grid(c, V.R, C.n), kBlock, st, V.R, C.n, (const float4*)E.r,
          EC.b, (const float*)C.dinv, (float)C.inv_theta, EC.x, deg >= 2 ? EC.dA : nullptr, first);
-  float4* cpend = ens_vcycle_level(c, l + 1, st);
-  launch(k4_prolong, mat_grid(c, V.P, V.n), kBlock, st, V.P, V.n, (const float4*)EC.x,
-         (const float4*)cpend, E.x);
+  const float4* xc = ens_vcycle_level(c, l + 1, st);
+  launch(k4_prolong, mat_grid(c, V.P, V.n), kBlock, st, V.P, V.n, xc, (const float4*)nullptr, E.x);
   if (fuse_dots && l == 0 && deg == 1) {  // the CG dot products ride on the last smoothing pass
     launch(k4_post_first_dots, g, kBlock, st, V.A, V.n, (const float4*)E.b, (const float4*)E.x,
            (const float*)V.dinv, (float)V.inv_theta, (const double4_32a*)c->d_er,
@@ -1104,7 +1106,7 @@ static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st, bool fuse_do
     return nullptr;
   }
   launch(k4_post_first, g, kBlock, st, V.A, V.n, (const float4*)E.b, (const float4*)E.x, (const float*)V.dinv,
-         (float)V.inv_theta, deg >= 2 ? E.r : nullptr, E.dA);
+         (float)V.inv_theta, deg >= 2 ? E.r : nullptr, E.dA, deg == 1 ? 1 : 0);
   din = E.dA;
   dout = E.dB;
   for (int k = 2; k <= deg; ++k) {
@@ -1112,7 +1114,7 @@ static float4* ens_vcycle_level(eqs_ctx* c, int l, cudaStream_t st, bool fuse_do
            (float)c1[k], (float)c2[k], E.r, dout, E.x, k == 2 ? 1 : 0);
     std::swap(din, dout);
   }
-  return deg == 1 ? E.dA : nullptr;
+  return deg == 1 ? E.dA : E.x;
 }
 
 struct EnsSlots {
@@ -1146,10 +1148,10 @@ static void ens_body_launch(eqs_ctx* c, cudaStream_t st, double4_32a* x, double 
   const int g = vec_grid(c, n);
   EnsScalars* sc = (EnsScalars*)c->d_esc;
   const bool fuse = c->opts.cheb_degree == 1 && c->lev32.size() > 1;
-  float4* zpend = ens_vcycle_level(c, 0, st, fuse);
+  const float4* z = ens_vcycle_level(c, 0, st, fuse);
   if (!fuse)
     launch(k4_pcg_dots, g, kBlock, st, n, (const double4_32a*)c->d_er, (const double4_32a*)c->d_eq,
-           (const float4*)E.x, (const float4*)zpend, c->d_ez32, sc, c->d_epart, c->red.counter,
+           z, (const float4*)nullptr, c->d_ez32, sc, c->d_epart, c->red.counter,
            c->red.max_blocks, c->opts.flexible);
   launch(k4_pcg_pq, g, kBlock, st, c->M64, (const float*)c->d_M_hi, (const float*)c->d_M_lo, n,
          (const float4*)c->d_ez32, c->d_ep, c->d_eq, sc, c->d_epart, c->red.counter, c->red.max_blocks);
