@@ -160,3 +160,25 @@ def test_spe_correction_inputs_and_line_search():
     T = mlp.spe_target(z, x0)
     assert np.sqrt(np.mean(T * T)) == pytest.approx(1.0)
     np.testing.assert_allclose(T * np.sqrt(np.mean((z - x0) ** 2)), z - x0, rtol=1e-12, atol=0)
+
+
+def test_features_hand_computed_on_a_path_graph():
+    """Inputs of the previous-solution mode on the free path graph 0-1-2:
+    columns h1..h4 and their neighbour means, all divided by s_h = RMS(h1)
+    (values worked out by hand; a normalisation by another history vector
+    or a ring mean that counted the node itself would differ)."""
+    import scipy.sparse as sp
+
+    A = sp.csr_matrix(np.array([[0, 1, 0], [1, 0, 1], [0, 1, 0]], dtype=float))
+    H = [np.array([3.0, 0.0, 4.0]), np.array([1.0, 2.0, 3.0]), np.array([0.0, 0.0, 6.0]),
+         np.array([-2.0, 2.0, 0.0])]
+    X, s_h = mlp.features(A, H)
+    assert s_h == pytest.approx(math.sqrt(25.0 / 3.0), rel=1e-15)
+    means = [np.array([0.0, 3.5, 0.0]), np.array([2.0, 2.0, 2.0]), np.array([0.0, 3.0, 0.0]),
+             np.array([2.0, -1.0, 2.0])]
+    want = np.stack(H + means, axis=1) / math.sqrt(25.0 / 3.0)
+    np.testing.assert_allclose(X, want, rtol=1e-15, atol=0)
+    # z0 = h1 + s_h o: an output layer with bias b alone shifts h1 by s_h b
+    th = ei.mlp_init().astype(np.float64)
+    th[1376] = 0.5  # output bias (a BF16-exact value)
+    np.testing.assert_allclose(mlp.guess(th, A, H), H[0] + 0.5 * math.sqrt(25.0 / 3.0), rtol=1e-15)
