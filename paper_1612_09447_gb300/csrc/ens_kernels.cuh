@@ -1180,31 +1180,82 @@ __global__ void k4_elem32(int64_t nt, const int4* __restrict__ conn, const uint8
 
 // K(x)x for four columns on Kuhn cells (as k_elem32_cell): the cell's
 // corners, coordinates and four potentials loaded once, the six tets'
-// residuals summed per corner, one 16-byte atomic add per corner.
+// residuals summed per corner, one 16-byte atomic add per corner.  Columns
+// (0, 1) and (2, 3) travel as packed FP32 pairs: one f32x2 instruction
+// (__ffma2_rn, __fadd2_rn, __fmul2_rn; per component the same rounding as
+// the scalar operation) does the work of two columns.
+constexpr int kElemBlock4 = 128;  // threads per block of k4_elem32_cell (4 blocks per SM at 128 registers)
+
+__device__ __forceinline__ float2 bcast2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float4 cat2(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+// One tet (corners 0, B, C, D of the cell) into the corner sums; pa/pb hold
+// the corners' potential offsets to corner 0 of columns (0, 1) and (2, 3).
+// With d_l the offsets at B, C, D and c_k the cofactors, r_k = s c_k . g,
+// g = sum_l d_l c_l, s = kappa / (6 D), and r_0 = -(r_1 + r_2 + r_3).  For a
+// constant kappa this is r_k = sum_l G_kl d_l with G_kl = s c_k . c_l: the
+// 3x3 Gram matrix is formed once for the four columns; a field-dependent
+// kappa needs |g| per column, so there g is formed as written.
 template <int B, int C, int D>
-__device__ __forceinline__ void cell_tet32x4(const float (&dx)[8][3], const float4 (&dp)[8], const MaterialDev& m,
-                                             float4 (&acc)[8]) {
+__device__ __forceinline__ void cell_tet32x4(const float (&dx)[8][3], const float2 (&pa)[8], const float2 (&pb)[8],
+                                             const MaterialDev& m, float2 (&aa)[8], float2 (&ab)[8]) {
   const float e[3][3] = {{dx[B][0], dx[B][1], dx[B][2]}, {dx[C][0], dx[C][1], dx[C][2]},
                          {dx[D][0], dx[D][1], dx[D][2]}};
   const TetGeom<float> g = tet_geom<float>(e);  // one division for the four columns
-  float r[4][4];  // [column][local vertex]
-#pragma unroll
-  for (int col = 0; col < kEnsW; ++col) {
-    float rr[4];
-    tet_column<float>(g, comp(dp[B], col), comp(dp[C], col), comp(dp[D], col), m, 1.0f, rr);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) r[col][k] = rr[k];
+  float2 u1a, u2a, u3a, u1b, u2b, u3b;
+  if (m.is_const) {
+    const float s = m.klo_f * (g.invD * (1.0f / 6.0f));
+    const float2 G11 = bcast2(s * (g.c[0][0] * g.c[0][0] + g.c[0][1] * g.c[0][1] + g.c[0][2] * g.c[0][2]));
+    const float2 G12 = bcast2(s * (g.c[0][0] * g.c[1][0] + g.c[0][1] * g.c[1][1] + g.c[0][2] * g.c[1][2]));
+    const float2 G13 = bcast2(s * (g.c[0][0] * g.c[2][0] + g.c[0][1] * g.c[2][1] + g.c[0][2] * g.c[2][2]));
+    const float2 G22 = bcast2(s * (g.c[1][0] * g.c[1][0] + g.c[1][1] * g.c[1][1] + g.c[1][2] * g.c[1][2]));
+    const float2 G23 = bcast2(s * (g.c[1][0] * g.c[2][0] + g.c[1][1] * g.c[2][1] + g.c[1][2] * g.c[2][2]));
+    const float2 G33 = bcast2(s * (g.c[2][0] * g.c[2][0] + g.c[2][1] * g.c[2][1] + g.c[2][2] * g.c[2][2]));
+    u1a = __ffma2_rn(G11, pa[B], __ffma2_rn(G12, pa[C], __fmul2_rn(G13, pa[D])));
+    u2a = __ffma2_rn(G12, pa[B], __ffma2_rn(G22, pa[C], __fmul2_rn(G23, pa[D])));
+    u3a = __ffma2_rn(G13, pa[B], __ffma2_rn(G23, pa[C], __fmul2_rn(G33, pa[D])));
+    u1b = __ffma2_rn(G11, pb[B], __ffma2_rn(G12, pb[C], __fmul2_rn(G13, pb[D])));
+    u2b = __ffma2_rn(G12, pb[B], __ffma2_rn(G22, pb[C], __fmul2_rn(G23, pb[D])));
+    u3b = __ffma2_rn(G13, pb[B], __ffma2_rn(G23, pb[C], __fmul2_rn(G33, pb[D])));
+  } else {
+    const float2 C00 = bcast2(g.c[0][0]), C01 = bcast2(g.c[0][1]), C02 = bcast2(g.c[0][2]);
+    const float2 C10 = bcast2(g.c[1][0]), C11 = bcast2(g.c[1][1]), C12 = bcast2(g.c[1][2]);
+    const float2 C20 = bcast2(g.c[2][0]), C21 = bcast2(g.c[2][1]), C22 = bcast2(g.c[2][2]);
+    const float2 gxa = __ffma2_rn(pa[B], C00, __ffma2_rn(pa[C], C10, __fmul2_rn(pa[D], C20)));
+    const float2 gya = __ffma2_rn(pa[B], C01, __ffma2_rn(pa[C], C11, __fmul2_rn(pa[D], C21)));
+    const float2 gza = __ffma2_rn(pa[B], C02, __ffma2_rn(pa[C], C12, __fmul2_rn(pa[D], C22)));
+    const float2 gxb = __ffma2_rn(pb[B], C00, __ffma2_rn(pb[C], C10, __fmul2_rn(pb[D], C20)));
+    const float2 gyb = __ffma2_rn(pb[B], C01, __ffma2_rn(pb[C], C11, __fmul2_rn(pb[D], C21)));
+    const float2 gzb = __ffma2_rn(pb[B], C02, __ffma2_rn(pb[C], C12, __fmul2_rn(pb[D], C22)));
+    // |E| = |g| / D per column, kappa(|E|), s = kappa / (6 D)
+    const float2 na = __ffma2_rn(gxa, gxa, __ffma2_rn(gya, gya, __fmul2_rn(gza, gza)));
+    const float2 nb = __ffma2_rn(gxb, gxb, __ffma2_rn(gyb, gyb, __fmul2_rn(gzb, gzb)));
+    const float q = g.invD * (1.0f / 6.0f);
+    const float2 sa = make_float2(kappa32(m, sqrtf(na.x) * g.invD) * q, kappa32(m, sqrtf(na.y) * g.invD) * q);
+    const float2 sb = make_float2(kappa32(m, sqrtf(nb.x) * g.invD) * q, kappa32(m, sqrtf(nb.y) * g.invD) * q);
+    u1a = __fmul2_rn(sa, __ffma2_rn(C00, gxa, __ffma2_rn(C01, gya, __fmul2_rn(C02, gza))));
+    u2a = __fmul2_rn(sa, __ffma2_rn(C10, gxa, __ffma2_rn(C11, gya, __fmul2_rn(C12, gza))));
+    u3a = __fmul2_rn(sa, __ffma2_rn(C20, gxa, __ffma2_rn(C21, gya, __fmul2_rn(C22, gza))));
+    u1b = __fmul2_rn(sb, __ffma2_rn(C00, gxb, __ffma2_rn(C01, gyb, __fmul2_rn(C02, gzb))));
+    u2b = __fmul2_rn(sb, __ffma2_rn(C10, gxb, __ffma2_rn(C11, gyb, __fmul2_rn(C12, gzb))));
+    u3b = __fmul2_rn(sb, __ffma2_rn(C20, gxb, __ffma2_rn(C21, gyb, __fmul2_rn(C22, gzb))));
   }
-  acc[0] = acc[0] + make_float4(r[0][0], r[1][0], r[2][0], r[3][0]);
-  acc[B] = acc[B] + make_float4(r[0][1], r[1][1], r[2][1], r[3][1]);
-  acc[C] = acc[C] + make_float4(r[0][2], r[1][2], r[2][2], r[3][2]);
-  acc[D] = acc[D] + make_float4(r[0][3], r[1][3], r[2][3], r[3][3]);
+  aa[B] = __fadd2_rn(aa[B], u1a);
+  aa[C] = __fadd2_rn(aa[C], u2a);
+  aa[D] = __fadd2_rn(aa[D], u3a);
+  aa[0] = __fadd2_rn(aa[0], neg2(__fadd2_rn(__fadd2_rn(u1a, u2a), u3a)));
+  ab[B] = __fadd2_rn(ab[B], u1b);
+  ab[C] = __fadd2_rn(ab[C], u2b);
+  ab[D] = __fadd2_rn(ab[D], u3b);
+  ab[0] = __fadd2_rn(ab[0], neg2(__fadd2_rn(__fadd2_rn(u1b, u2b), u3b)));
 }
 
 // Only the corners' offsets to corner 0 stay live across the six tets (all
-// share the diagonal 0-7): positions dx[k] and the four potentials dp[k],
-// each formed from the (hi, lo) FP32 pairs as (hi_k - hi_0) + (lo_k - lo_0).
-__global__ void __launch_bounds__(kBlock, 2)
+// share the diagonal 0-7): positions dx[k] and the potential pairs pa[k],
+// pb[k], each formed from the (hi, lo) FP32 pairs as (hi_k - hi_0) +
+// (lo_k - lo_0).
+__global__ void __launch_bounds__(kElemBlock4, 4)
 k4_elem32_cell(int64_t ncell, const int32_t* __restrict__ corner, const uint8_t* __restrict__ mat,
                const MaterialDev* __restrict__ mats, const float4* __restrict__ xh, const float4* __restrict__ xl,
                const float4* __restrict__ Y2, int n_limit, float4* __restrict__ y) {
@@ -1213,40 +1264,47 @@ k4_elem32_cell(int64_t ncell, const int32_t* __restrict__ corner, const uint8_t*
   if (cidx >= ncell) return;
   int v[8];
   float dx[8][3];
-  float4 dp[8], acc[8];
+  float2 pa[8], pb[8], aa[8], ab[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) v[k] = __ldg(corner + (int64_t)k * ncell + cidx);
   const float4 h0 = xh[v[0]], l0 = xl[v[0]], a0 = Y2[2 * (int64_t)v[0]], b0 = Y2[2 * (int64_t)v[0] + 1];
+  const float2 nh0 = make_float2(-h0.x, -h0.y), nl0 = make_float2(-l0.x, -l0.y);
+  const float2 na0 = make_float2(-a0.x, -a0.y), na1 = make_float2(-a0.z, -a0.w);
+  const float2 nb0 = make_float2(-b0.x, -b0.y), nb1 = make_float2(-b0.z, -b0.w);
 #pragma unroll
   for (int k = 1; k < 8; ++k) {
     const float4 h = xh[v[k]], l = xl[v[k]];
     const float4 a = Y2[2 * (int64_t)v[k]], b = Y2[2 * (int64_t)v[k] + 1];
-    dx[k][0] = (h.x - h0.x) + (l.x - l0.x);
-    dx[k][1] = (h.y - h0.y) + (l.y - l0.y);
+    const float2 dxy = __fadd2_rn(__fadd2_rn(make_float2(h.x, h.y), nh0), __fadd2_rn(make_float2(l.x, l.y), nl0));
+    dx[k][0] = dxy.x;
+    dx[k][1] = dxy.y;
     dx[k][2] = (h.z - h0.z) + (l.z - l0.z);
-    // columns 0, 1 in a as (hi, lo, hi, lo), columns 2, 3 in b
-    dp[k] = make_float4((a.x - a0.x) + (a.y - a0.y), (a.z - a0.z) + (a.w - a0.w), (b.x - b0.x) + (b.y - b0.y),
-                        (b.z - b0.z) + (b.w - b0.w));
+    // columns 0, 1 in a as (hi, lo, hi, lo), columns 2, 3 in b: the (hi, lo)
+    // differences of one column as a pair, then their sum
+    const float2 t0 = __fadd2_rn(make_float2(a.x, a.y), na0), t1 = __fadd2_rn(make_float2(a.z, a.w), na1);
+    const float2 t2 = __fadd2_rn(make_float2(b.x, b.y), nb0), t3 = __fadd2_rn(make_float2(b.z, b.w), nb1);
+    pa[k] = make_float2(t0.x + t0.y, t1.x + t1.y);
+    pb[k] = make_float2(t2.x + t2.y, t3.x + t3.y);
   }
 #pragma unroll
-  for (int k = 0; k < 8; ++k) acc[k] = zero4();
+  for (int k = 0; k < 8; ++k) aa[k] = ab[k] = make_float2(0.f, 0.f);
   const uint8_t* mt = mat + 6 * cidx;
   // tets ordered so that corners retire early: each corner's atomic add
   // goes out after the last tet that touches it
-  cell_tet32x4<1, 3, 7>(dx, dp, mats[mt[0]], acc);
-  cell_tet32x4<1, 7, 5>(dx, dp, mats[mt[1]], acc);
-  if (v[1] < n_limit) atomicAdd(y + v[1], acc[1]);
-  cell_tet32x4<2, 7, 3>(dx, dp, mats[mt[2]], acc);
-  if (v[3] < n_limit) atomicAdd(y + v[3], acc[3]);
-  cell_tet32x4<4, 5, 7>(dx, dp, mats[mt[4]], acc);
-  if (v[5] < n_limit) atomicAdd(y + v[5], acc[5]);
-  cell_tet32x4<4, 7, 6>(dx, dp, mats[mt[5]], acc);
-  if (v[4] < n_limit) atomicAdd(y + v[4], acc[4]);
-  cell_tet32x4<2, 6, 7>(dx, dp, mats[mt[3]], acc);
-  if (v[0] < n_limit) atomicAdd(y + v[0], acc[0]);
-  if (v[2] < n_limit) atomicAdd(y + v[2], acc[2]);
-  if (v[6] < n_limit) atomicAdd(y + v[6], acc[6]);
-  if (v[7] < n_limit) atomicAdd(y + v[7], acc[7]);
+  cell_tet32x4<1, 3, 7>(dx, pa, pb, mats[mt[0]], aa, ab);
+  cell_tet32x4<1, 7, 5>(dx, pa, pb, mats[mt[1]], aa, ab);
+  if (v[1] < n_limit) atomicAdd(y + v[1], cat2(aa[1], ab[1]));
+  cell_tet32x4<2, 7, 3>(dx, pa, pb, mats[mt[2]], aa, ab);
+  if (v[3] < n_limit) atomicAdd(y + v[3], cat2(aa[3], ab[3]));
+  cell_tet32x4<4, 5, 7>(dx, pa, pb, mats[mt[4]], aa, ab);
+  if (v[5] < n_limit) atomicAdd(y + v[5], cat2(aa[5], ab[5]));
+  cell_tet32x4<4, 7, 6>(dx, pa, pb, mats[mt[5]], aa, ab);
+  if (v[4] < n_limit) atomicAdd(y + v[4], cat2(aa[4], ab[4]));
+  cell_tet32x4<2, 6, 7>(dx, pa, pb, mats[mt[3]], aa, ab);
+  if (v[0] < n_limit) atomicAdd(y + v[0], cat2(aa[0], ab[0]));
+  if (v[2] < n_limit) atomicAdd(y + v[2], cat2(aa[2], ab[2]));
+  if (v[6] < n_limit) atomicAdd(y + v[6], cat2(aa[6], ab[6]));
+  if (v[7] < n_limit) atomicAdd(y + v[7], cat2(aa[7], ab[7]));
 }
 
 __device__ __forceinline__ void store_split4(float4* __restrict__ Y2, int64_t i, const double4_32a& v) {

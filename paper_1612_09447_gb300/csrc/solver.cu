@@ -1283,9 +1283,9 @@ static eqs_status ens_enqueue_step(eqs_ctx* c, int s, const double* d_cj, cudaSt
       if (last) break;
     }
     if (c->n_cells > 0)  // Kuhn cells: one 16-byte atomic per corner, 8 per six tets
-      launch(k4_elem32_cell, nblk(c->n_cells), kBlock, st, c->n_cells, (const int32_t*)c->d_corner,
-             (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi,
-             (const float4*)c->d_xyz_lo, (const float4*)c->d_eY2, nf, c->d_ey32);
+      launch(k4_elem32_cell, (int)((c->n_cells + kElemBlock4 - 1) / kElemBlock4), kElemBlock4, st, c->n_cells,
+             (const int32_t*)c->d_corner, (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats,
+             (const float4*)c->d_xyz_hi, (const float4*)c->d_xyz_lo, (const float4*)c->d_eY2, nf, c->d_ey32);
     else
       launch(k4_elem32, nblk(c->n_tets), kBlock, st, c->n_tets, (const int4*)c->d_conn, (const uint8_t*)c->d_mat,
              (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi, (const float4*)c->d_xyz_lo,
@@ -2103,9 +2103,9 @@ eqs_status eqs_launch_kernel(eqs_ctx* c, int kernel) {
       break;
     case EQS_KERNEL_ENS_ELEM:
       if (c->n_cells > 0)
-        launch(k4_elem32_cell, nblk(c->n_cells), kBlock, st, c->n_cells, (const int32_t*)c->d_corner,
-               (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi,
-               (const float4*)c->d_xyz_lo, (const float4*)c->d_eY2, nf, c->d_ktime);
+        launch(k4_elem32_cell, (int)((c->n_cells + kElemBlock4 - 1) / kElemBlock4), kElemBlock4, st, c->n_cells,
+               (const int32_t*)c->d_corner, (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats,
+               (const float4*)c->d_xyz_hi, (const float4*)c->d_xyz_lo, (const float4*)c->d_eY2, nf, c->d_ktime);
       else
         launch(k4_elem32, nblk(c->n_tets), kBlock, st, c->n_tets, (const int4*)c->d_conn, (const uint8_t*)c->d_mat,
                (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi, (const float4*)c->d_xyz_lo,
