@@ -65,7 +65,7 @@ SPE_N = 6  # solutions spanning the SPE subspace
 # workload), from an ncu capture of the lone launches of the current build on
 # the full 128^3 workload (dram__bytes_read.sum + dram__bytes_write.sum, mean
 # of 20 launches; the Gram pass is two kernels, summed); a kernel without an
-# entry reports null.
+# entry, or a run on another mesh size (--N), reports null.
 TRAFFIC = {(16, 2): 943696013, (17, 2): 274488525, (18, 2): 524417740}
 
 
@@ -327,7 +327,7 @@ def run_ours(args, rank, world):
     roof = kernel_roofline(torch, eqs, solver, p, flush,
                            {eqs.EQS_KERNEL_SPE_GRAM: S_STAGES, eqs.EQS_KERNEL_ELEM: S_STAGES,
                             eqs.EQS_KERNEL_PCG_PQ: float(np.mean(iters)) * S_STAGES},
-                           total_ms / args.steps, CONFIG_INDEX)
+                           total_ms / args.steps, CONFIG_INDEX if args.N is None else None)
     solver.close()
 
     variants = {}
@@ -927,7 +927,7 @@ def run_ensemble_headline(args, rank, world):
     roof = kernel_roofline(torch, eqs, S, p, flush,
                            {eqs.EQS_KERNEL_ENS_SPE_GRAM: S_STAGES, eqs.EQS_KERNEL_ENS_ELEM: S_STAGES,
                             eqs.EQS_KERNEL_ENS_PCG_PQ: passes / args.steps},
-                           ms_step, CONFIG_INDEX)
+                           ms_step, CONFIG_INDEX if args.N is None else None)
     S.close()
     forms = {}
     if not args.no_fp64:
