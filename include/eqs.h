@@ -219,23 +219,23 @@ eqs_status eqs_amg_setup(eqs_ctx* ctx, const eqs_opts* opts);
 eqs_status eqs_apply_K(eqs_ctx* ctx, const double* x, double* y);
 
 /* y = K(x) x as eqs_apply_K computes it (the same element kernel; results
- * differ only by the order of the atomic additions), for callers that must not allocate
- * device memory during the call: code running where cudaMalloc is not
- * allowed or not wanted, e.g. under a fixed device-memory budget that was
- * claimed up front, or on a real-time or callback path where an allocation
- * could block or fail.  The paper has no counterpart; this is a library
- * convenience.  The call allocates nothing: its scratch (the potential and
- * the result staged in the library's internal node order) is a static
- * 12 MiB device array inside the library, which every GPU that loads the
- * library holds until the process exits.  Limit: n_nodes <= 524288, else
- * EQS_ERR_ARG.  The first call on a device looks up the array's address
- * and keeps it for the rest of the process; make that first call before
- * any stream capture.  A device reset (cudaDeviceReset) may move the array,
- * so after one this entry point must not be used again in that process.  All calls share the one
- * array, so calls whose work overlaps on the GPU (other streams, other
- * threads, several contexts on one device) race; serialise them.  x, y:
- * device, n_nodes doubles, mesh order; the context's device must be
- * current.  Asynchronous on the context stream. */
+ * differ only by the order of the atomic additions), for callers that must
+ * not allocate device memory during the call: code running where cudaMalloc
+ * is not allowed or not wanted, e.g. under a fixed device-memory budget that
+ * was claimed up front, or on a real-time or callback path where an
+ * allocation could block or fail.  The paper has no counterpart; this is a
+ * library convenience.  The call allocates nothing: its scratch (the
+ * potential and the result staged in the library's internal node order) is
+ * a static 12 MiB device array inside the library, which every GPU that
+ * loads the library holds until the process exits.  Limit: n_nodes <=
+ * 524288, else EQS_ERR_ARG.  The first call on a device looks up the
+ * array's address and keeps it for the rest of the process; make that first
+ * call before any stream capture.  A device reset (cudaDeviceReset) may move
+ * the array, so after one this entry point must not be used again in that
+ * process.  All calls share the one array, so calls whose work overlaps on
+ * the GPU (other streams, other threads, several contexts on one device)
+ * race; serialise them.  x, y: device, n_nodes doubles, mesh order; the
+ * context's device must be current.  Asynchronous on the context stream. */
 eqs_status eqs_apply_K_static(eqs_ctx* ctx, const double* x, double* y);
 
 /* Solve M_ff z = rhs for nrhs right-hand sides (Sec. IV) by AMG-PCG.
