@@ -415,10 +415,23 @@ typedef struct {
  *   x + c n_nodes), mesh order; in x(t), out x(t + dt), Dirichlet entries
  *   replaced by v0_scale[c] g(t).
  * v0_scale: host, EQS_ENS_W finite doubles.
- * The step is one CUDA graph per (s, x); stats: host or NULL (then the call
- * is asynchronous).  EQS_ERR_STATE if the context is not mixed / split. */
+ * The step is one CUDA graph per s (x reaches it through a per-call
+ * parameter block, so any buffer reuses it); stats: host or NULL (then the
+ * call is asynchronous).  EQS_ERR_STATE if the context is not mixed /
+ * split. */
 eqs_status eqs_ens_rkc_step(eqs_ctx* ctx, double* x, const double* v0_scale, double t, double dt,
                             int s, eqs_ens_stats* stats);
+
+/* Y = K(X) X for the EQS_ENS_W columns at once with the ensemble's element
+ * kernel (Sec. III: formed tet by tet, never assembling K; the four columns
+ * share each tet's geometry), before any boundary condition.  X, Y: device,
+ * EQS_ENS_W x n_nodes doubles, column-major (column c at X + c n_nodes), mesh
+ * order; Y is overwritten.  FP32 arithmetic as in the mixed step: X is
+ * carried as FP32 (hi, lo) pairs, Y is the FP32 result widened.  Needs a
+ * context set up in EQS_PREC_MIXED on linear (4-node) tets, else
+ * EQS_ERR_STATE.  Device memory for the staged columns is allocated by the
+ * first call.  Asynchronous on the context stream. */
+eqs_status eqs_ens_apply_K(eqs_ctx* ctx, const double* X, double* Y);
 
 /* Statistics of the last ensemble step (synchronises). */
 eqs_status eqs_ens_get_step_stats(eqs_ctx* ctx, eqs_ens_stats* stats);

@@ -1313,6 +1313,37 @@ __device__ __forceinline__ void store_split4(float4* __restrict__ Y2, int64_t i,
   Y2[2 * i + 1] = make_float4(z.x, z.y, w.x, w.y);
 }
 
+// Four column-major mesh-order columns (src + c n) into the FP32-pair layout
+// in internal order (internal node i is mesh node perm[i]).
+__global__ void k4_gather_pair_perm(int n, const double* __restrict__ src, const int32_t* __restrict__ perm,
+                                    float4* __restrict__ dst2) {
+  pdl_enter();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t m = perm[i];
+  double4_32a v;
+  v.x = src[m];
+  v.y = src[(int64_t)n + m];
+  v.z = src[2 * (int64_t)n + m];
+  v.w = src[3 * (int64_t)n + m];
+  store_split4(dst2, i, v);
+}
+
+// Four FP32 columns (internal order, one float4 per node) widened into
+// column-major FP64 columns in mesh order.
+__global__ void k4_scatter_perm(int n, const float4* __restrict__ y, const int32_t* __restrict__ perm,
+                                double* __restrict__ dst) {
+  pdl_enter();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 v = y[i];
+  const int64_t m = perm[i];
+  dst[m] = (double)v.x;
+  dst[(int64_t)n + m] = (double)v.y;
+  dst[2 * (int64_t)n + m] = (double)v.z;
+  dst[3 * (int64_t)n + m] = (double)v.w;
+}
+
 // Four column-major columns (src + c n) into the interleaved FP64 layout and
 // the FP32-pair layout.
 __global__ void k4_interleave_pair(int n, const double* __restrict__ src, double4_32a* __restrict__ dst,

@@ -266,7 +266,8 @@ struct eqs_ctx {
   int64_t ens_body_kernels = 0;
   std::map<int, eqs::GraphEntry> ens_graphs;   // key: s (graph), -s (host-loop entry)
   const eqs::GraphEntry* ens_last = nullptr;
-  float4* d_ktime = nullptr;  // private K(x)x target of eqs_launch_kernel (n_nodes float4)
+  float4* d_ktime = nullptr;  // private K(x)x target of eqs_launch_kernel and eqs_ens_apply_K (n_nodes float4)
+  float4* d_ekx2 = nullptr;   // eqs_ens_apply_K: the four input columns as FP32 pairs (2 n_nodes float4)
   eqs::GraphEntry ens_solve_graph;   // eqs_ens_solve_M (rtol of the setup)
   double ens_solve_tol = -1.0;
 

@@ -2063,6 +2063,31 @@ eqs_status eqs_ens_rkc_step(eqs_ctx* c, double* x, const double* v0_scale, doubl
   return stats ? eqs_ens_get_step_stats(c, stats) : EQS_OK;
 }
 
+eqs_status eqs_ens_apply_K(eqs_ctx* c, const double* x, double* y) {
+  REQUIRE_SETUP(c);
+  if (!x || !y) return fail(c, EQS_ERR_ARG, "null vector");
+  if (!mixed(c) || c->npe != 4)
+    return fail(c, EQS_ERR_STATE, "the four-column element kernel needs EQS_PREC_MIXED on linear (4-node) tets");
+  const int n = (int)c->n_nodes;
+  cudaStream_t st = c->stream;
+  if (!c->d_ekx2) CK(dalloc(c, &c->d_ekx2, 2 * (size_t)n));
+  if (!c->d_ktime) CK(dalloc(c, &c->d_ktime, (size_t)n));
+  const int32_t* perm = (const int32_t*)c->d_node_of_internal;
+  launch(k4_gather_pair_perm, nblk(n), kBlock, st, n, x, perm, c->d_ekx2);
+  CK(cudaMemsetAsync(c->d_ktime, 0, (size_t)n * sizeof(float4), st));
+  if (c->n_cells > 0)
+    launch(k4_elem32_cell, (int)((c->n_cells + kElemBlock4 - 1) / kElemBlock4), kElemBlock4, st, c->n_cells,
+           (const int32_t*)c->d_corner, (const uint8_t*)c->d_mat, (const MaterialDev*)c->d_mats,
+           (const float4*)c->d_xyz_hi, (const float4*)c->d_xyz_lo, (const float4*)c->d_ekx2, n, c->d_ktime);
+  else
+    launch(k4_elem32, nblk(c->n_tets), kBlock, st, c->n_tets, (const int4*)c->d_conn, (const uint8_t*)c->d_mat,
+           (const MaterialDev*)c->d_mats, (const float4*)c->d_xyz_hi, (const float4*)c->d_xyz_lo,
+           (const float4*)c->d_ekx2, n, c->d_ktime);
+  launch(k4_scatter_perm, nblk(n), kBlock, st, n, (const float4*)c->d_ktime, perm, y);
+  CK(cudaGetLastError());
+  return EQS_OK;
+}
+
 eqs_status eqs_launch_kernel(eqs_ctx* c, int kernel) {
   REQUIRE_SETUP(c);
   if (!((kernel >= EQS_KERNEL_SPE_GRAM && kernel <= EQS_KERNEL_PCG_PQ) ||

@@ -127,6 +127,7 @@ def _declare(L):
         "eqs_batch_destroy": (I, [P]),
         "eqs_batch_last_error": (C.c_char_p, [P]),
         "eqs_ens_rkc_step": (I, [P, P, P, D, D, I, C.POINTER(eqs_ens_stats)]),
+        "eqs_ens_apply_K": (I, [P, P, P]),
         "eqs_ens_get_step_stats": (I, [P, C.POINTER(eqs_ens_stats)]),
         "eqs_ens_solve_M": (I, [P, P, P, P]),
         "eqs_pod_eval": (I, [P, P, I, P, P]),
@@ -392,6 +393,12 @@ def eqs_ens_rkc_step(ctx, x, v0_scale, t, dt, s, want_stats=True):
         raise ValueError("v0_scale needs 4 values")
     _check(lib().eqs_ens_rkc_step(ctx, _dev(x), vp, t, dt, s, C.byref(st) if st is not None else None), ctx)
     return st
+
+
+def eqs_ens_apply_K(ctx, X, Y):
+    """Y = K(X) X for four columns; X, Y: CUDA float64 tensors of shape
+    (4, n_nodes) (column c in row c)."""
+    _check(lib().eqs_ens_apply_K(ctx, _dev(X), _dev(Y)), ctx)
 
 
 def eqs_ens_get_step_stats(ctx):

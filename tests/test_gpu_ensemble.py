@@ -217,3 +217,51 @@ def test_ensemble_spe_start_matches_oracle_and_true_residual(E):
         true_r = b[c] - Sy.Mff @ x0[c]
         assert np.linalg.norm(r0[c] - true_r) <= 1e-11 * np.linalg.norm(b[c]), c
     S.close()
+
+
+def _field_state(p, seed):
+    """A potential whose field reaches the varistor switching range."""
+    rng = np.random.default_rng(seed)
+    Emag = 5.2e5
+    return -Emag * p.xyz[:, 2] + 0.3 * Emag * (0.1 / p.N) * rng.standard_normal(p.n_nodes)
+
+
+def _shuffled(p, seed=1):
+    perm = np.random.default_rng(seed).permutation(p.n_tets)
+    return ei.Problem(p.N, p.xyz, p.tets[perm], p.tet_mat[perm], p.node_tag, p.materials, p.V0)
+
+
+@pytest.mark.parametrize("name", ["cube12", "jitter10", "batch7", "jitter6_shuffled"])
+def test_ens_apply_K_matches_oracle(E, name):
+    """The ensemble's four-column element kernel (Section III) through
+    eqs_ens_apply_K: every column equals the oracle's K(x)x to the mixed
+    tolerance of the single-column kernel, on Kuhn-cell meshes (cell kernel)
+    and on a mesh with its tets shuffled (per-tet kernel), with fields that
+    span the varistor's switching range (drive scales 0.5 to 2), on two
+    calls in a row."""
+    from oracle import fem
+
+    p = {"cube12": lambda: ei.config_problem(0), "jitter10": lambda: ei.config_problem(2, N=10),
+         "batch7": lambda: ei.config_problem(4, N=7, instance=3),
+         "jitter6_shuffled": lambda: _shuffled(ei.config_problem(2, N=6))}[name]()
+    S = E.Solver(p, precision=MIXED)
+    cols = [sc * _field_state(p, seed=k) for k, sc in enumerate(SCALES)]
+    X = torch.tensor(np.stack(cols), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        Y = torch.full_like(X, np.nan)
+        E.eqs_ens_apply_K(S.ctx, X, Y)
+        got = Y.cpu().numpy()
+        for k, x in enumerate(cols):
+            ref = fem.apply_K(p.xyz, p.tets, p.tet_mat, p.materials, x)
+            assert np.abs(got[k] - ref).max() <= 2e-5 * np.abs(ref).max(), (name, k)
+    S.close()
+
+
+def test_ens_apply_K_needs_mixed_linear(E):
+    p = ei.config_problem(0)
+    S = E.Solver(p, precision=FP64)
+    X = torch.zeros((4, p.n_nodes), dtype=torch.float64, device="cuda")
+    with pytest.raises(E.EqsError) as ei_:
+        E.eqs_ens_apply_K(S.ctx, X, torch.empty_like(X))
+    assert ei_.value.status == E.EQS_ERR_STATE
+    S.close()
