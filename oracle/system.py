@@ -14,7 +14,9 @@ natural (homogeneous Neumann) conditions.
 
 Pins: tests/test_oracle_system.py (homogeneous slab against the
 closed-form exponential relaxation with time constant eps/kappa; the static
-lift is exactly linear in z).
+lift is exactly linear in z; a driven slab converges at second order; a
+nonlinear run in which the varistor switches converges at second order to
+an independent stiff integrator, SciPy's Radau IIA).
 """
 
 from __future__ import annotations

@@ -94,3 +94,38 @@ def test_step_at_bound_is_stable_beyond_is_not():
             x, _ = rkc.rkc_step(S.F, t, x, fac * c.beta / rho, c)
             t += fac * c.beta / rho
         assert (np.abs(x).max() > 10 * np.abs(x0).max()) == grows
+
+
+def test_nonlinear_switching_run_is_second_order_against_radau():
+    """The nonlinear system (Eq. 2 with the field-dependent varistor
+    conductivity) stepped by the oracle's RKC scheme (Section II, s = 10)
+    converges at second order to an independent stiff integrator (SciPy's
+    Radau IIA at rtol 1e-12) over ten steps of the stability-bound size, on
+    a drive strong enough that the varistor switches (its field passes E0
+    and its conductivity rises by orders of magnitude).  A dropped stage
+    term, a wrong stage time or a wrong coefficient breaks the order."""
+    from scipy.integrate import solve_ivp
+
+    p = ei.make_problem(3, V0=2e5)
+    Sy = system.EQSSystem(p)
+    s = 10
+    coef = rkc.RKCCoefficients(s)
+    T = 10 * dtbound.dt_bound(p.materials, s, coef)
+    ref = solve_ivp(lambda t, y: Sy.F(t, y), (0.0, T), np.zeros(p.n_free), method="Radau", rtol=1e-12,
+                    atol=1e-9)
+    assert ref.status == 0
+    kap, _ = fem.tet_kappa(p.xyz, p.tets, p.tet_mat, p.materials, Sy.full(T, ref.y[:, -1]))
+    lo = min(m.kappa_lo for m in p.materials if m.kappa_hi != m.kappa_lo)
+    assert kap.max() > 1e3 * lo  # switched
+    yT = ref.y[:, -1]
+    errs = []
+    for n in (10, 20, 40):
+        dt = T / n
+        xf, t = np.zeros(p.n_free), 0.0
+        for _ in range(n):
+            xf, _ = rkc.rkc_step(Sy.F, t, xf, dt, coef)
+            t += dt
+        errs.append(np.linalg.norm(xf - yT) / np.linalg.norm(yT))
+    ratios = [errs[0] / errs[1], errs[1] / errs[2]]
+    assert errs[0] < 0.1
+    assert all(3.5 < r < 4.7 for r in ratios), (errs, ratios)
