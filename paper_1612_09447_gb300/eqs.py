@@ -448,6 +448,10 @@ class Solver:
     def __init__(self, problem, precision=EQS_PREC_FP64, rtol=1e-8, **opt):
         import torch
 
+        self.ctx = None
+        unknown = sorted(set(opt) - {f[0] for f in eqs_opts._fields_})
+        if unknown:  # a misspelt option must not pass silently as a plain attribute
+            raise TypeError(f"unknown solver option(s): {', '.join(unknown)}")
         self.torch = torch
         self.p = problem
         self.ctx = eqs_mesh_create(problem.xyz, problem.tets, problem.node_tag)

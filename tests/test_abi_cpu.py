@@ -158,3 +158,12 @@ def test_option_defaults_match_the_header(E):
         assert m, field
         assert getattr(o, field) == int(m.group(1)), field
     assert o.precision == E.EQS_PREC_FP64 and o.rtol == 1e-8 and o.flexible == 1
+
+
+def test_solver_rejects_unknown_options():
+    """A misspelt solver option raises before anything is created (ctypes
+    would otherwise store it as a plain attribute and ignore it)."""
+    from paper_1612_09447_gb300 import eqs
+
+    with pytest.raises(TypeError, match="cheb_degre"):
+        eqs.Solver(ei.make_problem(2), cheb_degre=1)
